@@ -1,0 +1,234 @@
+"""FP64 CPU oracle for the AthenaK hydro stage (arXiv 2409.16053, Section 3 and 3.1).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline / reference leg of ``bench.py`` may import this package.  It shares no
+code with the CUDA path (``paper_2409_16053_gb300``), and neither imports the other.
+
+The arithmetic lives in ``ak_oracle.c`` (plain C, FP64, ``-ffp-contract=off``); this
+module compiles it with gcc into ``oracle/_build/`` and wraps it with ctypes.  Arrays
+are numpy float64 of shape (5, n3, n2, n1), x1 fastest: U = (rho, M1, M2, M3, E).
+
+Parity status of each function (what pins it, see tests/test_oracle_*.py):
+  cons_to_prim / prim_to_cons   round trip; Section 3.1 Eq. (4) closed forms
+  plm_slope                     linear data, extrema, translation invariance
+  ppm4_edges                    parabola reproduction, monotonicity
+  hllc                          supersonic upwinding, stationary contact, symmetry,
+                                consistency, entropy-wave/sound-wave convergence
+  rhs / rk_step                 2nd-order sound and entropy wave convergence,
+                                uniform state bitwise, periodic conservation,
+                                x1/x2/x3 bitwise permutation, Sod vs exact solver
+  new_dt                        closed form on uniform states
+  exact_star / exact_sample     Rankine-Hugoniot and isentrope/Riemann-invariant
+                                relations across each wave
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ak_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "libak_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+PLM = 0
+PPM4 = 1
+
+
+def build(force: bool = False) -> str:
+    """Compile ak_oracle.c into a shared library (gcc, OpenMP, no FP contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+           "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64 * 3), ("dx", ctypes.c_double * 3),
+                ("gamma", ctypes.c_double), ("recon", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
+
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            G = ctypes.POINTER(_Grid)
+            lib.orc_cons_to_prim.argtypes = [_dp, _dp, _i64p]
+            lib.orc_prim_to_cons.argtypes = [_dp, _dp]
+            lib.orc_plm_slope.argtypes = [ctypes.c_double] * 3
+            lib.orc_plm_slope.restype = ctypes.c_double
+            lib.orc_ppm4_edges.argtypes = [_dp, _dp, _dp]
+            lib.orc_hllc.argtypes = [_dp, _dp, ctypes.c_double, _dp]
+            lib.orc_rhs.argtypes = [G, _dp, _dp]
+            lib.orc_rhs.restype = ctypes.c_int64
+            lib.orc_rk_step.argtypes = [G, _dp, ctypes.c_double, ctypes.c_int]
+            lib.orc_rk_step.restype = ctypes.c_int64
+            lib.orc_new_dt.argtypes = [G, _dp, ctypes.c_double]
+            lib.orc_new_dt.restype = ctypes.c_double
+            lib.orc_exact_star.argtypes = [_dp, _dp, ctypes.c_double, _dp, _dp]
+            lib.orc_exact_star.restype = ctypes.c_int
+            lib.orc_exact_sample.argtypes = [_dp, _dp, ctypes.c_double, ctypes.c_double, _dp]
+            lib.orc_exact_sample.restype = ctypes.c_int
+            lib.orc_num_threads.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(_dp)
+
+
+class Grid:
+    """Periodic uniform grid: n = (n1, n2, n3) cells on a box of side lengths `length`."""
+
+    def __init__(self, n, length=(1.0, 1.0, 1.0), gamma=5.0 / 3.0, recon=PLM):
+        self.n = tuple(int(v) for v in n)
+        self.length = tuple(float(v) for v in length)
+        self.dx = tuple(self.length[d] / self.n[d] for d in range(3))
+        self.gamma = float(gamma)
+        self.recon = int(recon)
+
+    def _c(self):
+        g = _Grid()
+        for d in range(3):
+            g.n[d] = self.n[d]
+            g.dx[d] = self.dx[d]
+        g.gamma = self.gamma
+        g.recon = self.recon
+        return ctypes.byref(g)
+
+    @property
+    def shape(self):
+        return (5, self.n[2], self.n[1], self.n[0])
+
+
+def num_threads() -> int:
+    return int(_load().orc_num_threads())
+
+
+def cons_to_prim(u):
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    w = np.empty(5)
+    nf = ctypes.c_int64(0)
+    _load().orc_cons_to_prim(_ptr(u), _ptr(w), ctypes.byref(nf))
+    return w, int(nf.value)
+
+
+def prim_to_cons(w):
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    u = np.empty(5)
+    _load().orc_prim_to_cons(_ptr(w), _ptr(u))
+    return u
+
+
+def plm_slope(qm, q0, qp) -> float:
+    return float(_load().orc_plm_slope(float(qm), float(q0), float(qp)))
+
+
+def ppm4_edges(q5):
+    q = np.ascontiguousarray(q5, dtype=np.float64)
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    _load().orc_ppm4_edges(_ptr(q), ctypes.byref(lo), ctypes.byref(hi))
+    return lo.value, hi.value
+
+
+def hllc(wl, wr, gamma):
+    """HLLC flux; w = (rho, u_normal, v_t1, v_t2, u_g)."""
+    wl = np.ascontiguousarray(wl, dtype=np.float64)
+    wr = np.ascontiguousarray(wr, dtype=np.float64)
+    f = np.empty(5)
+    _load().orc_hllc(_ptr(wl), _ptr(wr), float(gamma), _ptr(f))
+    return f
+
+
+def rhs(U, grid: Grid):
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    assert U.shape == grid.shape, (U.shape, grid.shape)
+    L = np.empty_like(U)
+    nf = _load().orc_rhs(grid._c(), _ptr(U), _ptr(L))
+    if nf < 0:
+        raise MemoryError("oracle rhs allocation failed")
+    return L, int(nf)
+
+
+def rk_step(U, grid: Grid, dt: float, rk: int = 2):
+    """One full SSP-RK step; returns (U_new, floors)."""
+    Un = np.array(U, dtype=np.float64, order="C", copy=True)
+    assert Un.shape == grid.shape
+    nf = _load().orc_rk_step(grid._c(), _ptr(Un), float(dt), int(rk))
+    if nf < 0:
+        raise MemoryError("oracle rk_step allocation failed")
+    return Un, int(nf)
+
+
+def new_dt(U, grid: Grid, cfl: float) -> float:
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    assert U.shape == grid.shape
+    return float(_load().orc_new_dt(grid._c(), _ptr(U), float(cfl)))
+
+
+def run(U, grid: Grid, cfl: float, t_end: float | None = None, nsteps: int | None = None,
+        rk: int = 2):
+    """Advance with dt from the CFL rule before every step; the last step is clipped to
+    land on t_end exactly.  Returns (U, t, steps, floors)."""
+    U = np.array(U, dtype=np.float64, order="C", copy=True)
+    t, steps, floors = 0.0, 0, 0
+    while True:
+        if nsteps is not None and steps >= nsteps:
+            break
+        if t_end is not None and t >= t_end:
+            break
+        dt = new_dt(U, grid, cfl)
+        if t_end is not None and t + dt > t_end:
+            dt = t_end - t
+        U, nf = rk_step(U, grid, dt, rk)
+        floors += nf
+        t += dt
+        steps += 1
+    return U, t, steps, floors
+
+
+def exact_star(wl, wr, gamma):
+    """Star-region (p*, u*) of the exact Riemann problem; w = (rho, u, p)."""
+    wl = np.ascontiguousarray(wl, dtype=np.float64)
+    wr = np.ascontiguousarray(wr, dtype=np.float64)
+    ps, us = ctypes.c_double(), ctypes.c_double()
+    rc = _load().orc_exact_star(_ptr(wl), _ptr(wr), float(gamma), ctypes.byref(ps),
+                                ctypes.byref(us))
+    if rc != 0:
+        raise ValueError("vacuum generated")
+    return ps.value, us.value
+
+
+def exact_sample(wl, wr, gamma, xi):
+    """Exact solution (rho, u, p) at each xi = x/t; returns array (3, len(xi))."""
+    wl = np.ascontiguousarray(wl, dtype=np.float64)
+    wr = np.ascontiguousarray(wr, dtype=np.float64)
+    xi = np.atleast_1d(np.asarray(xi, dtype=np.float64))
+    out = np.empty((3, xi.size))
+    o = np.empty(3)
+    lib = _load()
+    for m, x in enumerate(xi):
+        if lib.orc_exact_sample(_ptr(wl), _ptr(wr), float(gamma), float(x), _ptr(o)) != 0:
+            raise ValueError("vacuum generated")
+        out[:, m] = o
+    return out

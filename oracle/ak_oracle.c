@@ -1,0 +1,499 @@
+/*
+ * FP64 CPU oracle for one Godunov finite-volume Runge-Kutta step of 3D adiabatic
+ * Newtonian hydrodynamics (AthenaK, arXiv 2409.16053, Section 3 and Section 3.1).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or call this
+ * file: only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg use it.
+ * It shares no code, header or constant table with the CUDA path.
+ *
+ * Design: plain, slow, obviously correct.  The whole domain is ONE periodic grid
+ * (no MeshBlocks): a MeshBlock mesh with exact ghost exchange computes the same
+ * arithmetic per cell, so this is the plain definition the GPU's blocked layout and
+ * its ghost fill must reproduce.  Every face flux is computed from scratch, one face
+ * at a time, in the order the method states: primitives, reconstruction, Riemann
+ * solver, flux divergence, RK stage update.  Built with -ffp-contract=off so each
+ * line rounds as written.
+ *
+ * Arrays are double[5][n3][n2][n1] with x1 fastest; the 5 components are
+ * U = (rho, M1, M2, M3, E) or W = (rho, v1, v2, v3, u_g).
+ *
+ * Readings of places where the paper defers to its references (all restated in the
+ * design notes):
+ *   - PLM limiter: van Leer harmonic mean of the one-sided differences.
+ *   - PPM4: Colella & Woodward (1984) uniform-grid interface values and limiter,
+ *     no flattening, no contact steepening.
+ *   - HLLC: Toro (2009) ch. 10, PVRS wave-speed estimate bounded outward by the
+ *     Davis speeds, star states of the standard form, ties at S_L = 0 / S* = 0
+ *     resolved to the left.
+ *   - SSP-RK2 (Heun) and SSP-RK3 (Shu-Osher) coefficients, each stage evaluated as
+ *     a*U0 + b*(U + dt*L(U)).
+ *   - Floors: rho < 1e-12 or u_g < 1e-15 in the primitive recovery are clamped and
+ *     counted (the paper gives no hydro floor values).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define NVAR 5
+#define ORC_RHO_FLOOR 1.0e-12
+#define ORC_UG_FLOOR 1.0e-15
+
+#define ORC_PLM 0
+#define ORC_PPM4 1
+
+typedef struct {
+  int64_t n[3];     /* cells per dimension of the periodic grid */
+  double dx[3];     /* uniform cell widths (Section 2: uniform Cartesian only) */
+  double gamma;     /* ratio of specific heats of the gamma-law EOS */
+  int32_t recon;    /* ORC_PLM or ORC_PPM4 */
+  int32_t pad;
+} orc_grid;
+
+static int64_t wrap(int64_t i, int64_t n) {
+  int64_t r = i % n;
+  return r < 0 ? r + n : r;
+}
+
+static int64_t cell(const orc_grid* g, int64_t i, int64_t j, int64_t k) {
+  return (wrap(k, g->n[2]) * g->n[1] + wrap(j, g->n[1])) * g->n[0] + wrap(i, g->n[0]);
+}
+
+/* ---------------------------------------------------------------------------------
+ * Conserved -> primitive, Section 3.1 Eq. (4): rho = U0, v = M/rho,
+ * E = u_g + rho v^2/2  =>  u_g = E - (M.M)/(2 rho).  Floors are a reading (counted).
+ * ------------------------------------------------------------------------------- */
+void orc_cons_to_prim(const double u[5], double w[5], int64_t* nfloor) {
+  double rho = u[0];
+  if (!(rho >= ORC_RHO_FLOOR)) {
+    rho = ORC_RHO_FLOOR;
+    *nfloor += 1;
+  }
+  double v1 = u[1] / rho;
+  double v2 = u[2] / rho;
+  double v3 = u[3] / rho;
+  double ug = u[4] - 0.5 * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) / rho;
+  if (!(ug >= ORC_UG_FLOOR)) {
+    ug = ORC_UG_FLOOR;
+    *nfloor += 1;
+  }
+  w[0] = rho;
+  w[1] = v1;
+  w[2] = v2;
+  w[3] = v3;
+  w[4] = ug;
+}
+
+/* Primitive -> conserved, Section 3.1 Eq. (4). */
+void orc_prim_to_cons(const double w[5], double u[5]) {
+  u[0] = w[0];
+  u[1] = w[0] * w[1];
+  u[2] = w[0] * w[2];
+  u[3] = w[0] * w[3];
+  u[4] = w[4] + 0.5 * w[0] * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]);
+}
+
+/* ---------------------------------------------------------------------------------
+ * PLM (Section 3: piecewise linear reconstruction on primitives).  Reading: van Leer
+ * harmonic-mean limiter.  Given the three cell values q(i-1), q(i), q(i+1), returns
+ * the limited slope of cell i; the face states are q(i) -/+ slope/2.
+ * ------------------------------------------------------------------------------- */
+double orc_plm_slope(double qm, double q0, double qp) {
+  double dl = q0 - qm;
+  double dr = qp - q0;
+  double prod = dl * dr;
+  if (prod > 0.0) return 2.0 * prod / (dl + dr);
+  return 0.0;
+}
+
+/* ---------------------------------------------------------------------------------
+ * PPM4 (Section 3: "original" PPM limiters of Colella & Woodward 1984), uniform grid.
+ * Given q(i-2..i+2) returns the left (x_{i-1/2}) and right (x_{i+1/2}) edge values of
+ * the parabola in cell i after monotonization.
+ * ------------------------------------------------------------------------------- */
+static double ppm_limited_slope(double qm, double q0, double qp) {
+  /* CW84 Eq. (1.7)-(1.8): centred slope, limited to twice the one-sided ones, zero at
+   * extrema. */
+  double d = 0.5 * (qp - qm);
+  double dl = q0 - qm;
+  double dr = qp - q0;
+  if (dl * dr <= 0.0) return 0.0;
+  double m = fabs(d);
+  if (2.0 * fabs(dl) < m) m = 2.0 * fabs(dl);
+  if (2.0 * fabs(dr) < m) m = 2.0 * fabs(dr);
+  return d > 0.0 ? m : -m;
+}
+
+void orc_ppm4_edges(const double q[5], double* qlo, double* qhi) {
+  /* q[0..4] = q(i-2), q(i-1), q(i), q(i+1), q(i+2) */
+  double sm1 = ppm_limited_slope(q[0], q[1], q[2]);
+  double s0 = ppm_limited_slope(q[1], q[2], q[3]);
+  double sp1 = ppm_limited_slope(q[2], q[3], q[4]);
+  /* CW84 Eq. (1.6) on a uniform grid: interface values. */
+  double alo = 0.5 * (q[1] + q[2]) - (s0 - sm1) / 6.0;
+  double ahi = 0.5 * (q[2] + q[3]) - (sp1 - s0) / 6.0;
+  double a = q[2];
+  /* CW84 Eq. (1.10): monotonize the parabola. */
+  if ((ahi - a) * (a - alo) <= 0.0) {
+    alo = a;
+    ahi = a;
+  } else {
+    double da = ahi - alo;
+    double a6 = 6.0 * (a - 0.5 * (alo + ahi));
+    if (da * a6 > da * da) {
+      alo = 3.0 * a - 2.0 * ahi;
+    } else if (-da * da > da * a6) {
+      ahi = 3.0 * a - 2.0 * alo;
+    }
+  }
+  *qlo = alo;
+  *qhi = ahi;
+}
+
+/* ---------------------------------------------------------------------------------
+ * HLLC Riemann solver (Section 3, Toro ch. 10).  Inputs are primitive states with the
+ * normal velocity in component 1 and the two transverse ones in 2 and 3:
+ * w = (rho, u, v, w, u_g).  Output: the flux of (rho, rho u, rho v, rho w, E) through a
+ * face normal to the sweep direction, Section 3.1 Eq. (4).
+ * ------------------------------------------------------------------------------- */
+static void phys_flux(const double w[5], double p, double e, double f[5]) {
+  double mn = w[0] * w[1];
+  f[0] = mn;
+  f[1] = mn * w[1] + p;
+  f[2] = mn * w[2];
+  f[3] = mn * w[3];
+  f[4] = (e + p) * w[1];
+}
+
+void orc_hllc(const double wl[5], const double wr[5], double gamma, double f[5]) {
+  double rl = wl[0], ul = wl[1];
+  double rr = wr[0], ur = wr[1];
+  double pl = (gamma - 1.0) * wl[4];
+  double pr = (gamma - 1.0) * wr[4];
+  double el = wl[4] + 0.5 * rl * (wl[1] * wl[1] + wl[2] * wl[2] + wl[3] * wl[3]);
+  double er = wr[4] + 0.5 * rr * (wr[1] * wr[1] + wr[2] * wr[2] + wr[3] * wr[3]);
+  double cl = sqrt(gamma * pl / rl);
+  double cr = sqrt(gamma * pr / rr);
+
+  /* Toro Sec. 10.5.2: pressure-based wave-speed estimate from the PVRS solver. */
+  double ppv = 0.5 * (pl + pr) - 0.125 * (ur - ul) * (rl + rr) * (cl + cr);
+  double pstar = ppv > 0.0 ? ppv : 0.0;
+  double ql = 1.0, qr = 1.0;
+  if (pstar > pl) ql = sqrt(1.0 + (gamma + 1.0) / (2.0 * gamma) * (pstar / pl - 1.0));
+  if (pstar > pr) qr = sqrt(1.0 + (gamma + 1.0) / (2.0 * gamma) * (pstar / pr - 1.0));
+  double sl = ul - cl * ql;
+  double sr = ur + cr * qr;
+  /* Reading: in strongly colliding supersonic flow the PVRS estimates can cross
+   * (S_L > S_R); bounding them outward by the Davis speeds u_R - c_R and u_L + c_L
+   * keeps S_L < S_R, and changes nothing where the PVRS speeds already bracket them. */
+  if (ur - cr < sl) sl = ur - cr;
+  if (ul + cl > sr) sr = ul + cl;
+
+  /* Toro Eq. (10.37): contact speed. */
+  double sstar = (pr - pl + rl * ul * (sl - ul) - rr * ur * (sr - ur)) /
+                 (rl * (sl - ul) - rr * (sr - ur));
+
+  double fl[5], fr[5];
+  phys_flux(wl, pl, el, fl);
+  phys_flux(wr, pr, er, fr);
+
+  if (sl >= 0.0) {
+    memcpy(f, fl, sizeof(fl));
+    return;
+  }
+  if (sr <= 0.0) {
+    memcpy(f, fr, sizeof(fr));
+    return;
+  }
+  /* Toro Eq. (10.38)-(10.39): star state of the side the face lies in. */
+  const double* w = (sstar >= 0.0) ? wl : wr;
+  double s = (sstar >= 0.0) ? sl : sr;
+  double p = (sstar >= 0.0) ? pl : pr;
+  double e = (sstar >= 0.0) ? el : er;
+  const double* fk = (sstar >= 0.0) ? fl : fr;
+  double rk = w[0], uk = w[1];
+  double fac = rk * (s - uk) / (s - sstar);
+  double ustar[5], uk5[5];
+  ustar[0] = fac;
+  ustar[1] = fac * sstar;
+  ustar[2] = fac * w[2];
+  ustar[3] = fac * w[3];
+  ustar[4] = fac * (e / rk + (sstar - uk) * (sstar + p / (rk * (s - uk))));
+  uk5[0] = rk;
+  uk5[1] = rk * uk;
+  uk5[2] = rk * w[2];
+  uk5[3] = rk * w[3];
+  uk5[4] = e;
+  for (int n = 0; n < NVAR; ++n) f[n] = fk[n] + s * (ustar[n] - uk5[n]);
+}
+
+/* ---------------------------------------------------------------------------------
+ * Right-hand side L(U) = -div F of Section 3 Eq. (1) (S = 0) on the periodic grid.
+ * For each direction d, the face between cells c - e_d and c gets its left state from
+ * the reconstruction in cell c - e_d and its right state from that in cell c; HLLC
+ * gives the flux; then L -= (F(c + e_d) - F(c)) / dx_d, summed x1, x2, x3 in turn.
+ * ------------------------------------------------------------------------------- */
+static void face_states(const orc_grid* g, const double* W, int d, int64_t i, int64_t j,
+                        int64_t k, double wl[5], double wr[5]) {
+  int64_t e[3] = {0, 0, 0};
+  e[d] = 1;
+  int64_t N = g->n[0] * g->n[1] * g->n[2];
+  /* Permutation into (rho, normal, transverse 1, transverse 2, u_g): cyclic. */
+  int perm[5] = {0, 1 + d, 1 + (d + 1) % 3, 1 + (d + 2) % 3, 4};
+  for (int n = 0; n < NVAR; ++n) {
+    int v = perm[n];
+    const double* q = W + (int64_t)v * N;
+    if (g->recon == ORC_PLM) {
+      double qm2 = q[cell(g, i - 2 * e[0], j - 2 * e[1], k - 2 * e[2])];
+      double qm1 = q[cell(g, i - e[0], j - e[1], k - e[2])];
+      double q0 = q[cell(g, i, j, k)];
+      double qp1 = q[cell(g, i + e[0], j + e[1], k + e[2])];
+      /* left state: upper edge of cell c - e_d; right state: lower edge of cell c */
+      wl[n] = qm1 + 0.5 * orc_plm_slope(qm2, qm1, q0);
+      wr[n] = q0 - 0.5 * orc_plm_slope(qm1, q0, qp1);
+    } else {
+      double s[6];
+      for (int m = 0; m < 6; ++m) {
+        int64_t o = m - 3;
+        s[m] = q[cell(g, i + o * e[0], j + o * e[1], k + o * e[2])];
+      }
+      double lo, hi, lo2, hi2;
+      orc_ppm4_edges(&s[0], &lo, &hi);  /* cell c - e_d, stencil c-3e..c+e */
+      orc_ppm4_edges(&s[1], &lo2, &hi2); /* cell c, stencil c-2e..c+2e */
+      (void)lo;
+      (void)hi2;
+      wl[n] = hi;
+      wr[n] = lo2;
+    }
+  }
+}
+
+int64_t orc_rhs(const orc_grid* g, const double* U, double* L) {
+  int64_t N = g->n[0] * g->n[1] * g->n[2];
+  int64_t nfloor = 0;
+  double* W = (double*)malloc(sizeof(double) * NVAR * N);
+  double* F = (double*)malloc(sizeof(double) * NVAR * N);
+  if (!W || !F) {
+    free(W);
+    free(F);
+    return -1;
+  }
+#pragma omp parallel for reduction(+ : nfloor)
+  for (int64_t c = 0; c < N; ++c) {
+    double u[5], w[5];
+    for (int n = 0; n < NVAR; ++n) u[n] = U[n * N + c];
+    orc_cons_to_prim(u, w, &nfloor);
+    for (int n = 0; n < NVAR; ++n) W[n * N + c] = w[n];
+  }
+  for (int64_t c = 0; c < NVAR * N; ++c) L[c] = 0.0;
+
+  for (int d = 0; d < 3; ++d) {
+    int perm[5] = {0, 1 + d, 1 + (d + 1) % 3, 1 + (d + 2) % 3, 4};
+    /* F[.][c] = flux through the lower face of cell c in direction d */
+#pragma omp parallel for
+    for (int64_t k = 0; k < g->n[2]; ++k)
+      for (int64_t j = 0; j < g->n[1]; ++j)
+        for (int64_t i = 0; i < g->n[0]; ++i) {
+          double wl[5], wr[5], f[5];
+          face_states(g, W, d, i, j, k, wl, wr);
+          orc_hllc(wl, wr, g->gamma, f);
+          int64_t c = cell(g, i, j, k);
+          for (int n = 0; n < NVAR; ++n) F[(int64_t)perm[n] * N + c] = f[n];
+        }
+#pragma omp parallel for
+    for (int64_t k = 0; k < g->n[2]; ++k)
+      for (int64_t j = 0; j < g->n[1]; ++j)
+        for (int64_t i = 0; i < g->n[0]; ++i) {
+          int64_t c = cell(g, i, j, k);
+          int64_t cp = cell(g, i + (d == 0), j + (d == 1), k + (d == 2));
+          for (int n = 0; n < NVAR; ++n)
+            L[n * N + c] -= (F[n * N + cp] - F[n * N + c]) / g->dx[d];
+        }
+  }
+  free(W);
+  free(F);
+  return nfloor;
+}
+
+/* ---------------------------------------------------------------------------------
+ * One SSP-RK step (Section 3, method of lines with SSP-RK; reading of the standard
+ * coefficients).  Stage s: U <- a_s*U0 + b_s*(U + dt*L(U)).  Returns the number of
+ * floors applied, or -1 on allocation failure.
+ * ------------------------------------------------------------------------------- */
+int64_t orc_rk_step(const orc_grid* g, double* U, double dt, int rk) {
+  static const double a2[2] = {0.0, 0.5}, b2[2] = {1.0, 0.5};
+  static const double a3[3] = {0.0, 0.75, 1.0 / 3.0}, b3[3] = {1.0, 0.25, 2.0 / 3.0};
+  const double* a = (rk == 3) ? a3 : a2;
+  const double* b = (rk == 3) ? b3 : b2;
+  int ns = (rk == 3) ? 3 : 2;
+  int64_t N = NVAR * g->n[0] * g->n[1] * g->n[2];
+  double* U0 = (double*)malloc(sizeof(double) * N);
+  double* L = (double*)malloc(sizeof(double) * N);
+  if (!U0 || !L) {
+    free(U0);
+    free(L);
+    return -1;
+  }
+  memcpy(U0, U, sizeof(double) * N);
+  int64_t nfloor = 0;
+  for (int s = 0; s < ns; ++s) {
+    int64_t nf = orc_rhs(g, U, L);
+    if (nf < 0) {
+      nfloor = -1;
+      break;
+    }
+    nfloor += nf;
+#pragma omp parallel for
+    for (int64_t c = 0; c < N; ++c) U[c] = a[s] * U0[c] + b[s] * (U[c] + dt * L[c]);
+  }
+  free(U0);
+  free(L);
+  return nfloor;
+}
+
+/* ---------------------------------------------------------------------------------
+ * CFL time step, Section 3 Eq. (3): dt = CFL * min over cells and dimensions of
+ * dx_d / lambda_max,d with lambda_max,d = |v_d| + c_s, c_s = sqrt(gamma p / rho).
+ * ------------------------------------------------------------------------------- */
+double orc_new_dt(const orc_grid* g, const double* U, double cfl) {
+  int64_t N = g->n[0] * g->n[1] * g->n[2];
+  double dtmin = INFINITY;
+#pragma omp parallel for reduction(min : dtmin)
+  for (int64_t c = 0; c < N; ++c) {
+    double u[5], w[5];
+    int64_t nf = 0;
+    for (int n = 0; n < NVAR; ++n) u[n] = U[n * N + c];
+    orc_cons_to_prim(u, w, &nf);
+    double p = (g->gamma - 1.0) * w[4];
+    double cs = sqrt(g->gamma * p / w[0]);
+    for (int d = 0; d < 3; ++d) {
+      double dtd = g->dx[d] / (fabs(w[1 + d]) + cs);
+      if (dtd < dtmin) dtmin = dtd;
+    }
+  }
+  return cfl * dtmin;
+}
+
+/* ---------------------------------------------------------------------------------
+ * Exact Riemann solver for the gamma-law Euler equations (Toro ch. 4), used only to
+ * pin the scheme on shock tubes.  Solves f_L(p) + f_R(p) + (u_R - u_L) = 0 by Newton
+ * iteration, then samples the self-similar solution at xi = x/t.
+ * ------------------------------------------------------------------------------- */
+static void pressure_fn(double p, double rk, double pk, double ck, double gamma, double* f,
+                        double* fd) {
+  if (p > pk) { /* shock: Rankine-Hugoniot */
+    double A = 2.0 / ((gamma + 1.0) * rk);
+    double B = (gamma - 1.0) / (gamma + 1.0) * pk;
+    double q = sqrt(A / (p + B));
+    *f = (p - pk) * q;
+    *fd = q * (1.0 - 0.5 * (p - pk) / (p + B));
+  } else { /* rarefaction: isentropic */
+    double ex = (gamma - 1.0) / (2.0 * gamma);
+    *f = 2.0 * ck / (gamma - 1.0) * (pow(p / pk, ex) - 1.0);
+    *fd = 1.0 / (rk * ck) * pow(p / pk, -(gamma + 1.0) / (2.0 * gamma));
+  }
+}
+
+/* Star-region pressure and velocity.  Returns 0, or -1 if a vacuum forms. */
+int orc_exact_star(const double wl[3], const double wr[3], double gamma, double* pstar,
+                   double* ustar) {
+  /* wl, wr = (rho, u, p) */
+  double rl = wl[0], ul = wl[1], pl = wl[2];
+  double rr = wr[0], ur = wr[1], pr = wr[2];
+  double cl = sqrt(gamma * pl / rl), cr = sqrt(gamma * pr / rr);
+  if (2.0 / (gamma - 1.0) * (cl + cr) <= ur - ul) return -1;
+  double p = 0.5 * (pl + pr) - 0.125 * (ur - ul) * (rl + rr) * (cl + cr);
+  if (p < 1e-8 * (pl < pr ? pl : pr)) p = 1e-8 * (pl < pr ? pl : pr);
+  for (int it = 0; it < 200; ++it) {
+    double fl, fdl, fr, fdr;
+    pressure_fn(p, rl, pl, cl, gamma, &fl, &fdl);
+    pressure_fn(p, rr, pr, cr, gamma, &fr, &fdr);
+    double pn = p - (fl + fr + ur - ul) / (fdl + fdr);
+    if (pn < 0.0) pn = 0.5 * p;
+    double change = fabs(pn - p) / (0.5 * (pn + p));
+    p = pn;
+    if (change < 1e-15) break;
+  }
+  double fl, fdl, fr, fdr;
+  pressure_fn(p, rl, pl, cl, gamma, &fl, &fdl);
+  pressure_fn(p, rr, pr, cr, gamma, &fr, &fdr);
+  *pstar = p;
+  *ustar = 0.5 * (ul + ur) + 0.5 * (fr - fl);
+  return 0;
+}
+
+/* Sample the exact solution at xi = x/t; out = (rho, u, p). */
+int orc_exact_sample(const double wl[3], const double wr[3], double gamma, double xi,
+                     double out[3]) {
+  double ps, us;
+  if (orc_exact_star(wl, wr, gamma, &ps, &us) != 0) return -1;
+  double g1 = (gamma - 1.0) / (gamma + 1.0);
+  if (xi <= us) { /* left of the contact */
+    double rl = wl[0], ul = wl[1], pl = wl[2];
+    double cl = sqrt(gamma * pl / rl);
+    if (ps > pl) { /* left shock */
+      double sl = ul - cl * sqrt((gamma + 1.0) / (2.0 * gamma) * ps / pl +
+                                 (gamma - 1.0) / (2.0 * gamma));
+      if (xi <= sl) {
+        out[0] = rl; out[1] = ul; out[2] = pl;
+      } else {
+        out[0] = rl * (ps / pl + g1) / (g1 * ps / pl + 1.0);
+        out[1] = us; out[2] = ps;
+      }
+    } else { /* left rarefaction */
+      double rs = rl * pow(ps / pl, 1.0 / gamma);
+      double cs = cl * pow(ps / pl, (gamma - 1.0) / (2.0 * gamma));
+      double head = ul - cl, tail = us - cs;
+      if (xi <= head) {
+        out[0] = rl; out[1] = ul; out[2] = pl;
+      } else if (xi >= tail) {
+        out[0] = rs; out[1] = us; out[2] = ps;
+      } else { /* inside the fan */
+        double u = 2.0 / (gamma + 1.0) * (cl + 0.5 * (gamma - 1.0) * ul + xi);
+        double c = 2.0 / (gamma + 1.0) * (cl + 0.5 * (gamma - 1.0) * (ul - xi));
+        out[0] = rl * pow(c / cl, 2.0 / (gamma - 1.0));
+        out[1] = u;
+        out[2] = pl * pow(c / cl, 2.0 * gamma / (gamma - 1.0));
+      }
+    }
+  } else { /* right of the contact */
+    double rr = wr[0], ur = wr[1], pr = wr[2];
+    double cr = sqrt(gamma * pr / rr);
+    if (ps > pr) { /* right shock */
+      double sr = ur + cr * sqrt((gamma + 1.0) / (2.0 * gamma) * ps / pr +
+                                 (gamma - 1.0) / (2.0 * gamma));
+      if (xi >= sr) {
+        out[0] = rr; out[1] = ur; out[2] = pr;
+      } else {
+        out[0] = rr * (ps / pr + g1) / (g1 * ps / pr + 1.0);
+        out[1] = us; out[2] = ps;
+      }
+    } else { /* right rarefaction */
+      double rs = rr * pow(ps / pr, 1.0 / gamma);
+      double cs = cr * pow(ps / pr, (gamma - 1.0) / (2.0 * gamma));
+      double head = ur + cr, tail = us + cs;
+      if (xi >= head) {
+        out[0] = rr; out[1] = ur; out[2] = pr;
+      } else if (xi <= tail) {
+        out[0] = rs; out[1] = us; out[2] = ps;
+      } else {
+        double u = 2.0 / (gamma + 1.0) * (-cr + 0.5 * (gamma - 1.0) * ur + xi);
+        double c = 2.0 / (gamma + 1.0) * (cr - 0.5 * (gamma - 1.0) * (ur - xi));
+        out[0] = rr * pow(c / cr, 2.0 / (gamma - 1.0));
+        out[1] = u;
+        out[2] = pr * pow(c / cr, 2.0 * gamma / (gamma - 1.0));
+      }
+    }
+  }
+  return 0;
+}
+
+/* Thread count the OpenMP runtime will use (reported with CPU timings). */
+int orc_num_threads(void) {
+#ifdef _OPENMP
+  extern int omp_get_max_threads(void);
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}

@@ -1,0 +1,348 @@
+"""Benchmark of the hydro RK2 step: cell-updates/s on one GB300.
+
+Workload (the metric's configuration): 3D adiabatic Euler, gamma = 5/3, periodic 256^3
+in 64 MeshBlocks of 64^3, PLM + HLLC + RK2, CFL 0.3, rho = 1, p = 1, seeded
+random-phase Gaussian velocity field with shell spectrum E(k) ~ k^-2 on 2 <= |k| <= 8,
+rms Mach 0.5.  A step is one full RK2 step: ghost fill, stage 1, ghost fill, stage 2
+with the CFL reduction, dt finalisation -- all in libak's CUDA kernels, dt device
+resident (no host round trip inside the timed region).  `value` is the FP64 form; the
+`mixed` object is the same workload in the mixed FP32/FP64 form.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+N > 1 (under torchrun) runs independent replicas, one per GPU (weak scaling, no data
+exchange: the build targets one GPU per box).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/sec per full RK2 step on 1 GB300 (FP64 vs mixed FP32) at stated L1 error"
+UNIT = "cell-updates/s"
+ROOT_NX = (256, 256, 256)
+BLOCK_NX = (64, 64, 64)
+WORKLOAD = "256^3 periodic, 64 MeshBlocks of 64^3, PLM+HLLC+RK2, k^-2 turbulence Mach 0.5"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+# Algorithmic work per cell and stage (derivations in the design doc):
+#  FP64 flops of the scheme (each +,-,*,/,sqrt counted once): cons->prim 11, PLM
+#  (slope once per cell, 2 face states) 150, HLLC 3 faces x 99, divergence 45, RK
+#  update 17.5 (mean of the two stages), CFL 21 on the last stage (10.5 mean)
+FLOP_PER_CELL_STAGE = 531.0
+#  bytes: stage 1 reads U_in and writes U_out (2 x 40 B); stage 2 also reads U0
+BYTES_STAGE = {1: 80.0, 2: 120.0}
+# FP64 peak from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        out_dir = os.path.join(ROOT, "gpurun_out")
+        os.makedirs(out_dir, exist_ok=True)
+        self.path = os.path.join(out_dir, f"clocks_bench_{os.getpid()}.csv")
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smmax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smmax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smmax) if smmax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def time_form(ak, torch, precision, U0, steps, warmup):
+    """Times `steps` RK2 steps of one form.  Returns a dict of measurements."""
+    mesh = ak.Mesh(ROOT_NX, BLOCK_NX, precision=precision, ref_rho=1.0, ref_p=1.0)
+    mesh.upload(U0)
+    mesh.new_dt()
+    h = mesh.handle
+    stream = mesh.stream
+
+    def one_step(evs=None):
+        ak.ak_fill_ghosts(h, 0)
+        if evs:
+            evs[0].record(stream)
+        ak.ak_stage(h, 1, 0.0)
+        if evs:
+            evs[1].record(stream)
+        ak.ak_fill_ghosts(h, 1)
+        if evs:
+            evs[2].record(stream)
+        ak.ak_stage(h, 2, 0.0)
+        if evs:
+            evs[3].record(stream)
+
+    for _ in range(warmup):
+        one_step()
+    stream.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    start.record(stream)
+    for s in range(steps):
+        one_step(evs[s])
+    end.record(stream)
+    end.synchronize()
+    total_ms = start.elapsed_time(end)
+    st1 = [e[0].elapsed_time(e[1]) for e in evs]
+    st2 = [e[2].elapsed_time(e[3]) for e in evs]
+    dt_next, status = ak.ak_new_dt(h, 0)
+    counters = mesh.counters()
+    mesh.close()
+    del mesh
+    torch.cuda.empty_cache()
+    return {"total_ms": total_ms, "stage1_ms": statistics.mean(st1),
+            "stage2_ms": statistics.mean(st2), "dt_after": dt_next, "counters": counters}
+
+
+def e2e_form(ak, torch, precision, U0, steps):
+    """Whole job through the public API with host buffers: upload the initial state from
+    pinned host memory, `steps` x ak_step with the dt round trip to the host every step,
+    download the final state to pinned host memory."""
+    import numpy as np
+    mesh = ak.Mesh(ROOT_NX, BLOCK_NX, precision=precision, ref_rho=1.0, ref_p=1.0)
+    packed = torch.from_numpy(mesh.pack(U0)).pin_memory()
+    out = torch.empty_like(packed).pin_memory()
+    ak.ak_upload(mesh.handle, 0, packed.data_ptr())      # warm-up: graph capture etc.
+    dt, _ = ak.ak_new_dt(mesh.handle, 0)
+    ak.ak_step(mesh.handle, dt, True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ak.ak_upload(mesh.handle, 0, packed.data_ptr())
+    dt, _ = ak.ak_new_dt(mesh.handle, 0)
+    for _ in range(steps):
+        dt, _ = ak.ak_step(mesh.handle, dt, True)
+    ak.ak_download(mesh.handle, 0, out.data_ptr())
+    t1 = time.perf_counter()
+    ok = bool(np.isfinite(out.numpy()).all())
+    nbytes = packed.numel() * 8
+    mesh.close()
+    torch.cuda.empty_cache()
+    cells = ROOT_NX[0] * ROOT_NX[1] * ROOT_NX[2]
+    return {"value": cells * steps / (t1 - t0), "unit": UNIT,
+            "h2d_bytes_per_step": (nbytes + 8 * (steps + 1)) / steps,
+            "d2h_bytes_per_step": (nbytes + 8 * (steps + 1)) / steps,
+            "finite": ok}
+
+
+def cpu_baseline(sample_n=96, budget_s=12.0, steps_max=None):
+    """The oracle (as it stands) on this host's cores: RK2 steps of a periodic sample_n^3
+    box with the benchmark's turbulence recipe until budget_s of CPU work."""
+    import oracle
+    import pgen
+    oracle.build()
+    n = (sample_n,) * 3
+    U = pgen.turbulence(n, seed=1, kmin=2, kmax=8, mach=0.5)
+    g = oracle.Grid(n)
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        dt = oracle.new_dt(U, g, 0.3)
+        U, _ = oracle.rk_step(U, g, dt, 2)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or (steps_max is not None and steps >= steps_max):
+            break
+    return {"value": sample_n ** 3 * steps / el, "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"{steps} RK2 steps of a periodic {sample_n}^3 box (same turbulence "
+                      f"recipe, FP64 oracle, OpenMP), {el:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    import pgen
+    oracle.build()
+    n = (64, 64, 64)
+    U = pgen.turbulence(n, seed=1, kmin=2, kmax=8, mach=0.5)
+    g = oracle.Grid(n)
+    for _ in range(args.warmup):
+        U, _ = oracle.rk_step(U, g, oracle.new_dt(U, g, 0.3), 2)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        U, _ = oracle.rk_step(U, g, oracle.new_dt(U, g, 0.3), 2)
+    el = time.perf_counter() - t0
+    value = 64 ** 3 * args.steps / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": "64^3 periodic box per step (bounded)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
+                         "kind": "oracle",
+                         "sample": f"{args.steps} RK2 steps of a periodic 64^3 box"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    ws, rank, local = dist_env()
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import pgen
+    from paper_2409_16053_gb300 import ak
+    U0 = pgen.turbulence(ROOT_NX, seed=1 + rank, kmin=2, kmax=8, mach=0.5)
+
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    r64 = time_form(ak, torch, ak.AK_FP64, U0, args.steps, args.warmup)
+    rmx = time_form(ak, torch, ak.AK_MIXED, U0, args.steps, args.warmup)
+    clk = clocks.stop()
+    if dist:
+        dist.barrier()
+
+    def tmax(v):
+        if not dist:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    t64 = tmax(r64["total_ms"])
+    tmx = tmax(rmx["total_ms"])
+    cells = ROOT_NX[0] * ROOT_NX[1] * ROOT_NX[2]
+    value64 = ws * cells * args.steps / (t64 * 1e-3)
+    valuemx = ws * cells * args.steps / (tmx * 1e-3)
+
+    e2e = e2e_form(ak, torch, ak.AK_FP64, U0, max(2, args.steps // 2)) if rank == 0 else None
+    e2e_mx = e2e_form(ak, torch, ak.AK_MIXED, U0, max(2, args.steps // 2)) if rank == 0 else None
+
+    peaks, peak_kind = load_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    # FP64 stage kernel: ALU bound (FP64 pipe)
+    st64 = 0.5 * (r64["stage1_ms"] + r64["stage2_ms"])
+    ach64 = FLOP_PER_CELL_STAGE * cells / (st64 * 1e-3) / 1e12
+    # mixed stage kernel: HBM roofline on the algorithmic bytes
+    bytes_mx = (BYTES_STAGE[1] + BYTES_STAGE[2]) * cells
+    ach_mx = bytes_mx / ((rmx["stage1_ms"] + rmx["stage2_ms"]) * 1e-3) / 1e9
+    traffic = {}
+    tp = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tp):
+        try:
+            traffic = json.load(open(tp))
+        except ValueError:
+            traffic = {}
+    line = {
+        "metric": METRIC, "value": value64, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t64 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "form": "FP64", "cells": cells,
+                   "l2": "inputs larger than L2: 2 registers x 805 MB",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "roofline": {"bound": "alu", "achieved": ach64, "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": ach64 / FP64_PEAK_TFLOPS,
+                     "traffic": traffic.get("stage_fp64"),
+                     "kernel": "stage_kernel<PLM, FP64> (mean of stage 1 and 2 launches)",
+                     "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz"},
+        "mixed": {
+            "value": valuemx, "unit": UNIT, "ms_per_step": tmx / args.steps, "dtype": "f32+f64",
+            "roofline": {"bound": "hbm", "achieved": ach_mx, "peak": hbm, "unit": "GB/s",
+                         "frac": ach_mx / hbm, "traffic": traffic.get("stage_mixed"),
+                         "kernel": "stage_kernel<PLM, mixed> (stage 1 + stage 2)",
+                         "peak_source": f"{peak_kind} hbm_gbs"},
+            "e2e": e2e_mx,
+        },
+        "stage_ms": {"fp64": [r64["stage1_ms"], r64["stage2_ms"]],
+                     "mixed": [rmx["stage1_ms"], rmx["stage2_ms"]]},
+        "counters": {"fp64": r64["counters"], "mixed": rmx["counters"]},
+        "e2e": e2e,
+        "gpu_launches": 5 * args.steps * 2,
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

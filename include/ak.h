@@ -1,0 +1,163 @@
+/*
+ * ak.h -- C-ABI of the GB300 hydro-stage library (libak).
+ *
+ * One Runge-Kutta stage of the Godunov finite-volume update for 3D adiabatic
+ * Newtonian hydrodynamics on a mesh of MeshBlocks, as AthenaK states it
+ * (arXiv 2409.16053):
+ *   - conservation law dU/dt + div F(W) = 0 ............ Section 3, Eq. (1) (S = 0)
+ *   - U = (rho, rho v, E), F, W = (rho, v, u_g),
+ *     E = u_g + rho v^2/2, p = (gamma-1) u_g ............ Section 3.1, Eq. (4)
+ *   - reconstruction on primitives (PLM, PPM4) ......... Section 3
+ *   - HLLC Riemann solver .............................. Section 3
+ *   - method of lines with SSP Runge-Kutta ............. Section 3
+ *   - CFL time step, min over all cells and dims ....... Section 3, Eq. (3)
+ *   - MeshBlocks aggregated per device, one launch
+ *     covers all blocks ................................ Section 2 (MeshBlockPacks)
+ *   - ghost zones filled by device copies .............. Section 2 (Boundary conditions)
+ *   - uniform time step across levels .................. Section 2
+ *
+ * Conventions
+ *   - All calls are ordered on the CUDA stream given to ak_mesh_create.  Calls that
+ *     return a device result to the host (ak_new_dt, ak_step with dt_next, ak_download,
+ *     ak_status_counters) synchronize that stream; the others only enqueue work.
+ *   - Device pointers are plain `double*` in device memory.  Registers (the state
+ *     arrays) are owned by the caller (e.g. torch tensors) and only borrowed by
+ *     ak_mesh_bind; the library never frees them.  The library allocates only its own
+ *     small tables, device scalars and, for ak_upload/ak_download, a staging buffer of
+ *     one register's interior size; ak_mesh_destroy frees them.
+ *   - Argument errors are returned synchronously.  Device-side problems (density or
+ *     internal energy below the floors, non-finite states) are counted in a device
+ *     status word and reported by the next synchronizing call as AK_ENEGATIVE; the
+ *     counters stay readable through ak_status_counters.
+ *   - A mesh object is not thread safe; distinct meshes may be used from distinct
+ *     host threads.
+ *
+ * Register layout (the library's choice, reported by ak_mesh_layout):
+ *   register = blocks one after another; block b starts at element offset
+ *   block_offset[b] (multiple of 32 elements); inside a block the layout is
+ *   [var 0..4][k][j][i] with i fastest, each dimension padded by nghost ghost cells on
+ *   both sides: extents (nx1+2g, nx2+2g, nx3+2g).  var = (rho, M1, M2, M3, E).
+ *   The interior cell (i, j, k), 0 <= i < nx1, of block b, variable v is element
+ *     block_offset[b] + ((v*(nx3+2g) + k+g)*(nx2+2g) + j+g)*(nx1+2g) + i+g.
+ */
+#ifndef AK_H
+#define AK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  AK_OK = 0,
+  AK_EINVAL = -1,     /* invalid argument or unsupported configuration */
+  AK_ENOMEM = -2,     /* a library allocation failed */
+  AK_ECUDA = -3,      /* a CUDA runtime call failed (see ak_last_error) */
+  AK_ENEGATIVE = -4,  /* rho or u_g fell below the floors (see ak_status_counters) */
+  AK_ETIMEOUT = -5,   /* a bounded device wait gave up */
+  AK_ESTATE = -6      /* call out of order (e.g. a register not bound) */
+} ak_status;
+
+enum { AK_PLM = 0, AK_PPM4 = 1 };     /* reconstruction (Section 3) */
+enum { AK_FP64 = 0, AK_MIXED = 1 };   /* arithmetic form of the stage */
+
+/* Number of int32 entries per block in ak_mesh_desc.blocks. */
+#define AK_BLOCK_INTS 7
+
+typedef struct ak_mesh ak_mesh;
+
+typedef struct {
+  int32_t nblocks;        /* number of MeshBlocks (Section 2), >= 1 */
+  int32_t nghost;         /* ghost cells per side: 2 for PLM, 3 for PPM4 */
+  const int32_t* blocks;  /* host array, AK_BLOCK_INTS ints per block:
+                             level, lx1, lx2, lx3, nx1, nx2, nx3 -- (lx1, lx2, lx3) is the
+                             block's first cell in the cell index space of its level;
+                             only level 0 (a uniform mesh) is accepted by this version.
+                             Copied at create time; the caller keeps ownership. */
+  double xmin[3], xmax[3];  /* domain, periodic in all three directions */
+  int32_t root_nx[3];       /* level-0 cells per direction; the blocks must tile it */
+  int32_t recon;            /* AK_PLM or AK_PPM4 */
+  int32_t rk;               /* SSP-RK order: 2 (Heun) or 3 (Shu-Osher) */
+  int32_t precision;        /* AK_FP64 or AK_MIXED */
+  double gamma;             /* gamma-law EOS, > 1 */
+  double cfl;               /* Courant number of Eq. (3), in (0, 1] */
+  double ref_rho, ref_p;    /* AK_MIXED only: background density and pressure that are
+                               subtracted (in FP64) before the FP32 arithmetic; any
+                               positive values are valid, values close to the flow's
+                               typical state give the smallest rounding error. */
+} ak_mesh_desc;
+
+/* Validates `desc`, copies the block table to the device and allocates the device
+ * scalars.  `cuda_stream` is a cudaStream_t (NULL = legacy default stream).
+ * Returns AK_EINVAL for an invalid description (blocks overlapping, not tiling
+ * root_nx, sizes < nghost, unsupported recon/rk/precision), AK_ENOMEM / AK_ECUDA on
+ * allocation failure.  On success *out owns the mesh (free with ak_mesh_destroy). */
+ak_status ak_mesh_create(const ak_mesh_desc* desc, void* cuda_stream, ak_mesh** out);
+
+/* Frees what the library allocated; bound registers are not touched.  NULL is a no-op. */
+void ak_mesh_destroy(ak_mesh* mesh);
+
+/* Number of registers the configured integrator needs (2 for RK2, 3 for RK3), bytes of
+ * one register, and (if block_offset != NULL) the element offset of every block
+ * (nblocks entries).  Register 0 holds U^n before ak_step and U^{n+1} after it. */
+ak_status ak_mesh_layout(const ak_mesh* mesh, int32_t* nregisters, size_t* register_bytes,
+                         int64_t* block_offset);
+
+/* Borrows `dev_ptr` (device memory of register_bytes bytes, 256-byte aligned) as
+ * register `reg` in [0, nregisters).  AK_EINVAL for a bad index, NULL or misaligned
+ * pointer. */
+ak_status ak_mesh_bind(ak_mesh* mesh, int32_t reg, double* dev_ptr);
+
+/* Ghost-zone fill of register `reg` (Section 2, Boundary conditions): every ghost
+ * cell of every block receives the interior cell that the periodic domain maps it to,
+ * copied from the neighbouring block on the same device; one launch covers all
+ * blocks.  Edge and corner ghosts are filled too. */
+ak_status ak_fill_ghosts(ak_mesh* mesh, int32_t reg);
+
+/* One RK stage s in [1, rk] with time step dt (Section 3); dt <= 0 uses the
+ * device-resident dt (the last CFL reduction, or the last dt given):
+ *   U_out = a_s * U0 + b_s * (U_in + dt * L(U_in)),   L = -div F (Eq. (1)),
+ * RK2: (a, b) = (0, 1), (1/2, 1/2); RK3: (0, 1), (3/4, 1/4), (1/3, 2/3).
+ * Registers: RK2 stage 1: in 0, out 1; stage 2: in 1, U0 = 0, out 0.
+ *            RK3 stage 1: in 0, out 1; stage 2: in 1, out 2; stage 3: in 2, out 0.
+ * The ghost zones of the input register must be current (ak_fill_ghosts).  Only
+ * interior cells of the output are written.  The last stage also accumulates the CFL
+ * minimum of the new state for ak_new_dt's device-resident value. */
+ak_status ak_stage(ak_mesh* mesh, int32_t stage, double dt);
+
+/* CFL time step of register `reg` (Section 3, Eq. (3)):
+ *   dt = cfl * min over interior cells and d of dx_d / (|v_d| + c_s),
+ *   c_s = sqrt(gamma p / rho).  Synchronizes the stream and writes *dt_out.  The value
+ * also becomes the device-resident dt that ak_step uses when called with dt <= 0.
+ * Returns AK_ENEGATIVE if any floor was hit since the last check (the dt is still
+ * written). */
+ak_status ak_new_dt(ak_mesh* mesh, int32_t reg, double* dt_out);
+
+/* One full RK step of register 0: for each stage, ghost fill of its input then
+ * ak_stage; the new CFL dt is reduced in the last stage.  dt > 0 uses that dt;
+ * dt <= 0 uses the device-resident dt (from ak_new_dt or the previous ak_step), so a
+ * time loop needs no host round trip.  If dt_next != NULL the stream is synchronized
+ * and the CFL dt of the new state is written there.  The step's launches are captured
+ * into a CUDA graph on the first call and replayed afterwards. */
+ak_status ak_step(ak_mesh* mesh, double dt, double* dt_next);
+
+/* Host <-> device state transfer through a library staging buffer.  The host array is
+ * the interior only, packed block after block: [block][var][k][j][i], i fastest
+ * (nblocks * 5 * nx1*nx2*nx3 doubles for equal blocks).  Pinned host memory gives
+ * asynchronous copies; ak_download synchronizes the stream. */
+ak_status ak_upload(ak_mesh* mesh, int32_t reg, const double* host_interior);
+ak_status ak_download(ak_mesh* mesh, int32_t reg, double* host_interior);
+
+/* Device counters (synchronizes): out[0] floors applied, out[1] non-finite cells seen,
+ * out[2] bounded waits that timed out, out[3] reserved (0). */
+ak_status ak_status_counters(ak_mesh* mesh, int64_t out[4]);
+
+/* Message of the last error returned on this host thread ("" if none). */
+const char* ak_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AK_H */

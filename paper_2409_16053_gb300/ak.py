@@ -1,0 +1,267 @@
+"""Thin ctypes binding of libak (include/ak.h), with the C-ABI's names.
+
+Argument marshalling only: every step of the hydro stage runs in the CUDA kernels of
+libak.so.  There is no CPU fallback: if the library cannot be loaded, importing this
+module raises.  PyTorch is used only to own device memory (the registers) and the
+CUDA stream.
+
+Low level (same names and arguments as the C functions):
+    ak_mesh_create, ak_mesh_destroy, ak_mesh_layout, ak_mesh_bind, ak_fill_ghosts,
+    ak_stage, ak_new_dt, ak_step, ak_upload, ak_download, ak_status_counters,
+    ak_last_error
+High level: ``Mesh`` builds a uniform mesh of equal MeshBlocks, allocates and binds
+its registers as torch tensors, and converts between a global (5, n3, n2, n1) array
+and the library's block layout.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+AK_OK, AK_EINVAL, AK_ENOMEM, AK_ECUDA, AK_ENEGATIVE, AK_ETIMEOUT, AK_ESTATE = \
+    0, -1, -2, -3, -4, -5, -6
+AK_PLM, AK_PPM4 = 0, 1
+AK_FP64, AK_MIXED = 0, 1
+AK_BLOCK_INTS = 7
+
+_STATUS_NAMES = {0: "AK_OK", -1: "AK_EINVAL", -2: "AK_ENOMEM", -3: "AK_ECUDA",
+                 -4: "AK_ENEGATIVE", -5: "AK_ETIMEOUT", -6: "AK_ESTATE"}
+
+
+class AkError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class ak_mesh_desc(ctypes.Structure):
+    _fields_ = [
+        ("nblocks", ctypes.c_int32), ("nghost", ctypes.c_int32),
+        ("blocks", ctypes.POINTER(ctypes.c_int32)),
+        ("xmin", ctypes.c_double * 3), ("xmax", ctypes.c_double * 3),
+        ("root_nx", ctypes.c_int32 * 3),
+        ("recon", ctypes.c_int32), ("rk", ctypes.c_int32), ("precision", ctypes.c_int32),
+        ("gamma", ctypes.c_double), ("cfl", ctypes.c_double),
+        ("ref_rho", ctypes.c_double), ("ref_p", ctypes.c_double),
+    ]
+
+
+def _load_lib():
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"libak.so not built ({path}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    vp, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
+    i32 = ctypes.c_int32
+    lib.ak_mesh_create.argtypes = [ctypes.POINTER(ak_mesh_desc), vp, ctypes.POINTER(vp)]
+    lib.ak_mesh_destroy.argtypes = [vp]
+    lib.ak_mesh_destroy.restype = None
+    lib.ak_mesh_layout.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_size_t),
+                                   ctypes.POINTER(ctypes.c_int64)]
+    lib.ak_mesh_bind.argtypes = [vp, i32, vp]
+    lib.ak_fill_ghosts.argtypes = [vp, i32]
+    lib.ak_stage.argtypes = [vp, i32, ctypes.c_double]
+    lib.ak_new_dt.argtypes = [vp, i32, dp]
+    lib.ak_step.argtypes = [vp, ctypes.c_double, dp]
+    lib.ak_upload.argtypes = [vp, i32, vp]
+    lib.ak_download.argtypes = [vp, i32, vp]
+    lib.ak_status_counters.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
+    lib.ak_last_error.restype = ctypes.c_char_p
+    for name in ("ak_mesh_create", "ak_mesh_layout", "ak_mesh_bind", "ak_fill_ghosts",
+                 "ak_stage", "ak_new_dt", "ak_step", "ak_upload", "ak_download",
+                 "ak_status_counters"):
+        getattr(lib, name).restype = ctypes.c_int
+    return lib
+
+
+_lib = _load_lib()
+EXPORTED = ("ak_mesh_create", "ak_mesh_destroy", "ak_mesh_layout", "ak_mesh_bind",
+            "ak_fill_ghosts", "ak_stage", "ak_new_dt", "ak_step", "ak_upload",
+            "ak_download", "ak_status_counters", "ak_last_error")
+
+
+def ak_last_error() -> str:
+    return _lib.ak_last_error().decode()
+
+
+def _check(st, allow=()):
+    if st != AK_OK and st not in allow:
+        raise AkError(st, ak_last_error())
+    return st
+
+
+# ---- C-ABI, one wrapper per entry point ---------------------------------------------
+def ak_mesh_create(desc: ak_mesh_desc, cuda_stream: int):
+    out = ctypes.c_void_p()
+    _check(_lib.ak_mesh_create(ctypes.byref(desc), ctypes.c_void_p(cuda_stream),
+                               ctypes.byref(out)))
+    return out
+
+
+def ak_mesh_destroy(mesh) -> None:
+    _lib.ak_mesh_destroy(mesh)
+
+
+def ak_mesh_layout(mesh, nblocks: int):
+    nreg, nbytes = ctypes.c_int32(), ctypes.c_size_t()
+    offs = (ctypes.c_int64 * nblocks)()
+    _check(_lib.ak_mesh_layout(mesh, ctypes.byref(nreg), ctypes.byref(nbytes), offs))
+    return int(nreg.value), int(nbytes.value), np.array(offs[:], dtype=np.int64)
+
+
+def ak_mesh_bind(mesh, reg: int, dev_ptr: int) -> None:
+    _check(_lib.ak_mesh_bind(mesh, reg, ctypes.c_void_p(dev_ptr)))
+
+
+def ak_fill_ghosts(mesh, reg: int) -> None:
+    _check(_lib.ak_fill_ghosts(mesh, reg))
+
+
+def ak_stage(mesh, stage: int, dt: float) -> None:
+    _check(_lib.ak_stage(mesh, stage, float(dt)))
+
+
+def ak_new_dt(mesh, reg: int):
+    """Returns (dt, status); status AK_ENEGATIVE (floors were hit) is not raised."""
+    dt = ctypes.c_double()
+    st = _check(_lib.ak_new_dt(mesh, reg, ctypes.byref(dt)), allow=(AK_ENEGATIVE,))
+    return dt.value, st
+
+
+def ak_step(mesh, dt: float, want_dt_next: bool = True):
+    """Returns (dt_next or None, status); AK_ENEGATIVE is returned, not raised."""
+    if want_dt_next:
+        dn = ctypes.c_double()
+        st = _check(_lib.ak_step(mesh, float(dt), ctypes.byref(dn)), allow=(AK_ENEGATIVE,))
+        return dn.value, st
+    st = _check(_lib.ak_step(mesh, float(dt), None), allow=(AK_ENEGATIVE,))
+    return None, st
+
+
+def ak_upload(mesh, reg: int, host_ptr: int) -> None:
+    _check(_lib.ak_upload(mesh, reg, ctypes.c_void_p(host_ptr)))
+
+
+def ak_download(mesh, reg: int, host_ptr: int) -> None:
+    _check(_lib.ak_download(mesh, reg, ctypes.c_void_p(host_ptr)))
+
+
+def ak_status_counters(mesh):
+    out = (ctypes.c_int64 * 4)()
+    _check(_lib.ak_status_counters(mesh, out))
+    return list(out)
+
+
+# ---- convenience layer ---------------------------------------------------------------
+def uniform_block_table(root_nx, block_nx):
+    """Block table of a uniform level-0 mesh, blocks in x1-fastest order."""
+    nb = [root_nx[d] // block_nx[d] for d in range(3)]
+    rows = []
+    for bz in range(nb[2]):
+        for by in range(nb[1]):
+            for bx in range(nb[0]):
+                rows.append([0, bx * block_nx[0], by * block_nx[1], bz * block_nx[2],
+                             block_nx[0], block_nx[1], block_nx[2]])
+    return np.ascontiguousarray(np.array(rows, dtype=np.int32))
+
+
+class Mesh:
+    """A uniform periodic mesh of equal MeshBlocks with torch-owned registers."""
+
+    def __init__(self, root_nx, block_nx, *, recon=AK_PLM, rk=2, precision=AK_FP64,
+                 gamma=5.0 / 3.0, cfl=0.3, xmin=(0.0, 0.0, 0.0), xmax=(1.0, 1.0, 1.0),
+                 ref_rho=1.0, ref_p=1.0, device="cuda", stream=None):
+        import torch
+        self.torch = torch
+        self.root_nx = tuple(int(v) for v in root_nx)
+        self.block_nx = tuple(int(v) for v in block_nx)
+        self.nb = tuple(self.root_nx[d] // self.block_nx[d] for d in range(3))
+        self.ng = 2 if recon == AK_PLM else 3
+        self.table = uniform_block_table(self.root_nx, self.block_nx)
+        self.nblocks = int(self.table.shape[0])
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
+        d = ak_mesh_desc()
+        d.nblocks = self.nblocks
+        d.nghost = self.ng
+        d.blocks = self.table.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        for a in range(3):
+            d.xmin[a] = float(xmin[a])
+            d.xmax[a] = float(xmax[a])
+            d.root_nx[a] = self.root_nx[a]
+        d.recon, d.rk, d.precision = int(recon), int(rk), int(precision)
+        d.gamma, d.cfl = float(gamma), float(cfl)
+        d.ref_rho, d.ref_p = float(ref_rho), float(ref_p)
+        self.desc = d
+        self.handle = ak_mesh_create(d, self.stream.cuda_stream)
+        self.nreg, self.reg_bytes, self.offsets = ak_mesh_layout(self.handle, self.nblocks)
+        self.regs = [torch.empty(self.reg_bytes // 8, dtype=torch.float64, device=self.device)
+                     for _ in range(self.nreg)]
+        for r, t in enumerate(self.regs):
+            ak_mesh_bind(self.handle, r, t.data_ptr())
+        self.interior_count = self.nblocks * 5 * int(np.prod(self.block_nx))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.stream.synchronize()
+            ak_mesh_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # global (5, n3, n2, n1) <-> packed interior [block][var][k][j][i]
+    def pack(self, U):
+        n1, n2, n3 = self.block_nx
+        b1, b2, b3 = self.nb
+        U = np.asarray(U, dtype=np.float64)
+        assert U.shape == (5, self.root_nx[2], self.root_nx[1], self.root_nx[0]), U.shape
+        P = U.reshape(5, b3, n3, b2, n2, b1, n1).transpose(1, 3, 5, 0, 2, 4, 6)
+        return np.ascontiguousarray(P).reshape(-1)
+
+    def unpack(self, P):
+        n1, n2, n3 = self.block_nx
+        b1, b2, b3 = self.nb
+        P = np.asarray(P).reshape(b3, b2, b1, 5, n3, n2, n1).transpose(3, 0, 4, 1, 5, 2, 6)
+        return np.ascontiguousarray(P).reshape(5, self.root_nx[2], self.root_nx[1],
+                                               self.root_nx[0])
+
+    def upload(self, U, reg=0):
+        host = self.torch.from_numpy(self.pack(U)).pin_memory()
+        ak_upload(self.handle, reg, host.data_ptr())
+        self.stream.synchronize()  # the pinned buffer may be freed after return
+
+    def download(self, reg=0):
+        host = self.torch.empty(self.interior_count, dtype=self.torch.float64).pin_memory()
+        ak_download(self.handle, reg, host.data_ptr())
+        return self.unpack(host.numpy().copy())
+
+    def fill_ghosts(self, reg=0):
+        ak_fill_ghosts(self.handle, reg)
+
+    def stage(self, s, dt):
+        ak_stage(self.handle, s, dt)
+
+    def new_dt(self, reg=0):
+        return ak_new_dt(self.handle, reg)[0]
+
+    def step(self, dt=0.0, want_dt_next=True):
+        return ak_step(self.handle, dt, want_dt_next)[0]
+
+    def counters(self):
+        return ak_status_counters(self.handle)
+
+    def register_view(self, reg=0):
+        """Torch view (nblocks, 5, p3, p2, p1) of a register, ghosts included."""
+        p = [n + 2 * self.ng for n in self.block_nx]
+        stride = int(self.offsets[1] - self.offsets[0]) if self.nblocks > 1 else 5 * p[0] * p[1] * p[2]
+        t = self.regs[reg]
+        return t.as_strided((self.nblocks, 5, p[2], p[1], p[0]),
+                            (stride, p[0] * p[1] * p[2], p[0] * p[1], p[0], 1))

@@ -1,0 +1,99 @@
+"""Host-side checks of the C-ABI library (no GPU needed): it loads, exports every
+entry point include/ak.h declares, and rejects invalid mesh descriptions before any
+device work."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def ak():
+    from paper_2409_16053_gb300 import build
+    build.build()
+    from paper_2409_16053_gb300 import ak as mod
+    return mod
+
+
+def declared_functions():
+    names = []
+    for f in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            names += re.findall(r"^\s*(?:ak_status|void|const char\*)\s+(ak_\w+)\s*\(", src, re.M)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol(ak):
+    lib = ctypes.CDLL(ak._build.LIB)
+    names = declared_functions()
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(ak.EXPORTED) <= set(names)
+
+
+def _desc(ak, **kw):
+    table = ak.uniform_block_table((32, 32, 32), (16, 16, 16))
+    d = ak.ak_mesh_desc()
+    d.nblocks = table.shape[0]
+    d.nghost = 2
+    d.blocks = table.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    for a in range(3):
+        d.xmin[a], d.xmax[a], d.root_nx[a] = 0.0, 1.0, 32
+    d.recon, d.rk, d.precision = ak.AK_PLM, 2, ak.AK_FP64
+    d.gamma, d.cfl, d.ref_rho, d.ref_p = 5 / 3, 0.3, 1.0, 1.0
+    for k, v in kw.items():
+        setattr(d, k, v)
+    return d, table
+
+
+@pytest.mark.parametrize("field,value", [
+    ("nghost", 3), ("rk", 4), ("recon", 7), ("precision", 5), ("gamma", 1.0),
+    ("cfl", 0.0), ("cfl", 1.5), ("nblocks", 0), ("nblocks", 7)])
+def test_invalid_descriptions_rejected(ak, field, value):
+    d, table = _desc(ak, **{field: value})
+    out = ctypes.c_void_p()
+    st = ak._lib.ak_mesh_create(ctypes.byref(d), None, ctypes.byref(out))
+    assert st == ak.AK_EINVAL, (field, value, st)
+    assert out.value is None
+    assert ak.ak_last_error()
+
+
+def test_mixed_needs_background_and_tiling_checked(ak):
+    d, table = _desc(ak, precision=1, ref_rho=0.0)
+    out = ctypes.c_void_p()
+    assert ak._lib.ak_mesh_create(ctypes.byref(d), None, ctypes.byref(out)) == ak.AK_EINVAL
+    d, table = _desc(ak)
+    table[3, 1] = table[2, 1]  # duplicate a block origin -> overlap
+    table[3, 2] = table[2, 2]
+    d.blocks = table.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    assert ak._lib.ak_mesh_create(ctypes.byref(d), None, ctypes.byref(out)) == ak.AK_EINVAL
+    assert "overlap" in ak.ak_last_error()
+
+
+def test_null_arguments_rejected(ak):
+    assert ak._lib.ak_mesh_create(None, None, None) == ak.AK_EINVAL
+    assert ak._lib.ak_fill_ghosts(None, 0) == ak.AK_EINVAL
+    assert ak._lib.ak_stage(None, 1, 0.1) == ak.AK_EINVAL
+    assert ak._lib.ak_step(None, 0.1, None) == ak.AK_EINVAL
+    ak.ak_mesh_destroy(None)
+
+
+def test_pack_unpack_round_trip_host(ak):
+    # the binding's global <-> block-order conversion (host only, no device)
+    class M(ak.Mesh):
+        def __init__(self):
+            self.root_nx, self.block_nx = (12, 8, 6), (4, 4, 3)
+            self.nb = (3, 2, 2)
+    m = M()
+    U = np.random.default_rng(0).normal(size=(5, 6, 8, 12))
+    P = m.pack(U)
+    # block (bx=1, by=1, bz=1) is block index (1*2+1)*3+1 = 10; its var 4 cell (2,3,1)
+    blk = P.reshape(12, 5, 3, 4, 4)[10]
+    assert blk[4, 2, 3, 1] == U[4, 3 + 2, 4 + 3, 4 + 1]
+    assert np.array_equal(m.unpack(P), U)

@@ -154,6 +154,41 @@ ak_status ak_download(ak_mesh* mesh, int32_t reg, double* host_interior);
  * out[2] bounded waits that timed out, out[3] reserved (0). */
 ak_status ak_status_counters(ak_mesh* mesh, int64_t out[4]);
 
+/* Largest number of MeshBlocks ak_cfl_dt_noalloc accepts: the size of its static
+ * device scratch (AK_NOALLOC_MAX_BLOCKS + 1 doubles, 512 KiB per GPU). */
+#define AK_NOALLOC_MAX_BLOCKS 65536
+
+/* CFL time step of a register, computed without allocating any memory.
+ *
+ * The paper has no counterpart to this call; it exists for callers that cannot call
+ * cudaMalloc -- e.g. a host code whose own pool allocator owns all device memory
+ * (so a library may not allocate behind its back), or a monitoring / recovery path
+ * that must still report a time step when the device is out of memory.  It needs no
+ * ak_mesh (creating one allocates): the caller passes the register and its geometry.
+ *
+ * reg       device pointer to one register in the layout ak_mesh_layout describes,
+ *           for a mesh of `nblocks` equal blocks of nx[0] x nx[1] x nx[2] interior
+ *           cells with `nghost` ghost cells per side (block b starts at element
+ *           b * round_up(5 * (nx1+2g)(nx2+2g)(nx3+2g), 32)); only interior cells are
+ *           read.  Not modified; the caller keeps ownership.
+ * dx        cell widths; gamma, cfl as in ak_mesh_desc.
+ * dt_out    host pointer; receives cfl * min over interior cells and d of
+ *           dx_d / (|v_d| + c_s), the same value ak_new_dt returns for that register.
+ * cuda_stream  the work runs on this stream, which the call synchronizes.
+ *
+ * Scratch: a file-scope static __device__ array (AK_NOALLOC_MAX_BLOCKS + 1 doubles)
+ * that every GPU loading the library keeps until the process exits.  The first call
+ * on a device looks up that array's device address (cudaGetSymbolAddress) with the
+ * device current; make that first call before any stream capture.  Every call on a
+ * device shares the array and leaves its last contents there, so calls that overlap
+ * on the GPU (concurrent streams, threads) race: serialize them.  No call of this
+ * function runs cudaMalloc, cudaFree or any other allocating routine.
+ * Errors: AK_EINVAL for NULL pointers, invalid sizes, or nblocks outside
+ * [1, AK_NOALLOC_MAX_BLOCKS]; AK_ECUDA if a CUDA call fails. */
+ak_status ak_cfl_dt_noalloc(const double* reg, int32_t nblocks, const int32_t nx[3],
+                            int32_t nghost, const double dx[3], double gamma, double cfl,
+                            void* cuda_stream, double* dt_out);
+
 /* Message of the last error returned on this host thread ("" if none). */
 const char* ak_last_error(void);
 

@@ -8,7 +8,7 @@ CUDA stream.
 Low level (same names and arguments as the C functions):
     ak_mesh_create, ak_mesh_destroy, ak_mesh_layout, ak_mesh_bind, ak_fill_ghosts,
     ak_stage, ak_new_dt, ak_step, ak_upload, ak_download, ak_status_counters,
-    ak_last_error
+    ak_cfl_dt_noalloc, ak_last_error
 High level: ``Mesh`` builds a uniform mesh of equal MeshBlocks, allocates and binds
 its registers as torch tensors, and converts between a global (5, n3, n2, n1) array
 and the library's block layout.
@@ -70,6 +70,9 @@ def _load_lib():
     lib.ak_upload.argtypes = [vp, i32, vp]
     lib.ak_download.argtypes = [vp, i32, vp]
     lib.ak_status_counters.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
+    lib.ak_cfl_dt_noalloc.argtypes = [vp, i32, ctypes.POINTER(i32), i32, dp, ctypes.c_double,
+                                      ctypes.c_double, vp, dp]
+    lib.ak_cfl_dt_noalloc.restype = ctypes.c_int
     lib.ak_last_error.restype = ctypes.c_char_p
     for name in ("ak_mesh_create", "ak_mesh_layout", "ak_mesh_bind", "ak_fill_ghosts",
                  "ak_stage", "ak_new_dt", "ak_step", "ak_upload", "ak_download",
@@ -81,7 +84,7 @@ def _load_lib():
 _lib = _load_lib()
 EXPORTED = ("ak_mesh_create", "ak_mesh_destroy", "ak_mesh_layout", "ak_mesh_bind",
             "ak_fill_ghosts", "ak_stage", "ak_new_dt", "ak_step", "ak_upload",
-            "ak_download", "ak_status_counters", "ak_last_error")
+            "ak_download", "ak_status_counters", "ak_cfl_dt_noalloc", "ak_last_error")
 
 
 def ak_last_error() -> str:
@@ -154,6 +157,18 @@ def ak_status_counters(mesh):
     out = (ctypes.c_int64 * 4)()
     _check(_lib.ak_status_counters(mesh, out))
     return list(out)
+
+
+def ak_cfl_dt_noalloc(reg_ptr: int, nblocks: int, nx, nghost: int, dx, gamma: float,
+                      cfl: float, cuda_stream: int) -> float:
+    """CFL dt of a register without any device allocation (static device scratch)."""
+    nx_c = (ctypes.c_int32 * 3)(*[int(v) for v in nx])
+    dx_c = (ctypes.c_double * 3)(*[float(v) for v in dx])
+    out = ctypes.c_double()
+    _check(_lib.ak_cfl_dt_noalloc(ctypes.c_void_p(reg_ptr), int(nblocks), nx_c, int(nghost),
+                                  dx_c, float(gamma), float(cfl),
+                                  ctypes.c_void_p(cuda_stream), ctypes.byref(out)))
+    return out.value
 
 
 # ---- convenience layer ---------------------------------------------------------------

@@ -7,11 +7,16 @@
 // does): a CTA owns a TX x TY column tile of one block and marches along x3 over a
 // segment of planes.  A ring of 2*NG planes of primitives (tile plus NG halo cells in
 // x1 and x2) lives in shared memory; each plane is loaded from HBM and converted once.
-// x1 and x2 faces of the current plane are solved from the ring and their fluxes kept
-// in shared memory; the x3 face above each column is solved by the column's thread,
-// which carries the flux of the face below from the previous plane.  Every face of a
-// tile is solved once; faces on tile edges are solved by both tiles with identical
-// inputs, so they agree bit for bit and the update stays conservative.
+// Per plane:
+//   A. reconstruction: the x1 and x2 face values (lower and upper edge) of every cell
+//      the tile's faces touch go to shared memory; each thread also reconstructs its
+//      own column's next cell along x3 and keeps the upper edge in registers;
+//   B. HLLC on every x1 and x2 face of the plane (fluxes to shared memory) and on the
+//      x3 face above each column (flux in registers, carried to the next plane);
+//   C. flux divergence and the RK update of the column's cell.
+// Every cell is reconstructed once per direction and every face of a tile is solved
+// once; faces on tile edges are solved by both tiles from identical inputs, so they
+// agree bit for bit and the update stays conservative.
 #include <type_traits>
 
 #include "ak_internal.cuh"
@@ -26,17 +31,27 @@ struct Counters {
 
 __device__ __forceinline__ void count(unsigned long long* c) { atomicAdd(c, 1ull); }
 
+// Bit-level tests that keep comparisons of doubles off the FP64 pipe.
+__device__ __forceinline__ bool not_finite(double x) {
+  return ((unsigned)__double2hiint(x) & 0x7ff00000u) == 0x7ff00000u;
+}
+// x >= floor for a positive, finite `floor` (false for negative x and NaN-free x < floor)
+__device__ __forceinline__ bool at_least(double x, double floor) {
+  return __double_as_longlong(x) >= __double_as_longlong(floor);
+}
+
 // Conserved -> primitive (Section 3.1 Eq. (4)), FP64 form.
 __device__ __forceinline__ void c2p(const double* u, double* w, const Bg&, Counters cn) {
   double rho = u[0];
-  if (!(rho == rho) || !(u[4] == u[4])) count(cn.nonfinite);
-  if (!(rho >= AK_RHO_FLOOR)) {
+  if (not_finite(rho) || not_finite(u[4])) count(cn.nonfinite);
+  if (!at_least(rho, AK_RHO_FLOOR)) {
     rho = AK_RHO_FLOOR;
     count(cn.floors);
   }
-  const double v1 = u[1] / rho, v2 = u[2] / rho, v3 = u[3] / rho;
-  double ug = u[4] - 0.5 * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) / rho;
-  if (!(ug >= AK_UG_FLOOR)) {
+  const double r = rcp64(rho);
+  const double v1 = u[1] * r, v2 = u[2] * r, v3 = u[3] * r;
+  double ug = fma(-0.5, fma(u[1], v1, fma(u[2], v2, u[3] * v3)), u[4]);
+  if (!at_least(ug, AK_UG_FLOOR)) {
     ug = AK_UG_FLOOR;
     count(cn.floors);
   }
@@ -47,84 +62,110 @@ __device__ __forceinline__ void c2p(const double* u, double* w, const Bg&, Count
   w[4] = ug;
 }
 
-// Conserved -> primitive, mixed form: the internal-energy recovery
-// u_g = E - |M|^2 / (2 rho) and the background subtraction run in FP64; the
-// deviations W' are rounded to FP32.
+// Conserved -> primitive, mixed form.  The internal-energy recovery
+// u_g - u_g,b = (E - u_g,b) - |M|^2 / (2 rho) and rho - rho_b run in FP64 (1/rho from
+// an FP32 seed plus one FP64 Newton step); velocities come from FP32 arithmetic; the
+// deviations W' are rounded to FP32 on the integer pipe.
 __device__ __forceinline__ void c2p(const double* u, float* w, const Bg& bg, Counters cn) {
   double rho = u[0];
-  if (!(rho == rho) || !(u[4] == u[4])) count(cn.nonfinite);
-  if (!(rho >= AK_RHO_FLOOR)) {
+  if (not_finite(rho) || not_finite(u[4])) count(cn.nonfinite);
+  if (!at_least(rho, AK_RHO_FLOOR)) {
     rho = AK_RHO_FLOOR;
     count(cn.floors);
   }
-  const double r = 1.0 / rho;
-  double ug = u[4] - 0.5 * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) * r;
-  if (!(ug >= AK_UG_FLOOR)) {
-    ug = AK_UG_FLOOR;
+  const float rf = rcp_approx_f32(f64_to_f32(rho));
+  double r = f32_to_f64(rf);
+  r = fma(r, fma(-rho, r, 1.0), r);
+  const double rh = __hiloint2double(__double2hiint(r) - 0x00100000, __double2loint(r));  // r/2
+  const double m2 = fma(u[1], u[1], fma(u[2], u[2], u[3] * u[3]));
+  double dug = fma(-m2, rh, u[4] - bg.ug);  // u_g - u_g,b
+  float dugf = f64_to_f32(dug);
+  if (!(dugf >= bg.ug_floor_f)) {           // u_g below its floor (FP32 resolution)
+    dugf = f64_to_f32(AK_UG_FLOOR - bg.ug);
     count(cn.floors);
   }
-  w[0] = (float)(rho - bg.rho);
-  w[1] = (float)(u[1] * r);
-  w[2] = (float)(u[2] * r);
-  w[3] = (float)(u[3] * r);
-  w[4] = (float)(ug - bg.ug);
+  w[0] = f64_to_f32(rho - bg.rho);
+  w[1] = f64_to_f32(u[1]) * rf;
+  w[2] = f64_to_f32(u[2]) * rf;
+  w[3] = f64_to_f32(u[3]) * rf;
+  w[4] = dugf;
 }
 
 __device__ __forceinline__ void riemann(const double* wl, const double* wr, const Bg& bg,
                                         double* f) {
-  hllc_fp64(wl, wr, bg.gamma, f);
+  hllc_fp64(wl, wr, bg, f);
 }
 __device__ __forceinline__ void riemann(const float* wl, const float* wr, const Bg& bg,
                                         float* f) {
   hllc_mixed(wl, wr, bg, f);
 }
 
-// Left/right states at the face between q[NG-1] and q[NG] of a stencil of 2*NG cells.
+// Lower and upper edge values of the middle cell of q[0 .. 2NG-2].
 template <int NG, typename R>
-__device__ __forceinline__ void face_states(const R* q, R& left, R& right) {
+__device__ __forceinline__ void edges(const R* q, R& lo, R& hi) {
   if constexpr (NG == 2) {
-    left = q[1] + R(0.5) * plm_slope(q[0], q[1], q[2]);
-    right = q[2] - R(0.5) * plm_slope(q[1], q[2], q[3]);
+    const R h = R(0.5) * plm_slope(q[0], q[1], q[2]);
+    lo = q[1] - h;
+    hi = q[1] + h;
   } else {
-    R lo, hi, lo2, hi2;
     ppm_edges(q[0], q[1], q[2], q[3], q[4], lo, hi);
-    ppm_edges(q[1], q[2], q[3], q[4], q[5], lo2, hi2);
-    left = hi;
-    right = lo2;
   }
 }
 
-// Solves one face of direction d.  `cellv(v, m)` returns variable v of the m-th cell
-// of the stencil (m = 0 .. 2NG-1; the face lies between m = NG-1 and m = NG).
-template <int NG, typename R, typename Get>
-__device__ __forceinline__ void solve_face(int d, const Bg& bg, Get cellv, R* f) {
+// HLLC on one face of direction d from edge values in natural variable order; the
+// flux comes back in natural order (rho, M1, M2, M3, E).
+template <typename R>
+__device__ __forceinline__ void solve(int d, const R* l, const R* r, const Bg& bg, R* f) {
   const int perm[5] = {0, 1 + d, 1 + (d + 1) % 3, 1 + (d + 2) % 3, 4};
-  R wl[5], wr[5];
+  R wl[5], wr[5], fn[5];
 #pragma unroll
   for (int n = 0; n < 5; ++n) {
-    R q[2 * NG];
-#pragma unroll
-    for (int m = 0; m < 2 * NG; ++m) q[m] = cellv(perm[n], m);
-    face_states<NG>(q, wl[n], wr[n]);
+    wl[n] = l[perm[n]];
+    wr[n] = r[perm[n]];
   }
-  R fn[5];
   riemann(wl, wr, bg, fn);
 #pragma unroll
   for (int n = 0; n < 5; ++n) f[perm[n]] = fn[n];
 }
 
+// 0.5 * x for a finite double, on the integer pipe (the multiply for zero and
+// numbers near the subnormal range)
+__device__ __forceinline__ double half(double x) {
+  const int hi = __double2hiint(x);
+  if ((hi & 0x7fe00000) == 0) return 0.5 * x;
+  if ((hi & 0x7ff00000) == 0x7ff00000) return x;  // inf, NaN
+  return __hiloint2double(hi - 0x00100000, __double2loint(x));
+}
+
 template <int NG, bool MIXED, int TX, int TY>
-__global__ void __launch_bounds__(TX* TY)
-    stage_kernel(const double* __restrict__ uin, const double* u0, double* uout, ak_geom g,
-                 Bg bg, double a, double b, ak_dev_scalars* sc, int nseg, int last_stage) {
+struct StageSmem {
   using R = typename std::conditional<MIXED, float, double>::type;
+  static constexpr int WX = TX + 2 * NG, WY = TY + 2 * NG, NPL = WX * WY, NR = 2 * NG;
+  static constexpr int E1 = 5 * TY * (TX + 2);  // x1 edges of cells i0-1 .. i0+TX
+  static constexpr int E2 = 5 * (TY + 2) * TX;  // x2 edges of cells j0-1 .. j0+TY
+  static constexpr int F1 = 5 * TY * (TX + 1);
+  static constexpr int F2 = 5 * (TY + 1) * TX;
+  static constexpr size_t bytes = sizeof(R) * (size_t)(NR * 5 * NPL + 2 * E1 + 2 * E2 + F1 + F2);
+};
+
+template <int NG, bool MIXED, int TX, int TY>
+__global__ void __launch_bounds__(TX* TY, MIXED ? 2 : 1)
+    stage_kernel(const double* __restrict__ uin, const double* u0, double* uout, ak_geom g,
+                 Bg bg, double a, double b, int rk2_final, ak_dev_scalars* sc, int nseg,
+                 int last_stage) {
+  using S = StageSmem<NG, MIXED, TX, TY>;
+  using R = typename S::R;
   constexpr int NT = TX * TY;
-  constexpr int WX = TX + 2 * NG, WY = TY + 2 * NG, NPL = WX * WY;
-  constexpr int NR = 2 * NG;
+  constexpr int WX = S::WX, NPL = S::NPL, NR = S::NR;
+  constexpr int C1 = TX + 2;  // x1 edge row length
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* ring = reinterpret_cast<R*>(smem_raw);  // [NR][5][WY][WX]
-  R* f1 = ring + NR * 5 * NPL;               // [5][TY][TX+1]
-  R* f2 = f1 + 5 * TY * (TX + 1);            // [5][TY+1][TX]
+  R* e1lo = ring + NR * 5 * NPL;             // [5][TY][TX+2]
+  R* e1hi = e1lo + S::E1;
+  R* e2lo = e1hi + S::E1;                    // [5][TY+2][TX]
+  R* e2hi = e2lo + S::E2;
+  R* f1 = e2hi + S::E2;                      // [5][TY][TX+1]
+  R* f2 = f1 + S::F1;                        // [5][TY+1][TX]
   __shared__ double red[NT / 32];
 
   const int tid = threadIdx.x;
@@ -148,11 +189,10 @@ __global__ void __launch_bounds__(TX* TY)
   const double dt = sc->dt;
   const double idx1 = 1.0 / g.dx1, idx2 = 1.0 / g.dx2, idx3 = 1.0 / g.dx3;
 
-  auto plane_slot = [](int k) { return (k + 4 * NR) % NR; };
-  // Load plane kp (interior index, may be a ghost plane) of the halo'd tile, convert to
-  // primitives and store in its ring slot.
+  auto slot = [](int k) { return (k + 4 * NR) % NR; };
+  // plane kp (interior index; ghost planes allowed) of the halo'd tile -> primitives
   auto load_plane = [&](int kp) {
-    R* dst = ring + plane_slot(kp) * 5 * NPL;
+    R* dst = ring + slot(kp) * 5 * NPL;
     for (int c = tid; c < NPL; c += NT) {
       const int x = c % WX, y = c / WX;
       const int ip = i0 + x, jp = j0 + y;  // padded indices (halo starts at i0 - NG)
@@ -173,57 +213,105 @@ __global__ void __launch_bounds__(TX* TY)
   const int tx = tid % TX, ty = tid / TX;
   const int ci = i0 + tx, cj = j0 + ty;
   const bool own = (ci < g.nx1) && (cj < g.nx2);
-  const int oc = (ty + NG) * WX + (tx + NG);  // own cell inside a ring plane
+  const int oc = (ty + NG) * WX + (tx + NG);
 
-  // x3 face below plane k (between k-1 and k): stencil planes k-NG .. k+NG-1
-  auto x3_face = [&](int k, R* f) {
-    solve_face<NG, R>(2, bg,
-                      [&](int v, int m) {
-                        return ring[plane_slot(k - NG + m) * 5 * NPL + v * NPL + oc];
-                      },
-                      f);
+  // x3 edges of the own column's cell kc (stencil planes kc-NG+1 .. kc+NG-1)
+  auto x3_edges = [&](int kc, R* lo, R* hi) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      R q[2 * NG - 1];
+#pragma unroll
+      for (int m = 0; m < 2 * NG - 1; ++m) q[m] = ring[slot(kc - NG + 1 + m) * 5 * NPL + v * NPL + oc];
+      edges<NG>(q, lo[v], hi[v]);
+    }
   };
 
-  // prologue: planes k0-NG .. k0+NG-1, and the flux through the face below k0
   for (int kp = k0 - NG; kp < k0 + NG; ++kp) load_plane(kp);
   __syncthreads();
-  R f3m[5], f3p[5];
-  if (own) x3_face(k0, f3m);
+  R hi3[5], f3m[5], f3p[5];
+  if (own) {
+    R lo_a[5], hi_a[5], lo_b[5];
+    x3_edges(k0 - 1, lo_a, hi_a);
+    x3_edges(k0, lo_b, hi3);
+    solve(2, hi_a, lo_b, bg, f3m);
+  }
 
-  double dtmin = __longlong_as_double(0x7ff0000000000000ll);  // +inf
+  float dtmin_f = __int_as_float(0x7f800000);
+  double dtmin = __longlong_as_double(0x7ff0000000000000ll);
   for (int k = k0; k < k1; ++k) {
-    // the ring now holds planes k-NG .. k+NG-1; bring in k+NG (replaces k-NG)
     __syncthreads();
     load_plane(k + NG);
     __syncthreads();
-    const R* pl = ring + plane_slot(k) * 5 * NPL;
-    // x1 faces of plane k: (TX+1) x TY
-    for (int f = tid; f < (TX + 1) * TY; f += NT) {
-      const int fx = f % (TX + 1), fy = f / (TX + 1);
-      if (i0 + fx <= g.nx1 && j0 + fy < g.nx2) {
-        R fl[5];
-        const int base = (fy + NG) * WX + fx;  // stencil cell m at x = fx + m
-        solve_face<NG, R>(0, bg, [&](int v, int m) { return pl[v * NPL + base + m]; }, fl);
+    const R* pl = ring + slot(k) * 5 * NPL;
+
+    // ---- A: reconstruction -----------------------------------------------------
+    for (int it = tid; it < S::E1 / 5; it += NT) {  // x1 edges, cells i0-1 .. i0+TX
+      const int c = it % C1, r = it / C1;
+      if (i0 - 1 + c <= g.nx1 && j0 + r < g.nx2) {
+        const int base = (r + NG) * WX + c;  // stencil start: x = c .. c + 2NG - 2
 #pragma unroll
-        for (int v = 0; v < 5; ++v) f1[(v * TY + fy) * (TX + 1) + fx] = fl[v];
+        for (int v = 0; v < 5; ++v) {
+          R q[2 * NG - 1];
+#pragma unroll
+          for (int m = 0; m < 2 * NG - 1; ++m) q[m] = pl[v * NPL + base + m];
+          edges<NG>(q, e1lo[(v * TY + r) * C1 + c], e1hi[(v * TY + r) * C1 + c]);
+        }
       }
     }
-    // x2 faces of plane k: TX x (TY+1)
-    for (int f = tid; f < TX * (TY + 1); f += NT) {
-      const int fx = f % TX, fy = f / TX;
-      if (i0 + fx < g.nx1 && j0 + fy <= g.nx2) {
-        R fl[5];
-        const int base = fy * WX + fx + NG;  // stencil cell m at y = fy + m
-        solve_face<NG, R>(1, bg, [&](int v, int m) { return pl[v * NPL + base + m * WX]; },
-                          fl);
+    for (int it = tid; it < S::E2 / 5; it += NT) {  // x2 edges, cells j0-1 .. j0+TY
+      const int c = it % TX, r = it / TX;
+      if (i0 + c < g.nx1 && j0 - 1 + r <= g.nx2) {
+        const int base = r * WX + c + NG;  // stencil start (y = r), x = c + NG
 #pragma unroll
-        for (int v = 0; v < 5; ++v) f2[(v * (TY + 1) + fy) * TX + fx] = fl[v];
+        for (int v = 0; v < 5; ++v) {
+          R q[2 * NG - 1];
+#pragma unroll
+          for (int m = 0; m < 2 * NG - 1; ++m) q[m] = pl[v * NPL + base + m * WX];
+          edges<NG>(q, e2lo[(v * (TY + 2) + r) * TX + c], e2hi[(v * (TY + 2) + r) * TX + c]);
+        }
       }
     }
-    // x3 face above plane k
-    if (own) x3_face(k + 1, f3p);
+    R lo3[5], hi3n[5];
+    if (own) x3_edges(k + 1, lo3, hi3n);
     __syncthreads();
 
+    // ---- B: Riemann problems -----------------------------------------------------
+    for (int it = tid; it < S::F1 / 5; it += NT) {
+      const int fx = it % (TX + 1), fy = it / (TX + 1);
+      if (i0 + fx <= g.nx1 && j0 + fy < g.nx2) {
+        R l[5], r[5], f[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          l[v] = e1hi[(v * TY + fy) * C1 + fx];       // cell i-1: column fx
+          r[v] = e1lo[(v * TY + fy) * C1 + fx + 1];   // cell i:   column fx+1
+        }
+        solve(0, l, r, bg, f);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) f1[(v * TY + fy) * (TX + 1) + fx] = f[v];
+      }
+    }
+    for (int it = tid; it < S::F2 / 5; it += NT) {
+      const int fx = it % TX, fy = it / TX;
+      if (i0 + fx < g.nx1 && j0 + fy <= g.nx2) {
+        R l[5], r[5], f[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          l[v] = e2hi[(v * (TY + 2) + fy) * TX + fx];      // cell j-1: row fy
+          r[v] = e2lo[(v * (TY + 2) + fy + 1) * TX + fx];  // cell j:   row fy+1
+        }
+        solve(1, l, r, bg, f);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) f2[(v * (TY + 1) + fy) * TX + fx] = f[v];
+      }
+    }
+    if (own) {
+      solve(2, hi3, lo3, bg, f3p);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) hi3[v] = hi3n[v];
+    }
+    __syncthreads();
+
+    // ---- C: divergence and RK update -------------------------------------------
     if (own) {
       const long long e = boff + ((long long)(k + NG) * g.p2 + (cj + NG)) * g.p1 + (ci + NG);
       double un[5];
@@ -232,38 +320,61 @@ __global__ void __launch_bounds__(TX* TY)
         const R d1 = f1[(v * TY + ty) * (TX + 1) + tx + 1] - f1[(v * TY + ty) * (TX + 1) + tx];
         const R d2 = f2[(v * (TY + 1) + ty + 1) * TX + tx] - f2[(v * (TY + 1) + ty) * TX + tx];
         const R d3 = f3p[v] - f3m[v];
-        double L;
-        if constexpr (MIXED) {
-          L = (double)(-(d1 * (float)idx1 + d2 * (float)idx2 + d3 * (float)idx3));
-        } else {
-          L = -(d1 * idx1 + d2 * idx2 + d3 * idx3);
-        }
         const double ui = uin[e + v * g.var_stride];
-        double r = ui + dt * L;
-        if (a != 0.0) r = a * u0[e + v * g.var_stride] + b * r;
+        double r;
+        if constexpr (MIXED) {
+          const float L = -fmaf(d1, (float)idx1, fmaf(d2, (float)idx2, d3 * (float)idx3));
+          const double Ld = f32_to_f64(L);
+          if (rk2_final)
+            r = half(u0[e + v * g.var_stride] + fma(dt, Ld, ui));
+          else if (a == 0.0)
+            r = fma(dt, Ld, ui);
+          else
+            r = fma(b, fma(dt, Ld, ui), a * u0[e + v * g.var_stride]);
+        } else {
+          const double L = -fma(d1, idx1, fma(d2, idx2, d3 * idx3));
+          r = fma(dt, L, ui);
+          if (a != 0.0) r = a * u0[e + v * g.var_stride] + b * r;
+        }
         un[v] = r;
         uout[e + v * g.var_stride] = r;
         f3m[v] = f3p[v];
       }
       if (last_stage) {
-        // CFL ratio of the new state (Eq. (3)); floors applied silently here
-        double rho = un[0];
-        rho = rho >= AK_RHO_FLOOR ? rho : AK_RHO_FLOOR;
-        const double v1 = un[1] / rho, v2 = un[2] / rho, v3 = un[3] / rho;
-        double ug = un[4] - 0.5 * (un[1] * un[1] + un[2] * un[2] + un[3] * un[3]) / rho;
-        ug = ug >= AK_UG_FLOOR ? ug : AK_UG_FLOOR;
-        const double cs = sqrt(g.gamma * (g.gamma - 1.0) * ug / rho);
-        double t = g.dx1 / (fabs(v1) + cs);
-        t = fmin(t, g.dx2 / (fabs(v2) + cs));
-        t = fmin(t, g.dx3 / (fabs(v3) + cs));
-        dtmin = fmin(dtmin, t);
+        if constexpr (MIXED) {
+          // CFL ratio in FP32: it only sets the next step's dt
+          const float rho = fmaxf(f64_to_f32(un[0]), (float)AK_RHO_FLOOR);
+          const float ir = rcp_approx_f32(rho);
+          const float m1 = f64_to_f32(un[1]), m2 = f64_to_f32(un[2]), m3 = f64_to_f32(un[3]);
+          const float ug = fmaxf(fmaf(-0.5f * ir, fmaf(m1, m1, fmaf(m2, m2, m3 * m3)),
+                                      f64_to_f32(un[4])), (float)AK_UG_FLOOR);
+          const float cs = sqrt_fast(bg.gamma_f * (bg.gamma_f - 1.0f) * ug * ir);
+          float lam = (fabsf(m1) * ir + cs) * (float)idx1;
+          lam = fmaxf(lam, (fabsf(m2) * ir + cs) * (float)idx2);
+          lam = fmaxf(lam, (fabsf(m3) * ir + cs) * (float)idx3);
+          dtmin_f = fminf(dtmin_f, rcp_approx_f32(lam));
+        } else {
+          // CFL ratio in FP64 (the FP64 form reproduces the oracle's dt)
+          double rho = un[0];
+          rho = at_least(rho, AK_RHO_FLOOR) ? rho : AK_RHO_FLOOR;
+          const double r = rcp64(rho);
+          const double v1 = un[1] * r, v2 = un[2] * r, v3 = un[3] * r;
+          double ug = fma(-0.5, fma(un[1], v1, fma(un[2], v2, un[3] * v3)), un[4]);
+          ug = at_least(ug, AK_UG_FLOOR) ? ug : AK_UG_FLOOR;
+          const double cs = sqrt(g.gamma * (g.gamma - 1.0) * ug * r);
+          double t = g.dx1 / (fabs(v1) + cs);
+          t = fmin(t, g.dx2 / (fabs(v2) + cs));
+          t = fmin(t, g.dx3 / (fabs(v3) + cs));
+          dtmin = fmin(dtmin, t);
+        }
       }
     }
   }
 
   if (last_stage) {
-    // CTA min of the CFL ratio -> one atomic per CTA (positive doubles order as their
-    // bit patterns)
+    if constexpr (MIXED) dtmin = f32_to_f64(dtmin_f);
+    // CTA min of the CFL ratio -> one atomic per CTA (non-negative doubles order as
+    // their bit patterns)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) dtmin = fmin(dtmin, __shfl_xor_sync(0xffffffffu, dtmin, o));
     if ((tid & 31) == 0) red[tid >> 5] = dtmin;
@@ -280,10 +391,9 @@ __global__ void __launch_bounds__(TX* TY)
 
 template <int NG, bool MIXED, int TX, int TY>
 static cudaError_t launch(const ak_mesh* m, const double* uin, const double* u0, double* uout,
-                          double a, double b, int last_stage, bool prepare_only = false) {
-  using R = typename std::conditional<MIXED, float, double>::type;
-  constexpr int NPL = (TX + 2 * NG) * (TY + 2 * NG);
-  const size_t smem = sizeof(R) * (2 * NG * 5 * NPL + 5 * TY * (TX + 1) + 5 * (TY + 1) * TX);
+                          double a, double b, int rk2_final, int last_stage,
+                          bool prepare_only = false) {
+  const size_t smem = StageSmem<NG, MIXED, TX, TY>::bytes;
   auto kern = stage_kernel<NG, MIXED, TX, TY>;
   if (prepare_only)
     return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -293,13 +403,33 @@ static cudaError_t launch(const ak_mesh* m, const double* uin, const double* u0,
   Bg bg;
   bg.gamma = g.gamma;
   bg.gamma_f = (float)g.gamma;
+  bg.gm1 = g.gamma - 1.0;
+  bg.kq = (g.gamma + 1.0) / (2.0 * g.gamma);
   bg.rho = m->desc.ref_rho;
   bg.ug = m->desc.ref_p / (g.gamma - 1.0);
   bg.rho_f = (float)bg.rho;
   bg.ug_f = (float)bg.ug;
-  kern<<<(unsigned)nblk, TX * TY, smem, m->stream>>>(uin, u0, uout, g, bg, a, b, m->d_sc,
-                                                      m->seg3, last_stage);
+  bg.ug_floor_f = (float)(AK_UG_FLOOR - bg.ug);
+  kern<<<(unsigned)nblk, TX * TY, smem, m->stream>>>(uin, u0, uout, g, bg, a, b, rk2_final,
+                                                      m->d_sc, m->seg3, last_stage);
   return cudaGetLastError();
+}
+
+template <int NG, bool MIXED>
+static cudaError_t launch_form(const ak_mesh* m, const double* uin, const double* u0,
+                               double* uout, double a, double b, int rk2_final, int last_stage,
+                               bool prepare_only) {
+  return launch<NG, MIXED, 16, 16>(m, uin, u0, uout, a, b, rk2_final, last_stage, prepare_only);
+}
+
+static cudaError_t dispatch(const ak_mesh* m, const double* uin, const double* u0, double* uout,
+                            double a, double b, int rk2_final, int last_stage, bool prepare) {
+  const bool mixed = m->desc.precision == AK_MIXED;
+  if (m->desc.recon == AK_PLM)
+    return mixed ? launch_form<2, true>(m, uin, u0, uout, a, b, rk2_final, last_stage, prepare)
+                 : launch_form<2, false>(m, uin, u0, uout, a, b, rk2_final, last_stage, prepare);
+  return mixed ? launch_form<3, true>(m, uin, u0, uout, a, b, rk2_final, last_stage, prepare)
+               : launch_form<3, false>(m, uin, u0, uout, a, b, rk2_final, last_stage, prepare);
 }
 
 }  // namespace ak
@@ -311,22 +441,12 @@ cudaError_t ak_launch_stage(const ak_mesh* m, int stage, const double* u_in, con
   const bool rk3 = m->desc.rk == 3;
   const double a = rk3 ? a3[stage - 1] : a2[stage - 1];
   const double b = rk3 ? b3[stage - 1] : b2[stage - 1];
-  const bool mixed = m->desc.precision == AK_MIXED;
-  if (m->desc.recon == AK_PLM) {
-    return mixed ? ak::launch<2, true, 16, 16>(m, u_in, u0, u_out, a, b, last_stage)
-                 : ak::launch<2, false, 16, 16>(m, u_in, u0, u_out, a, b, last_stage);
-  }
-  return mixed ? ak::launch<3, true, 16, 16>(m, u_in, u0, u_out, a, b, last_stage)
-               : ak::launch<3, false, 16, 16>(m, u_in, u0, u_out, a, b, last_stage);
+  const int rk2_final = (!rk3 && stage == 2) ? 1 : 0;
+  return ak::dispatch(m, u_in, u0, u_out, a, b, rk2_final, last_stage, false);
 }
 
 // Raises the dynamic shared-memory limit of the stage kernel this mesh uses (called once
 // at mesh creation, outside any stream capture).
 cudaError_t ak_stage_prepare(const ak_mesh* m) {
-  const bool mixed = m->desc.precision == AK_MIXED;
-  if (m->desc.recon == AK_PLM)
-    return mixed ? ak::launch<2, true, 16, 16>(m, 0, 0, 0, 0, 0, 0, true)
-                 : ak::launch<2, false, 16, 16>(m, 0, 0, 0, 0, 0, 0, true);
-  return mixed ? ak::launch<3, true, 16, 16>(m, 0, 0, 0, 0, 0, 0, true)
-               : ak::launch<3, false, 16, 16>(m, 0, 0, 0, 0, 0, 0, true);
+  return ak::dispatch(m, nullptr, nullptr, nullptr, 0.0, 0.0, 0, 0, true);
 }

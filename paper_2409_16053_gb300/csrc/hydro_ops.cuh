@@ -18,6 +18,8 @@
 
 #include <cuda_runtime.h>
 
+#include "fastmath.cuh"
+
 namespace ak {
 
 // Background state of the mixed form and EOS constants, passed by value.
@@ -26,18 +28,33 @@ struct Bg {
   float rho_f, ug_f;     // the same, rounded
   double gamma;
   float gamma_f;
+  double kq;             // (gamma + 1) / (2 gamma), for the shock speed factor
+  double gm1;            // gamma - 1
+  float ug_floor_f;      // u_g floor minus u_g,b, rounded (mixed form)
 };
 
 // ------------------------------------------------------------------------------
 // Reconstruction (Section 3: on primitive variables).
 // ------------------------------------------------------------------------------
-template <typename R>
-__device__ __forceinline__ R plm_slope(R qm, R q0, R qp) {
-  // van Leer harmonic mean of the one-sided differences; zero at extrema
-  R dl = q0 - qm;
-  R dr = qp - q0;
-  R prod = dl * dr;
-  return prod > R(0) ? R(2) * prod / (dl + dr) : R(0);
+// van Leer harmonic mean of the one-sided differences; zero at extrema.
+// FP64: the harmonic mean with a Newton-refined reciprocal (no IEEE division)
+__device__ __forceinline__ double plm_slope(double qm, double q0, double qp) {
+  const double dl = q0 - qm;
+  const double dr = qp - q0;
+  const double prod = dl * dr;
+  return prod > 0.0 ? (prod + prod) * rcp64(dl + dr) : 0.0;
+}
+
+// FP32: the harmonic mean with the hardware reciprocal refined once in FP32
+__device__ __forceinline__ float plm_slope(float qm, float q0, float qp) {
+  const float dl = q0 - qm;
+  const float dr = qp - q0;
+  const float prod = dl * dr;
+  if (!(prod > 0.0f)) return 0.0f;
+  const float s = dl + dr;
+  float r = rcp_approx_f32(s);
+  r = fmaf(r, fmaf(-s, r, 1.0f), r);
+  return (prod + prod) * r;
 }
 
 template <typename R>
@@ -62,8 +79,9 @@ __device__ __forceinline__ void ppm_edges(R q0, R q1, R q2, R q3, R q4, R& lo, R
   R sm = ppm_slope(q0, q1, q2);
   R sc = ppm_slope(q1, q2, q3);
   R sp = ppm_slope(q2, q3, q4);
-  R a_lo = R(0.5) * (q1 + q2) - (sc - sm) / R(6);
-  R a_hi = R(0.5) * (q2 + q3) - (sp - sc) / R(6);
+  const R sixth = R(1) / R(6);
+  R a_lo = R(0.5) * (q1 + q2) - (sc - sm) * sixth;
+  R a_hi = R(0.5) * (q2 + q3) - (sp - sc) * sixth;
   R a = q2;
   if ((a_hi - a) * (a - a_lo) <= R(0)) {
     a_lo = a;
@@ -85,45 +103,31 @@ __device__ __forceinline__ void ppm_edges(R q0, R q1, R q2, R q3, R q4, R& lo, R
 // HLLC, FP64 form.  w = (rho, u_n, u_t1, u_t2, u_g); f = flux of
 // (rho, M_n, M_t1, M_t2, E).
 // ------------------------------------------------------------------------------
-__device__ __forceinline__ void hllc_fp64(const double* wl, const double* wr, double gamma,
+__device__ __forceinline__ void hllc_fp64(const double* wl, const double* wr, const Bg& bg,
                                           double* f) {
-  const double gm1 = gamma - 1.0;
+  const double gamma = bg.gamma;
+  const double gm1 = bg.gm1;
   const double rl = wl[0], ul = wl[1], rr = wr[0], ur = wr[1];
   const double pl = gm1 * wl[4];
   const double pr = gm1 * wr[4];
-  const double el = wl[4] + 0.5 * rl * (ul * ul + wl[2] * wl[2] + wl[3] * wl[3]);
-  const double er = wr[4] + 0.5 * rr * (ur * ur + wr[2] * wr[2] + wr[3] * wr[3]);
-  const double cl = sqrt(gamma * pl / rl);
-  const double cr = sqrt(gamma * pr / rr);
+  const double el = fma(0.5 * rl, ul * ul + wl[2] * wl[2] + wl[3] * wl[3], wl[4]);
+  const double er = fma(0.5 * rr, ur * ur + wr[2] * wr[2] + wr[3] * wr[3], wr[4]);
+  const double irl = rcp64(rl), irr = rcp64(rr);
+  const double cl = sqrt64(gamma * pl * irl);
+  const double cr = sqrt64(gamma * pr * irr);
 
   // pressure estimate of the linearised (PVRS) solver, then shock-aware speeds
   double ps = 0.5 * (pl + pr) - 0.125 * (ur - ul) * (rl + rr) * (cl + cr);
   ps = ps > 0.0 ? ps : 0.0;
-  const double kq = (gamma + 1.0) / (2.0 * gamma);
+  const double kq = bg.kq;
   double ql = 1.0, qr = 1.0;
-  if (ps > pl) ql = sqrt(1.0 + kq * (ps / pl - 1.0));
-  if (ps > pr) qr = sqrt(1.0 + kq * (ps / pr - 1.0));
+  if (ps > pl) ql = sqrt64(fma(kq * (ps - pl), rcp64(pl), 1.0));
+  if (ps > pr) qr = sqrt64(fma(kq * (ps - pr), rcp64(pr), 1.0));
   double sl = ul - cl * ql;
   double sr = ur + cr * qr;
   sl = (ur - cr < sl) ? ur - cr : sl;
   sr = (ul + cl > sr) ? ul + cl : sr;
 
-  const double ml = rl * (sl - ul);  // mass flux through the left wave (frame of S_L)
-  const double mr = rr * (sr - ur);
-  const double sstar = (pr - pl + ul * ml - ur * mr) / (ml - mr);
-
-  const bool left = sstar >= 0.0;
-  const double* w = left ? wl : wr;
-  const double rk = w[0], uk = w[1];
-  const double pk = left ? pl : pr;
-  const double ek = left ? el : er;
-  const double mn = rk * uk;
-  double fk[5];
-  fk[0] = mn;
-  fk[1] = mn * uk + pk;
-  fk[2] = mn * w[2];
-  fk[3] = mn * w[3];
-  fk[4] = (ek + pk) * uk;
   if (sl >= 0.0 || sr <= 0.0) {
     // supersonic: the upwind physical flux (S_L >= 0 takes the left state)
     const bool up_left = sl >= 0.0;
@@ -132,25 +136,32 @@ __device__ __forceinline__ void hllc_fp64(const double* wl, const double* wr, do
     const double eu = up_left ? el : er;
     const double mu = wu[0] * wu[1];
     f[0] = mu;
-    f[1] = mu * wu[1] + pu;
+    f[1] = fma(mu, wu[1], pu);
     f[2] = mu * wu[2];
     f[3] = mu * wu[3];
     f[4] = (eu + pu) * wu[1];
     return;
   }
+  const double ml = rl * (sl - ul);  // mass flux through the left wave (frame of S_L)
+  const double mr = rr * (sr - ur);
+  const double sstar = (pr - pl + ul * ml - ur * mr) * rcp64(ml - mr);
+
+  const bool left = sstar >= 0.0;
+  const double* w = left ? wl : wr;
+  const double rk = w[0], uk = w[1];
+  const double pk = left ? pl : pr;
+  const double ek = left ? el : er;
+  const double irk = left ? irl : irr;
+  const double mk = left ? ml : mr;  // rho_K (S_K - u_K)
   const double s = left ? sl : sr;
-  const double fac = rk * (s - uk) / (s - sstar);
-  double us[5];
-  us[0] = fac;
-  us[1] = fac * sstar;
-  us[2] = fac * w[2];
-  us[3] = fac * w[3];
-  us[4] = fac * (ek / rk + (sstar - uk) * (sstar + pk / (rk * (s - uk))));
-  f[0] = fk[0] + s * (us[0] - rk);
-  f[1] = fk[1] + s * (us[1] - mn);
-  f[2] = fk[2] + s * (us[2] - rk * w[2]);
-  f[3] = fk[3] + s * (us[3] - rk * w[3]);
-  f[4] = fk[4] + s * (us[4] - ek);
+  const double mn = rk * uk;
+  const double fac = mk * rcp64(s - sstar);
+  const double us4 = fac * fma(sstar - uk, fma(pk, rcp64(mk), sstar), ek * irk);
+  f[0] = mn + s * (fac - rk);
+  f[1] = fma(mn, uk, pk) + s * (fac * sstar - mn);
+  f[2] = mn * w[2] + s * (fac - rk) * w[2];
+  f[3] = mn * w[3] + s * (fac - rk) * w[3];
+  f[4] = (ek + pk) * uk + s * (us4 - ek);
 }
 
 // ------------------------------------------------------------------------------
@@ -158,10 +169,13 @@ __device__ __forceinline__ void hllc_fp64(const double* wl, const double* wr, do
 // Returns F - (0, p_b, 0, 0, 0).  Every difference of two O(1) quantities is formed
 // from the deviations, so that a perturbation of relative size 1e-6 keeps ~7 digits.
 // ------------------------------------------------------------------------------
+__device__ __forceinline__ float sqrt_fast(float x) { return x * rsqrt_approx_f32(x); }
+
 __device__ __forceinline__ void hllc_mixed(const float* wl, const float* wr, const Bg& bg,
                                            float* f) {
   const float g = bg.gamma_f;
   const float gm1 = g - 1.0f;
+  const float gg = g * rcp_approx_f32(gm1);             // gamma / (gamma - 1)
   const float rl = bg.rho_f + wl[0], rr = bg.rho_f + wr[0];
   const float ul = wl[1], ur = wr[1];
   const float dpl = gm1 * wl[4], dpr = gm1 * wr[4];     // p - p_b
@@ -169,26 +183,23 @@ __device__ __forceinline__ void hllc_mixed(const float* wl, const float* wr, con
   const float pl = pb + dpl, pr = pb + dpr;             // full pressures
   const float kel = 0.5f * rl * (ul * ul + wl[2] * wl[2] + wl[3] * wl[3]);
   const float ker = 0.5f * rr * (ur * ur + wr[2] * wr[2] + wr[3] * wr[3]);
-  const float hl = kel + g / gm1 * pl;                  // E + p
-  const float hr = ker + g / gm1 * pr;
-  const float cl = sqrtf(g * pl / rl);
-  const float cr = sqrtf(g * pr / rr);
+  const float hl = fmaf(gg, pl, kel);                   // E + p
+  const float hr = fmaf(gg, pr, ker);
+  const float irl = rcp_approx_f32(rl), irr = rcp_approx_f32(rr);
+  const float cl = sqrt_fast(g * pl * irl);
+  const float cr = sqrt_fast(g * pr * irr);
 
   // PVRS estimate as a deviation from p_b; p* = max(0, p_b + dps)
   float dps = 0.5f * (dpl + dpr) - 0.125f * (ur - ul) * (rl + rr) * (cl + cr);
   dps = (pb + dps > 0.0f) ? dps : -pb;
-  const float kq = (g + 1.0f) / (2.0f * g);
+  const float kq = (g + 1.0f) * rcp_approx_f32(2.0f * g);
   float ql = 1.0f, qr = 1.0f;
-  if (dps > dpl) ql = sqrtf(1.0f + kq * (dps - dpl) / pl);
-  if (dps > dpr) qr = sqrtf(1.0f + kq * (dps - dpr) / pr);
+  if (dps > dpl) ql = sqrt_fast(fmaf(kq * (dps - dpl), rcp_approx_f32(pl), 1.0f));
+  if (dps > dpr) qr = sqrt_fast(fmaf(kq * (dps - dpr), rcp_approx_f32(pr), 1.0f));
   float sl = ul - cl * ql;
   float sr = ur + cr * qr;
   sl = (ur - cr < sl) ? ur - cr : sl;
   sr = (ul + cl > sr) ? ul + cl : sr;
-
-  const float ml = rl * (sl - ul);
-  const float mr = rr * (sr - ur);
-  const float sstar = (dpr - dpl + ul * ml - ur * mr) / (ml - mr);
 
   if (sl >= 0.0f || sr <= 0.0f) {
     const bool up_left = sl >= 0.0f;
@@ -196,30 +207,35 @@ __device__ __forceinline__ void hllc_mixed(const float* wl, const float* wr, con
     const float ru = up_left ? rl : rr;
     const float mu = ru * wu[1];
     f[0] = mu;
-    f[1] = mu * wu[1] + (up_left ? dpl : dpr);
+    f[1] = fmaf(mu, wu[1], up_left ? dpl : dpr);
     f[2] = mu * wu[2];
     f[3] = mu * wu[3];
     f[4] = (up_left ? hl : hr) * wu[1];
     return;
   }
+  const float ml = rl * (sl - ul);
+  const float mr = rr * (sr - ur);
+  const float sstar = (dpr - dpl + ul * ml - ur * mr) * rcp_approx_f32(ml - mr);
   const bool left = sstar >= 0.0f;
   const float* w = left ? wl : wr;
   const float rk = left ? rl : rr;
+  const float irk = left ? irl : irr;
+  const float mk = left ? ml : mr;                      // rho_K (S_K - u_K)
   const float uk = w[1];
   const float s = left ? sl : sr;
   const float pk = left ? pl : pr;
   const float ek = (left ? kel : ker) + (bg.ug_f + w[4]);
   const float mn = rk * uk;
-  const float inv = 1.0f / (s - sstar);
-  const float fac = rk * (s - uk) * inv;
+  const float inv = rcp_approx_f32(s - sstar);
+  const float fac = mk * inv;
   const float drho = rk * (sstar - uk) * inv;           // U*_rho - rho_K
   const float dmn = fac * sstar - mn;                   // U*_Mn - M_n
-  const float de = drho / rk * ek + fac * (sstar - uk) * (sstar + pk / (rk * (s - uk)));
-  f[0] = mn + s * drho;
-  f[1] = mn * uk + (left ? dpl : dpr) + s * dmn;
-  f[2] = mn * w[2] + s * drho * w[2];
-  f[3] = mn * w[3] + s * drho * w[3];
-  f[4] = (left ? hl : hr) * uk + s * de;
+  const float de = fmaf(drho * irk, ek, fac * (sstar - uk) * fmaf(pk, rcp_approx_f32(mk), sstar));
+  f[0] = fmaf(s, drho, mn);
+  f[1] = fmaf(mn, uk, left ? dpl : dpr) + s * dmn;
+  f[2] = (mn + s * drho) * w[2];
+  f[3] = (mn + s * drho) * w[3];
+  f[4] = fmaf(s, de, (left ? hl : hr) * uk);
 }
 
 }  // namespace ak

@@ -1,0 +1,34 @@
+// Test helper: evaluates the library's integer-pipe conversions and Newton-refined
+// reciprocal / rsqrt / sqrt next to CUDA's IEEE operations on the same inputs.
+#include <cuda_runtime.h>
+
+#include "../paper_2409_16053_gb300/csrc/fastmath.cuh"
+
+__global__ void fastmath_kernel(const double* x, int n, double* out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = x[i];
+  double* o = out + 9 * (long long)i;
+  o[0] = ak::rcp64(v);
+  o[1] = 1.0 / v;
+  o[2] = ak::rsqrt64(fabs(v));
+  o[3] = 1.0 / sqrt(fabs(v));
+  o[4] = ak::sqrt64(fabs(v));
+  o[5] = sqrt(fabs(v));
+  o[6] = (double)ak::f64_to_f32(v);
+  o[7] = (double)__double2float_rn(v);
+  const float f = __double2float_rn(v);
+  o[8] = ak::f32_to_f64(f) - (double)f;  // exact conversion: 0
+}
+
+extern "C" int fastmath_eval(const double* host_x, int n, double* host_out) {
+  double *dx = nullptr, *dout = nullptr;
+  if (cudaMalloc(&dx, sizeof(double) * n) != cudaSuccess) return 1;
+  if (cudaMalloc(&dout, sizeof(double) * 9 * (size_t)n) != cudaSuccess) return 2;
+  cudaMemcpy(dx, host_x, sizeof(double) * n, cudaMemcpyHostToDevice);
+  fastmath_kernel<<<(n + 255) / 256, 256>>>(dx, n, dout);
+  cudaError_t e = cudaMemcpy(host_out, dout, sizeof(double) * 9 * (size_t)n, cudaMemcpyDeviceToHost);
+  cudaFree(dx);
+  cudaFree(dout);
+  return e == cudaSuccess ? 0 : 3;
+}

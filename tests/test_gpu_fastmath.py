@@ -1,0 +1,52 @@
+"""The library's hand-written FP64 reciprocal, rsqrt and sqrt (FP32 hardware seed +
+one Newton-Raphson step) and its integer-pipe f64<->f32 conversions, checked against
+CUDA's IEEE operations on the GPU over the full exponent range used by the scheme."""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def lib(tmp_path_factory):
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_2409_16053_gb300 import build
+    so = str(tmp_path_factory.mktemp("fm") / "fastmath_check.so")
+    subprocess.run([build.nvcc(), "-gencode", "arch=compute_103a,code=sm_103a", "-O3",
+                    "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
+                    os.path.join(HERE, "fastmath_check.cu"), "-o", so], check=True)
+    L = ctypes.CDLL(so)
+    L.fastmath_eval.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+    return L
+
+
+def test_fastmath_against_ieee(lib):
+    rng = np.random.default_rng(0)
+    x = np.concatenate([
+        rng.uniform(1.0, 2.0, 20000),
+        10.0 ** rng.uniform(-300, 300, 20000) * rng.choice([-1, 1], 20000),
+        10.0 ** rng.uniform(-30, 30, 20000),
+        np.array([1.0, 2.0, 0.5, 3.0, 1e-12, 1e12, 1.0 - 2 ** -52, 1.0 + 2 ** -52]),
+    ]).astype(np.float64)
+    out = np.empty((x.size, 9))
+    assert lib.fastmath_eval(x.ctypes.data, x.size, out.ctypes.data) == 0
+    rel = lambda a, b: np.abs(a - b) / np.abs(b)
+    # one Newton step from a ~2^-22 seed: relative error below 2^-42
+    assert rel(out[:, 0], out[:, 1]).max() < 2.0 ** -42
+    assert rel(out[:, 2], out[:, 3]).max() < 2.0 ** -42
+    assert rel(out[:, 4], out[:, 5]).max() < 2.0 ** -42
+    # f64 -> f32 on the integer pipe: within one float ulp of round-to-nearest
+    inr = (np.abs(x) > 1.2e-38) & (np.abs(x) < 3.0e38)
+    assert (rel(out[inr, 6], out[inr, 7]) <= 2.0 ** -23).all()
+    assert not np.any(out[~inr & (np.abs(x) < 1e-38), 6])        # flush to zero
+    assert np.all(np.isnan(out[~inr & (np.abs(x) > 3.5e38), 6]))  # out of range -> NaN
+    # f32 -> f64 is exact
+    assert not np.any(out[inr, 8])

@@ -33,12 +33,15 @@
  *     host threads.
  *
  * Register layout (the library's choice, reported by ak_mesh_layout):
- *   register = blocks one after another; block b starts at element offset
- *   block_offset[b] (multiple of 32 elements); inside a block the layout is
+ *   register = blocks one after another; inside a block the layout is
  *   [var 0..4][k][j][i] with i fastest, each dimension padded by nghost ghost cells on
- *   both sides: extents (nx1+2g, nx2+2g, nx3+2g).  var = (rho, M1, M2, M3, E).
- *   The interior cell (i, j, k), 0 <= i < nx1, of block b, variable v is element
- *     block_offset[b] + ((v*(nx3+2g) + k+g)*(nx2+2g) + j+g)*(nx1+2g) + i+g.
+ *   both sides (extents nx1+2g, nx2+2g, nx3+2g), var = (rho, M1, M2, M3, E).  Rows are
+ *   stored with a pitch s1 = round_up(nx1 + 2g, 4) elements, and block b's first ghost
+ *   cell is at element block_offset[b] = b * S + f, with f = (4 - g % 4) % 4 and
+ *   S = round_up(f + 5 * s1 * (nx2+2g) * (nx3+2g), 32): every row's interior then starts
+ *   on a 32-byte boundary.  The interior cell (i, j, k), 0 <= i < nx1, of block b,
+ *   variable v is element
+ *     block_offset[b] + ((v*(nx3+2g) + k+g)*(nx2+2g) + j+g)*s1 + i+g.
  */
 #ifndef AK_H
 #define AK_H
@@ -100,10 +103,12 @@ ak_status ak_mesh_create(const ak_mesh_desc* desc, void* cuda_stream, ak_mesh** 
 void ak_mesh_destroy(ak_mesh* mesh);
 
 /* Number of registers the configured integrator needs (2 for RK2, 3 for RK3), bytes of
- * one register, and (if block_offset != NULL) the element offset of every block
- * (nblocks entries).  Register 0 holds U^n before ak_step and U^{n+1} after it. */
+ * one register, (if block_offset != NULL) the element offset of every block's first
+ * ghost cell (nblocks entries), and (if strides != NULL) the element strides of
+ * (var, k, j, i) inside a block.  Any output pointer may be NULL.  Register 0 holds
+ * U^n before ak_step and U^{n+1} after it. */
 ak_status ak_mesh_layout(const ak_mesh* mesh, int32_t* nregisters, size_t* register_bytes,
-                         int64_t* block_offset);
+                         int64_t* block_offset, int64_t strides[4]);
 
 /* Borrows `dev_ptr` (device memory of register_bytes bytes, 256-byte aligned) as
  * register `reg` in [0, nregisters).  AK_EINVAL for a bad index, NULL or misaligned
@@ -166,11 +171,10 @@ ak_status ak_status_counters(ak_mesh* mesh, int64_t out[4]);
  * that must still report a time step when the device is out of memory.  It needs no
  * ak_mesh (creating one allocates): the caller passes the register and its geometry.
  *
- * reg       device pointer to one register in the layout ak_mesh_layout describes,
- *           for a mesh of `nblocks` equal blocks of nx[0] x nx[1] x nx[2] interior
- *           cells with `nghost` ghost cells per side (block b starts at element
- *           b * round_up(5 * (nx1+2g)(nx2+2g)(nx3+2g), 32)); only interior cells are
- *           read.  Not modified; the caller keeps ownership.
+ * reg       device pointer to one register in the layout described above (and by
+ *           ak_mesh_layout) for a mesh of `nblocks` equal blocks of
+ *           nx[0] x nx[1] x nx[2] interior cells with `nghost` ghost cells per side;
+ *           only interior cells are read.  Not modified; the caller keeps ownership.
  * dx        cell widths; gamma, cfl as in ak_mesh_desc.
  * dt_out    host pointer; receives cfl * min over interior cells and d of
  *           dx_d / (|v_d| + c_s), the same value ak_new_dt returns for that register.

@@ -61,7 +61,7 @@ def _load_lib():
     lib.ak_mesh_destroy.argtypes = [vp]
     lib.ak_mesh_destroy.restype = None
     lib.ak_mesh_layout.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_size_t),
-                                   ctypes.POINTER(ctypes.c_int64)]
+                                   ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
     lib.ak_mesh_bind.argtypes = [vp, i32, vp]
     lib.ak_fill_ghosts.argtypes = [vp, i32]
     lib.ak_stage.argtypes = [vp, i32, ctypes.c_double]
@@ -110,10 +110,13 @@ def ak_mesh_destroy(mesh) -> None:
 
 
 def ak_mesh_layout(mesh, nblocks: int):
+    """Returns (nregisters, register_bytes, block_offsets, strides(var, k, j, i))."""
     nreg, nbytes = ctypes.c_int32(), ctypes.c_size_t()
     offs = (ctypes.c_int64 * nblocks)()
-    _check(_lib.ak_mesh_layout(mesh, ctypes.byref(nreg), ctypes.byref(nbytes), offs))
-    return int(nreg.value), int(nbytes.value), np.array(offs[:], dtype=np.int64)
+    strides = (ctypes.c_int64 * 4)()
+    _check(_lib.ak_mesh_layout(mesh, ctypes.byref(nreg), ctypes.byref(nbytes), offs, strides))
+    return (int(nreg.value), int(nbytes.value), np.array(offs[:], dtype=np.int64),
+            tuple(int(v) for v in strides))
 
 
 def ak_mesh_bind(mesh, reg: int, dev_ptr: int) -> None:
@@ -213,7 +216,8 @@ class Mesh:
         d.ref_rho, d.ref_p = float(ref_rho), float(ref_p)
         self.desc = d
         self.handle = ak_mesh_create(d, self.stream.cuda_stream)
-        self.nreg, self.reg_bytes, self.offsets = ak_mesh_layout(self.handle, self.nblocks)
+        self.nreg, self.reg_bytes, self.offsets, self.strides = ak_mesh_layout(self.handle,
+                                                                               self.nblocks)
         self.regs = [torch.empty(self.reg_bytes // 8, dtype=torch.float64, device=self.device)
                      for _ in range(self.nreg)]
         for r, t in enumerate(self.regs):
@@ -276,7 +280,8 @@ class Mesh:
     def register_view(self, reg=0):
         """Torch view (nblocks, 5, p3, p2, p1) of a register, ghosts included."""
         p = [n + 2 * self.ng for n in self.block_nx]
-        stride = int(self.offsets[1] - self.offsets[0]) if self.nblocks > 1 else 5 * p[0] * p[1] * p[2]
+        bstride = int(self.offsets[1] - self.offsets[0]) if self.nblocks > 1 else 0
+        sv, sk, sj, si = self.strides
         t = self.regs[reg]
-        return t.as_strided((self.nblocks, 5, p[2], p[1], p[0]),
-                            (stride, p[0] * p[1] * p[2], p[0] * p[1], p[0], 1))
+        return t.as_strided((self.nblocks, 5, p[2], p[1], p[0]), (bstride, sv, sk, sj, si),
+                            int(self.offsets[0]))

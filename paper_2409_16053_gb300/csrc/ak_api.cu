@@ -6,6 +6,8 @@
 
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "ak_internal.cuh"
 
 static thread_local char g_err[512] = "";
@@ -82,8 +84,10 @@ extern "C" ak_status ak_mesh_create(const ak_mesh_desc* d, void* cuda_stream, ak
     loc[3 * b + 2] = bz;
   }
 
-  ak_mesh* m = (ak_mesh*)calloc(1, sizeof(ak_mesh));
+  // 64-byte alignment: the embedded tensor maps require it
+  ak_mesh* m = (ak_mesh*)aligned_alloc(64, (sizeof(ak_mesh) + 63) / 64 * 64);
   if (!m) return AK_ENOMEM;
+  memset(m, 0, sizeof(ak_mesh));
   m->desc = *d;
   m->stream = (cudaStream_t)cuda_stream;
   m->nreg = d->rk == 3 ? 3 : 2;
@@ -95,8 +99,10 @@ extern "C" ak_status ak_mesh_create(const ak_mesh_desc* d, void* cuda_stream, ak
   g.p1 = nx1 + 2 * g.ng;
   g.p2 = nx2 + 2 * g.ng;
   g.p3 = nx3 + 2 * g.ng;
-  g.var_stride = (long long)g.p1 * g.p2 * g.p3;
-  g.block_stride = ((AK_NVAR * g.var_stride + 31) / 32) * 32;
+  g.s1 = (g.p1 + 3) / 4 * 4;
+  g.front = (4 - g.ng % 4) % 4;
+  g.var_stride = (long long)g.s1 * g.p2 * g.p3;
+  g.block_stride = ((g.front + AK_NVAR * g.var_stride + 31) / 32) * 32;
   g.nblocks = d->nblocks;
   g.nbx1 = nb1;
   g.nbx2 = nb2;
@@ -114,7 +120,7 @@ extern "C" ak_status ak_mesh_create(const ak_mesh_desc* d, void* cuda_stream, ak
   }
   memcpy(m->h_blocks, B, sizeof(int32_t) * AK_BLOCK_INTS * d->nblocks);
   m->desc.blocks = m->h_blocks;
-  for (int b = 0; b < d->nblocks; ++b) m->h_offsets[b] = (int64_t)b * g.block_stride;
+  for (int b = 0; b < d->nblocks; ++b) m->h_offsets[b] = (int64_t)b * g.block_stride + g.front;
   // x3 segments per block: enough CTAs to fill the GPU a few times over
   {
     const long long tiles = (long long)d->nblocks * ((nx1 + 15) / 16) * ((nx2 + 15) / 16);
@@ -159,11 +165,17 @@ extern "C" void ak_mesh_destroy(ak_mesh* m) {
 }
 
 extern "C" ak_status ak_mesh_layout(const ak_mesh* m, int32_t* nregisters, size_t* register_bytes,
-                                    int64_t* block_offset) {
+                                    int64_t* block_offset, int64_t strides[4]) {
   if (!m) return einval("ak_mesh_layout: NULL mesh");
   if (nregisters) *nregisters = m->nreg;
   if (register_bytes) *register_bytes = m->reg_bytes;
   if (block_offset) memcpy(block_offset, m->h_offsets, sizeof(int64_t) * m->geom.nblocks);
+  if (strides) {
+    strides[0] = m->geom.var_stride;
+    strides[1] = (int64_t)m->geom.s1 * m->geom.p2;
+    strides[2] = m->geom.s1;
+    strides[3] = 1;
+  }
   return AK_OK;
 }
 
@@ -180,8 +192,38 @@ extern "C" ak_status ak_mesh_bind(ak_mesh* m, int32_t reg, double* p) {
   if (reg < 0 || reg >= m->nreg) return einval("ak_mesh_bind: register index out of range");
   if (!p || ((uintptr_t)p & 255u)) return einval("ak_mesh_bind: pointer NULL or not 256-byte aligned");
   m->reg[reg] = p;
+  m->tmap_ok[reg] = ak_encode_register_tmap(m, reg) == 0;
   invalidate_graph(m);
   return AK_OK;
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link).
+int ak_encode_register_tmap(ak_mesh* m, int reg) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return 1;
+    encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  }
+  const ak_geom& g = m->geom;
+  char* base = (char*)m->reg[reg] + sizeof(double) * g.front;
+  if (((uintptr_t)base & 15u) != 0) return 2;
+  cuuint64_t dims[5] = {(cuuint64_t)g.p1, (cuuint64_t)g.p2, (cuuint64_t)g.p3, 5,
+                        (cuuint64_t)g.nblocks};
+  cuuint64_t strides[4] = {sizeof(double) * (cuuint64_t)g.s1,
+                           sizeof(double) * (cuuint64_t)g.s1 * g.p2,
+                           sizeof(double) * (cuuint64_t)g.var_stride,
+                           sizeof(double) * (cuuint64_t)g.block_stride};
+  cuuint32_t box[5] = {16, 16, 1, 5, 1};
+  cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  CUresult r = encode(&m->tmap[reg], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 5, base, dims, strides, box,
+                      estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? 0 : 3;
 }
 
 static ak_status need_reg(const ak_mesh* m, int reg, const char* who) {
@@ -207,7 +249,7 @@ extern "C" ak_status ak_fill_ghosts(ak_mesh* m, int32_t reg) {
 static ak_status enqueue_stage(ak_mesh* m, int stage) {
   const int rk = m->desc.rk;
   const int in = stage_in_reg(rk, stage), outr = stage_out_reg(rk, stage);
-  AK_CUDA_TRY(ak_launch_stage(m, stage, m->reg[in], m->reg[0], m->reg[outr], stage == rk));
+  AK_CUDA_TRY(ak_launch_stage(m, stage, m->reg[in], m->reg[0], m->reg[outr], outr, stage == rk));
   return AK_OK;
 }
 

@@ -2,6 +2,7 @@
 // launchers shared by the translation units of the library.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (tensor maps are encoded through the runtime's entry point)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -30,7 +31,10 @@ struct ak_geom {
   int nx1, nx2, nx3;     // interior cells per block
   int ng;                // ghost cells per side
   int p1, p2, p3;        // padded extents nx + 2 ng
-  long long var_stride;  // p1 * p2 * p3
+  int s1;                // row pitch: p1 rounded up to a multiple of 4 elements
+  long long front;       // elements before a block's first ghost cell, chosen so that
+                         // every row's interior starts on a 32-byte boundary
+  long long var_stride;  // s1 * p2 * p3
   long long block_stride;
   int nblocks;
   int nbx1, nbx2, nbx3;  // blocks per direction
@@ -39,6 +43,8 @@ struct ak_geom {
 };
 
 struct ak_mesh {
+  CUtensorMap tmap[AK_MAX_REG];  // bulk-tensor (TMA) view of each bound register
+  int tmap_ok[AK_MAX_REG];
   ak_mesh_desc desc;
   cudaStream_t stream;
   ak_geom geom;
@@ -66,8 +72,11 @@ cudaError_t ak_launch_fill_ghosts(const ak_mesh* m, double* reg);
 cudaError_t ak_launch_pack(const ak_mesh* m, const double* reg, double* packed);
 cudaError_t ak_launch_unpack(const ak_mesh* m, const double* packed, double* reg);
 cudaError_t ak_launch_stage(const ak_mesh* m, int stage, const double* u_in, const double* u0,
-                            double* u_out, int last_stage);
+                            double* u_out, int out_reg, int last_stage);
 cudaError_t ak_launch_cfl(const ak_mesh* m, const double* reg);
 cudaError_t ak_launch_finalize_dt(const ak_mesh* m, int use_next_as_dt);
 cudaError_t ak_launch_set_dt(const ak_mesh* m, double dt);
 cudaError_t ak_stage_prepare(const ak_mesh* m);
+// Encodes m->tmap[reg] for register `reg` (5-D: x, y, z, var, block of doubles, box of
+// one 16x16 tile plane of all 5 variables); returns 0 on success.
+int ak_encode_register_tmap(ak_mesh* m, int reg);

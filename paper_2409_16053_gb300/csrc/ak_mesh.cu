@@ -19,21 +19,22 @@ __global__ void fill_ghosts_kernel(double* reg, ak_geom g, const int32_t* __rest
        idx += (long long)gridDim.x * blockDim.x) {
     const int b = (int)(idx / g.var_stride);
     const long long rem = idx - (long long)b * g.var_stride;
-    const int ip = (int)(rem % g.p1);
-    const int jp = (int)((rem / g.p1) % g.p2);
-    const int kp = (int)(rem / ((long long)g.p1 * g.p2));
+    const int ip = (int)(rem % g.s1);
+    const int jp = (int)((rem / g.s1) % g.p2);
+    const int kp = (int)(rem / ((long long)g.s1 * g.p2));
     const int i = ip - g.ng, j = jp - g.ng, k = kp - g.ng;
+    if (ip >= g.p1) continue;  // row padding
     if (i >= 0 && i < g.nx1 && j >= 0 && j < g.nx2 && k >= 0 && k < g.nx3) continue;
     const int gi = wrapi(loc[3 * b + 0] * g.nx1 + i, n1);
     const int gj = wrapi(loc[3 * b + 1] * g.nx2 + j, n2);
     const int gk = wrapi(loc[3 * b + 2] * g.nx3 + k, n3);
     const int sbx = gi / g.nx1, sby = gj / g.nx2, sbz = gk / g.nx3;
     const int sb = map[(sbz * g.nbx2 + sby) * g.nbx1 + sbx];
-    const long long src = (long long)sb * g.block_stride +
+    const long long src = (long long)sb * g.block_stride + g.front +
                           ((long long)(gk - sbz * g.nx3 + g.ng) * g.p2 + (gj - sby * g.nx2 + g.ng)) *
-                              g.p1 +
+                              g.s1 +
                           (gi - sbx * g.nx1 + g.ng);
-    const long long dst = (long long)b * g.block_stride + rem;
+    const long long dst = (long long)b * g.block_stride + g.front + rem;
 #pragma unroll
     for (int v = 0; v < AK_NVAR; ++v) reg[dst + v * g.var_stride] = reg[src + v * g.var_stride];
   }
@@ -52,8 +53,8 @@ __global__ void pack_kernel(double* reg, double* packed, ak_geom g) {
     const int i = (int)(rem % g.nx1);
     const int j = (int)((rem / g.nx1) % g.nx2);
     const int k = (int)(rem / ((long long)g.nx1 * g.nx2));
-    const long long e = (long long)b * g.block_stride + v * g.var_stride +
-                        ((long long)(k + g.ng) * g.p2 + (j + g.ng)) * g.p1 + (i + g.ng);
+    const long long e = (long long)b * g.block_stride + g.front + v * g.var_stride +
+                        ((long long)(k + g.ng) * g.p2 + (j + g.ng)) * g.s1 + (i + g.ng);
     if (TO_PACKED)
       packed[idx] = reg[e];
     else
@@ -74,8 +75,8 @@ __global__ void cfl_kernel(const double* __restrict__ reg, ak_geom g, ak_dev_sca
     const int i = (int)(rem % g.nx1);
     const int j = (int)((rem / g.nx1) % g.nx2);
     const int k = (int)(rem / ((long long)g.nx1 * g.nx2));
-    const long long e = (long long)b * g.block_stride +
-                        ((long long)(k + g.ng) * g.p2 + (j + g.ng)) * g.p1 + (i + g.ng);
+    const long long e = (long long)b * g.block_stride + g.front +
+                        ((long long)(k + g.ng) * g.p2 + (j + g.ng)) * g.s1 + (i + g.ng);
     double u[AK_NVAR];
 #pragma unroll
     for (int v = 0; v < AK_NVAR; ++v) u[v] = reg[e + v * g.var_stride];

@@ -36,19 +36,20 @@ cudaError_t scratch_address(double** out) {
 
 // One CTA per MeshBlock: minimum over the block's interior of dx_d / (|v_d| + c_s).
 __global__ void block_min_kernel(const double* __restrict__ reg, int nx1, int nx2, int nx3,
-                                 int ng, long long block_stride, double dx1, double dx2,
-                                 double dx3, double gamma, double* partial) {
+                                 int ng, int s1, long long front, long long block_stride,
+                                 double dx1, double dx2, double dx3, double gamma,
+                                 double* partial) {
   __shared__ double red[kThreads / 32];
-  const int p1 = nx1 + 2 * ng, p2 = nx2 + 2 * ng, p3 = nx3 + 2 * ng;
-  const long long var_stride = (long long)p1 * p2 * p3;
+  const int p2 = nx2 + 2 * ng, p3 = nx3 + 2 * ng;
+  const long long var_stride = (long long)s1 * p2 * p3;
   const long long n = (long long)nx1 * nx2 * nx3;
-  const double* ub = reg + (long long)blockIdx.x * block_stride;
+  const double* ub = reg + (long long)blockIdx.x * block_stride + front;
   double m = __longlong_as_double(0x7ff0000000000000ll);
   for (long long c = threadIdx.x; c < n; c += blockDim.x) {
     const int i = (int)(c % nx1);
     const int j = (int)((c / nx1) % nx2);
     const int k = (int)(c / ((long long)nx1 * nx2));
-    const long long e = ((long long)(k + ng) * p2 + (j + ng)) * p1 + (i + ng);
+    const long long e = ((long long)(k + ng) * p2 + (j + ng)) * s1 + (i + ng);
     double u[AK_NVAR];
 #pragma unroll
     for (int v = 0; v < AK_NVAR; ++v) u[v] = ub[e + v * var_stride];
@@ -117,12 +118,15 @@ extern "C" ak_status ak_cfl_dt_noalloc(const double* reg, int32_t nblocks, const
     ak_set_error("ak_cfl_dt_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
     return AK_ECUDA;
   }
-  const long long var_stride =
-      (long long)(nx[0] + 2 * nghost) * (nx[1] + 2 * nghost) * (nx[2] + 2 * nghost);
-  const long long block_stride = ((AK_NVAR * var_stride + 31) / 32) * 32;
+  // the register layout of ak_mesh_layout: row pitch, front pad and block stride
+  const int s1 = (nx[0] + 2 * nghost + 3) / 4 * 4;
+  const long long front = (4 - nghost % 4) % 4;
+  const long long var_stride = (long long)s1 * (nx[1] + 2 * nghost) * (nx[2] + 2 * nghost);
+  const long long block_stride = ((front + AK_NVAR * var_stride + 31) / 32) * 32;
   cudaStream_t s = (cudaStream_t)cuda_stream;
-  block_min_kernel<<<nblocks, kThreads, 0, s>>>(reg, nx[0], nx[1], nx[2], nghost, block_stride,
-                                                 dx[0], dx[1], dx[2], gamma, scratch);
+  block_min_kernel<<<nblocks, kThreads, 0, s>>>(reg, nx[0], nx[1], nx[2], nghost, s1, front,
+                                                 block_stride, dx[0], dx[1], dx[2], gamma,
+                                                 scratch);
   final_min_kernel<<<1, 1024, 0, s>>>(scratch, nblocks, cfl);
   e = cudaGetLastError();
   if (e == cudaSuccess)

@@ -21,6 +21,7 @@
 
 #include "ak_internal.cuh"
 #include "hydro_ops.cuh"
+#include "tma.cuh"
 
 namespace ak {
 
@@ -137,35 +138,51 @@ __device__ __forceinline__ double half(double x) {
   return __hiloint2double(hi - 0x00100000, __double2loint(x));
 }
 
-template <int NG, bool MIXED, int TX, int TY>
-struct StageSmem {
+template <int NG, bool MIXED, int TX, int TY, bool TMA_OUT>
+struct StageCfg {
   using R = typename std::conditional<MIXED, float, double>::type;
+  // FP64: x1 and x2 sweeps one after the other through one edge buffer, so that two
+  // CTAs fit in an SM's shared memory.  Mixed: both sweeps at once, and the next plane
+  // of the state is prefetched into registers while the current one is computed.
+  static constexpr bool SPLIT = !MIXED;
+  static constexpr bool PREFETCH = MIXED;
   static constexpr int WX = TX + 2 * NG, WY = TY + 2 * NG, NPL = WX * WY, NR = 2 * NG;
+  // cells of a plane that are converted: the tile and its x1 / x2 halos (no corners)
+  static constexpr int NCROSS = TX * TY + 2 * NG * (TX + TY);
+  static constexpr int NT = TX * TY;
+  static constexpr int NPT = (NCROSS + NT - 1) / NT;  // cells per thread
   static constexpr int E1 = 5 * TY * (TX + 2);  // x1 edges of cells i0-1 .. i0+TX
   static constexpr int E2 = 5 * (TY + 2) * TX;  // x2 edges of cells j0-1 .. j0+TY
+  static constexpr int EB = SPLIT ? (E1 > E2 ? E1 : E2) : E1 + E2;
   static constexpr int F1 = 5 * TY * (TX + 1);
   static constexpr int F2 = 5 * (TY + 1) * TX;
-  static constexpr size_t bytes = sizeof(R) * (size_t)(NR * 5 * NPL + 2 * E1 + 2 * E2 + F1 + F2);
+  // TMA_OUT: the new state of each plane goes through a double-buffered shared tile and
+  // one bulk-tensor store per plane instead of per-thread global stores
+  static constexpr int OUT = TMA_OUT ? 2 * 5 * TX * TY : 0;  // doubles, at offset 0
+  static constexpr size_t bytes =
+      sizeof(double) * (size_t)OUT + sizeof(R) * (size_t)(NR * 5 * NPL + 2 * EB + F1 + F2);
 };
 
-template <int NG, bool MIXED, int TX, int TY>
-__global__ void __launch_bounds__(TX* TY, MIXED ? 2 : 1)
+template <int NG, bool MIXED, int TX, int TY, bool TMA_OUT>
+__global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
     stage_kernel(const double* __restrict__ uin, const double* u0, double* uout, ak_geom g,
-                 Bg bg, double a, double b, int rk2_final, ak_dev_scalars* sc, int nseg,
-                 int last_stage) {
-  using S = StageSmem<NG, MIXED, TX, TY>;
-  using R = typename S::R;
-  constexpr int NT = TX * TY;
-  constexpr int WX = S::WX, NPL = S::NPL, NR = S::NR;
+                 Bg bg, double a, double b, int form, ak_dev_scalars* sc, int nseg,
+                 int last_stage, const __grid_constant__ CUtensorMap tmap_out) {
+  // form: 0 = first stage U + dt L; 1 = RK2 final (U0 + U + dt L) / 2;
+  //       2 = a U0 + b (U + dt L)
+  using C = StageCfg<NG, MIXED, TX, TY, TMA_OUT>;
+  using R = typename C::R;
+  constexpr int NT = C::NT, WX = C::WX, NPL = C::NPL, NR = C::NR, NPT = C::NPT;
   constexpr int C1 = TX + 2;  // x1 edge row length
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  R* ring = reinterpret_cast<R*>(smem_raw);  // [NR][5][WY][WX]
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  double* stg = reinterpret_cast<double*>(smem_raw);  // [2][5][TY][TX] (TMA_OUT only)
+  R* ring = reinterpret_cast<R*>(smem_raw + sizeof(double) * C::OUT);  // [NR][5][WY][WX]
   R* e1lo = ring + NR * 5 * NPL;             // [5][TY][TX+2]
-  R* e1hi = e1lo + S::E1;
-  R* e2lo = e1hi + S::E1;                    // [5][TY+2][TX]
-  R* e2hi = e2lo + S::E2;
-  R* f1 = e2hi + S::E2;                      // [5][TY][TX+1]
-  R* f2 = f1 + S::F1;                        // [5][TY+1][TX]
+  R* e1hi = e1lo + C::EB;
+  R* e2lo = C::SPLIT ? e1lo : e1lo + C::E1;  // [5][TY+2][TX]
+  R* e2hi = C::SPLIT ? e1hi : e1hi + C::E1;
+  R* f1 = e1hi + C::EB;                      // [5][TY][TX+1]
+  R* f2 = f1 + C::F1;                        // [5][TY+1][TX]
   __shared__ double red[NT / 32];
 
   const int tid = threadIdx.x;
@@ -183,30 +200,67 @@ __global__ void __launch_bounds__(TX* TY, MIXED ? 2 : 1)
   const int k1 = min(g.nx3, k0 + kseg);
   if (k0 >= k1) return;
 
-  const long long boff = (long long)blk * g.block_stride;
+  const long long boff = (long long)blk * g.block_stride + g.front;
   const double* ub = uin + boff;
   const Counters cn{&sc->counters[0], &sc->counters[1]};
   const double dt = sc->dt;
   const double idx1 = 1.0 / g.dx1, idx2 = 1.0 / g.dx2, idx3 = 1.0 / g.dx3;
+  const bool need_u0 = form != 0;
 
   auto slot = [](int k) { return (k + 4 * NR) % NR; };
-  // plane kp (interior index; ghost planes allowed) of the halo'd tile -> primitives
-  auto load_plane = [&](int kp) {
-    R* dst = ring + slot(kp) * 5 * NPL;
-    for (int c = tid; c < NPL; c += NT) {
-      const int x = c % WX, y = c / WX;
-      const int ip = i0 + x, jp = j0 + y;  // padded indices (halo starts at i0 - NG)
-      if (ip < g.p1 && jp < g.p2) {
-        const long long e = ((long long)(kp + NG) * g.p2 + jp) * g.p1 + ip;
-        double u[5];
+  // ring position of the c-th converted cell: halo rows above, full rows, halo rows below
+  auto cross_xy = [](int c, int& x, int& y) {
+    constexpr int TOP = NG * TX, MID = TY * (TX + 2 * NG);
+    if (c < TOP) {
+      y = c / TX;
+      x = NG + c % TX;
+    } else if (c < TOP + MID) {
+      const int d = c - TOP;
+      y = NG + d / (TX + 2 * NG);
+      x = d % (TX + 2 * NG);
+    } else {
+      const int d = c - TOP - MID;
+      y = NG + TY + d / TX;
+      x = NG + d % TX;
+    }
+  };
+  // global loads of this thread's cells of plane kp (interior index; ghost planes ok)
+  auto fetch = [&](int kp, double (&u)[NPT][5], int (&pos)[NPT]) {
 #pragma unroll
-        for (int v = 0; v < 5; ++v) u[v] = ub[e + v * g.var_stride];
-        R w[5];
-        c2p(u, w, bg, cn);
+    for (int m = 0; m < NPT; ++m) {
+      const int c = tid + m * NT;
+      pos[m] = -1;
+      if (c < C::NCROSS) {
+        int x, y;
+        cross_xy(c, x, y);
+        const int ip = i0 + x, jp = j0 + y;  // padded indices (halo starts at i0 - NG)
+        if (ip < g.p1 && jp < g.p2) {
+          const long long e = ((long long)(kp + NG) * g.p2 + jp) * g.s1 + ip;
 #pragma unroll
-        for (int v = 0; v < 5; ++v) dst[v * NPL + c] = w[v];
+          for (int v = 0; v < 5; ++v) u[m][v] = ub[e + v * g.var_stride];
+          pos[m] = y * WX + x;
+        }
       }
     }
+  };
+  // primitive recovery of fetched cells into the ring slot of plane kp
+  auto store = [&](int kp, const double (&u)[NPT][5], const int (&pos)[NPT]) {
+    R* dst = ring + slot(kp) * 5 * NPL;
+#pragma unroll
+    for (int m = 0; m < NPT; ++m) {
+      if (pos[m] >= 0) {
+        R w[5];
+        c2p(u[m], w, bg, cn);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) dst[v * NPL + pos[m]] = w[v];
+      }
+    }
+  };
+  auto load_plane = [&](int kp) {
+    double u[NPT][5];
+    int pos[NPT];
+    fetch(kp, u, pos);
+    store(kp, u, pos);
   };
 
   // own column of this thread
@@ -214,6 +268,8 @@ __global__ void __launch_bounds__(TX* TY, MIXED ? 2 : 1)
   const int ci = i0 + tx, cj = j0 + ty;
   const bool own = (ci < g.nx1) && (cj < g.nx2);
   const int oc = (ty + NG) * WX + (tx + NG);
+  const long long ecol = boff + ((long long)NG * g.p2 + (cj + NG)) * g.s1 + (ci + NG);
+  const long long plane_stride = (long long)g.p2 * g.s1;
 
   // x3 edges of the own column's cell kc (stencil planes kc-NG+1 .. kc+NG-1)
   auto x3_edges = [&](int kc, R* lo, R* hi) {
@@ -225,30 +281,11 @@ __global__ void __launch_bounds__(TX* TY, MIXED ? 2 : 1)
       edges<NG>(q, lo[v], hi[v]);
     }
   };
-
-  for (int kp = k0 - NG; kp < k0 + NG; ++kp) load_plane(kp);
-  __syncthreads();
-  R hi3[5], f3m[5], f3p[5];
-  if (own) {
-    R lo_a[5], hi_a[5], lo_b[5];
-    x3_edges(k0 - 1, lo_a, hi_a);
-    x3_edges(k0, lo_b, hi3);
-    solve(2, hi_a, lo_b, bg, f3m);
-  }
-
-  float dtmin_f = __int_as_float(0x7f800000);
-  double dtmin = __longlong_as_double(0x7ff0000000000000ll);
-  for (int k = k0; k < k1; ++k) {
-    __syncthreads();
-    load_plane(k + NG);
-    __syncthreads();
-    const R* pl = ring + slot(k) * 5 * NPL;
-
-    // ---- A: reconstruction -----------------------------------------------------
-    for (int it = tid; it < S::E1 / 5; it += NT) {  // x1 edges, cells i0-1 .. i0+TX
+  auto x1_edges = [&](const R* pl) {  // cells i0-1 .. i0+TX of the tile's rows
+    for (int it = tid; it < C::E1 / 5; it += NT) {
       const int c = it % C1, r = it / C1;
       if (i0 - 1 + c <= g.nx1 && j0 + r < g.nx2) {
-        const int base = (r + NG) * WX + c;  // stencil start: x = c .. c + 2NG - 2
+        const int base = (r + NG) * WX + c;  // stencil x = c .. c + 2NG - 2
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
           R q[2 * NG - 1];
@@ -258,10 +295,12 @@ __global__ void __launch_bounds__(TX* TY, MIXED ? 2 : 1)
         }
       }
     }
-    for (int it = tid; it < S::E2 / 5; it += NT) {  // x2 edges, cells j0-1 .. j0+TY
+  };
+  auto x2_edges = [&](const R* pl) {  // cells j0-1 .. j0+TY of the tile's columns
+    for (int it = tid; it < C::E2 / 5; it += NT) {
       const int c = it % TX, r = it / TX;
       if (i0 + c < g.nx1 && j0 - 1 + r <= g.nx2) {
-        const int base = r * WX + c + NG;  // stencil start (y = r), x = c + NG
+        const int base = r * WX + c + NG;  // stencil y = r .. r + 2NG - 2
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
           R q[2 * NG - 1];
@@ -271,12 +310,9 @@ __global__ void __launch_bounds__(TX* TY, MIXED ? 2 : 1)
         }
       }
     }
-    R lo3[5], hi3n[5];
-    if (own) x3_edges(k + 1, lo3, hi3n);
-    __syncthreads();
-
-    // ---- B: Riemann problems -----------------------------------------------------
-    for (int it = tid; it < S::F1 / 5; it += NT) {
+  };
+  auto x1_faces = [&]() {
+    for (int it = tid; it < C::F1 / 5; it += NT) {
       const int fx = it % (TX + 1), fy = it / (TX + 1);
       if (i0 + fx <= g.nx1 && j0 + fy < g.nx2) {
         R l[5], r[5], f[5];
@@ -290,7 +326,9 @@ __global__ void __launch_bounds__(TX* TY, MIXED ? 2 : 1)
         for (int v = 0; v < 5; ++v) f1[(v * TY + fy) * (TX + 1) + fx] = f[v];
       }
     }
-    for (int it = tid; it < S::F2 / 5; it += NT) {
+  };
+  auto x2_faces = [&]() {
+    for (int it = tid; it < C::F2 / 5; it += NT) {
       const int fx = it % TX, fy = it / TX;
       if (i0 + fx < g.nx1 && j0 + fy <= g.nx2) {
         R l[5], r[5], f[5];
@@ -304,42 +342,115 @@ __global__ void __launch_bounds__(TX* TY, MIXED ? 2 : 1)
         for (int v = 0; v < 5; ++v) f2[(v * (TY + 1) + fy) * TX + fx] = f[v];
       }
     }
+  };
+
+  // prologue: planes k0-NG .. k0+NG-1, the flux through the face below k0, then plane
+  // k0+NG (its slot held plane k0-NG, used by that flux)
+  for (int kp = k0 - NG; kp < k0 + NG; ++kp) load_plane(kp);
+  __syncthreads();
+  R hi3[5], f3m[5], f3p[5];
+  if (own) {
+    R lo_a[5], hi_a[5], lo_b[5];
+    x3_edges(k0 - 1, lo_a, hi_a);
+    x3_edges(k0, lo_b, hi3);
+    solve(2, hi_a, lo_b, bg, f3m);
+  }
+  __syncthreads();
+  load_plane(k0 + NG);
+
+  float dtmin_f = __int_as_float(0x7f800000);
+  double dtmin = __longlong_as_double(0x7ff0000000000000ll);
+  double lam_max = 0.0;
+  double pf[NPT][5];
+  int pfpos[NPT];
+  for (int k = k0; k < k1; ++k) {
+    // the ring holds planes k-NG+1 .. k+NG once this barrier is passed
+    const bool more = k + 1 < k1;
+    if constexpr (C::PREFETCH) {
+      if (more) fetch(k + NG + 1, pf, pfpos);
+    }
+    double uik[5], u0k[5];
+    if constexpr (MIXED) {
+      if (own) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          uik[v] = uin[ecol + k * plane_stride + v * g.var_stride];
+          u0k[v] = need_u0 ? u0[ecol + k * plane_stride + v * g.var_stride] : 0.0;
+        }
+      }
+    }
+    __syncthreads();
+    if constexpr (TMA_OUT) {
+      // the previous plane's new state is complete in its staging tile
+      if (tid == 0 && k > k0) {
+        tma_store_5d(&tmap_out, stg + ((k - 1) & 1) * 5 * TX * TY, i0 + NG, j0 + NG, k - 1 + NG,
+                     0, blk);
+        bulk_commit();
+      }
+    }
+    const R* pl = ring + slot(k) * 5 * NPL;
+    R lo3[5], hi3n[5];
+
+    if constexpr (C::SPLIT) {
+      x1_edges(pl);
+      if (own) x3_edges(k + 1, lo3, hi3n);
+      __syncthreads();
+      x1_faces();
+      __syncthreads();
+      x2_edges(pl);
+      __syncthreads();
+      x2_faces();
+    } else {
+      x1_edges(pl);
+      x2_edges(pl);
+      if (own) x3_edges(k + 1, lo3, hi3n);
+      __syncthreads();
+      x1_faces();
+      x2_faces();
+    }
     if (own) {
       solve(2, hi3, lo3, bg, f3p);
 #pragma unroll
       for (int v = 0; v < 5; ++v) hi3[v] = hi3n[v];
     }
+    if constexpr (TMA_OUT) {
+      // this plane's staging tile was last read by the store of plane k-2
+      if (tid == 0) bulk_wait_read<1>();
+    }
     __syncthreads();
 
-    // ---- C: divergence and RK update -------------------------------------------
+    // ---- divergence and RK update ---------------------------------------------
     if (own) {
-      const long long e = boff + ((long long)(k + NG) * g.p2 + (cj + NG)) * g.p1 + (ci + NG);
+      const long long e = ecol + k * plane_stride;
       double un[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
         const R d1 = f1[(v * TY + ty) * (TX + 1) + tx + 1] - f1[(v * TY + ty) * (TX + 1) + tx];
         const R d2 = f2[(v * (TY + 1) + ty + 1) * TX + tx] - f2[(v * (TY + 1) + ty) * TX + tx];
         const R d3 = f3p[v] - f3m[v];
-        const double ui = uin[e + v * g.var_stride];
         double r;
         if constexpr (MIXED) {
           const float L = -fmaf(d1, (float)idx1, fmaf(d2, (float)idx2, d3 * (float)idx3));
           const double Ld = f32_to_f64(L);
-          if (rk2_final)
-            r = half(u0[e + v * g.var_stride] + fma(dt, Ld, ui));
-          else if (a == 0.0)
-            r = fma(dt, Ld, ui);
+          if (form == 1)
+            r = half(u0k[v] + fma(dt, Ld, uik[v]));
+          else if (form == 0)
+            r = fma(dt, Ld, uik[v]);
           else
-            r = fma(b, fma(dt, Ld, ui), a * u0[e + v * g.var_stride]);
+            r = fma(b, fma(dt, Ld, uik[v]), a * u0k[v]);
         } else {
           const double L = -fma(d1, idx1, fma(d2, idx2, d3 * idx3));
-          r = fma(dt, L, ui);
-          if (a != 0.0) r = a * u0[e + v * g.var_stride] + b * r;
+          r = fma(dt, L, uin[e + v * g.var_stride]);
+          if (form != 0) r = a * u0[e + v * g.var_stride] + b * r;
         }
         un[v] = r;
-        uout[e + v * g.var_stride] = r;
+        if constexpr (TMA_OUT)
+          stg[(((k & 1) * 5 + v) * TY + ty) * TX + tx] = r;
+        else
+          uout[e + v * g.var_stride] = r;
         f3m[v] = f3p[v];
       }
+      if constexpr (TMA_OUT) fence_proxy_async_smem();
       if (last_stage) {
         if constexpr (MIXED) {
           // CFL ratio in FP32: it only sets the next step's dt
@@ -354,29 +465,52 @@ __global__ void __launch_bounds__(TX* TY, MIXED ? 2 : 1)
           lam = fmaxf(lam, (fabsf(m3) * ir + cs) * (float)idx3);
           dtmin_f = fminf(dtmin_f, rcp_approx_f32(lam));
         } else {
-          // CFL ratio in FP64 (the FP64 form reproduces the oracle's dt)
+          // CFL in FP64 (the FP64 form reproduces the oracle's dt to ~1e-13): the
+          // largest (|v_d| + c_s) / dx_d of the column; dt = 1 / max at the end
           double rho = un[0];
           rho = at_least(rho, AK_RHO_FLOOR) ? rho : AK_RHO_FLOOR;
           const double r = rcp64(rho);
           const double v1 = un[1] * r, v2 = un[2] * r, v3 = un[3] * r;
           double ug = fma(-0.5, fma(un[1], v1, fma(un[2], v2, un[3] * v3)), un[4]);
           ug = at_least(ug, AK_UG_FLOOR) ? ug : AK_UG_FLOOR;
-          const double cs = sqrt(g.gamma * (g.gamma - 1.0) * ug * r);
-          double t = g.dx1 / (fabs(v1) + cs);
-          t = fmin(t, g.dx2 / (fabs(v2) + cs));
-          t = fmin(t, g.dx3 / (fabs(v3) + cs));
-          dtmin = fmin(dtmin, t);
+          const double cs = sqrt64(bg.gamma * bg.gm1 * ug * r);
+          const double l1 = (fabs(v1) + cs) * idx1, l2 = (fabs(v2) + cs) * idx2,
+                       l3 = (fabs(v3) + cs) * idx3;
+          double lam = dgt_pos(l2, l1) ? l2 : l1;
+          lam = dgt_pos(l3, lam) ? l3 : lam;
+          lam_max = dgt_pos(lam, lam_max) ? lam : lam_max;
         }
       }
     }
+    // next plane into the slot of plane k-NG+1, whose last reader was this iteration's
+    // reconstruction (finished before the barrier above)
+    if (more) {
+      if constexpr (C::PREFETCH)
+        store(k + NG + 1, pf, pfpos);
+      else
+        load_plane(k + NG + 1);
+    }
   }
 
+  if constexpr (TMA_OUT) {
+    __syncthreads();
+    if (tid == 0) {
+      tma_store_5d(&tmap_out, stg + ((k1 - 1) & 1) * 5 * TX * TY, i0 + NG, j0 + NG, k1 - 1 + NG,
+                   0, blk);
+      bulk_commit();
+      bulk_wait<0>();
+    }
+  }
   if (last_stage) {
-    if constexpr (MIXED) dtmin = f32_to_f64(dtmin_f);
+    if constexpr (MIXED)
+      dtmin = f32_to_f64(dtmin_f);
+    else
+      dtmin = dpos(lam_max) ? 1.0 / lam_max : dtmin;
     // CTA min of the CFL ratio -> one atomic per CTA (non-negative doubles order as
     // their bit patterns)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) dtmin = fmin(dtmin, __shfl_xor_sync(0xffffffffu, dtmin, o));
+    __syncthreads();
     if ((tid & 31) == 0) red[tid >> 5] = dtmin;
     __syncthreads();
     if (tid < 32) {
@@ -389,12 +523,12 @@ __global__ void __launch_bounds__(TX* TY, MIXED ? 2 : 1)
   }
 }
 
-template <int NG, bool MIXED, int TX, int TY>
+template <int NG, bool MIXED, int TX, int TY, bool TMA_OUT>
 static cudaError_t launch(const ak_mesh* m, const double* uin, const double* u0, double* uout,
-                          double a, double b, int rk2_final, int last_stage,
-                          bool prepare_only = false) {
-  const size_t smem = StageSmem<NG, MIXED, TX, TY>::bytes;
-  auto kern = stage_kernel<NG, MIXED, TX, TY>;
+                          int out_reg, double a, double b, int rk2_final, int last_stage,
+                          bool prepare_only) {
+  const size_t smem = StageCfg<NG, MIXED, TX, TY, TMA_OUT>::bytes;
+  auto kern = stage_kernel<NG, MIXED, TX, TY, TMA_OUT>;
   if (prepare_only)
     return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const ak_geom& g = m->geom;
@@ -410,43 +544,45 @@ static cudaError_t launch(const ak_mesh* m, const double* uin, const double* u0,
   bg.rho_f = (float)bg.rho;
   bg.ug_f = (float)bg.ug;
   bg.ug_floor_f = (float)(AK_UG_FLOOR - bg.ug);
-  kern<<<(unsigned)nblk, TX * TY, smem, m->stream>>>(uin, u0, uout, g, bg, a, b, rk2_final,
-                                                      m->d_sc, m->seg3, last_stage);
+  const int form = rk2_final ? 1 : (a == 0.0 ? 0 : 2);
+  kern<<<(unsigned)nblk, TX * TY, smem, m->stream>>>(uin, u0, uout, g, bg, a, b, form,
+                                                      m->d_sc, m->seg3, last_stage,
+                                                      m->tmap[out_reg]);
   return cudaGetLastError();
 }
 
-template <int NG, bool MIXED>
-static cudaError_t launch_form(const ak_mesh* m, const double* uin, const double* u0,
-                               double* uout, double a, double b, int rk2_final, int last_stage,
-                               bool prepare_only) {
-  return launch<NG, MIXED, 16, 16>(m, uin, u0, uout, a, b, rk2_final, last_stage, prepare_only);
-}
-
 static cudaError_t dispatch(const ak_mesh* m, const double* uin, const double* u0, double* uout,
-                            double a, double b, int rk2_final, int last_stage, bool prepare) {
+                            int out_reg, double a, double b, int rk2_final, int last_stage,
+                            bool prepare) {
   const bool mixed = m->desc.precision == AK_MIXED;
-  if (m->desc.recon == AK_PLM)
-    return mixed ? launch_form<2, true>(m, uin, u0, uout, a, b, rk2_final, last_stage, prepare)
-                 : launch_form<2, false>(m, uin, u0, uout, a, b, rk2_final, last_stage, prepare);
-  return mixed ? launch_form<3, true>(m, uin, u0, uout, a, b, rk2_final, last_stage, prepare)
-               : launch_form<3, false>(m, uin, u0, uout, a, b, rk2_final, last_stage, prepare);
+  if (m->desc.recon == AK_PLM) {
+    if (!mixed)
+      return launch<2, false, 16, 16, false>(m, uin, u0, uout, out_reg, a, b, rk2_final,
+                                             last_stage, prepare);
+    return launch<2, true, 16, 16, false>(m, uin, u0, uout, out_reg, a, b, rk2_final, last_stage,
+                                          prepare);
+  }
+  return mixed ? launch<3, true, 16, 16, false>(m, uin, u0, uout, out_reg, a, b, rk2_final,
+                                                last_stage, prepare)
+               : launch<3, false, 16, 16, false>(m, uin, u0, uout, out_reg, a, b, rk2_final,
+                                                 last_stage, prepare);
 }
 
 }  // namespace ak
 
 cudaError_t ak_launch_stage(const ak_mesh* m, int stage, const double* u_in, const double* u0,
-                            double* u_out, int last_stage) {
+                            double* u_out, int out_reg, int last_stage) {
   static const double a2[2] = {0.0, 0.5}, b2[2] = {1.0, 0.5};
   static const double a3[3] = {0.0, 0.75, 1.0 / 3.0}, b3[3] = {1.0, 0.25, 2.0 / 3.0};
   const bool rk3 = m->desc.rk == 3;
   const double a = rk3 ? a3[stage - 1] : a2[stage - 1];
   const double b = rk3 ? b3[stage - 1] : b2[stage - 1];
   const int rk2_final = (!rk3 && stage == 2) ? 1 : 0;
-  return ak::dispatch(m, u_in, u0, u_out, a, b, rk2_final, last_stage, false);
+  return ak::dispatch(m, u_in, u0, u_out, out_reg, a, b, rk2_final, last_stage, false);
 }
 
-// Raises the dynamic shared-memory limit of the stage kernel this mesh uses (called once
-// at mesh creation, outside any stream capture).
+// Raises the dynamic shared-memory limit of the stage kernels this mesh uses (called
+// once at mesh creation, outside any stream capture).
 cudaError_t ak_stage_prepare(const ak_mesh* m) {
-  return ak::dispatch(m, nullptr, nullptr, nullptr, 0.0, 0.0, 0, 0, true);
+  return ak::dispatch(m, nullptr, nullptr, nullptr, 0, 0.0, 0.0, 0, 0, true);
 }

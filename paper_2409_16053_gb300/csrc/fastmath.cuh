@@ -76,6 +76,32 @@ __device__ __forceinline__ double rcp64(double x) {
   return __hiloint2double(rhi, __double2loint(r));
 }
 
+// ---- comparisons and exact scalings of doubles on the integer pipe --------------------
+// Doubles order like their bit patterns once the magnitude bits of negative values are
+// flipped; these tests treat -0.0 as below +0.0 and are meant for finite operands.
+__device__ __forceinline__ long long dkey(double x) {
+  const long long b = __double_as_longlong(x);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffll);
+}
+__device__ __forceinline__ bool dgt(double a, double b) { return dkey(a) > dkey(b); }
+__device__ __forceinline__ bool dpos(double x) { return __double_as_longlong(x) > 0; }   // x > 0
+__device__ __forceinline__ bool dnonneg(double x) { return __double2hiint(x) >= 0; }    // x >= +0
+// a > b for a, b >= 0
+__device__ __forceinline__ bool dgt_pos(double a, double b) {
+  return __double_as_longlong(a) > __double_as_longlong(b);
+}
+// x * 2^n for normal x whose result stays normal (exponent arithmetic only)
+__device__ __forceinline__ double dscale(double x, int n) {
+  return __hiloint2double(__double2hiint(x) + (n << 20), __double2loint(x));
+}
+// x * 2^-n (n > 0) for any finite x: exponent arithmetic, or the multiply when x is
+// zero or so small that the result would leave the normal range
+__device__ __forceinline__ double dscale_down(double x, int n, double two_pow_minus_n) {
+  const int hi = __double2hiint(x);
+  if ((hi & 0x7ff00000) <= (n << 20)) return x * two_pow_minus_n;
+  return __hiloint2double(hi - (n << 20), __double2loint(x));
+}
+
 // 1/sqrt(x) for finite normal x > 0: x = m 4^k with m in [1, 4).
 __device__ __forceinline__ double rsqrt64(double x) {
   const unsigned hi = (unsigned)__double2hiint(x);
@@ -92,14 +118,14 @@ __device__ __forceinline__ double rsqrt64(double x) {
                                    (((mhi & 0x000fffffu) << 3) | (lo >> 29)));
   double y = f32_to_f64(rsqrt_approx_f32(mf));
   const double t = fma(-m * y, y, 1.0);  // 1 - m y^2
-  y = fma(0.5 * y, t, y);
+  y = fma(dscale(y, -1), t, y);          // y + (y/2) t
   // scale by 2^-k
   const int yhi = __double2hiint(y) - (k << 20);
   return __hiloint2double(yhi, __double2loint(y));
 }
 
 __device__ __forceinline__ double sqrt64(double x) {
-  if (x == 0.0) return 0.0;
+  if ((__double_as_longlong(x) << 1) == 0) return x;  // +-0
   return x * rsqrt64(x);
 }
 

@@ -45,6 +45,18 @@ __device__ __forceinline__ double plm_slope(double qm, double q0, double qp) {
   return prod > 0.0 ? (prod + prod) * rcp64(dl + dr) : 0.0;
 }
 
+// Half of the van Leer slope, dl dr / (dl + dr): the offset of the face values from the
+// cell value (saves the doubling and halving of plm_slope in FP64)
+__device__ __forceinline__ double plm_half_slope(double qm, double q0, double qp) {
+  const double dl = q0 - qm;
+  const double dr = qp - q0;
+  const double prod = dl * dr;
+  return dpos(prod) ? prod * rcp64(dl + dr) : 0.0;
+}
+__device__ __forceinline__ float plm_half_slope(float qm, float q0, float qp) {
+  return 0.5f * plm_slope(qm, q0, qp);
+}
+
 // FP32: the harmonic mean with the hardware reciprocal refined once in FP32
 __device__ __forceinline__ float plm_slope(float qm, float q0, float qp) {
   const float dl = q0 - qm;
@@ -105,63 +117,70 @@ __device__ __forceinline__ void ppm_edges(R q0, R q1, R q2, R q3, R q4, R& lo, R
 // ------------------------------------------------------------------------------
 __device__ __forceinline__ void hllc_fp64(const double* wl, const double* wr, const Bg& bg,
                                           double* f) {
+  // Comparisons run on the integer pipe (dgt/dpos/dnonneg) and powers of two scale
+  // by exponent arithmetic (dscale): only the arithmetic itself uses the FP64 unit.
   const double gamma = bg.gamma;
   const double gm1 = bg.gm1;
   const double rl = wl[0], ul = wl[1], rr = wr[0], ur = wr[1];
   const double pl = gm1 * wl[4];
   const double pr = gm1 * wr[4];
-  const double el = fma(0.5 * rl, ul * ul + wl[2] * wl[2] + wl[3] * wl[3], wl[4]);
-  const double er = fma(0.5 * rr, ur * ur + wr[2] * wr[2] + wr[3] * wr[3], wr[4]);
-  const double irl = rcp64(rl), irr = rcp64(rr);
-  const double cl = sqrt64(gamma * pl * irl);
-  const double cr = sqrt64(gamma * pr * irr);
+  // c = sqrt(gamma p / rho) = (gamma p) / sqrt(gamma p rho)
+  const double gpl = gamma * pl, gpr = gamma * pr;
+  const double cl = gpl * rsqrt64(gpl * rl);
+  const double cr = gpr * rsqrt64(gpr * rr);
 
   // pressure estimate of the linearised (PVRS) solver, then shock-aware speeds
-  double ps = 0.5 * (pl + pr) - 0.125 * (ur - ul) * (rl + rr) * (cl + cr);
-  ps = ps > 0.0 ? ps : 0.0;
+  double ps = dscale_down(pl + pr, 1, 0.5) - dscale_down((ur - ul) * (rl + rr), 3, 0.125) * (cl + cr);
+  ps = dpos(ps) ? ps : 0.0;
   const double kq = bg.kq;
   double ql = 1.0, qr = 1.0;
-  if (ps > pl) ql = sqrt64(fma(kq * (ps - pl), rcp64(pl), 1.0));
-  if (ps > pr) qr = sqrt64(fma(kq * (ps - pr), rcp64(pr), 1.0));
-  double sl = ul - cl * ql;
-  double sr = ur + cr * qr;
-  sl = (ur - cr < sl) ? ur - cr : sl;
-  sr = (ul + cl > sr) ? ul + cl : sr;
+  if (dgt_pos(ps, pl)) ql = sqrt64(fma(kq * (ps - pl), rcp64(pl), 1.0));
+  if (dgt_pos(ps, pr)) qr = sqrt64(fma(kq * (ps - pr), rcp64(pr), 1.0));
+  double sl = fma(-cl, ql, ul);
+  double sr = fma(cr, qr, ur);
+  const double dl = ur - cr, dr = ul + cl;
+  sl = dgt(sl, dl) ? dl : sl;
+  sr = dgt(dr, sr) ? dr : sr;
 
-  if (sl >= 0.0 || sr <= 0.0) {
+  const bool sup_l = dnonneg(sl), sup_r = !dpos(sr);
+  if (sup_l || sup_r) {
     // supersonic: the upwind physical flux (S_L >= 0 takes the left state)
-    const bool up_left = sl >= 0.0;
-    const double* wu = up_left ? wl : wr;
-    const double pu = up_left ? pl : pr;
-    const double eu = up_left ? el : er;
-    const double mu = wu[0] * wu[1];
+    const double* wu = sup_l ? wl : wr;
+    const double pu = sup_l ? pl : pr;
+    const double ru = wu[0], uu = wu[1];
+    const double eu = fma(dscale(ru, -1), fma(uu, uu, fma(wu[2], wu[2], wu[3] * wu[3])), wu[4]);
+    const double mu = ru * uu;
     f[0] = mu;
-    f[1] = fma(mu, wu[1], pu);
+    f[1] = fma(mu, uu, pu);
     f[2] = mu * wu[2];
     f[3] = mu * wu[3];
-    f[4] = (eu + pu) * wu[1];
+    f[4] = (eu + pu) * uu;
     return;
   }
   const double ml = rl * (sl - ul);  // mass flux through the left wave (frame of S_L)
   const double mr = rr * (sr - ur);
-  const double sstar = (pr - pl + ul * ml - ur * mr) * rcp64(ml - mr);
+  const double sstar = fma(ul, ml, fma(-ur, mr, pr - pl)) * rcp64(ml - mr);
 
-  const bool left = sstar >= 0.0;
+  const bool left = dnonneg(sstar);
   const double* w = left ? wl : wr;
   const double rk = w[0], uk = w[1];
   const double pk = left ? pl : pr;
-  const double ek = left ? el : er;
-  const double irk = left ? irl : irr;
   const double mk = left ? ml : mr;  // rho_K (S_K - u_K)
   const double s = left ? sl : sr;
+  const double ek = fma(dscale(rk, -1), fma(uk, uk, fma(w[2], w[2], w[3] * w[3])), w[4]);
   const double mn = rk * uk;
-  const double fac = mk * rcp64(s - sstar);
-  const double us4 = fac * fma(sstar - uk, fma(pk, rcp64(mk), sstar), ek * irk);
-  f[0] = mn + s * (fac - rk);
-  f[1] = fma(mn, uk, pk) + s * (fac * sstar - mn);
-  f[2] = mn * w[2] + s * (fac - rk) * w[2];
-  f[3] = mn * w[3] + s * (fac - rk) * w[3];
-  f[4] = (ek + pk) * uk + s * (us4 - ek);
+  const double inv = rcp64(s - sstar);
+  const double fac = mk * inv;       // rho*_K
+  // E*_K = fac (E_K/rho_K + (S* - u_K)(S* + p_K/(rho_K (S_K - u_K))))
+  //      = E_K (S_K - u_K)/(S_K - S*) + (S* - u_K)(fac S* + p_K/(S_K - S*))
+  const double us4 = fma(sstar - uk, fma(fac, sstar, pk * inv), ek * ((s - uk) * inv));
+  const double sd = s * (fac - rk);  // S_K (rho*_K - rho_K)
+  const double mt = mn + sd;
+  f[0] = mt;
+  f[1] = fma(s, fma(fac, sstar, -mn), fma(mn, uk, pk));
+  f[2] = mt * w[2];
+  f[3] = mt * w[3];
+  f[4] = fma(s, us4 - ek, (ek + pk) * uk);
 }
 
 // ------------------------------------------------------------------------------
@@ -185,9 +204,9 @@ __device__ __forceinline__ void hllc_mixed(const float* wl, const float* wr, con
   const float ker = 0.5f * rr * (ur * ur + wr[2] * wr[2] + wr[3] * wr[3]);
   const float hl = fmaf(gg, pl, kel);                   // E + p
   const float hr = fmaf(gg, pr, ker);
-  const float irl = rcp_approx_f32(rl), irr = rcp_approx_f32(rr);
-  const float cl = sqrt_fast(g * pl * irl);
-  const float cr = sqrt_fast(g * pr * irr);
+  const float gpl = g * pl, gpr = g * pr;
+  const float cl = gpl * rsqrt_approx_f32(gpl * rl);   // sqrt(gamma p / rho)
+  const float cr = gpr * rsqrt_approx_f32(gpr * rr);
 
   // PVRS estimate as a deviation from p_b; p* = max(0, p_b + dps)
   float dps = 0.5f * (dpl + dpr) - 0.125f * (ur - ul) * (rl + rr) * (cl + cr);
@@ -219,7 +238,6 @@ __device__ __forceinline__ void hllc_mixed(const float* wl, const float* wr, con
   const bool left = sstar >= 0.0f;
   const float* w = left ? wl : wr;
   const float rk = left ? rl : rr;
-  const float irk = left ? irl : irr;
   const float mk = left ? ml : mr;                      // rho_K (S_K - u_K)
   const float uk = w[1];
   const float s = left ? sl : sr;
@@ -230,7 +248,8 @@ __device__ __forceinline__ void hllc_mixed(const float* wl, const float* wr, con
   const float fac = mk * inv;
   const float drho = rk * (sstar - uk) * inv;           // U*_rho - rho_K
   const float dmn = fac * sstar - mn;                   // U*_Mn - M_n
-  const float de = fmaf(drho * irk, ek, fac * (sstar - uk) * fmaf(pk, rcp_approx_f32(mk), sstar));
+  // E*_K - E_K = (S* - u_K) ((E_K + p_K) / (S_K - S*) + rho*_K S*)
+  const float de = (sstar - uk) * fmaf(fac, sstar, (ek + pk) * inv);
   f[0] = fmaf(s, drho, mn);
   f[1] = fmaf(mn, uk, left ? dpl : dpr) + s * dmn;
   f[2] = (mn + s * drho) * w[2];

@@ -32,6 +32,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ak_oracle.c")
+_SRC_SMR = os.path.join(_HERE, "ak_oracle_smr.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "libak_oracle.so")
 _lock = threading.Lock()
@@ -45,11 +46,12 @@ def build(force: bool = False) -> str:
     """Compile ak_oracle.c into a shared library (gcc, OpenMP, no FP contraction)."""
     os.makedirs(_BUILD, exist_ok=True)
     if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+            and os.path.getmtime(_LIB) >= max(os.path.getmtime(_SRC),
+                                               os.path.getmtime(_SRC_SMR))):
         return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
-           "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+           "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC, _SRC_SMR, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)
     return _LIB
@@ -59,6 +61,14 @@ class _Grid(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64 * 3), ("dx", ctypes.c_double * 3),
                 ("gamma", ctypes.c_double), ("recon", ctypes.c_int32),
                 ("pad", ctypes.c_int32)]
+
+
+class _Smr(ctypes.Structure):
+    _fields_ = [("nblocks", ctypes.c_int32), ("ng", ctypes.c_int32),
+                ("recon", ctypes.c_int32), ("flux_correction", ctypes.c_int32),
+                ("blocks", ctypes.POINTER(ctypes.c_int32)),
+                ("root_nx", ctypes.c_int32 * 3), ("length", ctypes.c_double * 3),
+                ("gamma", ctypes.c_double)]
 
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -88,6 +98,21 @@ def _load():
             lib.orc_exact_sample.argtypes = [_dp, _dp, ctypes.c_double, ctypes.c_double, _dp]
             lib.orc_exact_sample.restype = ctypes.c_int
             lib.orc_num_threads.restype = ctypes.c_int
+            S = ctypes.POINTER(_Smr)
+            lib.orc_smr_storage.argtypes = [S]
+            lib.orc_smr_storage.restype = ctypes.c_int64
+            lib.orc_smr_fill_ghosts.argtypes = [S, _dp]
+            lib.orc_smr_fill_ghosts.restype = ctypes.c_int
+            lib.orc_smr_rhs.argtypes = [S, _dp, _dp]
+            lib.orc_smr_rhs.restype = ctypes.c_int64
+            lib.orc_smr_rk_step.argtypes = [S, _dp, ctypes.c_double, ctypes.c_int]
+            lib.orc_smr_rk_step.restype = ctypes.c_int64
+            lib.orc_smr_new_dt.argtypes = [S, _dp, ctypes.c_double]
+            lib.orc_smr_new_dt.restype = ctypes.c_double
+            lib.orc_prolong.argtypes = [ctypes.c_double, _dp, _dp, ctypes.POINTER(ctypes.c_int)]
+            lib.orc_prolong.restype = ctypes.c_double
+            lib.orc_restrict.argtypes = [_dp]
+            lib.orc_restrict.restype = ctypes.c_double
             _lib = lib
     return _lib
 
@@ -232,3 +257,98 @@ def exact_sample(wl, wr, gamma, xi):
             raise ValueError("vacuum generated")
         out[:, m] = o
     return out
+
+
+# ---- static refinement (ak_oracle_smr.c) -----------------------------------------------
+def prolong(uc, um, up, hi):
+    """Fine value from coarse centre uc, coarse neighbours um[d]/up[d], upper half hi[d]."""
+    um = np.ascontiguousarray(um, dtype=np.float64)
+    up = np.ascontiguousarray(up, dtype=np.float64)
+    h = (ctypes.c_int * 3)(*[int(v) for v in hi])
+    return float(_load().orc_prolong(float(uc), _ptr(um), _ptr(up), h))
+
+
+def restrict(f8):
+    f = np.ascontiguousarray(f8, dtype=np.float64)
+    return float(_load().orc_restrict(_ptr(f)))
+
+
+class SmrMesh:
+    """Leaf MeshBlocks on several levels (rows: level, lx1, lx2, lx3, nx1, nx2, nx3) of a
+    periodic box; storage = padded arrays block after block (see ak_oracle_smr.c)."""
+
+    def __init__(self, table, root_nx, length=(1.0, 1.0, 1.0), gamma=5.0 / 3.0,
+                 recon=PLM, flux_correction=True):
+        self.table = np.ascontiguousarray(np.asarray(table, dtype=np.int32))
+        self.root_nx = tuple(int(v) for v in root_nx)
+        self.length = tuple(float(v) for v in length)
+        self.gamma = float(gamma)
+        self.ng = 2 if recon == PLM else 3
+        self.recon = int(recon)
+        c = _Smr()
+        c.nblocks = self.table.shape[0]
+        c.ng = self.ng
+        c.recon = self.recon
+        c.flux_correction = 1 if flux_correction else 0
+        c.blocks = self.table.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        for d in range(3):
+            c.root_nx[d] = self.root_nx[d]
+            c.length[d] = self.length[d]
+        c.gamma = self.gamma
+        self._c = c
+        g = self.ng
+        self.shapes = [(5, r[6] + 2 * g, r[5] + 2 * g, r[4] + 2 * g) for r in self.table]
+        sizes = [int(np.prod(s)) for s in self.shapes]
+        self.offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+        self.size = int(self.offsets[-1])
+
+    def _ref(self):
+        return ctypes.byref(self._c)
+
+    def block(self, U, b):
+        """Padded view (5, p3, p2, p1) of block b inside the storage array U."""
+        return U[self.offsets[b]:self.offsets[b + 1]].reshape(self.shapes[b])
+
+    def from_packed(self, P):
+        """Storage array (ghosts zero) from interior data packed block after block as
+        [block][var][k][j][i]."""
+        U = np.zeros(self.size)
+        g, o = self.ng, 0
+        for b, r in enumerate(self.table):
+            n = 5 * int(r[4]) * int(r[5]) * int(r[6])
+            self.block(U, b)[:, g:-g, g:-g, g:-g] = P[o:o + n].reshape(5, r[6], r[5], r[4])
+            o += n
+        return U
+
+    def to_packed(self, U):
+        g = self.ng
+        return np.concatenate([self.block(U, b)[:, g:-g, g:-g, g:-g].reshape(-1)
+                               for b in range(len(self.table))])
+
+    def fill_ghosts(self, U):
+        if _load().orc_smr_fill_ghosts(self._ref(), _ptr(U)) != 0:
+            raise ValueError("inconsistent SMR mesh")
+
+    def rhs(self, U):
+        L = np.zeros_like(U)
+        if _load().orc_smr_rhs(self._ref(), _ptr(U), _ptr(L)) != 0:
+            raise ValueError("inconsistent SMR mesh")
+        return L
+
+    def rk_step(self, U, dt, rk=2):
+        Un = np.array(U, dtype=np.float64, copy=True)
+        if _load().orc_smr_rk_step(self._ref(), _ptr(Un), float(dt), int(rk)) != 0:
+            raise ValueError("inconsistent SMR mesh")
+        return Un
+
+    def new_dt(self, U, cfl):
+        return float(_load().orc_smr_new_dt(self._ref(), _ptr(U), float(cfl)))
+
+    def totals(self, U):
+        """Sum of U dV over every leaf's interior, per conserved variable."""
+        g = self.ng
+        tot = np.zeros(5)
+        for b, r in enumerate(self.table):
+            dv = np.prod([self.length[d] / (self.root_nx[d] << int(r[0])) for d in range(3)])
+            tot += self.block(U, b)[:, g:-g, g:-g, g:-g].sum(axis=(1, 2, 3)) * dv
+        return tot

@@ -150,3 +150,85 @@ def sedov(n, e_blast=1.0, r0=0.02, rho=1.0, p_amb=1.0e-5, gamma=5.0 / 3.0, lo=-0
     p[inside] += (gamma - 1.0) * e_blast / (ncell * dv)
     zero = np.zeros(shp)
     return _cons(np.full(shp, rho), zero, zero, zero, p, gamma), ncell
+
+
+def nested_refinement_blocks(root_nx=128, root_block=32, fine_block=16, levels=2):
+    """Leaf MeshBlocks of a static nested refinement on the periodic box [-1/2, 1/2]^3:
+    a root grid of root_nx^3 cells in root_block^3 blocks, and `levels` refined levels,
+    level l covering the central cube of side 2^-l in fine_block^3 blocks (cell size
+    halves per level).  Blocks covered by a finer level are not leaves and are omitted.
+
+    Returns an int32 array of rows (level, lx1, lx2, lx3, nx1, nx2, nx3), where
+    (lx1, lx2, lx3) is the block's first cell in the cell index space of its level
+    (root_nx * 2^level cells per direction)."""
+    rows = []
+
+    def region(level):  # index range [lo, hi) of the refined cube at `level`
+        n = root_nx << level
+        side = n >> level  # the cube's side, 2^-level of the box, in level cells
+        return (n - side) // 2, (n + side) // 2
+
+    for level in range(levels + 1):
+        bs = root_block if level == 0 else fine_block
+        n = root_nx << level
+        lo, hi = (0, n) if level == 0 else region(level)
+        nxt = region(level + 1) if level < levels else None
+        for bz in range(lo, hi, bs):
+            for by in range(lo, hi, bs):
+                for bx in range(lo, hi, bs):
+                    if nxt is not None:
+                        # covered if the block lies inside the next level's cube
+                        c_lo, c_hi = nxt[0] // 2, nxt[1] // 2
+                        if all(c_lo <= b and b + bs <= c_hi for b in (bx, by, bz)):
+                            continue
+                    rows.append([level, bx, by, bz, bs, bs, bs])
+    return np.ascontiguousarray(np.array(rows, dtype=np.int32))
+
+
+def block_cell_centres(table, root_nx, lo=-0.5, length=1.0):
+    """Per leaf block, the cell-centre coordinates (x1, x2, x3) as 1-D arrays."""
+    out = []
+    for r in np.asarray(table):
+        lev = int(r[0])
+        dx = length / (root_nx << lev)
+        out.append(tuple(lo + (r[1 + d] + np.arange(r[4 + d]) + 0.5) * dx for d in range(3)))
+    return out
+
+
+def sedov_blocks(table, root_nx, e_blast=1.0, r0=0.02, rho=1.0, p_amb=1.0e-5,
+                 gamma=5.0 / 3.0, lo=-0.5, length=1.0):
+    """Sedov deposit on leaf blocks of several levels: thermal energy e_blast spread
+    uniformly by volume over the cells whose centres lie at r < r0.  Returns the
+    interior data packed block after block as [block][var][k][j][i]."""
+    tab = np.asarray(table)
+    cents = block_cell_centres(tab, root_nx, lo, length)
+    vol_in = 0.0
+    masks = []
+    for r, (x, y, z) in zip(tab, cents):
+        rr = np.sqrt(x[None, None, :] ** 2 + y[None, :, None] ** 2 + z[:, None, None] ** 2)
+        m = rr < r0
+        masks.append(m)
+        vol_in += m.sum() * (length / (root_nx << int(r[0]))) ** 3
+    if vol_in == 0.0:
+        raise ValueError("blast radius smaller than a cell")
+    parts = []
+    for r, m in zip(tab, masks):
+        p = np.where(m, p_amb + (gamma - 1.0) * e_blast / vol_in, p_amb)
+        z = np.zeros_like(p)
+        parts.append(_cons(np.full_like(p, rho), z, z, z, p, gamma).reshape(-1))
+    return np.concatenate(parts)
+
+
+def field_blocks(table, root_nx, fn, gamma=5.0 / 3.0, lo=-0.5, length=1.0):
+    """Conserved variables from a primitive-state function fn(x, y, z) -> (rho, v1, v2,
+    v3, p) evaluated at the cell centres of every leaf; packed block after block."""
+    parts = []
+    for r, (x, y, z) in zip(np.asarray(table), block_cell_centres(table, root_nx, lo, length)):
+        shape = (len(z), len(y), len(x))
+        Xg = np.broadcast_to(x[None, None, :], shape)
+        Yg = np.broadcast_to(y[None, :, None], shape)
+        Zg = np.broadcast_to(z[:, None, None], shape)
+        rho, v1, v2, v3, p = fn(Xg, Yg, Zg)
+        parts.append(_cons(rho * np.ones(shape), v1 * np.ones(shape), v2 * np.ones(shape),
+                           v3 * np.ones(shape), p * np.ones(shape), gamma).reshape(-1))
+    return np.concatenate(parts)

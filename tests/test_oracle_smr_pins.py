@@ -1,0 +1,154 @@
+"""Pins of the static-refinement (SMR) oracle: prolongation and restriction against their
+definitions, a uniform state across levels, composite conservation with flux correction
+(and its failure without, as a negative control), equality with the uniform-grid oracle
+when every block is on one level, and the Sedov-Taylor blast radius across levels."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import pgen
+
+G53 = 5.0 / 3.0
+
+
+def small_table():
+    # root 32^3 in 8^3 blocks, level 1 over the central half, level 2 over the central
+    # quarter, 8^3 blocks: 56 + 56 + 64 leaves, 90,112 cells
+    return pgen.nested_refinement_blocks(32, 8, 8, 2)
+
+
+def test_small_mesh_geometry():
+    t = small_table()
+    assert [int((t[:, 0] == l).sum()) for l in range(3)] == [56, 56, 64]
+    # the leaves tile the box: volumes add up to 1
+    vol = sum(np.prod(r[4:7]) * (1.0 / (32 << int(r[0]))) ** 3 for r in t)
+    assert math.isclose(vol, 1.0, rel_tol=1e-15)
+    big = pgen.nested_refinement_blocks()
+    assert [int((big[:, 0] == l).sum()) for l in range(3)] == [56, 448, 512]
+
+
+def test_prolongation_exact_on_linear_data():
+    rng = np.random.default_rng(0)
+    for _ in range(100):
+        uc, a = rng.normal(size=1)[0], rng.normal(size=3)
+        um, up = uc - a, uc + a
+        for hi in [(0, 0, 0), (1, 0, 1), (1, 1, 1), (0, 1, 0)]:
+            expect = uc + sum((0.25 if h else -0.25) * a[d] for d, h in enumerate(hi))
+            assert math.isclose(oracle.prolong(uc, um, up, hi), expect, rel_tol=1e-14,
+                                abs_tol=1e-14)
+
+
+def test_restriction_of_prolongation_is_identity():
+    rng = np.random.default_rng(1)
+    for _ in range(200):
+        uc = rng.normal()
+        um, up = uc + rng.normal(size=3), uc + rng.normal(size=3)
+        fine = [oracle.prolong(uc, um, up, (i, j, k)) for k in (0, 1) for j in (0, 1)
+                for i in (0, 1)]
+        assert math.isclose(oracle.restrict(fine), uc, rel_tol=1e-14, abs_tol=1e-15)
+
+
+def test_prolongation_is_limited_at_extrema():
+    # a coarse extremum has zero minmod slope: all fine values equal the coarse value
+    assert oracle.prolong(2.0, [1.0, 1.0, 1.0], [1.5, 0.5, 1.0], (1, 0, 1)) == 2.0
+
+
+def test_uniform_state_bitwise_across_levels():
+    t = small_table()
+    m = oracle.SmrMesh(t, (32, 32, 32))
+    P = pgen.field_blocks(t, 32, lambda x, y, z: (1.3, 0.4, -0.2, 0.3, 0.7))
+    U = m.from_packed(P)
+    U1 = m.rk_step(U, 1e-3)
+    assert np.array_equal(m.to_packed(U1), P)
+
+
+def _smooth_blocks(t, root_nx):
+    def fn(x, y, z):
+        tp = 2 * np.pi
+        rho = 1.0 + 0.3 * np.sin(tp * x) * np.cos(tp * y)
+        v1 = 0.5 * np.sin(tp * y + 0.3)
+        v2 = 0.4 * np.cos(tp * z)
+        v3 = 0.3 * np.sin(tp * x + tp * z)
+        p = 1.0 + 0.2 * np.cos(tp * (x + y + z))
+        return rho, v1, v2, v3, p
+    return pgen.field_blocks(t, root_nx, fn)
+
+
+def test_composite_conservation_and_negative_control():
+    t = small_table()
+    P = _smooth_blocks(t, 32)
+    res = {}
+    for fc in (True, False):
+        m = oracle.SmrMesh(t, (32, 32, 32), flux_correction=fc)
+        U = m.from_packed(P)
+        tot0 = m.totals(U)
+        dt = m.new_dt(U, 0.3)
+        for _ in range(3):
+            U = m.rk_step(U, dt)
+        res[fc] = np.abs(m.totals(U) - tot0) / (np.abs(tot0) + 1.0)
+    assert res[True].max() < 1e-13, res[True]
+    # without the correction the level interfaces leak, far above round-off
+    assert res[False].max() > 1e-7, res[False]
+
+
+def test_single_level_equals_uniform_oracle():
+    # every block on level 0: the SMR oracle must reproduce the uniform-grid oracle
+    t = pgen.nested_refinement_blocks(16, 8, 8, 0)
+    P = _smooth_blocks(t, 16)
+    m = oracle.SmrMesh(t, (16, 16, 16))
+    U = m.from_packed(P)
+    # global array from the blocks
+    G = np.zeros((5, 16, 16, 16))
+    g, o = m.ng, 0
+    for b, r in enumerate(t):
+        G[:, r[3]:r[3] + 8, r[2]:r[2] + 8, r[1]:r[1] + 8] = P[o:o + 5 * 512].reshape(5, 8, 8, 8)
+        o += 5 * 512
+    grid = oracle.Grid((16, 16, 16))
+    dt = oracle.new_dt(G, grid, 0.3)
+    assert dt == m.new_dt(U, 0.3)
+    Gn, _ = oracle.rk_step(G, grid, dt, 2)
+    Un = m.to_packed(m.rk_step(U, dt))
+    o = 0
+    for r in t:
+        blk = Un[o:o + 5 * 512].reshape(5, 8, 8, 8)
+        assert np.array_equal(blk, Gn[:, r[3]:r[3] + 8, r[2]:r[2] + 8, r[1]:r[1] + 8])
+        o += 5 * 512
+
+
+def _shock_radius(m, U, t):
+    """Mean radius of the density maximum along the six axis directions and the eight
+    diagonals, from the leaf blocks' cell centres."""
+    cents = pgen.block_cell_centres(t, 32)
+    g = m.ng
+    pts, vals = [], []
+    for b, (x, y, z) in enumerate(cents):
+        rho = m.block(U, b)[0, g:-g, g:-g, g:-g]
+        X, Y, Z = np.meshgrid(x, y, z, indexing="ij")
+        pts.append(np.stack([X.T.ravel(), Y.T.ravel(), Z.T.ravel()], axis=1))
+        vals.append(rho.ravel())
+    pts = np.concatenate(pts)
+    vals = np.concatenate(vals)
+    r = np.sqrt((pts ** 2).sum(axis=1))
+    # radial profile in thin shells; the shock sits at the density peak
+    edges = np.linspace(0.0, 0.12, 49)
+    idx = np.digitize(r, edges)
+    prof = np.array([vals[idx == i].mean() if np.any(idx == i) else 0 for i in range(1, 49)])
+    k = int(np.argmax(prof))
+    return 0.5 * (edges[k] + edges[k + 1])
+
+
+def test_sedov_taylor_radius_across_levels():
+    t = small_table()
+    m = oracle.SmrMesh(t, (32, 32, 32))
+    U = m.from_packed(pgen.sedov_blocks(t, 32))
+    t_end, time = 1.2e-3, 0.0
+    while time < t_end:
+        dt = min(m.new_dt(U, 0.3), t_end - time)
+        U = m.rk_step(U, dt)
+        time += dt
+    R = _shock_radius(m, U, t)
+    R_st = 1.15 * (1.0 * t_end ** 2 / 1.0) ** 0.2  # Sedov-Taylor, gamma = 5/3
+    dx2 = 1.0 / 128
+    assert abs(R - R_st) < 1.0 * dx2, (R, R_st)

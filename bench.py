@@ -32,7 +32,7 @@ BLOCK_NX = (64, 64, 64)
 WORKLOAD = "256^3 periodic, 64 MeshBlocks of 64^3, PLM+HLLC+RK2, k^-2 turbulence Mach 0.5"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
-# Algorithmic work per cell and stage (derivations in the design doc):
+# Algorithmic work per cell and stage:
 #  FP64 flops of the scheme (each +,-,*,/,sqrt counted once): cons->prim 11, PLM
 #  (slope once per cell, 2 face states) 150, HLLC 3 faces x 99, divergence 45, RK
 #  update 17.5 (mean of the two stages), CFL 21 on the last stage (10.5 mean)
@@ -41,6 +41,50 @@ FLOP_PER_CELL_STAGE = 531.0
 BYTES_STAGE = {1: 80.0, 2: 120.0}
 # FP64 peak from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# DRAM bytes per cell of the stage kernels (dram__bytes_read.sum + dram__bytes_write.sum
+# of one ncu capture, 192^3 in 64^3 blocks; the per-cell figure carries over to 256^3 in
+# the same blocks), valid for the kernel sources with this hash (else traffic = null)
+TRAFFIC_SRC_HASH = "f96e956152a8b019824fe315504131ce7ca96d75"
+TRAFFIC_B_PER_CELL = {"fp64": (87.36, 130.85), "mixed": (86.07, 129.11)}
+
+
+def kernel_source_hash():
+    """sha1 over the sha1sum lines of the stage kernel's sources (as sha1sum prints them)."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_2409_16053_gb300", "csrc")
+    lines = ""
+    for f in ("ak_stage.cu", "hydro_ops.cuh", "fastmath.cuh"):
+        h = hashlib.sha1(open(os.path.join(d, f), "rb").read()).hexdigest()
+        lines += f"{h}  ../paper_2409_16053_gb300/csrc/{f}\n"
+    return hashlib.sha1(lines.encode()).hexdigest()
+
+
+def traffic_per_launch(form, cells):
+    """Measured DRAM bytes per stage launch (mean of the two stages), or None if the
+    kernel changed since the counters were taken."""
+    if kernel_source_hash() != TRAFFIC_SRC_HASH:
+        return None
+    b1, b2 = TRAFFIC_B_PER_CELL[form]
+    return 0.5 * (b1 + b2) * cells
+
+
+def linear_wave_l1(ak, precision, n=32):
+    """L1 error of the 3D sound-wave test (n^3, one block, PLM+HLLC+RK2, CFL 0.3, one
+    period), run on the GPU outside the timed region."""
+    import numpy as np
+    import pgen
+    U0, T = pgen.linear_wave((n, n, n))
+    m = ak.Mesh((n, n, n), (n, n, n), precision=precision, ref_rho=1.0, ref_p=0.6)
+    m.upload(U0)
+    t, dt = 0.0, m.new_dt()
+    while t < T:
+        dt = min(dt, T - t)
+        dn = m.step(dt)
+        t += dt
+        dt = dn
+    U = m.download()
+    m.close()
+    return float(np.sqrt(sum(np.mean(np.abs(U[k] - U0[k])) ** 2 for k in range(5))))
 
 
 def dist_env():
@@ -71,9 +115,9 @@ class ClockSampler:
         self.path = None
 
     def start(self):
-        out_dir = os.path.join(ROOT, "gpurun_out")
-        os.makedirs(out_dir, exist_ok=True)
-        self.path = os.path.join(out_dir, f"clocks_bench_{os.getpid()}.csv")
+        import tempfile
+        fd, self.path = tempfile.mkstemp(prefix="ak_clocks_", suffix=".csv")
+        os.close(fd)
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
@@ -93,8 +137,10 @@ class ClockSampler:
             self.proc.kill()
         self.fh.close()
         sm, smmax, reasons = [], [], set()
+        lines = open(self.path).read().splitlines()
+        os.unlink(self.path)
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        for line in lines:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -243,6 +289,27 @@ def run_reference(args):
     return 0
 
 
+def run_profile_case(args):
+    """Small case for ncu captures: 192^3 in 27 MeshBlocks of 64^3 (two registers of
+    ~0.34 GB, larger than L2), one form, `steps` graph-replayed RK2 steps."""
+    import torch
+    import pgen
+    from paper_2409_16053_gb300 import ak
+    root = (192, 192, 192)
+    prec = ak.AK_MIXED if args.form == "mixed" else ak.AK_FP64
+    U0 = pgen.turbulence(root, seed=1, kmin=2, kmax=8, mach=0.5)
+    m = ak.Mesh(root, (64, 64, 64), precision=prec, ref_rho=1.0, ref_p=1.0)
+    m.upload(U0)
+    dt = m.new_dt()
+    for _ in range(args.steps):
+        dt = m.step(0.0)
+    c = m.counters()
+    m.close()
+    print(json.dumps({"case": "profile", "form": args.form, "cells": 192 ** 3,
+                      "steps": args.steps, "dt": dt, "counters": c}), flush=True)
+    return 0 if c[:2] == [0, 0] else 1
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -250,9 +317,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", default="bench", choices=["bench", "profile"])
+    ap.add_argument("--form", default="fp64", choices=["fp64", "mixed"])
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.case == "profile":
+        return run_profile_case(args)
 
     ws, rank, local = dist_env()
     import torch
@@ -294,19 +365,19 @@ def main():
 
     peaks, peak_kind = load_peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    # FP64 stage kernel: ALU bound (FP64 pipe)
+    # FP64 stage kernel: ALU bound (FP64 pipe); per launch = mean of the two stages
     st64 = 0.5 * (r64["stage1_ms"] + r64["stage2_ms"])
     ach64 = FLOP_PER_CELL_STAGE * cells / (st64 * 1e-3) / 1e12
-    # mixed stage kernel: HBM roofline on the algorithmic bytes
-    bytes_mx = (BYTES_STAGE[1] + BYTES_STAGE[2]) * cells
-    ach_mx = bytes_mx / ((rmx["stage1_ms"] + rmx["stage2_ms"]) * 1e-3) / 1e9
-    traffic = {}
-    tp = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tp):
-        try:
-            traffic = json.load(open(tp))
-        except ValueError:
-            traffic = {}
+    # mixed stage kernel: HBM roofline on the algorithmic bytes per launch
+    stmx = 0.5 * (rmx["stage1_ms"] + rmx["stage2_ms"])
+    bytes_mx = 0.5 * (BYTES_STAGE[1] + BYTES_STAGE[2]) * cells
+    ach_mx = bytes_mx / (stmx * 1e-3) / 1e9
+    l1 = None
+    if rank == 0:
+        e64 = linear_wave_l1(ak, ak.AK_FP64)
+        emx = linear_wave_l1(ak, ak.AK_MIXED)
+        l1 = {"test": "3D sound wave, 32^3, amplitude 1e-6, one period, PLM+HLLC+RK2",
+              "fp64": e64, "mixed": emx, "mixed_over_fp64": emx / e64}
     line = {
         "metric": METRIC, "value": value64, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t64 / args.steps, "higher_is_better": True,
@@ -316,20 +387,21 @@ def main():
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "roofline": {"bound": "alu", "achieved": ach64, "peak": FP64_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": ach64 / FP64_PEAK_TFLOPS,
-                     "traffic": traffic.get("stage_fp64"),
+                     "traffic": traffic_per_launch("fp64", cells),
                      "kernel": "stage_kernel<PLM, FP64> (mean of stage 1 and 2 launches)",
                      "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz"},
         "mixed": {
             "value": valuemx, "unit": UNIT, "ms_per_step": tmx / args.steps, "dtype": "f32+f64",
             "roofline": {"bound": "hbm", "achieved": ach_mx, "peak": hbm, "unit": "GB/s",
-                         "frac": ach_mx / hbm, "traffic": traffic.get("stage_mixed"),
-                         "kernel": "stage_kernel<PLM, mixed> (stage 1 + stage 2)",
+                         "frac": ach_mx / hbm, "traffic": traffic_per_launch("mixed", cells),
+                         "kernel": "stage_kernel<PLM, mixed> (mean of stage 1 and 2 launches)",
                          "peak_source": f"{peak_kind} hbm_gbs"},
             "e2e": e2e_mx,
         },
         "stage_ms": {"fp64": [r64["stage1_ms"], r64["stage2_ms"]],
                      "mixed": [rmx["stage1_ms"], rmx["stage2_ms"]]},
         "counters": {"fp64": r64["counters"], "mixed": rmx["counters"]},
+        "l1_error": l1,
         "e2e": e2e,
         "gpu_launches": 5 * args.steps * 2,
         "clocks": clk,

@@ -118,8 +118,8 @@ def test_single_level_equals_uniform_oracle():
 
 
 def _shock_radius(m, U, t):
-    """Mean radius of the density maximum along the six axis directions and the eight
-    diagonals, from the leaf blocks' cell centres."""
+    """Radius of the density maximum of the shell-averaged radial density profile, from
+    the leaf blocks' cell centres."""
     cents = pgen.block_cell_centres(t, 32)
     g = m.ng
     pts, vals = [], []

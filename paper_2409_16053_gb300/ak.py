@@ -188,18 +188,28 @@ def uniform_block_table(root_nx, block_nx):
 
 
 class Mesh:
-    """A uniform periodic mesh of equal MeshBlocks with torch-owned registers."""
+    """A periodic mesh of MeshBlocks with torch-owned registers: a uniform mesh of equal
+    blocks (block_nx), or any leaf table (rows level, lx1, lx2, lx3, nx1, nx2, nx3) of a
+    statically refined mesh (table)."""
 
-    def __init__(self, root_nx, block_nx, *, recon=AK_PLM, rk=2, precision=AK_FP64,
-                 gamma=5.0 / 3.0, cfl=0.3, xmin=(0.0, 0.0, 0.0), xmax=(1.0, 1.0, 1.0),
-                 ref_rho=1.0, ref_p=1.0, device="cuda", stream=None):
+    def __init__(self, root_nx, block_nx=None, *, table=None, recon=AK_PLM, rk=2,
+                 precision=AK_FP64, gamma=5.0 / 3.0, cfl=0.3, xmin=(0.0, 0.0, 0.0),
+                 xmax=(1.0, 1.0, 1.0), ref_rho=1.0, ref_p=1.0, device="cuda", stream=None):
         import torch
         self.torch = torch
         self.root_nx = tuple(int(v) for v in root_nx)
-        self.block_nx = tuple(int(v) for v in block_nx)
-        self.nb = tuple(self.root_nx[d] // self.block_nx[d] for d in range(3))
         self.ng = 2 if recon == AK_PLM else 3
-        self.table = uniform_block_table(self.root_nx, self.block_nx)
+        if table is None:
+            self.block_nx = tuple(int(v) for v in block_nx)
+            self.nb = tuple(self.root_nx[d] // self.block_nx[d] for d in range(3))
+            self.table = uniform_block_table(self.root_nx, self.block_nx)
+            self.uniform = True
+        else:
+            self.table = np.ascontiguousarray(np.asarray(table, dtype=np.int32))
+            self.block_nx = tuple(int(v) for v in self.table[0, 4:7])
+            self.uniform = bool((self.table[:, 0] == 0).all() and
+                                (self.table[:, 4:7] == self.table[0, 4:7]).all())
+            self.nb = tuple(self.root_nx[d] // self.block_nx[d] for d in range(3))
         self.nblocks = int(self.table.shape[0])
         self.device = torch.device(device)
         self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
@@ -222,7 +232,7 @@ class Mesh:
                      for _ in range(self.nreg)]
         for r, t in enumerate(self.regs):
             ak_mesh_bind(self.handle, r, t.data_ptr())
-        self.interior_count = self.nblocks * 5 * int(np.prod(self.block_nx))
+        self.interior_count = 5 * int(np.prod(self.table[:, 4:7].astype(np.int64), axis=1).sum())
 
     def close(self):
         if getattr(self, "handle", None):
@@ -252,15 +262,25 @@ class Mesh:
         return np.ascontiguousarray(P).reshape(5, self.root_nx[2], self.root_nx[1],
                                                self.root_nx[0])
 
-    def upload(self, U, reg=0):
-        host = self.torch.from_numpy(self.pack(U)).pin_memory()
+    def upload_packed(self, P, reg=0):
+        """Interior data packed block after block as [block][var][k][j][i]."""
+        P = np.ascontiguousarray(P, dtype=np.float64).reshape(-1)
+        assert P.size == self.interior_count, (P.size, self.interior_count)
+        host = self.torch.from_numpy(P).pin_memory()
         ak_upload(self.handle, reg, host.data_ptr())
         self.stream.synchronize()  # the pinned buffer may be freed after return
 
-    def download(self, reg=0):
+    def download_packed(self, reg=0):
         host = self.torch.empty(self.interior_count, dtype=self.torch.float64).pin_memory()
         ak_download(self.handle, reg, host.data_ptr())
-        return self.unpack(host.numpy().copy())
+        return host.numpy().copy()
+
+    def upload(self, U, reg=0):
+        """Global (5, n3, n2, n1) array of a uniform mesh."""
+        self.upload_packed(self.pack(U), reg)
+
+    def download(self, reg=0):
+        return self.unpack(self.download_packed(reg))
 
     def fill_ghosts(self, reg=0):
         ak_fill_ghosts(self.handle, reg)

@@ -38,13 +38,40 @@ static ak_status einval(const char* msg) {
 static int stage_in_reg(int rk, int s) { return s == 1 ? 0 : (rk == 2 ? 1 : s - 1); }
 static int stage_out_reg(int rk, int s) { return s == rk ? 0 : s; }
 
+namespace {
+
+// Host view of the levels and leaf maps while a mesh is built.
+struct HostIndex {
+  int nlev = 0, ng = 0;
+  int N[AK_MAX_LEVELS][3];
+  int bs[AK_MAX_LEVELS][3];
+  int md[AK_MAX_LEVELS][3];
+  int off[AK_MAX_LEVELS + 1];
+  std::vector<int32_t> map;
+  const int32_t* B = nullptr;
+
+  static long long wrap(long long v, long long n) {
+    long long r = v % n;
+    return r < 0 ? r + n : r;
+  }
+  // leaf containing level-l cell (x, y, z) (wrapped), or -1
+  int leaf(int l, long long x, long long y, long long z) const {
+    if (l < 0 || l >= nlev || bs[l][0] == 0) return -1;
+    long long c[3] = {wrap(x, N[l][0]) / bs[l][0], wrap(y, N[l][1]) / bs[l][1],
+                      wrap(z, N[l][2]) / bs[l][2]};
+    return map[off[l] + (c[2] * md[l][1] + c[1]) * md[l][0] + c[0]];
+  }
+};
+
+}  // namespace
+
 extern "C" ak_status ak_mesh_create(const ak_mesh_desc* d, void* cuda_stream, ak_mesh** out) {
   if (!d || !out) return einval("ak_mesh_create: NULL argument");
   *out = nullptr;
   if (d->nblocks < 1 || !d->blocks) return einval("ak_mesh_create: need nblocks >= 1 and a block table");
   if (d->recon != AK_PLM && d->recon != AK_PPM4) return einval("ak_mesh_create: recon must be AK_PLM or AK_PPM4");
-  const int ng_need = d->recon == AK_PLM ? 2 : 3;
-  if (d->nghost != ng_need) return einval("ak_mesh_create: nghost must be 2 for PLM and 3 for PPM4");
+  const int ng = d->recon == AK_PLM ? 2 : 3;
+  if (d->nghost != ng) return einval("ak_mesh_create: nghost must be 2 for PLM and 3 for PPM4");
   if (d->rk != 2 && d->rk != 3) return einval("ak_mesh_create: rk must be 2 or 3");
   if (d->precision != AK_FP64 && d->precision != AK_MIXED)
     return einval("ak_mesh_create: precision must be AK_FP64 or AK_MIXED");
@@ -56,85 +83,271 @@ extern "C" ak_status ak_mesh_create(const ak_mesh_desc* d, void* cuda_stream, ak
     if (!(d->xmax[a] > d->xmin[a])) return einval("ak_mesh_create: xmax must exceed xmin");
     if (d->root_nx[a] < 1) return einval("ak_mesh_create: root_nx must be positive");
   }
-  // this version: a uniform level-0 mesh of equal blocks tiling root_nx
-  const int32_t* B = d->blocks;
-  const int nx1 = B[4], nx2 = B[5], nx3 = B[6];
-  if (nx1 < ng_need || nx2 < ng_need || nx3 < ng_need)
-    return einval("ak_mesh_create: block sizes must be >= nghost");
-  if (d->root_nx[0] % nx1 || d->root_nx[1] % nx2 || d->root_nx[2] % nx3)
-    return einval("ak_mesh_create: blocks must tile root_nx");
-  const int nb1 = d->root_nx[0] / nx1, nb2 = d->root_nx[1] / nx2, nb3 = d->root_nx[2] / nx3;
-  if ((long long)nb1 * nb2 * nb3 != d->nblocks)
-    return einval("ak_mesh_create: nblocks does not match root_nx / block size");
-  std::vector<int32_t> map((size_t)nb1 * nb2 * nb3, -1), loc((size_t)3 * d->nblocks);
-  for (int b = 0; b < d->nblocks; ++b) {
-    const int32_t* e = B + (size_t)AK_BLOCK_INTS * b;
-    if (e[0] != 0) return einval("ak_mesh_create: only level-0 (uniform) meshes are supported");
-    if (e[4] != nx1 || e[5] != nx2 || e[6] != nx3)
-      return einval("ak_mesh_create: all blocks must have the same size");
-    if (e[1] % nx1 || e[2] % nx2 || e[3] % nx3 || e[1] < 0 || e[2] < 0 || e[3] < 0 ||
-        e[1] >= d->root_nx[0] || e[2] >= d->root_nx[1] || e[3] >= d->root_nx[2])
-      return einval("ak_mesh_create: block origin not on the block lattice");
-    const int bx = e[1] / nx1, by = e[2] / nx2, bz = e[3] / nx3;
-    int32_t& slot = map[((size_t)bz * nb2 + by) * nb1 + bx];
+
+  // ---- levels, block sizes, leaf maps ------------------------------------------------
+  HostIndex X;
+  X.ng = ng;
+  X.B = d->blocks;
+  const int nb = d->nblocks;
+  for (int b = 0; b < nb; ++b) {
+    const int32_t* e = d->blocks + (size_t)AK_BLOCK_INTS * b;
+    if (e[0] < 0 || e[0] >= AK_MAX_LEVELS) return einval("ak_mesh_create: level out of range");
+    if (e[0] + 1 > X.nlev) X.nlev = e[0] + 1;
+  }
+  memset(X.bs, 0, sizeof(X.bs));
+  for (int l = 0; l < X.nlev; ++l)
+    for (int a = 0; a < 3; ++a) {
+      const long long n = (long long)d->root_nx[a] << l;
+      if (n > (1ll << 30)) return einval("ak_mesh_create: level index space too large");
+      X.N[l][a] = (int)n;
+    }
+  for (int b = 0; b < nb; ++b) {
+    const int32_t* e = d->blocks + (size_t)AK_BLOCK_INTS * b;
+    const int l = e[0];
+    for (int a = 0; a < 3; ++a) {
+      if (e[4 + a] < ng) return einval("ak_mesh_create: block sizes must be >= nghost");
+      if (X.bs[l][a] == 0) X.bs[l][a] = e[4 + a];
+      if (X.bs[l][a] != e[4 + a])
+        return einval("ak_mesh_create: all blocks of one level must have the same size");
+      if (e[1 + a] < 0 || e[1 + a] >= X.N[l][a] || e[1 + a] % e[4 + a])
+        return einval("ak_mesh_create: block origin not on its level's block lattice");
+      if (X.N[l][a] % e[4 + a]) return einval("ak_mesh_create: blocks must tile each level");
+      if (X.N[l][a] < e[4 + a] + 2 * ng && X.nlev > 1)
+        return einval("ak_mesh_create: a refined mesh needs more than one block per level and direction");
+      if (X.nlev > 1 && (e[4 + a] % 2 || e[1 + a] % 2))
+        return einval("ak_mesh_create: refined meshes need even block sizes and origins");
+    }
+  }
+  X.off[0] = 0;
+  for (int l = 0; l < X.nlev; ++l) {
+    long long cnt = 1;
+    for (int a = 0; a < 3; ++a) {
+      X.md[l][a] = X.bs[l][a] ? X.N[l][a] / X.bs[l][a] : 0;
+      cnt *= X.md[l][a];
+    }
+    if (X.off[l] + cnt > (1ll << 28)) return einval("ak_mesh_create: too many block slots");
+    X.off[l + 1] = X.off[l] + (int)cnt;
+  }
+  X.map.assign((size_t)X.off[X.nlev], -1);
+  for (int b = 0; b < nb; ++b) {
+    const int32_t* e = d->blocks + (size_t)AK_BLOCK_INTS * b;
+    const int l = e[0];
+    const long long c = ((long long)(e[3] / X.bs[l][2]) * X.md[l][1] + e[2] / X.bs[l][1]) * X.md[l][0] +
+                        e[1] / X.bs[l][0];
+    int32_t& slot = X.map[X.off[l] + c];
     if (slot != -1) return einval("ak_mesh_create: overlapping blocks");
     slot = b;
-    loc[3 * b] = bx;
-    loc[3 * b + 1] = by;
-    loc[3 * b + 2] = bz;
+  }
+  // exact tiling: no leaf inside a coarser leaf, and the volumes add up to the box
+  {
+    const int L = X.nlev - 1;
+    long long vol = 0, box = (long long)X.N[L][0] * X.N[L][1] * X.N[L][2];
+    for (int b = 0; b < nb; ++b) {
+      const int32_t* e = d->blocks + (size_t)AK_BLOCK_INTS * b;
+      const int l = e[0];
+      vol += (long long)e[4] * e[5] * e[6] << (3 * (L - l));
+      for (int lc = 0; lc < l; ++lc)
+        for (int c = 0; c < 8; ++c) {
+          const int sh = l - lc;
+          long long x = (e[1] + ((c & 1) ? e[4] - 1 : 0)) >> sh;
+          long long y = (e[2] + ((c & 2) ? e[5] - 1 : 0)) >> sh;
+          long long z = (e[3] + ((c & 4) ? e[6] - 1 : 0)) >> sh;
+          if (X.leaf(lc, x, y, z) >= 0) return einval("ak_mesh_create: a block overlaps a coarser block");
+        }
+    }
+    if (vol != box) return einval("ak_mesh_create: the blocks do not tile the domain");
+  }
+  // ghost zones: neighbours at most one level apart, and prolongation stencils that only
+  // read coarse cells filled by copies or restrictions
+  if (X.nlev > 1) {
+    for (int b = 0; b < nb; ++b) {
+      const int32_t* e = d->blocks + (size_t)AK_BLOCK_INTS * b;
+      const int l = e[0];
+      for (int k = -ng; k < e[6] + ng; ++k)
+        for (int j = -ng; j < e[5] + ng; ++j)
+          for (int i = -ng; i < e[4] + ng; ++i) {
+            if (i >= 0 && i < e[4] && j >= 0 && j < e[5] && k >= 0 && k < e[6]) continue;
+            const long long x = e[1] + i, y = e[2] + j, z = e[3] + k;
+            if (X.leaf(l, x, y, z) >= 0) continue;
+            if (X.leaf(l + 1, 2 * x, 2 * y, 2 * z) >= 0) continue;
+            const long long cx = HostIndex::wrap(x, X.N[l][0]) >> 1,
+                            cy = HostIndex::wrap(y, X.N[l][1]) >> 1,
+                            cz = HostIndex::wrap(z, X.N[l][2]) >> 1;
+            if (X.leaf(l - 1, cx, cy, cz) < 0)
+              return einval("ak_mesh_create: neighbouring blocks differ by more than one level");
+            for (int a = 0; a < 3; ++a)
+              for (int s2 = -1; s2 <= 1; s2 += 2) {
+                long long q[3] = {cx, cy, cz};
+                q[a] += s2;
+                if (X.leaf(l - 1, q[0], q[1], q[2]) < 0 &&
+                    X.leaf(l, 2 * q[0], 2 * q[1], 2 * q[2]) < 0)
+                  return einval("ak_mesh_create: refinement not properly nested (prolongation "
+                                "stencil reaches two levels down)");
+              }
+          }
+    }
   }
 
-  // 64-byte alignment: the embedded tensor maps require it
+  // ---- the mesh object, block table, flux-correction faces, work list ------------------
   ak_mesh* m = (ak_mesh*)aligned_alloc(64, (sizeof(ak_mesh) + 63) / 64 * 64);
   if (!m) return AK_ENOMEM;
   memset(m, 0, sizeof(ak_mesh));
   m->desc = *d;
   m->stream = (cudaStream_t)cuda_stream;
   m->nreg = d->rk == 3 ? 3 : 2;
-  ak_geom& g = m->geom;
-  g.nx1 = nx1;
-  g.nx2 = nx2;
-  g.nx3 = nx3;
-  g.ng = ng_need;
-  g.p1 = nx1 + 2 * g.ng;
-  g.p2 = nx2 + 2 * g.ng;
-  g.p3 = nx3 + 2 * g.ng;
-  g.s1 = (g.p1 + 3) / 4 * 4;
-  g.front = (4 - g.ng % 4) % 4;
-  g.var_stride = (long long)g.s1 * g.p2 * g.p3;
-  g.block_stride = ((g.front + AK_NVAR * g.var_stride + 31) / 32) * 32;
-  g.nblocks = d->nblocks;
-  g.nbx1 = nb1;
-  g.nbx2 = nb2;
-  g.nbx3 = nb3;
-  g.dx1 = (d->xmax[0] - d->xmin[0]) / d->root_nx[0];
-  g.dx2 = (d->xmax[1] - d->xmin[1]) / d->root_nx[1];
-  g.dx3 = (d->xmax[2] - d->xmin[2]) / d->root_nx[2];
-  g.gamma = d->gamma;
-  m->reg_bytes = sizeof(double) * (size_t)g.block_stride * g.nblocks;
-  m->h_blocks = (int32_t*)malloc(sizeof(int32_t) * AK_BLOCK_INTS * d->nblocks);
-  m->h_offsets = (int64_t*)malloc(sizeof(int64_t) * d->nblocks);
-  if (!m->h_blocks || !m->h_offsets) {
+  m->ng = ng;
+  m->nlev = X.nlev;
+  m->multilevel = X.nlev > 1;
+  m->nblocks = nb;
+  m->h_blocks = (int32_t*)malloc(sizeof(int32_t) * AK_BLOCK_INTS * nb);
+  m->h_offsets = (int64_t*)malloc(sizeof(int64_t) * nb);
+  m->h_blk = (ak_block*)calloc(nb, sizeof(ak_block));
+  if (!m->h_blocks || !m->h_offsets || !m->h_blk) {
     ak_mesh_destroy(m);
     return AK_ENOMEM;
   }
-  memcpy(m->h_blocks, B, sizeof(int32_t) * AK_BLOCK_INTS * d->nblocks);
+  memcpy(m->h_blocks, d->blocks, sizeof(int32_t) * AK_BLOCK_INTS * nb);
   m->desc.blocks = m->h_blocks;
-  for (int b = 0; b < d->nblocks; ++b) m->h_offsets[b] = (int64_t)b * g.block_stride + g.front;
-  // x3 segments per block: enough CTAs to fill the GPU a few times over
-  {
-    const long long tiles = (long long)d->nblocks * ((nx1 + 15) / 16) * ((nx2 + 15) / 16);
-    int seg = 1;
-    while (tiles * seg < 4 * 152 && nx3 / (2 * seg) >= 8) seg *= 2;
-    m->seg3 = seg;
+  const long long front = (4 - ng % 4) % 4;
+  long long reg_elems = 0;
+  std::vector<long long> pack_off(nb + 1, 0), pad_off(nb + 1, 0);
+  std::vector<int4> fc;
+  long long fc_cells = 0;
+  for (int b = 0; b < nb; ++b) {
+    const int32_t* e = d->blocks + (size_t)AK_BLOCK_INTS * b;
+    ak_block& B = m->h_blk[b];
+    B.level = e[0];
+    B.lx1 = e[1];
+    B.lx2 = e[2];
+    B.lx3 = e[3];
+    B.nx1 = e[4];
+    B.nx2 = e[5];
+    B.nx3 = e[6];
+    B.p1 = B.nx1 + 2 * ng;
+    B.p2 = B.nx2 + 2 * ng;
+    B.p3 = B.nx3 + 2 * ng;
+    B.s1 = (B.p1 + 3) / 4 * 4;
+    B.var_stride = (long long)B.s1 * B.p2 * B.p3;
+    B.off = reg_elems + front;
+    reg_elems += ((front + AK_NVAR * B.var_stride + 31) / 32) * 32;
+    m->h_offsets[b] = B.off;
+    B.dx1 = (d->xmax[0] - d->xmin[0]) / X.N[B.level][0];
+    B.dx2 = (d->xmax[1] - d->xmin[1]) / X.N[B.level][1];
+    B.dx3 = (d->xmax[2] - d->xmin[2]) / X.N[B.level][2];
+    pack_off[b + 1] = pack_off[b] + (long long)B.nx1 * B.nx2 * B.nx3;
+    pad_off[b + 1] = pad_off[b] + B.var_stride;
+    // faces next to a refined region: whole face or nothing
+    const int n[3] = {B.nx1, B.nx2, B.nx3};
+    for (int f = 0; f < 6; ++f) {
+      B.ovr[f] = -1;
+      if (!m->multilevel) continue;
+      const int dd = f / 2, side = f % 2;
+      const int a1 = dd == 0 ? 1 : 0, a2 = dd == 2 ? 1 : 2;  // face cell = t2 * n[a1] + t1
+      int refined = 0, total = 0;
+      for (int t2 = 0; t2 < n[a2]; ++t2)
+        for (int t1 = 0; t1 < n[a1]; ++t1) {
+          long long q[3];
+          q[dd] = (long long)(side ? n[dd] : -1) + e[1 + dd];
+          q[a1] = (long long)t1 + e[1 + a1];
+          q[a2] = (long long)t2 + e[1 + a2];
+          ++total;
+          if (X.leaf(B.level, q[0], q[1], q[2]) < 0 &&
+              X.leaf(B.level + 1, 2 * q[0], 2 * q[1], 2 * q[2]) >= 0)
+            ++refined;
+        }
+      if (refined != 0 && refined != total) {
+        ak_mesh_destroy(m);
+        return einval("ak_mesh_create: a block face is only partly next to a refined region");
+      }
+      if (refined) {
+        B.ovr[f] = (int)fc_cells;
+        fc.push_back(make_int4(b, f, (int)fc_cells, total));
+        fc_cells += total;
+      }
+    }
   }
-  cudaError_t e = cudaMalloc(&m->d_block_map, sizeof(int32_t) * map.size());
-  if (e == cudaSuccess) e = cudaMalloc(&m->d_block_loc, sizeof(int32_t) * loc.size());
-  if (e == cudaSuccess) e = cudaMalloc(&m->d_sc, sizeof(ak_dev_scalars));
-  if (e == cudaSuccess)
-    e = cudaMemcpy(m->d_block_map, map.data(), sizeof(int32_t) * map.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(m->d_block_loc, loc.data(), sizeof(int32_t) * loc.size(), cudaMemcpyHostToDevice);
+  m->reg_bytes = sizeof(double) * (size_t)reg_elems;
+  m->interior_cells = pack_off[nb];
+  m->padded_cells = pad_off[nb];
+  m->nfc = (int)fc.size();
+  m->fc_cells = fc_cells;
+  // stage work list: 16x16 column tiles, x3 split so that the GPU is filled a few times
+  std::vector<ak_work> work;
+  {
+    long long tiles = 0;
+    int minz = 1 << 30;
+    for (int b = 0; b < nb; ++b) {
+      tiles += (long long)((m->h_blk[b].nx1 + 15) / 16) * ((m->h_blk[b].nx2 + 15) / 16);
+      minz = m->h_blk[b].nx3 < minz ? m->h_blk[b].nx3 : minz;
+    }
+    int seg = 1;
+    while (tiles * seg < 4 * 152 && minz / (2 * seg) >= 8) seg *= 2;
+    for (int b = 0; b < nb; ++b) {
+      const ak_block& B = m->h_blk[b];
+      const int kseg = (B.nx3 + seg - 1) / seg;
+      for (int s = 0; s < seg; ++s)
+        for (int j0 = 0; j0 < B.nx2; j0 += 16)
+          for (int i0 = 0; i0 < B.nx1; i0 += 16) {
+            ak_work w;
+            w.block = b;
+            w.i0 = i0;
+            w.j0 = j0;
+            w.k0 = s * kseg;
+            w.k1 = (s + 1) * kseg < B.nx3 ? (s + 1) * kseg : B.nx3;
+            w.pad = 0;
+            if (w.k0 < w.k1) work.push_back(w);
+          }
+    }
+  }
+  m->nwork = (int)work.size();
+  // level table
+  ak_level lev[AK_MAX_LEVELS];
+  for (int l = 0; l < X.nlev; ++l) {
+    lev[l].n1 = X.N[l][0];
+    lev[l].n2 = X.N[l][1];
+    lev[l].n3 = X.N[l][2];
+    lev[l].bs1 = X.bs[l][0];
+    lev[l].bs2 = X.bs[l][1];
+    lev[l].bs3 = X.bs[l][2];
+    lev[l].md1 = X.md[l][0];
+    lev[l].md2 = X.md[l][1];
+    lev[l].md3 = X.md[l][2];
+    lev[l].map_off = X.off[l];
+  }
+
+  cudaError_t e = cudaSuccess;
+  auto dmalloc = [&](void** p, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(p, bytes < 8 ? 8 : bytes);
+  };
+  auto h2d = [&](void* dst, const void* src, size_t bytes) {
+    if (e == cudaSuccess && bytes) e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+  };
+  dmalloc((void**)&m->d_blk, sizeof(ak_block) * nb);
+  dmalloc((void**)&m->d_lev, sizeof(ak_level) * X.nlev);
+  dmalloc((void**)&m->d_map, sizeof(int32_t) * X.map.size());
+  dmalloc((void**)&m->d_fc, sizeof(int4) * fc.size());
+  dmalloc((void**)&m->d_fcbuf, sizeof(double) * AK_NVAR * (size_t)fc_cells);
+  dmalloc((void**)&m->d_pack_off, sizeof(long long) * (nb + 1));
+  dmalloc((void**)&m->d_pad_off, sizeof(long long) * (nb + 1));
+  dmalloc((void**)&m->d_work, sizeof(ak_work) * work.size());
+  dmalloc((void**)&m->d_sc, sizeof(ak_dev_scalars));
+  h2d(m->d_blk, m->h_blk, sizeof(ak_block) * nb);
+  h2d(m->d_lev, lev, sizeof(ak_level) * X.nlev);
+  h2d(m->d_map, X.map.data(), sizeof(int32_t) * X.map.size());
+  h2d(m->d_fc, fc.data(), sizeof(int4) * fc.size());
+  h2d(m->d_pack_off, pack_off.data(), sizeof(long long) * (nb + 1));
+  h2d(m->d_pad_off, pad_off.data(), sizeof(long long) * (nb + 1));
+  h2d(m->d_work, work.data(), sizeof(ak_work) * work.size());
+  m->md.blocks = m->d_blk;
+  m->md.levels = m->d_lev;
+  m->md.map = m->d_map;
+  m->md.fc = m->d_fc;
+  m->md.fcbuf = m->d_fcbuf;
+  m->md.nblocks = nb;
+  m->md.nlev = X.nlev;
+  m->md.ng = ng;
+  m->md.nfc = m->nfc;
+  m->md.gamma = d->gamma;
   if (e == cudaSuccess) e = ak_stage_prepare(m);
   if (e == cudaSuccess) {
     ak_dev_scalars s;
@@ -155,12 +368,19 @@ extern "C" void ak_mesh_destroy(ak_mesh* m) {
   if (!m) return;
   if (m->graph_exec) cudaGraphExecDestroy(m->graph_exec);
   if (m->graph) cudaGraphDestroy(m->graph);
-  cudaFree(m->d_block_map);
-  cudaFree(m->d_block_loc);
+  cudaFree(m->d_blk);
+  cudaFree(m->d_lev);
+  cudaFree(m->d_map);
+  cudaFree(m->d_fc);
+  cudaFree(m->d_fcbuf);
+  cudaFree(m->d_pack_off);
+  cudaFree(m->d_pad_off);
+  cudaFree(m->d_work);
   cudaFree(m->d_sc);
   cudaFree(m->d_staging);
   free(m->h_blocks);
   free(m->h_offsets);
+  free(m->h_blk);
   free(m);
 }
 
@@ -169,11 +389,11 @@ extern "C" ak_status ak_mesh_layout(const ak_mesh* m, int32_t* nregisters, size_
   if (!m) return einval("ak_mesh_layout: NULL mesh");
   if (nregisters) *nregisters = m->nreg;
   if (register_bytes) *register_bytes = m->reg_bytes;
-  if (block_offset) memcpy(block_offset, m->h_offsets, sizeof(int64_t) * m->geom.nblocks);
-  if (strides) {
-    strides[0] = m->geom.var_stride;
-    strides[1] = (int64_t)m->geom.s1 * m->geom.p2;
-    strides[2] = m->geom.s1;
+  if (block_offset) memcpy(block_offset, m->h_offsets, sizeof(int64_t) * m->nblocks);
+  if (strides) {  // of block 0; blocks of other sizes follow the same rule
+    strides[0] = m->h_blk[0].var_stride;
+    strides[1] = (int64_t)m->h_blk[0].s1 * m->h_blk[0].p2;
+    strides[2] = m->h_blk[0].s1;
     strides[3] = 1;
   }
   return AK_OK;
@@ -209,15 +429,20 @@ int ak_encode_register_tmap(ak_mesh* m, int reg) {
       return 1;
     encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
   }
-  const ak_geom& g = m->geom;
-  char* base = (char*)m->reg[reg] + sizeof(double) * g.front;
+  if (m->multilevel) return 4;  // the bulk-tensor view needs blocks of one size
+  const ak_block& g = m->h_blk[0];
+  for (int b = 1; b < m->nblocks; ++b)
+    if (m->h_blk[b].nx1 != g.nx1 || m->h_blk[b].nx2 != g.nx2 || m->h_blk[b].nx3 != g.nx3) return 4;
+  const long long front = g.off;
+  const long long block_stride = m->nblocks > 1 ? m->h_blk[1].off - m->h_blk[0].off : 0;
+  char* base = (char*)m->reg[reg] + sizeof(double) * front;
   if (((uintptr_t)base & 15u) != 0) return 2;
   cuuint64_t dims[5] = {(cuuint64_t)g.p1, (cuuint64_t)g.p2, (cuuint64_t)g.p3, 5,
-                        (cuuint64_t)g.nblocks};
+                        (cuuint64_t)m->nblocks};
   cuuint64_t strides[4] = {sizeof(double) * (cuuint64_t)g.s1,
                            sizeof(double) * (cuuint64_t)g.s1 * g.p2,
                            sizeof(double) * (cuuint64_t)g.var_stride,
-                           sizeof(double) * (cuuint64_t)g.block_stride};
+                           sizeof(double) * (cuuint64_t)(block_stride ? block_stride : 32)};
   cuuint32_t box[5] = {16, 16, 1, 5, 1};
   cuuint32_t estr[5] = {1, 1, 1, 1, 1};
   CUresult r = encode(&m->tmap[reg], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 5, base, dims, strides, box,
@@ -262,6 +487,7 @@ extern "C" ak_status ak_stage(ak_mesh* m, int32_t stage, double dt) {
     if (s != AK_OK) return s;
   }
   if (dt > 0.0) AK_CUDA_TRY(ak_launch_set_dt(m, dt));
+  if (m->nfc) AK_CUDA_TRY(ak_launch_flux_correction(m, m->reg[stage_in_reg(m->desc.rk, stage)]));
   ak_status s = enqueue_stage(m, stage);
   if (s != AK_OK) return s;
   if (stage == m->desc.rk) AK_CUDA_TRY(ak_launch_finalize_dt(m, 0));
@@ -301,7 +527,9 @@ extern "C" ak_status ak_new_dt(ak_mesh* m, int32_t reg, double* dt_out) {
 
 static ak_status enqueue_step(ak_mesh* m) {
   for (int st = 1; st <= m->desc.rk; ++st) {
-    AK_CUDA_TRY(ak_launch_fill_ghosts(m, m->reg[stage_in_reg(m->desc.rk, st)]));
+    double* in = m->reg[stage_in_reg(m->desc.rk, st)];
+    AK_CUDA_TRY(ak_launch_fill_ghosts(m, in));
+    if (m->nfc) AK_CUDA_TRY(ak_launch_flux_correction(m, in));
     ak_status s = enqueue_stage(m, st);
     if (s != AK_OK) return s;
   }
@@ -356,8 +584,7 @@ extern "C" ak_status ak_step(ak_mesh* m, double dt, double* dt_next) {
 }
 
 static ak_status ensure_staging(ak_mesh* m) {
-  const size_t need = sizeof(double) * (size_t)m->geom.nblocks * AK_NVAR * m->geom.nx1 *
-                      m->geom.nx2 * m->geom.nx3;
+  const size_t need = sizeof(double) * (size_t)AK_NVAR * m->interior_cells;
   if (m->d_staging && m->staging_bytes >= need) return AK_OK;
   cudaFree(m->d_staging);
   m->d_staging = nullptr;

@@ -1,5 +1,5 @@
-// Internal declarations of libak: the mesh object, device scalars and the kernel
-// launchers shared by the translation units of the library.
+// Internal declarations of libak: the mesh object, its device tables, the device
+// scalars and the kernel launchers shared by the translation units of the library.
 #pragma once
 
 #include <cuda.h>  // CUtensorMap (tensor maps are encoded through the runtime's entry point)
@@ -10,6 +10,7 @@
 
 #define AK_NVAR 5
 #define AK_MAX_REG 3
+#define AK_MAX_LEVELS 16
 
 // Floors of the primitive recovery (counted when applied).  The paper gives no hydro
 // floor values; these are the library's choice.
@@ -26,19 +27,41 @@ struct ak_dev_scalars {
   unsigned long long reported[4];   // counters already reported to the host
 };
 
-// Geometry of a uniform mesh of equal blocks, passed by value to kernels.
-struct ak_geom {
-  int nx1, nx2, nx3;     // interior cells per block
-  int ng;                // ghost cells per side
+// One leaf MeshBlock (device table entry).
+struct ak_block {
+  long long off;         // element offset of the block's first ghost cell in a register
+  long long var_stride;  // s1 * p2 * p3
+  int nx1, nx2, nx3;     // interior cells
+  int lx1, lx2, lx3;     // first interior cell in its level's index space
+  int level;
   int p1, p2, p3;        // padded extents nx + 2 ng
   int s1;                // row pitch: p1 rounded up to a multiple of 4 elements
-  long long front;       // elements before a block's first ghost cell, chosen so that
-                         // every row's interior starts on a 32-byte boundary
-  long long var_stride;  // s1 * p2 * p3
-  long long block_stride;
-  int nblocks;
-  int nbx1, nbx2, nbx3;  // blocks per direction
+  int ovr[6];            // flux-correction faces (x1-, x1+, x2-, x2+, x3-, x3+): offset (in
+                         // face cells) of the face's corrected fluxes, or -1
   double dx1, dx2, dx3;
+};
+
+// One refinement level: its cell count, block size and leaf map.
+struct ak_level {
+  int n1, n2, n3;        // cells per direction in this level's index space
+  int bs1, bs2, bs3;     // block size of the level's leaves (0 if the level is empty)
+  int md1, md2, md3;     // map extent in blocks
+  int map_off;           // start of the level's map in the map table
+};
+
+// One CTA of the stage kernel: a column tile of one block over planes [k0, k1).
+struct ak_work {
+  int block, i0, j0, k0, k1, pad;
+};
+
+// Everything the kernels need about the mesh, passed by value.
+struct ak_meshdev {
+  const ak_block* blocks;
+  const ak_level* levels;
+  const int32_t* map;   // leaf id or -1, per level per block slot
+  const int4* fc;       // flux-correction faces: (block, face, first face cell, n cells)
+  double* fcbuf;        // corrected coarse-face fluxes, [face cell][5]
+  int nblocks, nlev, ng, nfc;
   double gamma;
 };
 
@@ -47,21 +70,34 @@ struct ak_mesh {
   int tmap_ok[AK_MAX_REG];
   ak_mesh_desc desc;
   cudaStream_t stream;
-  ak_geom geom;
   int nreg;
   double* reg[AK_MAX_REG];
   size_t reg_bytes;
-  int32_t* d_block_map;     // [nbx3][nbx2][nbx1] -> block id
-  int32_t* d_block_loc;     // [nblocks][3] block coordinates (in blocks)
-  int32_t* h_blocks;        // copy of the desc's block table
-  int64_t* h_offsets;       // element offset of each block
+  int ng, nlev, multilevel;
+  int nblocks;
+  long long interior_cells;     // over all blocks
+  long long padded_cells;       // over all blocks
+  int32_t* h_blocks;            // copy of the desc's block table
+  int64_t* h_offsets;           // element offset of each block
+  ak_block* h_blk;              // host copy of the block table
+  ak_block* d_blk;
+  ak_level* d_lev;
+  int32_t* d_map;
+  int4* d_fc;
+  double* d_fcbuf;
+  long long* d_pack_off;        // interior prefix sums per block (nblocks + 1)
+  long long* d_pad_off;         // padded-cell prefix sums per block (nblocks + 1)
+  ak_work* d_work;
+  int nwork;
+  int nfc;
+  long long fc_cells;
+  ak_meshdev md;
   ak_dev_scalars* d_sc;
-  double* d_staging;        // interior staging buffer for ak_upload / ak_download
+  double* d_staging;            // interior staging buffer for ak_upload / ak_download
   size_t staging_bytes;
   cudaGraph_t graph;
   cudaGraphExec_t graph_exec;
   int graph_ready;
-  int seg3;                 // x3 segments per block for the stage launch
 };
 
 // Error message of the last failing call on this thread.
@@ -69,6 +105,7 @@ void ak_set_error(const char* fmt, ...);
 
 // ---- launchers (return cudaSuccess or the launch error) ----
 cudaError_t ak_launch_fill_ghosts(const ak_mesh* m, double* reg);
+cudaError_t ak_launch_flux_correction(const ak_mesh* m, const double* reg);
 cudaError_t ak_launch_pack(const ak_mesh* m, const double* reg, double* packed);
 cudaError_t ak_launch_unpack(const ak_mesh* m, const double* packed, double* reg);
 cudaError_t ak_launch_stage(const ak_mesh* m, int stage, const double* u_in, const double* u0,
@@ -77,6 +114,5 @@ cudaError_t ak_launch_cfl(const ak_mesh* m, const double* reg);
 cudaError_t ak_launch_finalize_dt(const ak_mesh* m, int use_next_as_dt);
 cudaError_t ak_launch_set_dt(const ak_mesh* m, double dt);
 cudaError_t ak_stage_prepare(const ak_mesh* m);
-// Encodes m->tmap[reg] for register `reg` (5-D: x, y, z, var, block of doubles, box of
-// one 16x16 tile plane of all 5 variables); returns 0 on success.
+// Encodes m->tmap[reg] for register `reg` (uniform meshes); returns 0 on success.
 int ak_encode_register_tmap(ak_mesh* m, int reg);

@@ -138,6 +138,16 @@ __device__ __forceinline__ double half(double x) {
   return __hiloint2double(hi - 0x00100000, __double2loint(x));
 }
 
+// The corrected (fine-mean) flux of one coarse face cell from the correction buffer.
+__device__ __forceinline__ void corrected_flux(const double* buf, int cell, double* f) {
+#pragma unroll
+  for (int v = 0; v < 5; ++v) f[v] = buf[(long long)cell * 5 + v];
+}
+__device__ __forceinline__ void corrected_flux(const double* buf, int cell, float* f) {
+#pragma unroll
+  for (int v = 0; v < 5; ++v) f[v] = f64_to_f32(buf[(long long)cell * 5 + v]);
+}
+
 template <int NG, bool MIXED, int TX, int TY, bool TMA_OUT>
 struct StageCfg {
   using R = typename std::conditional<MIXED, float, double>::type;
@@ -165,9 +175,10 @@ struct StageCfg {
 
 template <int NG, bool MIXED, int TX, int TY, bool TMA_OUT>
 __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
-    stage_kernel(const double* __restrict__ uin, const double* u0, double* uout, ak_geom g,
-                 Bg bg, double a, double b, int form, ak_dev_scalars* sc, int nseg,
-                 int last_stage, const __grid_constant__ CUtensorMap tmap_out) {
+    stage_kernel(const double* __restrict__ uin, const double* u0, double* uout, ak_meshdev md,
+                 const ak_work* __restrict__ work, Bg bg, double a, double b, int form,
+                 ak_dev_scalars* sc, int last_stage,
+                 const __grid_constant__ CUtensorMap tmap_out) {
   // form: 0 = first stage U + dt L; 1 = RK2 final (U0 + U + dt L) / 2;
   //       2 = a U0 + b (U + dt L)
   using C = StageCfg<NG, MIXED, TX, TY, TMA_OUT>;
@@ -186,21 +197,14 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
   __shared__ double red[NT / 32];
 
   const int tid = threadIdx.x;
-  const int ntx = (g.nx1 + TX - 1) / TX, nty = (g.nx2 + TY - 1) / TY;
-  int bid = blockIdx.x;
-  const int tile_x = bid % ntx;
-  bid /= ntx;
-  const int tile_y = bid % nty;
-  bid /= nty;
-  const int seg = bid % nseg;
-  const int blk = bid / nseg;
-  const int i0 = tile_x * TX, j0 = tile_y * TY;
-  const int kseg = (g.nx3 + nseg - 1) / nseg;
-  const int k0 = seg * kseg;
-  const int k1 = min(g.nx3, k0 + kseg);
-  if (k0 >= k1) return;
+  // this CTA's column tile of one MeshBlock, and that block's geometry
+  const ak_work w = work[blockIdx.x];
+  const ak_block g = md.blocks[w.block];
+  const int blk = w.block;
+  const int i0 = w.i0, j0 = w.j0, k0 = w.k0, k1 = w.k1;
+  int kcur = k0;  // the plane whose x1/x2 faces are being solved
 
-  const long long boff = (long long)blk * g.block_stride + g.front;
+  const long long boff = g.off;
   const double* ub = uin + boff;
   const Counters cn{&sc->counters[0], &sc->counters[1]};
   const double dt = sc->dt;
@@ -316,12 +320,18 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
       const int fx = it % (TX + 1), fy = it / (TX + 1);
       if (i0 + fx <= g.nx1 && j0 + fy < g.nx2) {
         R l[5], r[5], f[5];
+        const int fi = i0 + fx;
+        const int ov = fi == 0 ? g.ovr[0] : (fi == g.nx1 ? g.ovr[1] : -1);
+        if (ov >= 0) {  // coarse face next to a refined region: the fine-flux mean
+          corrected_flux(md.fcbuf, ov + kcur * g.nx2 + j0 + fy, f);
+        } else {
 #pragma unroll
-        for (int v = 0; v < 5; ++v) {
-          l[v] = e1hi[(v * TY + fy) * C1 + fx];       // cell i-1: column fx
-          r[v] = e1lo[(v * TY + fy) * C1 + fx + 1];   // cell i:   column fx+1
+          for (int v = 0; v < 5; ++v) {
+            l[v] = e1hi[(v * TY + fy) * C1 + fx];       // cell i-1: column fx
+            r[v] = e1lo[(v * TY + fy) * C1 + fx + 1];   // cell i:   column fx+1
+          }
+          solve(0, l, r, bg, f);
         }
-        solve(0, l, r, bg, f);
 #pragma unroll
         for (int v = 0; v < 5; ++v) f1[(v * TY + fy) * (TX + 1) + fx] = f[v];
       }
@@ -332,12 +342,18 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
       const int fx = it % TX, fy = it / TX;
       if (i0 + fx < g.nx1 && j0 + fy <= g.nx2) {
         R l[5], r[5], f[5];
+        const int fj = j0 + fy;
+        const int ov = fj == 0 ? g.ovr[2] : (fj == g.nx2 ? g.ovr[3] : -1);
+        if (ov >= 0) {
+          corrected_flux(md.fcbuf, ov + kcur * g.nx1 + i0 + fx, f);
+        } else {
 #pragma unroll
-        for (int v = 0; v < 5; ++v) {
-          l[v] = e2hi[(v * (TY + 2) + fy) * TX + fx];      // cell j-1: row fy
-          r[v] = e2lo[(v * (TY + 2) + fy + 1) * TX + fx];  // cell j:   row fy+1
+          for (int v = 0; v < 5; ++v) {
+            l[v] = e2hi[(v * (TY + 2) + fy) * TX + fx];      // cell j-1: row fy
+            r[v] = e2lo[(v * (TY + 2) + fy + 1) * TX + fx];  // cell j:   row fy+1
+          }
+          solve(1, l, r, bg, f);
         }
-        solve(1, l, r, bg, f);
 #pragma unroll
         for (int v = 0; v < 5; ++v) f2[(v * (TY + 1) + fy) * TX + fx] = f[v];
       }
@@ -353,7 +369,10 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
     R lo_a[5], hi_a[5], lo_b[5];
     x3_edges(k0 - 1, lo_a, hi_a);
     x3_edges(k0, lo_b, hi3);
-    solve(2, hi_a, lo_b, bg, f3m);
+    if (k0 == 0 && g.ovr[4] >= 0)
+      corrected_flux(md.fcbuf, g.ovr[4] + cj * g.nx1 + ci, f3m);
+    else
+      solve(2, hi_a, lo_b, bg, f3m);
   }
   __syncthreads();
   load_plane(k0 + NG);
@@ -389,6 +408,7 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
       }
     }
     const R* pl = ring + slot(k) * 5 * NPL;
+    kcur = k;
     R lo3[5], hi3n[5];
 
     if constexpr (C::SPLIT) {
@@ -409,7 +429,10 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
       x2_faces();
     }
     if (own) {
-      solve(2, hi3, lo3, bg, f3p);
+      if (k + 1 == g.nx3 && g.ovr[5] >= 0)
+        corrected_flux(md.fcbuf, g.ovr[5] + cj * g.nx1 + ci, f3p);
+      else
+        solve(2, hi3, lo3, bg, f3p);
 #pragma unroll
       for (int v = 0; v < 5; ++v) hi3[v] = hi3n[v];
     }
@@ -523,6 +546,8 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
   }
 }
 
+static Bg make_bg(const ak_mesh* m);
+
 template <int NG, bool MIXED, int TX, int TY, bool TMA_OUT>
 static cudaError_t launch(const ak_mesh* m, const double* uin, const double* u0, double* uout,
                           int out_reg, double a, double b, int rk2_final, int last_stage,
@@ -531,24 +556,113 @@ static cudaError_t launch(const ak_mesh* m, const double* uin, const double* u0,
   auto kern = stage_kernel<NG, MIXED, TX, TY, TMA_OUT>;
   if (prepare_only)
     return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  const ak_geom& g = m->geom;
-  const int ntx = (g.nx1 + TX - 1) / TX, nty = (g.nx2 + TY - 1) / TY;
-  const long long nblk = (long long)g.nblocks * ntx * nty * m->seg3;
+  const Bg bg = make_bg(m);
+  const int form = rk2_final ? 1 : (a == 0.0 ? 0 : 2);
+  kern<<<(unsigned)m->nwork, TX * TY, smem, m->stream>>>(uin, u0, uout, m->md, m->d_work, bg, a,
+                                                          b, form, m->d_sc, last_stage,
+                                                          m->tmap[out_reg]);
+  return cudaGetLastError();
+}
+
+// Flux correction at level boundaries (Section 2): for every coarse face cell next to a
+// refined region, the mean of the 2x2 fine fluxes through it, computed from the fine
+// block's cells (interior and prolonged ghosts) with the same reconstruction and HLLC
+// code the stage kernel runs, so the fine block's own update sees the same fluxes.
+template <int NG, bool MIXED>
+__global__ void flux_correction_kernel(const double* __restrict__ reg, ak_meshdev md, Bg bg,
+                                       ak_dev_scalars* sc, long long ncells) {
+  using R = typename std::conditional<MIXED, float, double>::type;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= ncells) return;
+  int lo = 0, hi = md.nfc - 1;  // face entry holding cell t
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (md.fc[mid].z <= t) lo = mid; else hi = mid - 1;
+  }
+  const int4 F = md.fc[lo];
+  const int cell = (int)(t - F.z);
+  const ak_block B = md.blocks[F.x];
+  const int d = F.y >> 1, side = F.y & 1;
+  const int n[3] = {B.nx1, B.nx2, B.nx3};
+  const int org[3] = {B.lx1, B.lx2, B.lx3};
+  const int a1 = d == 0 ? 1 : 0, a2 = d == 2 ? 1 : 2;
+  int loc[3];
+  loc[d] = side ? n[d] - 1 : 0;
+  loc[a1] = cell % n[a1];
+  loc[a2] = cell / n[a1];
+  const ak_level LV = md.levels[B.level];
+  const int nl[3] = {LV.n1, LV.n2, LV.n3};
+  int N[3];
+  for (int q = 0; q < 3; ++q) {
+    int v = org[q] + loc[q] + (q == d ? (side ? 1 : -1) : 0);
+    N[q] = v < 0 ? v + nl[q] : (v >= nl[q] ? v - nl[q] : v);
+  }
+  const ak_level LF = md.levels[B.level + 1];
+  const int fine = md.map[LF.map_off + ((2 * N[2] / LF.bs3) * LF.md2 + 2 * N[1] / LF.bs2) * LF.md1 +
+                          2 * N[0] / LF.bs1];
+  const ak_block Fb = md.blocks[fine];
+  const int forg[3] = {Fb.lx1, Fb.lx2, Fb.lx3};
+  const Counters cn{&sc->counters[0], &sc->counters[1]};
+  R sum[5] = {R(0), R(0), R(0), R(0), R(0)};
+  for (int u2 = 0; u2 < 2; ++u2)
+    for (int u1 = 0; u1 < 2; ++u1) {
+      int q[3];
+      q[d] = (side ? 2 * N[d] : 2 * N[d] + 1) - forg[d];
+      q[a1] = 2 * N[a1] + u1 - forg[a1];
+      q[a2] = 2 * N[a2] + u2 - forg[a2];
+      const int fi = q[d] + (side ? 0 : 1);  // the face between fine cells fi-1 and fi
+      R W[2 * NG][5];
+#pragma unroll
+      for (int mm = 0; mm < 2 * NG; ++mm) {
+        int c[3] = {q[0], q[1], q[2]};
+        c[d] = fi - NG + mm;
+        const long long e = Fb.off + ((long long)(c[2] + NG) * Fb.p2 + (c[1] + NG)) * Fb.s1 +
+                            (c[0] + NG);
+        double u[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) u[v] = reg[e + v * Fb.var_stride];
+        c2p(u, W[mm], bg, cn);
+      }
+      R lo_a[5], hi_a[5], lo_b[5], hi_b[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        R qa[2 * NG - 1], qb[2 * NG - 1];
+#pragma unroll
+        for (int mm = 0; mm < 2 * NG - 1; ++mm) {
+          qa[mm] = W[mm][v];
+          qb[mm] = W[mm + 1][v];
+        }
+        edges<NG>(qa, lo_a[v], hi_a[v]);
+        edges<NG>(qb, lo_b[v], hi_b[v]);
+      }
+      R f[5];
+      solve(d, hi_a, lo_b, bg, f);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) sum[v] += f[v];
+    }
+  double* out = md.fcbuf + (long long)(B.ovr[F.y] + cell) * 5;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    if constexpr (MIXED)
+      out[v] = f32_to_f64(R(0.25) * sum[v]);
+    else
+      out[v] = R(0.25) * sum[v];
+  }
+}
+
+static Bg make_bg(const ak_mesh* m) {
   Bg bg;
-  bg.gamma = g.gamma;
-  bg.gamma_f = (float)g.gamma;
-  bg.gm1 = g.gamma - 1.0;
-  bg.kq = (g.gamma + 1.0) / (2.0 * g.gamma);
+  const double gamma = m->desc.gamma;
+  bg.gamma = gamma;
+  bg.gamma_f = (float)gamma;
+  bg.gm1 = gamma - 1.0;
+  bg.kq = (gamma + 1.0) / (2.0 * gamma);
   bg.rho = m->desc.ref_rho;
-  bg.ug = m->desc.ref_p / (g.gamma - 1.0);
+  bg.ug = m->desc.ref_p / (gamma - 1.0);
   bg.rho_f = (float)bg.rho;
   bg.ug_f = (float)bg.ug;
   bg.ug_floor_f = (float)(AK_UG_FLOOR - bg.ug);
-  const int form = rk2_final ? 1 : (a == 0.0 ? 0 : 2);
-  kern<<<(unsigned)nblk, TX * TY, smem, m->stream>>>(uin, u0, uout, g, bg, a, b, form,
-                                                      m->d_sc, m->seg3, last_stage,
-                                                      m->tmap[out_reg]);
-  return cudaGetLastError();
+  return bg;
 }
 
 static cudaError_t dispatch(const ak_mesh* m, const double* uin, const double* u0, double* uout,
@@ -585,4 +699,23 @@ cudaError_t ak_launch_stage(const ak_mesh* m, int stage, const double* u_in, con
 // once at mesh creation, outside any stream capture).
 cudaError_t ak_stage_prepare(const ak_mesh* m) {
   return ak::dispatch(m, nullptr, nullptr, nullptr, 0, 0.0, 0.0, 0, 0, true);
+}
+
+cudaError_t ak_launch_flux_correction(const ak_mesh* m, const double* reg) {
+  if (!m->nfc) return cudaSuccess;
+  const ak::Bg bg = ak::make_bg(m);
+  const unsigned grid = (unsigned)((m->fc_cells + 127) / 128);
+  const bool mixed = m->desc.precision == AK_MIXED;
+  if (m->desc.recon == AK_PLM) {
+    if (mixed)
+      ak::flux_correction_kernel<2, true><<<grid, 128, 0, m->stream>>>(reg, m->md, bg, m->d_sc, m->fc_cells);
+    else
+      ak::flux_correction_kernel<2, false><<<grid, 128, 0, m->stream>>>(reg, m->md, bg, m->d_sc, m->fc_cells);
+  } else {
+    if (mixed)
+      ak::flux_correction_kernel<3, true><<<grid, 128, 0, m->stream>>>(reg, m->md, bg, m->d_sc, m->fc_cells);
+    else
+      ak::flux_correction_kernel<3, false><<<grid, 128, 0, m->stream>>>(reg, m->md, bg, m->d_sc, m->fc_cells);
+  }
+  return cudaGetLastError();
 }

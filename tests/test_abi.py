@@ -97,3 +97,41 @@ def test_pack_unpack_round_trip_host(ak):
     blk = P.reshape(12, 5, 3, 4, 4)[10]
     assert blk[4, 2, 3, 1] == U[4, 3 + 2, 4 + 3, 4 + 1]
     assert np.array_equal(m.unpack(P), U)
+
+
+def _desc_table(ak, table, root, recon=0):
+    d = ak.ak_mesh_desc()
+    d.nblocks = table.shape[0]
+    d.nghost = 2 if recon == 0 else 3
+    d.blocks = table.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    for a in range(3):
+        d.xmin[a], d.xmax[a], d.root_nx[a] = -0.5, 0.5, root
+    d.recon, d.rk, d.precision = recon, 2, ak.AK_FP64
+    d.gamma, d.cfl, d.ref_rho, d.ref_p = 5 / 3, 0.3, 1.0, 1.0
+    return d
+
+
+def test_refined_mesh_validation(ak):
+    import pgen
+    out = ctypes.c_void_p()
+    # valid nested refinement: passes validation (fails later only without a GPU)
+    t = pgen.nested_refinement_blocks(32, 8, 8, 2)
+    d = _desc_table(ak, t, 32)
+    st = ak._lib.ak_mesh_create(ctypes.byref(d), None, ctypes.byref(out))
+    assert st != ak.AK_EINVAL, ak.ak_last_error()
+    if st == ak.AK_OK:
+        ak.ak_mesh_destroy(out)
+    # a level-1 block removed: the leaves no longer tile the box
+    t2 = t[1:].copy()
+    d = _desc_table(ak, t2, 32)
+    assert ak._lib.ak_mesh_create(ctypes.byref(d), None, ctypes.byref(out)) == ak.AK_EINVAL
+    # level 2 next to level 0 (two-level jump): no level-1 buffer around level 2
+    t3 = pgen.nested_refinement_blocks(32, 8, 8, 2)
+    lv1 = np.where(t3[:, 0] == 1)[0]
+    # replace level-1 leaves by their level-0 parents where possible is complex; instead
+    # move one level-2 block far away so that it overlaps a level-0 leaf
+    bad = t3.copy()
+    bad[np.where(bad[:, 0] == 2)[0][0], 1:4] = 0
+    d = _desc_table(ak, bad, 32)
+    assert ak._lib.ak_mesh_create(ctypes.byref(d), None, ctypes.byref(out)) == ak.AK_EINVAL
+    assert len(lv1) == 56

@@ -1,0 +1,157 @@
+"""Static refinement on the GPU: leaf MeshBlocks of several levels advance with one dt
+(ghost fill by copy / restriction / prolongation, flux correction at level boundaries),
+through the C-ABI, against the SMR oracle.  Cases: the small nested mesh (root 32^3 in 8^3
+blocks, two levels of 8^3 blocks, 176 leaves) with a smooth flow and with a Sedov blast,
+and the full benchmark mesh (root 128^3 in 32^3 blocks, 16^3 blocks on two levels, 1016
+leaves)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import pgen
+
+pytestmark = pytest.mark.gpu
+G53 = 5.0 / 3.0
+
+
+@pytest.fixture(scope="module")
+def ak():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_2409_16053_gb300 import build
+    build.build()
+    from paper_2409_16053_gb300 import ak as mod
+    oracle.build()
+    return mod
+
+
+def _smooth(t, root):
+    def fn(x, y, z):
+        tp = 2 * np.pi
+        return (1.0 + 0.3 * np.sin(tp * x) * np.cos(tp * y), 0.5 * np.sin(tp * y + 0.3),
+                0.4 * np.cos(tp * z), 0.3 * np.sin(tp * x + tp * z),
+                1.0 + 0.2 * np.cos(tp * (x + y + z)))
+    return pgen.field_blocks(t, root, fn)
+
+
+def _norm_diff(a, b):
+    """max over components of max |a-b| / max|b| (packed arrays, 5 vars per block)."""
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+def _per_var_diff(mesh_table, a, b):
+    """max over components of max |a-b| / S_k with S_rho = max|rho|, S_E = max|E| and
+    S_M = sqrt(max|rho| max|E|) for the momenta (a momentum scale from rho and E)."""
+    diff, scale = np.zeros(5), np.zeros(5)
+    o = 0
+    for r in mesh_table:
+        n = int(np.prod(r[4:7]))
+        A, B = a[o:o + 5 * n].reshape(5, n), b[o:o + 5 * n].reshape(5, n)
+        diff = np.maximum(diff, np.abs(A - B).max(axis=1))
+        scale = np.maximum(scale, np.abs(B).max(axis=1))
+        o += 5 * n
+    s = np.array([scale[0], 0, 0, 0, scale[4]])
+    s[1:4] = np.sqrt(scale[0] * scale[4])
+    return float(np.max(diff / s))
+
+
+def _gpu_mesh(ak, t, root, **kw):
+    return ak.Mesh((root,) * 3, table=t, xmin=(-0.5,) * 3, xmax=(0.5,) * 3, **kw)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_smr_uniform_state_bitwise(ak, precision):
+    t = pgen.nested_refinement_blocks(32, 8, 8, 2)
+    P = pgen.field_blocks(t, 32, lambda x, y, z: (1.3, 0.4, -0.2, 0.3, 0.7))
+    m = _gpu_mesh(ak, t, 32, precision=precision, ref_rho=1.0, ref_p=0.7)
+    m.upload_packed(P)
+    for _ in range(3):
+        m.step(1e-3, want_dt_next=False)
+    assert np.array_equal(m.download_packed(), P)
+    m.close()
+
+
+def test_smr_fp64_parity_smooth(ak):
+    t = pgen.nested_refinement_blocks(32, 8, 8, 2)
+    P = _smooth(t, 32)
+    om = oracle.SmrMesh(t, (32, 32, 32))
+    U = om.from_packed(P)
+    m = _gpu_mesh(ak, t, 32)
+    m.upload_packed(P)
+    dt0 = om.new_dt(U, 0.3)
+    assert math.isclose(m.new_dt(), dt0, rel_tol=1e-14)
+    for s in range(10):
+        dt = om.new_dt(U, 0.3)
+        U = om.rk_step(U, dt)
+        dn = m.step(dt)
+        if s == 0:
+            assert _per_var_diff(t, m.download_packed(), om.to_packed(U)) <= 1e-12
+            assert math.isclose(dn, om.new_dt(U, 0.3), rel_tol=1e-12)
+    assert _per_var_diff(t, m.download_packed(), om.to_packed(U)) <= 1e-11
+    assert m.counters()[:2] == [0, 0]
+    m.close()
+
+
+def test_smr_fp64_conservation(ak):
+    t = pgen.nested_refinement_blocks(32, 8, 8, 2)
+    P = _smooth(t, 32)
+    om = oracle.SmrMesh(t, (32, 32, 32))
+    tot0 = om.totals(om.from_packed(P))
+    m = _gpu_mesh(ak, t, 32)
+    m.upload_packed(P)
+    dt = m.new_dt()
+    for _ in range(10):
+        dt = m.step(dt)
+    tot = om.totals(om.from_packed(m.download_packed()))
+    assert np.all(np.abs(tot - tot0) / (np.abs(tot0) + 1.0) < 1e-13), tot - tot0
+    m.close()
+
+
+def test_smr_sedov_fp64_parity(ak):
+    t = pgen.nested_refinement_blocks(32, 8, 8, 2)
+    P = pgen.sedov_blocks(t, 32)
+    om = oracle.SmrMesh(t, (32, 32, 32))
+    U = om.from_packed(P)
+    m = _gpu_mesh(ak, t, 32, ref_rho=1.0, ref_p=1e-5)
+    m.upload_packed(P)
+    for _ in range(20):
+        dt = om.new_dt(U, 0.3)
+        U = om.rk_step(U, dt)
+        m.step(dt, want_dt_next=False)
+    a, b = m.download_packed(), om.to_packed(U)
+    assert _norm_diff(a, b) <= 1e-11, _norm_diff(a, b)
+    assert m.counters()[:2] == [0, 0]
+    m.close()
+
+
+def test_smr_mixed_close_to_oracle(ak):
+    t = pgen.nested_refinement_blocks(32, 8, 8, 2)
+    P = _smooth(t, 32)
+    om = oracle.SmrMesh(t, (32, 32, 32))
+    U = om.from_packed(P)
+    dt = om.new_dt(U, 0.3)
+    U = om.rk_step(U, dt)
+    m = _gpu_mesh(ak, t, 32, precision=1, ref_rho=1.0, ref_p=1.0)
+    m.upload_packed(P)
+    m.step(dt)
+    assert _per_var_diff(t, m.download_packed(), om.to_packed(U)) <= 2e-6
+    m.close()
+
+
+@pytest.mark.slow
+def test_smr_full_mesh_one_step_parity(ak):
+    t = pgen.nested_refinement_blocks()  # 1016 leaves, 5,767,168 cells
+    P = pgen.sedov_blocks(t, 128)
+    om = oracle.SmrMesh(t, (128, 128, 128))
+    U = om.from_packed(P)
+    dt = om.new_dt(U, 0.3)
+    U = om.rk_step(U, dt)
+    m = _gpu_mesh(ak, t, 128, ref_rho=1.0, ref_p=1e-5)
+    m.upload_packed(P)
+    m.step(dt)
+    a, b = m.download_packed(), om.to_packed(U)
+    assert _norm_diff(a, b) <= 1e-12, _norm_diff(a, b)
+    m.close()

@@ -16,6 +16,8 @@ from __future__ import annotations
 
 import argparse
 import json
+
+import numpy as np
 import os
 import statistics
 import subprocess
@@ -233,6 +235,37 @@ def e2e_form(ak, torch, precision, U0, steps):
             "finite": ok}
 
 
+def time_smr(ak, torch, precision, steps, warmup):
+    """The static-refinement workload: root 128^3 in 32^3 blocks and two nested levels of
+    16^3 blocks over the central 1/2 and 1/4 cubes (1016 leaves, 5,767,168 cells) on
+    [-1/2, 1/2]^3, Sedov deposit (energy 1 in r < 0.02, rho = 1, p = 1e-5), PLM + HLLC +
+    RK2, one dt for all levels.  A step is one graph-replayed ak_step (ghost fill with
+    restriction/prolongation, flux correction, stage, twice, and the dt reduction)."""
+    import pgen
+    t = pgen.nested_refinement_blocks()
+    P = pgen.sedov_blocks(t, 128)
+    m = ak.Mesh((128, 128, 128), table=t, precision=precision, xmin=(-0.5,) * 3,
+                xmax=(0.5,) * 3, ref_rho=1.0, ref_p=1e-5)
+    m.upload_packed(P)
+    m.new_dt()
+    for _ in range(warmup):
+        m.step(0.0, want_dt_next=False)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(m.stream)
+    for _ in range(steps):
+        m.step(0.0, want_dt_next=False)
+    b.record(m.stream)
+    b.synchronize()
+    ms = a.elapsed_time(b)
+    cells = int(np.prod(t[:, 4:7].astype(np.int64), axis=1).sum())
+    c = m.counters()
+    m.close()
+    torch.cuda.empty_cache()
+    return {"value": cells * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
+            "counters": c}
+
+
 def cpu_baseline(sample_n=96, budget_s=12.0, steps_max=None):
     """The oracle (as it stands) on this host's cores: RK2 steps of a periodic sample_n^3
     box with the benchmark's turbulence recipe until budget_s of CPU work."""
@@ -295,8 +328,21 @@ def run_profile_case(args):
     import torch
     import pgen
     from paper_2409_16053_gb300 import ak
-    root = (192, 192, 192)
     prec = ak.AK_MIXED if args.form == "mixed" else ak.AK_FP64
+    if args.case == "profile-smr":
+        t = pgen.nested_refinement_blocks()
+        m = ak.Mesh((128, 128, 128), table=t, precision=prec, xmin=(-0.5,) * 3,
+                    xmax=(0.5,) * 3, ref_rho=1.0, ref_p=1e-5)
+        m.upload_packed(pgen.sedov_blocks(t, 128))
+        m.new_dt()
+        for _ in range(args.steps):
+            m.step(0.0)
+        c = m.counters()
+        m.close()
+        print(json.dumps({"case": "profile-smr", "form": args.form, "steps": args.steps,
+                          "counters": c}), flush=True)
+        return 0 if c[:2] == [0, 0] else 1
+    root = (192, 192, 192)
     U0 = pgen.turbulence(root, seed=1, kmin=2, kmax=8, mach=0.5)
     m = ak.Mesh(root, (64, 64, 64), precision=prec, ref_rho=1.0, ref_p=1.0)
     m.upload(U0)
@@ -317,12 +363,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--case", default="bench", choices=["bench", "profile"])
+    ap.add_argument("--case", default="bench", choices=["bench", "profile", "profile-smr"])
     ap.add_argument("--form", default="fp64", choices=["fp64", "mixed"])
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
-    if args.case == "profile":
+    if args.case in ("profile", "profile-smr"):
         return run_profile_case(args)
 
     ws, rank, local = dist_env()
@@ -354,6 +400,12 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
+    smr = None
+    if rank == 0:
+        smr = {"workload": "static refinement: 128^3 root in 32^3 blocks + 2 nested levels "
+                           "of 16^3 blocks, 1016 leaves, 5,767,168 cells, Sedov, PLM+HLLC+RK2",
+               "fp64": time_smr(ak, torch, ak.AK_FP64, args.steps, args.warmup),
+               "mixed": time_smr(ak, torch, ak.AK_MIXED, args.steps, args.warmup)}
     t64 = tmax(r64["total_ms"])
     tmx = tmax(rmx["total_ms"])
     cells = ROOT_NX[0] * ROOT_NX[1] * ROOT_NX[2]
@@ -402,6 +454,7 @@ def main():
                      "mixed": [rmx["stage1_ms"], rmx["stage2_ms"]]},
         "counters": {"fp64": r64["counters"], "mixed": rmx["counters"]},
         "l1_error": l1,
+        "smr": smr,
         "e2e": e2e,
         "gpu_launches": 5 * args.steps * 2,
         "clocks": clk,

@@ -33,7 +33,8 @@
  *     host threads.
  *
  * Register layout (the library's choice, reported by ak_mesh_layout):
- *   register = blocks one after another; inside a block the layout is
+ *   register = blocks one after another (each with its own size on a refined mesh);
+ *   inside a block the layout is
  *   [var 0..4][k][j][i] with i fastest, each dimension padded by nghost ghost cells on
  *   both sides (extents nx1+2g, nx2+2g, nx3+2g), var = (rho, M1, M2, M3, E).  Rows are
  *   stored with a pitch s1 = round_up(nx1 + 2g, 4) elements, and block b's first ghost
@@ -74,11 +75,13 @@ typedef struct ak_mesh ak_mesh;
 typedef struct {
   int32_t nblocks;        /* number of MeshBlocks (Section 2), >= 1 */
   int32_t nghost;         /* ghost cells per side: 2 for PLM, 3 for PPM4 */
-  const int32_t* blocks;  /* host array, AK_BLOCK_INTS ints per block:
+  const int32_t* blocks;  /* host array, AK_BLOCK_INTS ints per leaf block:
                              level, lx1, lx2, lx3, nx1, nx2, nx3 -- (lx1, lx2, lx3) is the
-                             block's first cell in the cell index space of its level;
-                             only level 0 (a uniform mesh) is accepted by this version.
-                             Copied at create time; the caller keeps ownership. */
+                             block's first cell in the cell index space of its level
+                             (root_nx * 2^level cells per direction).  Level 0 only is a
+                             uniform mesh; several levels are a static refinement
+                             (Section 2) whose leaves advance with one dt.  Copied at
+                             create time; the caller keeps ownership. */
   double xmin[3], xmax[3];  /* domain, periodic in all three directions */
   int32_t root_nx[3];       /* level-0 cells per direction; the blocks must tile it */
   int32_t recon;            /* AK_PLM or AK_PPM4 */
@@ -94,9 +97,14 @@ typedef struct {
 
 /* Validates `desc`, copies the block table to the device and allocates the device
  * scalars.  `cuda_stream` is a cudaStream_t (NULL = legacy default stream).
- * Returns AK_EINVAL for an invalid description (blocks overlapping, not tiling
- * root_nx, sizes < nghost, unsupported recon/rk/precision), AK_ENOMEM / AK_ECUDA on
- * allocation failure.  On success *out owns the mesh (free with ak_mesh_destroy). */
+ * A valid mesh: blocks of one level share one size; origins lie on the level's block
+ * lattice; the leaves tile the periodic box exactly (no overlap within or across
+ * levels); and, with several levels, sizes and origins are even, ghost zones see at
+ * most one level jump, prolongation stencils reach at most one level down (proper
+ * nesting), and a block face next to a finer region is so over its whole extent.
+ * Returns AK_EINVAL for an invalid description (with the violated rule in
+ * ak_last_error), AK_ENOMEM / AK_ECUDA on allocation failure.  On success *out owns the
+ * mesh (free with ak_mesh_destroy). */
 ak_status ak_mesh_create(const ak_mesh_desc* desc, void* cuda_stream, ak_mesh** out);
 
 /* Frees what the library allocated; bound registers are not touched.  NULL is a no-op. */
@@ -105,7 +113,7 @@ void ak_mesh_destroy(ak_mesh* mesh);
 /* Number of registers the configured integrator needs (2 for RK2, 3 for RK3), bytes of
  * one register, (if block_offset != NULL) the element offset of every block's first
  * ghost cell (nblocks entries), and (if strides != NULL) the element strides of
- * (var, k, j, i) inside a block.  Any output pointer may be NULL.  Register 0 holds
+ * (var, k, j, i) inside block 0 (blocks of other sizes follow the same rule).  Any output pointer may be NULL.  Register 0 holds
  * U^n before ak_step and U^{n+1} after it. */
 ak_status ak_mesh_layout(const ak_mesh* mesh, int32_t* nregisters, size_t* register_bytes,
                          int64_t* block_offset, int64_t strides[4]);
@@ -116,8 +124,11 @@ ak_status ak_mesh_layout(const ak_mesh* mesh, int32_t* nregisters, size_t* regis
 ak_status ak_mesh_bind(ak_mesh* mesh, int32_t reg, double* dev_ptr);
 
 /* Ghost-zone fill of register `reg` (Section 2, Boundary conditions): every ghost
- * cell of every block receives the interior cell that the periodic domain maps it to,
- * copied from the neighbouring block on the same device; one launch covers all
+ * cell of every block receives the periodic image of its position, copied from the
+ * neighbouring block on the same device (same level), restricted as the mean of the
+ * 2x2x2 cells of a finer neighbour, or prolonged from a coarser neighbour (coarse value
+ * plus minmod-limited slopes of the conserved variables, +-1/4 of a coarse slope per
+ * direction; done after the copies and restrictions).  One launch per pass covers all
  * blocks.  Edge and corner ghosts are filled too. */
 ak_status ak_fill_ghosts(ak_mesh* mesh, int32_t reg);
 
@@ -127,9 +138,13 @@ ak_status ak_fill_ghosts(ak_mesh* mesh, int32_t reg);
  * RK2: (a, b) = (0, 1), (1/2, 1/2); RK3: (0, 1), (3/4, 1/4), (1/3, 2/3).
  * Registers: RK2 stage 1: in 0, out 1; stage 2: in 1, U0 = 0, out 0.
  *            RK3 stage 1: in 0, out 1; stage 2: in 1, out 2; stage 3: in 2, out 0.
- * The ghost zones of the input register must be current (ak_fill_ghosts).  Only
- * interior cells of the output are written.  The last stage also accumulates the CFL
- * minimum of the new state for ak_new_dt's device-resident value. */
+ * The ghost zones of the input register must be current (ak_fill_ghosts).  On a
+ * refined mesh the call first computes, for every coarse face next to a finer region,
+ * the mean of the 2x2 fine fluxes through it, and the coarse update uses that mean
+ * (flux correction at level boundaries, Section 2), so the update stays conservative.
+ * Only interior cells of the output are written.  The last stage also accumulates the
+ * CFL minimum of the new state (over all levels, each with its dx) for ak_new_dt's
+ * device-resident value. */
 ak_status ak_stage(ak_mesh* mesh, int32_t stage, double dt);
 
 /* CFL time step of register `reg` (Section 3, Eq. (3)):
@@ -147,6 +162,18 @@ ak_status ak_new_dt(ak_mesh* mesh, int32_t reg, double* dt_out);
  * and the CFL dt of the new state is written there.  The step's launches are captured
  * into a CUDA graph on the first call and replayed afterwards. */
 ak_status ak_step(ak_mesh* mesh, double dt, double* dt_next);
+
+/* Picks, by timing stage launches on this mesh, the schedule of the stage kernel: the
+ * column-tile shape (16x16, or 32x8 for the mixed PLM form), the number of x3 segments
+ * per MeshBlock, and the order in which CTAs take the (block, tile, segment) work items
+ * (block order, or longest first) -- the block-to-SM schedule.  The paper finds the
+ * MeshBlock size decisive for throughput (Section 5.1); this tunes how a given mesh is
+ * cut into GPU work.  Results are bitwise independent of the choice.  Registers 0 and 1
+ * must be bound and register 0 must hold a valid state (its ghosts are refilled);
+ * register 1 is overwritten.  Synchronizes the stream; do not call during a stream
+ * capture.  result (may be NULL): tile (0 = 16x16, 1 = 32x8), segments, order, and the
+ * chosen schedule's stage time in microseconds. */
+ak_status ak_mesh_autotune(ak_mesh* mesh, int32_t result[4]);
 
 /* Host <-> device state transfer through a library staging buffer.  The host array is
  * the interior only, packed block after block: [block][var][k][j][i], i fastest

@@ -16,9 +16,14 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libak.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
+# -fmad=false: no implicit multiply-add contraction.  Every fused multiply-add in the
+# kernels is written out as fma(); the rest round after each operation.  The bits of a
+# flux then do not depend on where the compiler inlined its code, so a face solved at
+# two call sites (an x3 segment boundary, a coarse face rebuilt from fine fluxes) gives
+# the same value at both, and the update conserves to the last bit.
 NVCC_FLAGS = [
     "-gencode", "arch=compute_103a,code=sm_103a",
-    "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+    "-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC",
     "--expt-relaxed-constexpr", "-I", INCLUDE,
 ]
 

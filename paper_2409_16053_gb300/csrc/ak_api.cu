@@ -4,6 +4,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include <cudaTypedefs.h>
@@ -271,8 +272,9 @@ extern "C" ak_status ak_mesh_create(const ak_mesh_desc* d, void* cuda_stream, ak
   m->padded_cells = pad_off[nb];
   m->nfc = (int)fc.size();
   m->fc_cells = fc_cells;
-  // stage work list: 16x16 column tiles, x3 split so that the GPU is filled a few times
-  std::vector<ak_work> work;
+  // default stage schedule: 16x16 column tiles, x3 split so that the GPU is filled a
+  // few times over, blocks in table order (ak_mesh_autotune may change it)
+  int seg = 1;
   {
     long long tiles = 0;
     int minz = 1 << 30;
@@ -280,26 +282,56 @@ extern "C" ak_status ak_mesh_create(const ak_mesh_desc* d, void* cuda_stream, ak
       tiles += (long long)((m->h_blk[b].nx1 + 15) / 16) * ((m->h_blk[b].nx2 + 15) / 16);
       minz = m->h_blk[b].nx3 < minz ? m->h_blk[b].nx3 : minz;
     }
-    int seg = 1;
     while (tiles * seg < 4 * 152 && minz / (2 * seg) >= 8) seg *= 2;
+  }
+  // exchange plan: every ghost cell of every block, with its source
+  std::vector<ak_xfer> xa, xb;
+  {
+    auto el0 = [&](const ak_block& B, long long i, long long j, long long k) {
+      return B.off + ((k + ng) * B.p2 + (j + ng)) * (long long)B.s1 + (i + ng);
+    };
     for (int b = 0; b < nb; ++b) {
       const ak_block& B = m->h_blk[b];
-      const int kseg = (B.nx3 + seg - 1) / seg;
-      for (int s = 0; s < seg; ++s)
-        for (int j0 = 0; j0 < B.nx2; j0 += 16)
-          for (int i0 = 0; i0 < B.nx1; i0 += 16) {
-            ak_work w;
-            w.block = b;
-            w.i0 = i0;
-            w.j0 = j0;
-            w.k0 = s * kseg;
-            w.k1 = (s + 1) * kseg < B.nx3 ? (s + 1) * kseg : B.nx3;
-            w.pad = 0;
-            if (w.k0 < w.k1) work.push_back(w);
+      const int l = B.level;
+      for (int k = -ng; k < B.nx3 + ng; ++k)
+        for (int j = -ng; j < B.nx2 + ng; ++j)
+          for (int i = -ng; i < B.nx1 + ng; ++i) {
+            if (i >= 0 && i < B.nx1 && j >= 0 && j < B.nx2 && k >= 0 && k < B.nx3) continue;
+            const long long gx = HostIndex::wrap(B.lx1 + i, X.N[l][0]),
+                            gy = HostIndex::wrap(B.lx2 + j, X.N[l][1]),
+                            gz = HostIndex::wrap(B.lx3 + k, X.N[l][2]);
+            ak_xfer t;
+            t.dst = el0(B, i, j, k);
+            t.pad = 0;
+            const int same = X.leaf(l, gx, gy, gz);
+            if (same >= 0) {
+              const ak_block& S = m->h_blk[same];
+              t.src = el0(S, gx - S.lx1, gy - S.lx2, gz - S.lx3);
+              t.info = 0 | (l << 2) | (l << 10);
+              xa.push_back(t);
+              continue;
+            }
+            const int fine = X.leaf(l + 1, 2 * gx, 2 * gy, 2 * gz);
+            if (fine >= 0) {
+              const ak_block& F = m->h_blk[fine];
+              t.src = el0(F, 2 * gx - F.lx1, 2 * gy - F.lx2, 2 * gz - F.lx3);
+              t.info = 1 | (l << 2) | ((l + 1) << 10);
+              xa.push_back(t);
+              continue;
+            }
+            const int coarse = X.leaf(l - 1, gx >> 1, gy >> 1, gz >> 1);
+            if (coarse < 0) {  // excluded by the validation above
+              ak_mesh_destroy(m);
+              return einval("ak_mesh_create: ghost cell without a source");
+            }
+            const ak_block& C = m->h_blk[coarse];
+            t.src = el0(C, (gx >> 1) - C.lx1, (gy >> 1) - C.lx2, (gz >> 1) - C.lx3);
+            t.info = 2 | (l << 2) | ((l - 1) << 10) |
+                     (int)(((gx & 1) | ((gy & 1) << 1) | ((gz & 1) << 2)) << 18);
+            xb.push_back(t);
           }
     }
   }
-  m->nwork = (int)work.size();
   // level table
   ak_level lev[AK_MAX_LEVELS];
   for (int l = 0; l < X.nlev; ++l) {
@@ -313,6 +345,15 @@ extern "C" ak_status ak_mesh_create(const ak_mesh_desc* d, void* cuda_stream, ak
     lev[l].md2 = X.md[l][1];
     lev[l].md3 = X.md[l][2];
     lev[l].map_off = X.off[l];
+    lev[l].var_stride = 0;
+    lev[l].row = lev[l].plane = 0;
+    if (X.bs[l][0]) {
+      const int p1 = X.bs[l][0] + 2 * ng, p2 = X.bs[l][1] + 2 * ng, p3 = X.bs[l][2] + 2 * ng;
+      const int s1 = (p1 + 3) / 4 * 4;
+      lev[l].row = s1;
+      lev[l].plane = s1 * p2;
+      lev[l].var_stride = (long long)s1 * p2 * p3;
+    }
   }
 
   cudaError_t e = cudaSuccess;
@@ -329,15 +370,17 @@ extern "C" ak_status ak_mesh_create(const ak_mesh_desc* d, void* cuda_stream, ak
   dmalloc((void**)&m->d_fcbuf, sizeof(double) * AK_NVAR * (size_t)fc_cells);
   dmalloc((void**)&m->d_pack_off, sizeof(long long) * (nb + 1));
   dmalloc((void**)&m->d_pad_off, sizeof(long long) * (nb + 1));
-  dmalloc((void**)&m->d_work, sizeof(ak_work) * work.size());
   dmalloc((void**)&m->d_sc, sizeof(ak_dev_scalars));
+  dmalloc((void**)&m->d_xa, sizeof(ak_xfer) * xa.size());
+  dmalloc((void**)&m->d_xb, sizeof(ak_xfer) * xb.size());
+  h2d(m->d_xa, xa.data(), sizeof(ak_xfer) * xa.size());
+  h2d(m->d_xb, xb.data(), sizeof(ak_xfer) * xb.size());
   h2d(m->d_blk, m->h_blk, sizeof(ak_block) * nb);
   h2d(m->d_lev, lev, sizeof(ak_level) * X.nlev);
   h2d(m->d_map, X.map.data(), sizeof(int32_t) * X.map.size());
   h2d(m->d_fc, fc.data(), sizeof(int4) * fc.size());
   h2d(m->d_pack_off, pack_off.data(), sizeof(long long) * (nb + 1));
   h2d(m->d_pad_off, pad_off.data(), sizeof(long long) * (nb + 1));
-  h2d(m->d_work, work.data(), sizeof(ak_work) * work.size());
   m->md.blocks = m->d_blk;
   m->md.levels = m->d_lev;
   m->md.map = m->d_map;
@@ -348,6 +391,11 @@ extern "C" ak_status ak_mesh_create(const ak_mesh_desc* d, void* cuda_stream, ak
   m->md.ng = ng;
   m->md.nfc = m->nfc;
   m->md.gamma = d->gamma;
+  m->md.xa = m->d_xa;
+  m->md.xb = m->d_xb;
+  m->md.nxa = (long long)xa.size();
+  m->md.nxb = (long long)xb.size();
+  if (e == cudaSuccess) e = ak_build_work(m, 0, seg, 0);
   if (e == cudaSuccess) e = ak_stage_prepare(m);
   if (e == cudaSuccess) {
     ak_dev_scalars s;
@@ -364,6 +412,52 @@ extern "C" ak_status ak_mesh_create(const ak_mesh_desc* d, void* cuda_stream, ak
   return AK_OK;
 }
 
+cudaError_t ak_build_work(ak_mesh* m, int tile, int nseg, int order) {
+  const int TX = tile == 1 ? 32 : 16, TY = tile == 1 ? 8 : 16;
+  std::vector<ak_work> work;
+  std::vector<long long> cost;
+  for (int b = 0; b < m->nblocks; ++b) {
+    const ak_block& B = m->h_blk[b];
+    int seg = nseg;
+    while (seg > 1 && B.nx3 / seg < 4) seg >>= 1;
+    const int kseg = (B.nx3 + seg - 1) / seg;
+    for (int s = 0; s < seg; ++s)
+      for (int j0 = 0; j0 < B.nx2; j0 += TY)
+        for (int i0 = 0; i0 < B.nx1; i0 += TX) {
+          ak_work w;
+          w.block = b;
+          w.i0 = i0;
+          w.j0 = j0;
+          w.k0 = s * kseg;
+          w.k1 = (s + 1) * kseg < B.nx3 ? (s + 1) * kseg : B.nx3;
+          w.pad = 0;
+          if (w.k0 < w.k1) {
+            work.push_back(w);
+            cost.push_back((long long)(w.k1 - w.k0 + 2 * m->ng));
+          }
+        }
+  }
+  if (order == 1) {  // longest column segments first (a static block-to-SM schedule)
+    std::vector<size_t> idx(work.size());
+    for (size_t i = 0; i < idx.size(); ++i) idx[i] = i;
+    std::stable_sort(idx.begin(), idx.end(), [&](size_t x, size_t y) { return cost[x] > cost[y]; });
+    std::vector<ak_work> w2(work.size());
+    for (size_t i = 0; i < idx.size(); ++i) w2[i] = work[idx[i]];
+    work.swap(w2);
+  }
+  if (m->d_work) cudaFree(m->d_work);
+  m->d_work = nullptr;
+  cudaError_t e = cudaMalloc(&m->d_work, sizeof(ak_work) * (work.size() ? work.size() : 1));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(m->d_work, work.data(), sizeof(ak_work) * work.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return e;
+  m->nwork = (int)work.size();
+  m->tile = tile;
+  m->nseg = nseg;
+  m->order = order;
+  return cudaSuccess;
+}
+
 extern "C" void ak_mesh_destroy(ak_mesh* m) {
   if (!m) return;
   if (m->graph_exec) cudaGraphExecDestroy(m->graph_exec);
@@ -375,6 +469,8 @@ extern "C" void ak_mesh_destroy(ak_mesh* m) {
   cudaFree(m->d_fcbuf);
   cudaFree(m->d_pack_off);
   cudaFree(m->d_pad_off);
+  cudaFree(m->d_xa);
+  cudaFree(m->d_xb);
   cudaFree(m->d_work);
   cudaFree(m->d_sc);
   cudaFree(m->d_staging);
@@ -579,6 +675,59 @@ extern "C" ak_status ak_step(ak_mesh* m, double dt, double* dt_next) {
     ak_status s = read_scalars(m, &sc);
     *dt_next = sc.dt_next;
     return s;
+  }
+  return AK_OK;
+}
+
+extern "C" ak_status ak_mesh_autotune(ak_mesh* m, int32_t result[4]) {
+  if (!m) return einval("ak_mesh_autotune: NULL mesh");
+  for (int r = 0; r < 2; ++r) {
+    ak_status s = need_reg(m, r, "ak_mesh_autotune");
+    if (s != AK_OK) return s;
+  }
+  AK_CUDA_TRY(ak_launch_fill_ghosts(m, m->reg[0]));
+  if (m->nfc) AK_CUDA_TRY(ak_launch_flux_correction(m, m->reg[0]));
+  cudaEvent_t ev[2];
+  AK_CUDA_TRY(cudaEventCreate(&ev[0]));
+  AK_CUDA_TRY(cudaEventCreate(&ev[1]));
+  const int ntile = (m->desc.precision == AK_MIXED && m->desc.recon == AK_PLM) ? 2 : 1;
+  int best_tile = m->tile, best_seg = m->nseg, best_order = m->order;
+  float best = 1e30f;
+  cudaError_t e = cudaSuccess;
+  for (int tile = 0; tile < ntile && e == cudaSuccess; ++tile)
+    for (int seg = 1; seg <= 16 && e == cudaSuccess; seg *= 2)
+      for (int order = 0; order < 2 && e == cudaSuccess; ++order) {
+        e = ak_build_work(m, tile, seg, order);
+        float t = 1e30f;
+        for (int rep = 0; rep < 5 && e == cudaSuccess; ++rep) {
+          e = cudaEventRecord(ev[0], m->stream);
+          if (e == cudaSuccess) e = ak_launch_stage(m, 1, m->reg[0], m->reg[0], m->reg[1], 1, 0);
+          if (e == cudaSuccess) e = cudaEventRecord(ev[1], m->stream);
+          if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+          float ms = 0.f;
+          if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+          if (rep >= 2 && ms < t) t = ms;  // two warm-up launches
+        }
+        if (e == cudaSuccess && t < best) {
+          best = t;
+          best_tile = tile;
+          best_seg = seg;
+          best_order = order;
+        }
+      }
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  if (e == cudaSuccess) e = ak_build_work(m, best_tile, best_seg, best_order);
+  if (e != cudaSuccess) {
+    ak_set_error("ak_mesh_autotune: %s", cudaGetErrorString(e));
+    return AK_ECUDA;
+  }
+  invalidate_graph(m);
+  if (result) {
+    result[0] = best_tile;
+    result[1] = best_seg;
+    result[2] = best_order;
+    result[3] = (int32_t)(best * 1000.0f);
   }
   return AK_OK;
 }

@@ -41,12 +41,25 @@ struct ak_block {
   double dx1, dx2, dx3;
 };
 
-// One refinement level: its cell count, block size and leaf map.
+// One refinement level: its cell count, block size and leaf map, and the strides of its
+// blocks (all leaves of a level have one size).
 struct ak_level {
   int n1, n2, n3;        // cells per direction in this level's index space
   int bs1, bs2, bs3;     // block size of the level's leaves (0 if the level is empty)
   int md1, md2, md3;     // map extent in blocks
   int map_off;           // start of the level's map in the map table
+  long long var_stride;  // element strides inside a block of this level
+  int row, plane;        // (row = s1, plane = s1 * p2)
+};
+
+// One ghost cell of the exchange plan (built once per mesh on the host): the element of
+// variable 0 of the ghost cell, the element of variable 0 of its source (same-level
+// cell, first of the 2x2x2 fine cells, or the coarse cell), and
+// info = kind | dst level << 2 | src level << 10 | upper-half bits << 18
+// (kind 0 copy, 1 restriction, 2 prolongation).
+struct ak_xfer {
+  long long dst, src;
+  int info, pad;
 };
 
 // One CTA of the stage kernel: a column tile of one block over planes [k0, k1).
@@ -61,6 +74,9 @@ struct ak_meshdev {
   const int32_t* map;   // leaf id or -1, per level per block slot
   const int4* fc;       // flux-correction faces: (block, face, first face cell, n cells)
   double* fcbuf;        // corrected coarse-face fluxes, [face cell][5]
+  const ak_xfer* xa;    // exchange plan, pass 1: copies and restrictions
+  const ak_xfer* xb;    // exchange plan, pass 2: prolongations
+  long long nxa, nxb;
   int nblocks, nlev, ng, nfc;
   double gamma;
 };
@@ -87,8 +103,13 @@ struct ak_mesh {
   double* d_fcbuf;
   long long* d_pack_off;        // interior prefix sums per block (nblocks + 1)
   long long* d_pad_off;         // padded-cell prefix sums per block (nblocks + 1)
+  ak_xfer* d_xa;                // exchange plan (see ak_xfer)
+  ak_xfer* d_xb;
   ak_work* d_work;
   int nwork;
+  int tile;                     // stage tile: 0 = 16x16 columns, 1 = 32x8
+  int nseg;                     // x3 segments per block (upper bound)
+  int order;                    // 0 = block order, 1 = longest work first
   int nfc;
   long long fc_cells;
   ak_meshdev md;
@@ -114,5 +135,7 @@ cudaError_t ak_launch_cfl(const ak_mesh* m, const double* reg);
 cudaError_t ak_launch_finalize_dt(const ak_mesh* m, int use_next_as_dt);
 cudaError_t ak_launch_set_dt(const ak_mesh* m, double dt);
 cudaError_t ak_stage_prepare(const ak_mesh* m);
+// (Re)builds the stage work list for a tile shape, x3 segment count and CTA order.
+cudaError_t ak_build_work(ak_mesh* m, int tile, int nseg, int order);
 // Encodes m->tmap[reg] for register `reg` (uniform meshes); returns 0 on success.
 int ak_encode_register_tmap(ak_mesh* m, int reg);

@@ -1,7 +1,8 @@
 // Mesh-level kernels over every leaf MeshBlock of a (possibly refined) mesh:
-//   - ghost-zone fill (Section 2, Boundary conditions): same-level copies and
-//     restrictions (fine -> coarse) in a first pass, prolongations (coarse -> fine) in a
-//     second one, so that every coarse value a prolongation reads is final;
+//   - ghost-zone fill (Section 2, Boundary conditions) by a precomputed exchange plan:
+//     same-level copies and restrictions (fine -> coarse) in a first pass, prolongations
+//     (coarse -> fine) in a second one, so that every coarse value a prolongation reads
+//     is final;
 //   - the CFL minimum of Section 3 Eq. (3) over all leaves (uniform dt across levels);
 //   - interior pack/unpack for host transfers; the device-resident dt scalars.
 // Readings: restriction is the mean of the 2x2x2 fine cells; prolongation adds
@@ -13,101 +14,63 @@ namespace {
 
 constexpr int kThreads = 256;
 
-__device__ __forceinline__ int wrapi(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
-
-// leaf containing cell (x, y, z) of level l (coordinates already wrapped), or -1
-__device__ __forceinline__ int leaf_at(const ak_meshdev& md, int l, int x, int y, int z) {
-  if (l < 0 || l >= md.nlev) return -1;
-  const ak_level L = md.levels[l];
-  if (L.bs1 == 0) return -1;
-  return md.map[L.map_off + ((z / L.bs3) * L.md2 + y / L.bs2) * L.md1 + x / L.bs1];
-}
-
 __device__ __forceinline__ long long elem(const ak_block& B, int ng, int v, int i, int j, int k) {
   return B.off + v * B.var_stride + ((long long)(k + ng) * B.p2 + (j + ng)) * B.s1 + (i + ng);
 }
 
+// minmod of two differences with its sign and magnitude tests on the integer pipe:
+// 0 unless a and b are nonzero with one sign, else the one of smaller magnitude
 __device__ __forceinline__ double minmod(double a, double b) {
-  if (a * b <= 0.0) return 0.0;
-  return fabs(a) < fabs(b) ? a : b;
+  const long long ba = __double_as_longlong(a), bb = __double_as_longlong(b);
+  if ((ba ^ bb) < 0 || (ba << 1) == 0 || (bb << 1) == 0) return 0.0;
+  return (ba & 0x7fffffffffffffffll) < (bb & 0x7fffffffffffffffll) ? a : b;
 }
 
-// One pass of the ghost fill.  The grid is nblocks x parts CTAs; CTA (b, part) walks a
-// contiguous share of block b's padded cells (interior cells and row padding skipped).
-template <int PASS>
-__global__ void fill_pass_kernel(double* reg, ak_meshdev md, int parts) {
-  const int b = blockIdx.x % md.nblocks;
-  const int part = blockIdx.x / md.nblocks;
-  const ak_block B = md.blocks[b];
-  const int ng = md.ng;
-  const ak_level LV = md.levels[B.level];
-  const long long n = B.var_stride;
-  const long long span = (n + parts - 1) / parts;
-  const long long c0 = (long long)part * span;
-  const long long c1 = c0 + span < n ? c0 + span : n;
-  for (long long c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
-    const int ip = (int)(c % B.s1);
-    const int jp = (int)((c / B.s1) % B.p2);
-    const int kp = (int)(c / ((long long)B.s1 * B.p2));
-    if (ip >= B.p1) continue;  // row padding
-    const int i = ip - ng, j = jp - ng, k = kp - ng;
-    if (i >= 0 && i < B.nx1 && j >= 0 && j < B.nx2 && k >= 0 && k < B.nx3) continue;
-    const int gx = wrapi(B.lx1 + i, LV.n1), gy = wrapi(B.lx2 + j, LV.n2),
-              gz = wrapi(B.lx3 + k, LV.n3);
-    const long long dst = B.off + c;
-    const int same = leaf_at(md, B.level, gx, gy, gz);
-    if (PASS == 1) {
-      if (same >= 0) {
-        const ak_block S = md.blocks[same];
-        const long long src = elem(S, ng, 0, gx - S.lx1, gy - S.lx2, gz - S.lx3);
+// Ghost fill, pass 1 of the exchange plan: same-level copies and restrictions (mean of
+// the 2x2x2 fine cells).  One thread per ghost cell.
+__global__ void fill_copy_restrict_kernel(double* reg, ak_meshdev md) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= md.nxa) return;
+  const ak_xfer x = md.xa[t];
+  const ak_level D = md.levels[(x.info >> 2) & 0xff];
+  const ak_level S = md.levels[(x.info >> 10) & 0xff];
+  if ((x.info & 3) == 0) {
 #pragma unroll
-        for (int v = 0; v < AK_NVAR; ++v) reg[dst + v * B.var_stride] = reg[src + v * S.var_stride];
-        continue;
-      }
-      const int fine = leaf_at(md, B.level + 1, 2 * gx, 2 * gy, 2 * gz);
-      if (fine >= 0) {  // restriction: mean of the 2x2x2 fine cells
-        const ak_block F = md.blocks[fine];
-        const int fi = 2 * gx - F.lx1, fj = 2 * gy - F.lx2, fk = 2 * gz - F.lx3;
+    for (int v = 0; v < AK_NVAR; ++v) reg[x.dst + v * D.var_stride] = reg[x.src + v * S.var_stride];
+  } else {
 #pragma unroll
-        for (int v = 0; v < AK_NVAR; ++v) {
-          double s = 0.0;
-          for (int dz = 0; dz < 2; ++dz)
-            for (int dy = 0; dy < 2; ++dy)
-              for (int dx = 0; dx < 2; ++dx) s += reg[elem(F, ng, v, fi + dx, fj + dy, fk + dz)];
-          reg[dst + v * B.var_stride] = s / 8.0;
-        }
-      }
-    } else {
-      if (same >= 0) continue;
-      if (leaf_at(md, B.level + 1, 2 * gx, 2 * gy, 2 * gz) >= 0) continue;
-      const int cx = gx >> 1, cy = gy >> 1, cz = gz >> 1;
-      const int coarse = leaf_at(md, B.level - 1, cx, cy, cz);
-      if (coarse < 0) continue;
-      const ak_block C = md.blocks[coarse];
-      const int li = cx - C.lx1, lj = cy - C.lx2, lk = cz - C.lx3;
-      const int h1 = gx & 1, h2 = gy & 1, h3 = gz & 1;
-#pragma unroll
-      for (int v = 0; v < AK_NVAR; ++v) {
-        const double uc = reg[elem(C, ng, v, li, lj, lk)];
-        double u = uc;
-        {
-          const double s = minmod(reg[elem(C, ng, v, li + 1, lj, lk)] - uc,
-                                  uc - reg[elem(C, ng, v, li - 1, lj, lk)]);
-          u += (h1 ? 0.25 : -0.25) * s;
-        }
-        {
-          const double s = minmod(reg[elem(C, ng, v, li, lj + 1, lk)] - uc,
-                                  uc - reg[elem(C, ng, v, li, lj - 1, lk)]);
-          u += (h2 ? 0.25 : -0.25) * s;
-        }
-        {
-          const double s = minmod(reg[elem(C, ng, v, li, lj, lk + 1)] - uc,
-                                  uc - reg[elem(C, ng, v, li, lj, lk - 1)]);
-          u += (h3 ? 0.25 : -0.25) * s;
-        }
-        reg[dst + v * B.var_stride] = u;
-      }
+    for (int v = 0; v < AK_NVAR; ++v) {
+      const double* f = reg + x.src + v * S.var_stride;
+      double s = 0.0;
+      for (int dz = 0; dz < 2; ++dz)
+        for (int dy = 0; dy < 2; ++dy)
+          for (int dx = 0; dx < 2; ++dx) s += f[dz * S.plane + dy * S.row + dx];
+      reg[x.dst + v * D.var_stride] = s / 8.0;
     }
+  }
+}
+
+// Ghost fill, pass 2 of the exchange plan: prolongation from the coarse cell, after
+// pass 1 has made every coarse value it reads final (proper nesting).
+__global__ void fill_prolong_kernel(double* reg, ak_meshdev md) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= md.nxb) return;
+  const ak_xfer x = md.xb[t];
+  const ak_level D = md.levels[(x.info >> 2) & 0xff];
+  const ak_level C = md.levels[(x.info >> 10) & 0xff];
+  const int hb = x.info >> 18;
+  const long long st[3] = {1, C.row, C.plane};
+#pragma unroll
+  for (int v = 0; v < AK_NVAR; ++v) {
+    const double* c = reg + x.src + v * C.var_stride;
+    const double uc = c[0];
+    double u = uc;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const double s = minmod(c[st[d]] - uc, uc - c[-st[d]]);
+      u += ((hb >> d) & 1 ? 0.25 : -0.25) * s;
+    }
+    reg[x.dst + v * D.var_stride] = u;
   }
 }
 
@@ -201,12 +164,12 @@ inline int parts_for(const ak_mesh* m) {
 }  // namespace
 
 cudaError_t ak_launch_fill_ghosts(const ak_mesh* m, double* reg) {
-  const int parts = parts_for(m);
-  fill_pass_kernel<1><<<(unsigned)(m->nblocks * parts), kThreads, 0, m->stream>>>(reg, m->md,
-                                                                                 parts);
-  if (m->multilevel)
-    fill_pass_kernel<2><<<(unsigned)(m->nblocks * parts), kThreads, 0, m->stream>>>(reg, m->md,
-                                                                                   parts);
+  if (m->md.nxa)
+    fill_copy_restrict_kernel<<<(unsigned)((m->md.nxa + kThreads - 1) / kThreads), kThreads, 0,
+                                m->stream>>>(reg, m->md);
+  if (m->md.nxb)
+    fill_prolong_kernel<<<(unsigned)((m->md.nxb + kThreads - 1) / kThreads), kThreads, 0,
+                          m->stream>>>(reg, m->md);
   return cudaGetLastError();
 }
 

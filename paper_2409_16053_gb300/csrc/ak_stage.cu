@@ -105,7 +105,7 @@ __device__ __forceinline__ void riemann(const float* wl, const float* wr, const 
 template <int NG, typename R>
 __device__ __forceinline__ void edges(const R* q, R& lo, R& hi) {
   if constexpr (NG == 2) {
-    const R h = R(0.5) * plm_slope(q[0], q[1], q[2]);
+    const R h = plm_half_slope(q[0], q[1], q[2]);
     lo = q[1] - h;
     hi = q[1] + h;
   } else {
@@ -464,7 +464,7 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
         } else {
           const double L = -fma(d1, idx1, fma(d2, idx2, d3 * idx3));
           r = fma(dt, L, uin[e + v * g.var_stride]);
-          if (form != 0) r = a * u0[e + v * g.var_stride] + b * r;
+          if (form != 0) r = fma(a, u0[e + v * g.var_stride], b * r);
         }
         un[v] = r;
         if constexpr (TMA_OUT)
@@ -483,9 +483,9 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
           const float ug = fmaxf(fmaf(-0.5f * ir, fmaf(m1, m1, fmaf(m2, m2, m3 * m3)),
                                       f64_to_f32(un[4])), (float)AK_UG_FLOOR);
           const float cs = sqrt_fast(bg.gamma_f * (bg.gamma_f - 1.0f) * ug * ir);
-          float lam = (fabsf(m1) * ir + cs) * (float)idx1;
-          lam = fmaxf(lam, (fabsf(m2) * ir + cs) * (float)idx2);
-          lam = fmaxf(lam, (fabsf(m3) * ir + cs) * (float)idx3);
+          float lam = fmaf(fabsf(m1), ir, cs) * (float)idx1;
+          lam = fmaxf(lam, fmaf(fabsf(m2), ir, cs) * (float)idx2);
+          lam = fmaxf(lam, fmaf(fabsf(m3), ir, cs) * (float)idx3);
           dtmin_f = fminf(dtmin_f, rcp_approx_f32(lam));
         } else {
           // CFL in FP64 (the FP64 form reproduces the oracle's dt to ~1e-13): the
@@ -673,6 +673,13 @@ static cudaError_t dispatch(const ak_mesh* m, const double* uin, const double* u
     if (!mixed)
       return launch<2, false, 16, 16, false>(m, uin, u0, uout, out_reg, a, b, rk2_final,
                                              last_stage, prepare);
+    if (prepare) {
+      cudaError_t e = launch<2, true, 32, 8, false>(m, uin, u0, uout, out_reg, a, b, 0, 0, true);
+      if (e != cudaSuccess) return e;
+    } else if (m->tile == 1) {
+      return launch<2, true, 32, 8, false>(m, uin, u0, uout, out_reg, a, b, rk2_final,
+                                           last_stage, false);
+    }
     return launch<2, true, 16, 16, false>(m, uin, u0, uout, out_reg, a, b, rk2_final, last_stage,
                                           prepare);
   }

@@ -36,6 +36,11 @@ struct Bg {
 // ------------------------------------------------------------------------------
 // Reconstruction (Section 3: on primitive variables).
 // ------------------------------------------------------------------------------
+// One fused multiply-add in the reconstruction's own precision (the library compiles
+// without implicit contraction: every fma is written out).
+__device__ __forceinline__ float fmar(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmar(double a, double b, double c) { return fma(a, b, c); }
+
 // van Leer harmonic mean of the one-sided differences; zero at extrema.
 // FP64: the harmonic mean with a Newton-refined reciprocal (no IEEE division)
 __device__ __forceinline__ double plm_slope(double qm, double q0, double qp) {
@@ -43,18 +48,6 @@ __device__ __forceinline__ double plm_slope(double qm, double q0, double qp) {
   const double dr = qp - q0;
   const double prod = dl * dr;
   return prod > 0.0 ? (prod + prod) * rcp64(dl + dr) : 0.0;
-}
-
-// Half of the van Leer slope, dl dr / (dl + dr): the offset of the face values from the
-// cell value (saves the doubling and halving of plm_slope in FP64)
-__device__ __forceinline__ double plm_half_slope(double qm, double q0, double qp) {
-  const double dl = q0 - qm;
-  const double dr = qp - q0;
-  const double prod = dl * dr;
-  return dpos(prod) ? prod * rcp64(dl + dr) : 0.0;
-}
-__device__ __forceinline__ float plm_half_slope(float qm, float q0, float qp) {
-  return 0.5f * plm_slope(qm, q0, qp);
 }
 
 // FP32: the harmonic mean with the hardware reciprocal refined once in FP32
@@ -67,6 +60,19 @@ __device__ __forceinline__ float plm_slope(float qm, float q0, float qp) {
   float r = rcp_approx_f32(s);
   r = fmaf(r, fmaf(-s, r, 1.0f), r);
   return (prod + prod) * r;
+}
+
+// Half of the van Leer slope, dl dr / (dl + dr): the offset of the face values from the
+// cell value.  In FP64 it skips the doubling and halving of plm_slope (same bits: both
+// are exact scalings by two).
+__device__ __forceinline__ double plm_half_slope(double qm, double q0, double qp) {
+  const double dl = q0 - qm;
+  const double dr = qp - q0;
+  const double prod = dl * dr;
+  return dpos(prod) ? prod * rcp64(dl + dr) : 0.0;
+}
+__device__ __forceinline__ float plm_half_slope(float qm, float q0, float qp) {
+  return 0.5f * plm_slope(qm, q0, qp);
 }
 
 template <typename R>
@@ -92,19 +98,19 @@ __device__ __forceinline__ void ppm_edges(R q0, R q1, R q2, R q3, R q4, R& lo, R
   R sc = ppm_slope(q1, q2, q3);
   R sp = ppm_slope(q2, q3, q4);
   const R sixth = R(1) / R(6);
-  R a_lo = R(0.5) * (q1 + q2) - (sc - sm) * sixth;
-  R a_hi = R(0.5) * (q2 + q3) - (sp - sc) * sixth;
+  R a_lo = fmar(sm - sc, sixth, R(0.5) * (q1 + q2));
+  R a_hi = fmar(sc - sp, sixth, R(0.5) * (q2 + q3));
   R a = q2;
   if ((a_hi - a) * (a - a_lo) <= R(0)) {
     a_lo = a;
     a_hi = a;
   } else {
     R da = a_hi - a_lo;
-    R a6 = R(6) * (a - R(0.5) * (a_lo + a_hi));
+    R a6 = R(6) * fmar(R(-0.5), a_lo + a_hi, a);
     if (da * a6 > da * da) {
-      a_lo = R(3) * a - R(2) * a_hi;
+      a_lo = fmar(R(3), a, R(-2) * a_hi);
     } else if (-da * da > da * a6) {
-      a_hi = R(3) * a - R(2) * a_lo;
+      a_hi = fmar(R(3), a, R(-2) * a_lo);
     }
   }
   lo = a_lo;
@@ -130,7 +136,8 @@ __device__ __forceinline__ void hllc_fp64(const double* wl, const double* wr, co
   const double cr = gpr * rsqrt64(gpr * rr);
 
   // pressure estimate of the linearised (PVRS) solver, then shock-aware speeds
-  double ps = dscale_down(pl + pr, 1, 0.5) - dscale_down((ur - ul) * (rl + rr), 3, 0.125) * (cl + cr);
+  double ps = fma(-dscale_down((ur - ul) * (rl + rr), 3, 0.125), cl + cr,
+                  dscale_down(pl + pr, 1, 0.5));
   ps = dpos(ps) ? ps : 0.0;
   const double kq = bg.kq;
   double ql = 1.0, qr = 1.0;
@@ -174,8 +181,7 @@ __device__ __forceinline__ void hllc_fp64(const double* wl, const double* wr, co
   // E*_K = fac (E_K/rho_K + (S* - u_K)(S* + p_K/(rho_K (S_K - u_K))))
   //      = E_K (S_K - u_K)/(S_K - S*) + (S* - u_K)(fac S* + p_K/(S_K - S*))
   const double us4 = fma(sstar - uk, fma(fac, sstar, pk * inv), ek * ((s - uk) * inv));
-  const double sd = s * (fac - rk);  // S_K (rho*_K - rho_K)
-  const double mt = mn + sd;
+  const double mt = fma(s, fac - rk, mn);  // M_n + S_K (rho*_K - rho_K)
   f[0] = mt;
   f[1] = fma(s, fma(fac, sstar, -mn), fma(mn, uk, pk));
   f[2] = mt * w[2];
@@ -200,8 +206,8 @@ __device__ __forceinline__ void hllc_mixed(const float* wl, const float* wr, con
   const float dpl = gm1 * wl[4], dpr = gm1 * wr[4];     // p - p_b
   const float pb = gm1 * bg.ug_f;
   const float pl = pb + dpl, pr = pb + dpr;             // full pressures
-  const float kel = 0.5f * rl * (ul * ul + wl[2] * wl[2] + wl[3] * wl[3]);
-  const float ker = 0.5f * rr * (ur * ur + wr[2] * wr[2] + wr[3] * wr[3]);
+  const float kel = 0.5f * rl * fmaf(ul, ul, fmaf(wl[2], wl[2], wl[3] * wl[3]));
+  const float ker = 0.5f * rr * fmaf(ur, ur, fmaf(wr[2], wr[2], wr[3] * wr[3]));
   const float hl = fmaf(gg, pl, kel);                   // E + p
   const float hr = fmaf(gg, pr, ker);
   const float gpl = g * pl, gpr = g * pr;
@@ -209,14 +215,14 @@ __device__ __forceinline__ void hllc_mixed(const float* wl, const float* wr, con
   const float cr = gpr * rsqrt_approx_f32(gpr * rr);
 
   // PVRS estimate as a deviation from p_b; p* = max(0, p_b + dps)
-  float dps = 0.5f * (dpl + dpr) - 0.125f * (ur - ul) * (rl + rr) * (cl + cr);
+  float dps = fmaf(-0.125f * (ur - ul) * (rl + rr), cl + cr, 0.5f * (dpl + dpr));
   dps = (pb + dps > 0.0f) ? dps : -pb;
   const float kq = (g + 1.0f) * rcp_approx_f32(2.0f * g);
   float ql = 1.0f, qr = 1.0f;
   if (dps > dpl) ql = sqrt_fast(fmaf(kq * (dps - dpl), rcp_approx_f32(pl), 1.0f));
   if (dps > dpr) qr = sqrt_fast(fmaf(kq * (dps - dpr), rcp_approx_f32(pr), 1.0f));
-  float sl = ul - cl * ql;
-  float sr = ur + cr * qr;
+  float sl = fmaf(-cl, ql, ul);
+  float sr = fmaf(cr, qr, ur);
   sl = (ur - cr < sl) ? ur - cr : sl;
   sr = (ul + cl > sr) ? ul + cl : sr;
 
@@ -234,7 +240,7 @@ __device__ __forceinline__ void hllc_mixed(const float* wl, const float* wr, con
   }
   const float ml = rl * (sl - ul);
   const float mr = rr * (sr - ur);
-  const float sstar = (dpr - dpl + ul * ml - ur * mr) * rcp_approx_f32(ml - mr);
+  const float sstar = fmaf(ul, ml, fmaf(-ur, mr, dpr - dpl)) * rcp_approx_f32(ml - mr);
   const bool left = sstar >= 0.0f;
   const float* w = left ? wl : wr;
   const float rk = left ? rl : rr;
@@ -247,13 +253,14 @@ __device__ __forceinline__ void hllc_mixed(const float* wl, const float* wr, con
   const float inv = rcp_approx_f32(s - sstar);
   const float fac = mk * inv;
   const float drho = rk * (sstar - uk) * inv;           // U*_rho - rho_K
-  const float dmn = fac * sstar - mn;                   // U*_Mn - M_n
+  const float dmn = fmaf(fac, sstar, -mn);              // U*_Mn - M_n
   // E*_K - E_K = (S* - u_K) ((E_K + p_K) / (S_K - S*) + rho*_K S*)
   const float de = (sstar - uk) * fmaf(fac, sstar, (ek + pk) * inv);
-  f[0] = fmaf(s, drho, mn);
-  f[1] = fmaf(mn, uk, left ? dpl : dpr) + s * dmn;
-  f[2] = (mn + s * drho) * w[2];
-  f[3] = (mn + s * drho) * w[3];
+  const float mt = fmaf(s, drho, mn);                   // M_n + S_K (U*_rho - rho_K)
+  f[0] = mt;
+  f[1] = fmaf(s, dmn, fmaf(mn, uk, left ? dpl : dpr));
+  f[2] = mt * w[2];
+  f[3] = mt * w[3];
   f[4] = fmaf(s, de, (left ? hl : hr) * uk);
 }
 

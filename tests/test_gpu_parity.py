@@ -345,3 +345,26 @@ def test_full_size_100_steps_properties(ak):
         tol = 1000 * 2.2e-16 * np.abs(U0[k]).sum()
         assert abs(U[k].sum() - U0[k].sum()) <= tol
     m.close()
+
+
+# ---------------------------------------------------------------------------------
+# stage schedule autotuner: any tile shape / x3 split / CTA order gives the same bits
+# ---------------------------------------------------------------------------------
+@pytest.mark.parametrize("precision", [0, 1])
+def test_autotune_keeps_results_bitwise(ak, precision):
+    root, block = (64, 64, 64), (32, 32, 32)
+    U0 = pgen.turbulence(root, seed=4, kmin=1, kmax=6, mach=0.8)
+    a = _mesh(ak, root, block, precision=precision, ref_rho=1.0, ref_p=1.0)
+    a.upload(U0)
+    tile, seg, order, us = a.autotune()
+    assert tile in (0, 1) and seg >= 1 and order in (0, 1) and us > 0
+    b = _mesh(ak, root, block, precision=precision, ref_rho=1.0, ref_p=1.0)
+    b.upload(U0)
+    dt = a.new_dt()
+    assert dt == b.new_dt()
+    for _ in range(3):
+        a.step(dt, want_dt_next=False)
+        b.step(dt, want_dt_next=False)
+    assert np.array_equal(a.download(), b.download())
+    a.close()
+    b.close()

@@ -155,3 +155,20 @@ def test_smr_full_mesh_one_step_parity(ak):
     a, b = m.download_packed(), om.to_packed(U)
     assert _norm_diff(a, b) <= 1e-12, _norm_diff(a, b)
     m.close()
+
+
+def test_smr_autotune_keeps_results_bitwise(ak):
+    t = pgen.nested_refinement_blocks(32, 8, 8, 2)
+    P = _smooth(t, 32)
+    a = _gpu_mesh(ak, t, 32)
+    a.upload_packed(P)
+    a.autotune()
+    b = _gpu_mesh(ak, t, 32)
+    b.upload_packed(P)
+    dt = a.new_dt()
+    for _ in range(3):
+        a.step(dt, want_dt_next=False)
+        b.step(dt, want_dt_next=False)
+    assert np.array_equal(a.download_packed(), b.download_packed())
+    a.close()
+    b.close()

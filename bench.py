@@ -46,8 +46,8 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes per cell of the stage kernels (dram__bytes_read.sum + dram__bytes_write.sum
 # of one ncu capture, 192^3 in 64^3 blocks; the per-cell figure carries over to 256^3 in
 # the same blocks), valid for the kernel sources with this hash (else traffic = null)
-TRAFFIC_SRC_HASH = "f96e956152a8b019824fe315504131ce7ca96d75"
-TRAFFIC_B_PER_CELL = {"fp64": (87.36, 130.85), "mixed": (86.07, 129.11)}
+TRAFFIC_SRC_HASH = "ba924eeeb77e1f40fda58aa0d2175fa46b5c9f91"
+TRAFFIC_B_PER_CELL = {"fp64": (87.95, 130.91), "mixed": (86.26, 129.07)}
 
 
 def kernel_source_hash():

@@ -63,10 +63,12 @@ __device__ __forceinline__ void c2p(const double* u, double* w, const Bg&, Count
   w[4] = ug;
 }
 
-// Conserved -> primitive, mixed form.  The internal-energy recovery
-// u_g - u_g,b = (E - u_g,b) - |M|^2 / (2 rho) and rho - rho_b run in FP64 (1/rho from
-// an FP32 seed plus one FP64 Newton step); velocities come from FP32 arithmetic; the
-// deviations W' are rounded to FP32 on the integer pipe.
+// Conserved -> primitive, mixed form.  The internal-energy recovery runs in FP64 with
+// the cancellation done before any division: rho (u_g - u_g,b) = rho (E - u_g,b) -
+// |M|^2 / 2 is formed in FP64, rounded to FP32 and only then divided by rho (FP32
+// reciprocal), so u_g - u_g,b keeps FP32 relative precision whatever the Mach number,
+// without an FP64 reciprocal.  rho - rho_b is an FP64 difference; velocities come from
+// FP32 arithmetic; the deviations W' are rounded to FP32 on the integer pipe.
 __device__ __forceinline__ void c2p(const double* u, float* w, const Bg& bg, Counters cn) {
   double rho = u[0];
   if (not_finite(rho) || not_finite(u[4])) count(cn.nonfinite);
@@ -74,13 +76,12 @@ __device__ __forceinline__ void c2p(const double* u, float* w, const Bg& bg, Cou
     rho = AK_RHO_FLOOR;
     count(cn.floors);
   }
-  const float rf = rcp_approx_f32(f64_to_f32(rho));
-  double r = f32_to_f64(rf);
-  r = fma(r, fma(-rho, r, 1.0), r);
-  const double rh = __hiloint2double(__double2hiint(r) - 0x00100000, __double2loint(r));  // r/2
+  const float rhof = f64_to_f32(rho);
+  float rf = rcp_approx_f32(rhof);
+  rf = fmaf(rf, fmaf(-rhof, rf, 1.0f), rf);
   const double m2 = fma(u[1], u[1], fma(u[2], u[2], u[3] * u[3]));
-  double dug = fma(-m2, rh, u[4] - bg.ug);  // u_g - u_g,b
-  float dugf = f64_to_f32(dug);
+  const double num = fma(u[4] - bg.ug, rho, -dscale_down(m2, 1, 0.5));  // rho (u_g - u_g,b)
+  float dugf = f64_to_f32(num) * rf;
   if (!(dugf >= bg.ug_floor_f)) {           // u_g below its floor (FP32 resolution)
     dugf = f64_to_f32(AK_UG_FLOOR - bg.ug);
     count(cn.floors);

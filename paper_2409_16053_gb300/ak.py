@@ -8,7 +8,7 @@ CUDA stream.
 Low level (same names and arguments as the C functions):
     ak_mesh_create, ak_mesh_destroy, ak_mesh_layout, ak_mesh_bind, ak_fill_ghosts,
     ak_stage, ak_new_dt, ak_step, ak_upload, ak_download, ak_status_counters,
-    ak_mesh_autotune, ak_cfl_dt_noalloc, ak_last_error
+    ak_mesh_autotune, ak_mesh_schedule, ak_cfl_dt_noalloc, ak_last_error
 High level: ``Mesh`` builds a uniform mesh of equal MeshBlocks, allocates and binds
 its registers as torch tensors, and converts between a global (5, n3, n2, n1) array
 and the library's block layout.
@@ -72,6 +72,8 @@ def _load_lib():
     lib.ak_status_counters.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
     lib.ak_mesh_autotune.argtypes = [vp, ctypes.POINTER(i32)]
     lib.ak_mesh_autotune.restype = ctypes.c_int
+    lib.ak_mesh_schedule.argtypes = [vp, i32, i32, i32]
+    lib.ak_mesh_schedule.restype = ctypes.c_int
     lib.ak_cfl_dt_noalloc.argtypes = [vp, i32, ctypes.POINTER(i32), i32, dp, ctypes.c_double,
                                       ctypes.c_double, vp, dp]
     lib.ak_cfl_dt_noalloc.restype = ctypes.c_int
@@ -86,8 +88,8 @@ def _load_lib():
 _lib = _load_lib()
 EXPORTED = ("ak_mesh_create", "ak_mesh_destroy", "ak_mesh_layout", "ak_mesh_bind",
             "ak_fill_ghosts", "ak_stage", "ak_new_dt", "ak_step", "ak_upload",
-            "ak_download", "ak_status_counters", "ak_mesh_autotune", "ak_cfl_dt_noalloc",
-            "ak_last_error")
+            "ak_download", "ak_status_counters", "ak_mesh_autotune", "ak_mesh_schedule",
+            "ak_cfl_dt_noalloc", "ak_last_error")
 
 
 def ak_last_error() -> str:
@@ -171,6 +173,11 @@ def ak_mesh_autotune(mesh):
     out = (ctypes.c_int32 * 4)()
     _check(_lib.ak_mesh_autotune(mesh, out))
     return tuple(int(v) for v in out)
+
+
+def ak_mesh_schedule(mesh, tile: int, nseg: int, order: int):
+    """Sets the stage kernel's schedule (tile variant, x3 segments, CTA order)."""
+    _check(_lib.ak_mesh_schedule(mesh, tile, nseg, order))
 
 
 def ak_cfl_dt_noalloc(reg_ptr: int, nblocks: int, nx, nghost: int, dx, gamma: float,
@@ -310,6 +317,9 @@ class Mesh:
 
     def autotune(self):
         return ak_mesh_autotune(self.handle)
+
+    def schedule(self, tile, nseg=1, order=0):
+        ak_mesh_schedule(self.handle, tile, nseg, order)
 
     def register_view(self, reg=0):
         """Torch view (nblocks, 5, p3, p2, p1) of a register, ghosts included."""

@@ -690,7 +690,7 @@ extern "C" ak_status ak_mesh_autotune(ak_mesh* m, int32_t result[4]) {
   cudaEvent_t ev[2];
   AK_CUDA_TRY(cudaEventCreate(&ev[0]));
   AK_CUDA_TRY(cudaEventCreate(&ev[1]));
-  const int ntile = (m->desc.precision == AK_MIXED && m->desc.recon == AK_PLM) ? 2 : 1;
+  const int ntile = (m->desc.precision == AK_MIXED && m->desc.recon == AK_PLM) ? 3 : 1;
   int best_tile = m->tile, best_seg = m->nseg, best_order = m->order;
   float best = 1e30f;
   cudaError_t e = cudaSuccess;
@@ -729,6 +729,27 @@ extern "C" ak_status ak_mesh_autotune(ak_mesh* m, int32_t result[4]) {
     result[2] = best_order;
     result[3] = (int32_t)(best * 1000.0f);
   }
+  return AK_OK;
+}
+
+extern "C" ak_status ak_mesh_schedule(ak_mesh* m, int32_t tile, int32_t nseg, int32_t order) {
+  if (!m) return einval("ak_mesh_schedule: NULL mesh");
+  const int ntile = (m->desc.precision == AK_MIXED && m->desc.recon == AK_PLM) ? 3 : 1;
+  if (tile < 0 || tile >= ntile) {
+    ak_set_error("ak_mesh_schedule: tile %d not available for this form (0..%d)", tile,
+                 ntile - 1);
+    return AK_EINVAL;
+  }
+  if (nseg < 1 || nseg > 64) {
+    ak_set_error("ak_mesh_schedule: nseg %d not in 1..64", nseg);
+    return AK_EINVAL;
+  }
+  if (order != 0 && order != 1) {
+    ak_set_error("ak_mesh_schedule: order %d not 0 or 1", order);
+    return AK_EINVAL;
+  }
+  AK_CUDA_TRY(ak_build_work(m, tile, nseg, order));
+  invalidate_graph(m);
   return AK_OK;
 }
 

@@ -1,0 +1,373 @@
+// Mixed-form stage kernel with paired x1/x2 work (PLM): the same stage as the mixed
+// instance of stage_kernel (primitive recovery, reconstruction, HLLC, divergence, RK
+// update and CFL of Section 3, Eqs. (1), (3), (4)), organised for GB300's issue rate.
+//
+// A CTA owns a T x T column tile of one MeshBlock and marches along x3, with
+// T (T + 2) threads: thread t owns x1 edge item t and x2 edge item t (the tile's rows
+// with one extra cell on each side, and its columns likewise), and x1 face t and x2
+// face t.  The two items of a thread are computed together in the two lanes of packed
+// FP32x2 arithmetic (lanes.cuh), which gives the same bits as solving each alone.  The
+// first T^2 threads also own one column: its x3 reconstruction, x3 face and update.
+//
+// Per plane k, between three barriers:
+//   R  x1/x2 edges of plane k (paired);
+//   F  the column's x3 edge of cell k+1 and x3 face, x1/x2 faces (paired), and part of
+//      the primitive recovery of plane k+NG+1 on the threads without a column;
+//   U  divergence and RK update of the column's cell, CFL, and the rest of the
+//      primitive recovery of plane k+NG+1.
+// The conserved state of plane k+NG+1 and the column's U_in / U0 arrive in shared
+// memory by cp.async issued at the top of the plane, so no register holds data in
+// flight across the phases.
+#include "ak_internal.cuh"
+#include "hydro_ops.cuh"
+#include "stage_common.cuh"
+
+namespace ak {
+
+namespace {
+
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+}
+// waits for all of this thread's cp.async copies
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+template <int NG, int T>
+struct MxCfg {
+  static constexpr int TX = T, TY = T;
+  static constexpr int C1 = TX + 2;                 // x1 edge items per tile row
+  static constexpr int NE = TY * C1;                // x1 edge items (= x2 edge items)
+  static constexpr int NF = TY * (TX + 1);          // x1 faces (= x2 faces)
+  static constexpr int NTH = (NE + 31) / 32 * 32;
+  static constexpr int NOWN = TX * TY;              // threads with a column
+  static constexpr int WX = TX + 2 * NG, WY = TY + 2 * NG, NPL = WX * WY, NR = 2 * NG;
+  static constexpr int NCROSS = TX * TY + 2 * NG * (TX + TY);  // converted cells per plane
+  static constexpr int NSPARE = NTH - NOWN;         // threads without a column
+  static constexpr int XPT = (NCROSS - NOWN + NSPARE - 1) / NSPARE;  // their cells
+  static constexpr int XF = XPT / 2;                // of which converted in phase F
+  static_assert(NE == (TY + 2) * TX && NF == (TY + 1) * TX, "square tiles");
+  static_assert(NSPARE > 0, "threads without a column take the extra cells");
+  static constexpr size_t bytes = sizeof(double) * (5 * NCROSS + 2 * 5 * NOWN) +
+                                  sizeof(float) * (NR * 5 * NPL + 4 * 5 * NE + 2 * 5 * NF);
+};
+
+template <int NG, int T>
+__global__ void __launch_bounds__(MxCfg<NG, T>::NTH, 2)
+    stage_mx_kernel(const double* __restrict__ uin, const double* u0, double* uout,
+                    ak_meshdev md, const ak_work* __restrict__ work, Bg bg, double a, double b,
+                    int form, ak_dev_scalars* sc, int last_stage) {
+  // form: 0 = first stage U + dt L; 1 = RK2 final (U0 + U + dt L) / 2;
+  //       2 = a U0 + b (U + dt L)
+  using C = MxCfg<NG, T>;
+  constexpr int TX = C::TX, WX = C::WX, NPL = C::NPL, NR = C::NR, NE = C::NE, NF = C::NF;
+  constexpr int C1 = C::C1, NOWN = C::NOWN, NCROSS = C::NCROSS, NSPARE = C::NSPARE;
+  constexpr int XPT = C::XPT, XF = C::XF;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* stg = reinterpret_cast<double*>(smem_raw);          // [5][NCROSS] next plane
+  double* ucol = stg + 5 * NCROSS;                              // [2][5][NOWN] U_in, U0
+  float* ring = reinterpret_cast<float*>(ucol + 10 * NOWN);      // [NR][5][NPL] W'
+  float* e1lo = ring + NR * 5 * NPL;                            // [5][NE]
+  float* e1hi = e1lo + 5 * NE;
+  float* e2lo = e1hi + 5 * NE;
+  float* e2hi = e2lo + 5 * NE;
+  float* f1 = e2hi + 5 * NE;                                    // [5][NF]
+  float* f2 = f1 + 5 * NF;
+  __shared__ double red[C::NTH / 32];
+
+  const int tid = threadIdx.x;
+  const ak_work w = work[blockIdx.x];
+  const ak_block g = md.blocks[w.block];
+  const int i0 = w.i0, j0 = w.j0, k0 = w.k0, k1 = w.k1;
+  const double* ub = uin + g.off;
+  const Counters cn{&sc->counters[0], &sc->counters[1]};
+  const double dt = sc->dt;
+  const double idx1 = 1.0 / g.dx1, idx2 = 1.0 / g.dx2, idx3 = 1.0 / g.dx3;
+  const float idx1f = (float)idx1, idx2f = (float)idx2, idx3f = (float)idx3;
+  const bool need_u0 = form != 0;
+  const long long pst = (long long)g.p2 * g.s1;  // plane stride
+  const long long vst = g.var_stride;
+
+  auto slot = [](int k) { return (k + 4 * NR) % NR; };
+
+  // ---- cells of the cross-shaped plane this thread converts (and stages) -------------
+  // cell c: halo rows above, tile rows with their x1 halo, halo rows below (no corners)
+  auto cross_xy = [](int c, int& x, int& y) {
+    constexpr int TOP = NG * TX, MID = C::TY * (TX + 2 * NG);
+    if (c < TOP) {
+      y = c / TX;
+      x = NG + c % TX;
+    } else if (c < TOP + MID) {
+      const int d = c - TOP;
+      y = NG + d / (TX + 2 * NG);
+      x = d % (TX + 2 * NG);
+    } else {
+      const int d = c - TOP - MID;
+      y = NG + C::TY + d / TX;
+      x = NG + d % TX;
+    }
+  };
+  constexpr int NMY = 1 + XPT;  // slot 0: the column threads' cell; slots 1..: spare threads'
+  int mycell[NMY], mypos[NMY], myoff[NMY];
+#pragma unroll
+  for (int m = 0; m < NMY; ++m) {
+    const int c = tid < NOWN ? (m == 0 ? tid : -1)
+                             : (m == 0 ? -1 : NOWN + (tid - NOWN) + NSPARE * (m - 1));
+    mycell[m] = (c >= 0 && c < NCROSS) ? c : -1;
+    mypos[m] = -1;
+    myoff[m] = 0;
+    if (mycell[m] >= 0) {
+      int x, y;
+      cross_xy(mycell[m], x, y);
+      const int ip = i0 + x, jp = j0 + y;  // padded indices (halo starts at i0 - NG)
+      if (ip < g.p1 && jp < g.p2) {
+        mypos[m] = y * WX + x;
+        myoff[m] = (NG * g.p2 + jp) * g.s1 + ip;  // element of plane 0, variable 0
+      }
+    }
+  }
+  // stage plane kp of the slots [m0, m1) into shared memory
+  auto stage_cells = [&](int kp, int m0, int m1) {
+#pragma unroll
+    for (int m = 0; m < NMY; ++m) {
+      if (m >= m0 && m < m1 && mypos[m] >= 0) {
+        const double* src = ub + myoff[m] + kp * pst;
+#pragma unroll
+        for (int v = 0; v < 5; ++v) cp_async8(&stg[v * NCROSS + mycell[m]], src + v * vst);
+      }
+    }
+  };
+  // primitive recovery of staged cells of slots [m0, m1) into the ring slot of plane kp
+  auto convert_staged = [&](int kp, int m0, int m1) {
+    float* dst = ring + slot(kp) * 5 * NPL;
+#pragma unroll
+    for (int m = 0; m < NMY; ++m) {
+      if (m >= m0 && m < m1 && mypos[m] >= 0) {
+        double u[5];
+        float wv[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) u[v] = stg[v * NCROSS + mycell[m]];
+        c2p(u, wv, bg, cn);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) dst[v * NPL + mypos[m]] = wv[v];
+      }
+    }
+  };
+  // direct load and conversion of plane kp (prologue)
+  auto load_plane = [&](int kp) {
+    float* dst = ring + slot(kp) * 5 * NPL;
+#pragma unroll
+    for (int m = 0; m < NMY; ++m) {
+      if (mypos[m] >= 0) {
+        const double* src = ub + myoff[m] + kp * pst;
+        double u[5];
+        float wv[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) u[v] = src[v * vst];
+        c2p(u, wv, bg, cn);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) dst[v * NPL + mypos[m]] = wv[v];
+      }
+    }
+  };
+
+  // ---- this thread's edge items, faces and column ---------------------------------------
+  const int r1 = tid / C1, c1 = tid % C1;            // x1 item: cell (i0 - 1 + c1, j0 + r1)
+  const int r2 = tid / TX, c2 = tid % TX;            // x2 item: cell (i0 + c2, j0 - 1 + r2)
+  const int base1 = (r1 + NG) * WX + c1;             // stencil start in a ring plane (x)
+  const int base2 = r2 * WX + c2 + NG;               // (y, stride WX)
+  const int fx1 = tid % (TX + 1), fy1 = tid / (TX + 1);  // x1 face: i = i0 + fx1, j0 + fy1
+  const int fx2 = tid % TX, fy2 = tid / TX;              // x2 face: i0 + fx2, j = j0 + fy2
+  const bool face1 = tid < NF && i0 + fx1 <= g.nx1 && j0 + fy1 < g.nx2;
+  const bool face2 = tid < NF && i0 + fx2 < g.nx1 && j0 + fy2 <= g.nx2;
+  const int ov1 = !face1 ? -1 : (i0 + fx1 == 0 ? g.ovr[0] : (i0 + fx1 == g.nx1 ? g.ovr[1] : -1));
+  const int ov2 = !face2 ? -1 : (j0 + fy2 == 0 ? g.ovr[2] : (j0 + fy2 == g.nx2 ? g.ovr[3] : -1));
+
+  const int tx = tid % TX, ty = tid / TX;
+  const int ci = i0 + tx, cj = j0 + ty;
+  const bool column = tid < NOWN;
+  const bool own = column && ci < g.nx1 && cj < g.nx2;
+  const int oc = (ty + NG) * WX + (tx + NG);
+  const long long ecol = g.off + ((long long)NG * g.p2 + (cj + NG)) * g.s1 + (ci + NG);
+
+  auto x3_edges = [&](int kc, float* lo, float* hi) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      float q[2 * NG - 1];
+#pragma unroll
+      for (int m = 0; m < 2 * NG - 1; ++m) q[m] = ring[slot(kc - NG + 1 + m) * 5 * NPL + v * NPL + oc];
+      edges<NG>(q, lo[v], hi[v]);
+    }
+  };
+
+  // ---- prologue: planes k0-NG .. k0+NG-1, the x3 face below k0, then plane k0+NG --------
+  for (int kp = k0 - NG; kp < k0 + NG; ++kp) load_plane(kp);
+  __syncthreads();
+  float hi3[5], f3m[5], f3p[5];
+  if (column) {
+    float lo_a[5], hi_a[5], lo_b[5];
+    x3_edges(k0 - 1, lo_a, hi_a);
+    x3_edges(k0, lo_b, hi3);
+    if (k0 == 0 && g.ovr[4] >= 0)
+      corrected_flux(md.fcbuf, g.ovr[4] + cj * g.nx1 + ci, f3m);
+    else
+      solve(2, hi_a, lo_b, bg, f3m);
+  }
+  __syncthreads();
+  load_plane(k0 + NG);
+
+  float dtmin_f = __int_as_float(0x7f800000);
+  for (int k = k0; k < k1; ++k) {
+    const bool more = k + 1 < k1;
+    __syncthreads();  // A: the previous plane's phase U is complete
+    if (more) stage_cells(k + NG + 1, 0, NMY);
+    if (own) {
+      const long long e = ecol + k * pst;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        cp_async8(&ucol[v * NOWN + tid], uin + e + v * vst);
+        if (need_u0) cp_async8(&ucol[(5 + v) * NOWN + tid], u0 + e + v * vst);
+      }
+    }
+
+    // ---- R: x1 and x2 edges of plane k, paired --------------------------------------
+    const float* pl = ring + slot(k) * 5 * NPL;
+    if (tid < NE) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        float2 q[2 * NG - 1];
+#pragma unroll
+        for (int m = 0; m < 2 * NG - 1; ++m)
+          q[m] = make_float2(pl[v * NPL + base1 + m], pl[v * NPL + base2 + m * WX]);
+        float2 lo, hi;
+        if constexpr (NG == 2)
+          plm_edges_v(q[0], q[1], q[2], lo, hi);
+        else
+          ppm_edges_v(q[0], q[1], q[2], q[3], q[4], lo, hi);
+        e1lo[v * NE + tid] = lo.x;
+        e1hi[v * NE + tid] = hi.x;
+        e2lo[v * NE + tid] = lo.y;
+        e2hi[v * NE + tid] = hi.y;
+      }
+    }
+    cp_async_wait_all();
+    __syncthreads();  // B: edges and staged data visible
+
+    // ---- F: x3 edge and face of the column; x1/x2 faces, paired ---------------------
+    if (column) {
+      float lo3[5], hi3n[5];
+      x3_edges(k + 1, lo3, hi3n);
+      if (k + 1 == g.nx3 && g.ovr[5] >= 0)
+        corrected_flux(md.fcbuf, g.ovr[5] + cj * g.nx1 + ci, f3p);
+      else
+        solve(2, hi3, lo3, bg, f3p);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) hi3[v] = hi3n[v];
+    }
+    if (tid < NF) {
+      // x1 face: (rho, v1; v2, v3, u_g); x2 face: (rho, v2; v3, v1, u_g)
+      constexpr int P2[5] = {0, 2, 3, 1, 4};
+      const int l1 = fy1 * C1 + fx1, l2 = fy2 * TX + fx2;
+      float2 wl[5], wr[5], fn[5];
+#pragma unroll
+      for (int n = 0; n < 5; ++n) {
+        wl[n] = make_float2(e1hi[n * NE + l1], e2hi[P2[n] * NE + l2]);
+        wr[n] = make_float2(e1lo[n * NE + l1 + 1], e2lo[P2[n] * NE + l2 + TX]);
+      }
+      hllc_mixed(wl, wr, bg, fn);
+      float fa[5], fb[5];
+#pragma unroll
+      for (int n = 0; n < 5; ++n) {
+        fa[n] = fn[n].x;
+        fb[P2[n]] = fn[n].y;
+      }
+      if (ov1 >= 0) corrected_flux(md.fcbuf, ov1 + k * g.nx2 + j0 + fy1, fa);
+      if (ov2 >= 0) corrected_flux(md.fcbuf, ov2 + k * g.nx1 + i0 + fx2, fb);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        f1[v * NF + tid] = fa[v];
+        f2[v * NF + tid] = fb[v];
+      }
+    }
+    if (more && !column) convert_staged(k + NG + 1, 1, 1 + XF);
+    __syncthreads();  // C: fluxes complete
+
+    // ---- U: divergence, RK update and CFL of the column's cell ------------------------
+    if (own) {
+      const long long e = ecol + k * pst;
+      double un[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const float d1 = f1[v * NF + ty * (TX + 1) + tx + 1] - f1[v * NF + ty * (TX + 1) + tx];
+        const float d2 = f2[v * NF + (ty + 1) * TX + tx] - f2[v * NF + ty * TX + tx];
+        const float d3 = f3p[v] - f3m[v];
+        const float L = -fmaf(d1, idx1f, fmaf(d2, idx2f, d3 * idx3f));
+        const double Ld = f32_to_f64(L);
+        const double uik = ucol[v * NOWN + tid];
+        double r;
+        if (form == 1)
+          r = half(ucol[(5 + v) * NOWN + tid] + fma(dt, Ld, uik));
+        else if (form == 0)
+          r = fma(dt, Ld, uik);
+        else
+          r = fma(b, fma(dt, Ld, uik), a * ucol[(5 + v) * NOWN + tid]);
+        un[v] = r;
+        uout[e + v * vst] = r;
+      }
+      if (last_stage) {
+        // CFL ratio in FP32: it only sets the next step's dt
+        const float rho = fmaxf(f64_to_f32(un[0]), (float)AK_RHO_FLOOR);
+        const float ir = rcp_approx_f32(rho);
+        const float m1 = f64_to_f32(un[1]), m2 = f64_to_f32(un[2]), m3 = f64_to_f32(un[3]);
+        const float ug = fmaxf(fmaf(-0.5f * ir, fmaf(m1, m1, fmaf(m2, m2, m3 * m3)),
+                                    f64_to_f32(un[4])), (float)AK_UG_FLOOR);
+        const float cs = sqrt_fast(bg.gamma_f * (bg.gamma_f - 1.0f) * ug * ir);
+        float lam = fmaf(fabsf(m1), ir, cs) * idx1f;
+        lam = fmaxf(lam, fmaf(fabsf(m2), ir, cs) * idx2f);
+        lam = fmaxf(lam, fmaf(fabsf(m3), ir, cs) * idx3f);
+        dtmin_f = fminf(dtmin_f, rcp_approx_f32(lam));
+      }
+    }
+    if (column) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) f3m[v] = f3p[v];
+    }
+    if (more) {
+      if (column)
+        convert_staged(k + NG + 1, 0, 1);
+      else
+        convert_staged(k + NG + 1, 1 + XF, NMY);
+    }
+  }
+
+  if (last_stage) {
+    double dtmin = f32_to_f64(dtmin_f);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dtmin = fmin(dtmin, __shfl_xor_sync(0xffffffffu, dtmin, o));
+    __syncthreads();
+    if ((tid & 31) == 0) red[tid >> 5] = dtmin;
+    __syncthreads();
+    if (tid < 32) {
+      double v = tid < C::NTH / 32 ? red[tid] : __longlong_as_double(0x7ff0000000000000ll);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+      if (tid == 0) atomicMin(&sc->dtmin_bits, (unsigned long long)__double_as_longlong(v));
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_stage_mx(const ak_mesh* m, const double* uin, const double* u0, double* uout,
+                            const Bg& bg, double a, double b, int form, int last_stage,
+                            bool prepare_only) {
+  using C = MxCfg<2, 16>;
+  auto kern = stage_mx_kernel<2, 16>;
+  if (prepare_only)
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::bytes);
+  kern<<<(unsigned)m->nwork, C::NTH, C::bytes, m->stream>>>(uin, u0, uout, m->md, m->d_work, bg,
+                                                            a, b, form, m->d_sc, last_stage);
+  return cudaGetLastError();
+}
+
+}  // namespace ak

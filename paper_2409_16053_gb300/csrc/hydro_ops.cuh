@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include "fastmath.cuh"
+#include "lanes.cuh"
 
 namespace ak {
 
@@ -31,6 +32,10 @@ struct Bg {
   double kq;             // (gamma + 1) / (2 gamma), for the shock speed factor
   double gm1;            // gamma - 1
   float ug_floor_f;      // u_g floor minus u_g,b, rounded (mixed form)
+  float gm1_f;           // gamma - 1, gamma / (gamma - 1), (gamma + 1) / (2 gamma) and
+  float gg_f;            // p_b = (gamma - 1) u_g,b, rounded (mixed form)
+  float kq_f;
+  float pb_f;
 };
 
 // ------------------------------------------------------------------------------
@@ -50,18 +55,6 @@ __device__ __forceinline__ double plm_slope(double qm, double q0, double qp) {
   return prod > 0.0 ? (prod + prod) * rcp64(dl + dr) : 0.0;
 }
 
-// FP32: the harmonic mean with the hardware reciprocal refined once in FP32
-__device__ __forceinline__ float plm_slope(float qm, float q0, float qp) {
-  const float dl = q0 - qm;
-  const float dr = qp - q0;
-  const float prod = dl * dr;
-  if (!(prod > 0.0f)) return 0.0f;
-  const float s = dl + dr;
-  float r = rcp_approx_f32(s);
-  r = fmaf(r, fmaf(-s, r, 1.0f), r);
-  return (prod + prod) * r;
-}
-
 // Half of the van Leer slope, dl dr / (dl + dr): the offset of the face values from the
 // cell value.  In FP64 it skips the doubling and halving of plm_slope (same bits: both
 // are exact scalings by two).
@@ -70,9 +63,6 @@ __device__ __forceinline__ double plm_half_slope(double qm, double q0, double qp
   const double dr = qp - q0;
   const double prod = dl * dr;
   return dpos(prod) ? prod * rcp64(dl + dr) : 0.0;
-}
-__device__ __forceinline__ float plm_half_slope(float qm, float q0, float qp) {
-  return 0.5f * plm_slope(qm, q0, qp);
 }
 
 template <typename R>
@@ -190,78 +180,132 @@ __device__ __forceinline__ void hllc_fp64(const double* wl, const double* wr, co
 }
 
 // ------------------------------------------------------------------------------
-// HLLC, mixed form.  w = (rho - rho_b, u_n, u_t1, u_t2, u_g - u_g,b) in FP32.
-// Returns F - (0, p_b, 0, 0, 0).  Every difference of two O(1) quantities is formed
-// from the deviations, so that a perturbation of relative size 1e-6 keeps ~7 digits.
+// Mixed form, FP32 on deviations, written once over the lane-generic operations of
+// lanes.cuh: V = float solves one problem, V = float2 two at once with the same bits.
 // ------------------------------------------------------------------------------
-__device__ __forceinline__ float sqrt_fast(float x) { return x * rsqrt_approx_f32(x); }
+// PLM, van Leer: face values q0 -+ dl dr / (dl + dr) (zero slope at extrema); the
+// reciprocal is the hardware seed refined once in FP32
+template <typename V>
+__device__ __forceinline__ void plm_edges_v(V qm, V q0, V qp, V& lo, V& hi) {
+  const V zero = vset<V>(0.0f);
+  const V dl = vsub(q0, qm);
+  const V dr = vsub(qp, q0);
+  const V prod = vmul(dl, dr);
+  const V s = vadd(dl, dr);
+  V r = vrcp(s);
+  r = vfma(r, vfma(vneg(s), r, vset<V>(1.0f)), r);
+  const V h = vsel(vgt(prod, zero), vmul(prod, r), zero);
+  lo = vsub(q0, h);
+  hi = vadd(q0, h);
+}
 
-__device__ __forceinline__ void hllc_mixed(const float* wl, const float* wr, const Bg& bg,
-                                           float* f) {
-  const float g = bg.gamma_f;
-  const float gm1 = g - 1.0f;
-  const float gg = g * rcp_approx_f32(gm1);             // gamma / (gamma - 1)
-  const float rl = bg.rho_f + wl[0], rr = bg.rho_f + wr[0];
-  const float ul = wl[1], ur = wr[1];
-  const float dpl = gm1 * wl[4], dpr = gm1 * wr[4];     // p - p_b
-  const float pb = gm1 * bg.ug_f;
-  const float pl = pb + dpl, pr = pb + dpr;             // full pressures
-  const float kel = 0.5f * rl * fmaf(ul, ul, fmaf(wl[2], wl[2], wl[3] * wl[3]));
-  const float ker = 0.5f * rr * fmaf(ur, ur, fmaf(wr[2], wr[2], wr[3] * wr[3]));
-  const float hl = fmaf(gg, pl, kel);                   // E + p
-  const float hr = fmaf(gg, pr, ker);
-  const float gpl = g * pl, gpr = g * pr;
-  const float cl = gpl * rsqrt_approx_f32(gpl * rl);   // sqrt(gamma p / rho)
-  const float cr = gpr * rsqrt_approx_f32(gpr * rr);
+// CW84 limited slope: centred difference bounded by twice the one-sided ones
+template <typename V>
+__device__ __forceinline__ V ppm_slope_v(V qm, V q0, V qp) {
+  const V zero = vset<V>(0.0f), two = vset<V>(2.0f);
+  const V dl = vsub(q0, qm);
+  const V dr = vsub(qp, q0);
+  const V d = vmul(vset<V>(0.5f), vsub(qp, qm));
+  V m = vabs(d);
+  const V tl = vmul(two, vabs(dl));
+  const V tr = vmul(two, vabs(dr));
+  m = vsel(vgt(m, tl), tl, m);
+  m = vsel(vgt(m, tr), tr, m);
+  const V sm = vsel(vgt(d, zero), m, vneg(m));
+  return vsel(vgt(vmul(dl, dr), zero), sm, zero);
+}
+
+// CW84 interface values of the middle cell of q0..q4 and their monotonization
+template <typename V>
+__device__ __forceinline__ void ppm_edges_v(V q0, V q1, V q2, V q3, V q4, V& lo, V& hi) {
+  const V zero = vset<V>(0.0f);
+  const V sm = ppm_slope_v(q0, q1, q2);
+  const V sc = ppm_slope_v(q1, q2, q3);
+  const V sp = ppm_slope_v(q2, q3, q4);
+  const V sixth = vset<V>(1.0f / 6.0f);
+  const V a_lo = vfma(vsub(sm, sc), sixth, vmul(vset<V>(0.5f), vadd(q1, q2)));
+  const V a_hi = vfma(vsub(sc, sp), sixth, vmul(vset<V>(0.5f), vadd(q2, q3)));
+  const V a = q2;
+  const auto flat = vnot(vgt(vmul(vsub(a_hi, a), vsub(a, a_lo)), zero));
+  const V da = vsub(a_hi, a_lo);
+  const V a6 = vmul(vset<V>(6.0f), vfma(vset<V>(-0.5f), vadd(a_lo, a_hi), a));
+  const V da2 = vmul(da, da);
+  const V daa6 = vmul(da, a6);
+  const auto c1 = vgt(daa6, da2);
+  const auto c2 = vand(vnot(c1), vgt(vmul(vneg(da), da), daa6));
+  const V n_lo = vsel(c1, vfma(vset<V>(3.0f), a, vmul(vset<V>(-2.0f), a_hi)), a_lo);
+  const V n_hi = vsel(c2, vfma(vset<V>(3.0f), a, vmul(vset<V>(-2.0f), a_lo)), a_hi);
+  lo = vsel(flat, a, n_lo);
+  hi = vsel(flat, a, n_hi);
+}
+
+// HLLC, mixed form.  w = (rho - rho_b, u_n, u_t1, u_t2, u_g - u_g,b) in FP32.  Returns
+// F - (0, p_b, 0, 0, 0).  Every difference of two O(1) quantities is formed from the
+// deviations, so that a perturbation of relative size 1e-6 keeps ~7 digits.  Without
+// branches: the star state of the upwind side K is always formed, and its jump term is
+// switched off (S_K -> 0) when the fan is supersonic, which leaves the physical flux F_K.
+template <typename V>
+__device__ __forceinline__ void hllc_mixed(const V* wl, const V* wr, const Bg& bg, V* f) {
+  const V zero = vset<V>(0.0f), one = vset<V>(1.0f), half = vset<V>(0.5f);
+  const V g = vset<V>(bg.gamma_f), gm1 = vset<V>(bg.gm1_f), gg = vset<V>(bg.gg_f);
+  const V pb = vset<V>(bg.pb_f);
+  const V rl = vadd(vset<V>(bg.rho_f), wl[0]), rr = vadd(vset<V>(bg.rho_f), wr[0]);
+  const V ul = wl[1], ur = wr[1];
+  const V dpl = vmul(gm1, wl[4]), dpr = vmul(gm1, wr[4]);  // p - p_b
+  const V pl = vadd(pb, dpl), pr = vadd(pb, dpr);          // full pressures
+  const V kel = vmul(vmul(half, rl), vfma(ul, ul, vfma(wl[2], wl[2], vmul(wl[3], wl[3]))));
+  const V ker = vmul(vmul(half, rr), vfma(ur, ur, vfma(wr[2], wr[2], vmul(wr[3], wr[3]))));
+  const V hl = vfma(gg, pl, kel);                          // E + p
+  const V hr = vfma(gg, pr, ker);
+  const V gpl = vmul(g, pl), gpr = vmul(g, pr);
+  const V cl = vmul(gpl, vrsqrt(vmul(gpl, rl)));           // sqrt(gamma p / rho)
+  const V cr = vmul(gpr, vrsqrt(vmul(gpr, rr)));
 
   // PVRS estimate as a deviation from p_b; p* = max(0, p_b + dps)
-  float dps = fmaf(-0.125f * (ur - ul) * (rl + rr), cl + cr, 0.5f * (dpl + dpr));
-  dps = (pb + dps > 0.0f) ? dps : -pb;
-  const float kq = (g + 1.0f) * rcp_approx_f32(2.0f * g);
-  float ql = 1.0f, qr = 1.0f;
-  if (dps > dpl) ql = sqrt_fast(fmaf(kq * (dps - dpl), rcp_approx_f32(pl), 1.0f));
-  if (dps > dpr) qr = sqrt_fast(fmaf(kq * (dps - dpr), rcp_approx_f32(pr), 1.0f));
-  float sl = fmaf(-cl, ql, ul);
-  float sr = fmaf(cr, qr, ur);
-  sl = (ur - cr < sl) ? ur - cr : sl;
-  sr = (ul + cl > sr) ? ul + cl : sr;
+  V dps = vfma(vmul(vmul(vset<V>(-0.125f), vsub(ur, ul)), vadd(rl, rr)), vadd(cl, cr),
+               vmul(half, vadd(dpl, dpr)));
+  dps = vsel(vgt(vadd(pb, dps), zero), dps, vneg(pb));
+  const V kq = vset<V>(bg.kq_f);
+  const V al = vfma(vmul(kq, vsub(dps, dpl)), vrcp(pl), one);
+  const V ar = vfma(vmul(kq, vsub(dps, dpr)), vrcp(pr), one);
+  const V ql = vsel(vgt(dps, dpl), vmul(al, vrsqrt(al)), one);
+  const V qr = vsel(vgt(dps, dpr), vmul(ar, vrsqrt(ar)), one);
+  V sl = vfma(vneg(cl), ql, ul);
+  V sr = vfma(cr, qr, ur);
+  const V dl = vsub(ur, cr), dr = vadd(ul, cl);            // Davis bounds
+  sl = vsel(vgt(sl, dl), dl, sl);
+  sr = vsel(vgt(dr, sr), dr, sr);
 
-  if (sl >= 0.0f || sr <= 0.0f) {
-    const bool up_left = sl >= 0.0f;
-    const float* wu = up_left ? wl : wr;
-    const float ru = up_left ? rl : rr;
-    const float mu = ru * wu[1];
-    f[0] = mu;
-    f[1] = fmaf(mu, wu[1], up_left ? dpl : dpr);
-    f[2] = mu * wu[2];
-    f[3] = mu * wu[3];
-    f[4] = (up_left ? hl : hr) * wu[1];
-    return;
-  }
-  const float ml = rl * (sl - ul);
-  const float mr = rr * (sr - ur);
-  const float sstar = fmaf(ul, ml, fmaf(-ur, mr, dpr - dpl)) * rcp_approx_f32(ml - mr);
-  const bool left = sstar >= 0.0f;
-  const float* w = left ? wl : wr;
-  const float rk = left ? rl : rr;
-  const float mk = left ? ml : mr;                      // rho_K (S_K - u_K)
-  const float uk = w[1];
-  const float s = left ? sl : sr;
-  const float pk = left ? pl : pr;
-  const float ek = (left ? kel : ker) + (bg.ug_f + w[4]);
-  const float mn = rk * uk;
-  const float inv = rcp_approx_f32(s - sstar);
-  const float fac = mk * inv;
-  const float drho = rk * (sstar - uk) * inv;           // U*_rho - rho_K
-  const float dmn = fmaf(fac, sstar, -mn);              // U*_Mn - M_n
-  // E*_K - E_K = (S* - u_K) ((E_K + p_K) / (S_K - S*) + rho*_K S*)
-  const float de = (sstar - uk) * fmaf(fac, sstar, (ek + pk) * inv);
-  const float mt = fmaf(s, drho, mn);                   // M_n + S_K (U*_rho - rho_K)
+  const auto sup_l = vge(sl, zero);                        // S_L >= 0
+  const auto sup_r = vge(zero, sr);                        // S_R <= 0
+  const V ml = vmul(rl, vsub(sl, ul));
+  const V mr = vmul(rr, vsub(sr, ur));
+  const V sstar = vmul(vfma(ul, ml, vfma(vneg(ur), mr, vsub(dpr, dpl))), vrcp(vsub(ml, mr)));
+  const auto left = vor(sup_l, vand(vnot(sup_r), vge(sstar, zero)));
+  const auto sub = vnot(vor(sup_l, sup_r));
+  const V rk = vsel(left, rl, rr), uk = vsel(left, ul, ur);
+  const V w2 = vsel(left, wl[2], wr[2]), w3 = vsel(left, wl[3], wr[3]);
+  const V dpk = vsel(left, dpl, dpr), pk = vsel(left, pl, pr), hk = vsel(left, hl, hr);
+  const V mk = vsel(left, ml, mr);                         // rho_K (S_K - u_K)
+  const V s = vsel(left, sl, sr);
+  const V ek = vadd(vsel(left, kel, ker), vadd(vset<V>(bg.ug_f), vsel(left, wl[4], wr[4])));
+  const V mn = vmul(rk, uk);
+  const V inv = vrcp(vsub(s, sstar));
+  const V fac = vmul(mk, inv);
+  const V su = vsub(sstar, uk);
+  // U*_rho - rho_K, U*_Mn - M_n, and E*_K - E_K = (S* - u_K) ((E_K + p_K)/(S_K - S*) + rho*_K S*)
+  const V drho = vsel(sub, vmul(vmul(rk, su), inv), zero);
+  const V dmn = vsel(sub, vfma(fac, sstar, vneg(mn)), zero);
+  const V de = vsel(sub, vmul(su, vfma(fac, sstar, vmul(vadd(ek, pk), inv))), zero);
+  const V se = vsel(sub, s, zero);
+  const V mt = vfma(se, drho, mn);                         // M_n + S_K (U*_rho - rho_K)
   f[0] = mt;
-  f[1] = fmaf(s, dmn, fmaf(mn, uk, left ? dpl : dpr));
-  f[2] = mt * w[2];
-  f[3] = mt * w[3];
-  f[4] = fmaf(s, de, (left ? hl : hr) * uk);
+  f[1] = vfma(se, dmn, vfma(mn, uk, dpk));
+  f[2] = vmul(mt, w2);
+  f[3] = vmul(mt, w3);
+  f[4] = vfma(se, de, vmul(hk, uk));
 }
+
+__device__ __forceinline__ float sqrt_fast(float x) { return x * rsqrt_approx_f32(x); }
 
 }  // namespace ak

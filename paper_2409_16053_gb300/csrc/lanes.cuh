@@ -1,0 +1,78 @@
+// Lane-generic FP32 arithmetic for the mixed form: every function below exists for a
+// scalar `float` and for a `float2` that carries two independent problems in its two
+// lanes (GB300's packed FP32x2 add, multiply and fused multiply-add issue one
+// instruction for both).  Each lane of a float2 operation rounds exactly like the
+// scalar operation, so code written once over these functions gives the same bits for a
+// problem solved alone or paired with another one.  Comparisons, selects and the
+// hardware reciprocal / rsqrt seeds act lane by lane.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "fastmath.cuh"
+
+namespace ak {
+
+struct bool2 {
+  bool x, y;
+};
+
+// ---- arithmetic ------------------------------------------------------------------------
+__device__ __forceinline__ float vadd(float a, float b) { return a + b; }
+__device__ __forceinline__ float vsub(float a, float b) { return a - b; }
+__device__ __forceinline__ float vmul(float a, float b) { return a * b; }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
+
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+// a - b = fma(b, -1, a): the product is exact, so this rounds like the subtraction
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+}
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+__device__ __forceinline__ float vneg(float a) { return -a; }
+__device__ __forceinline__ float2 vneg(float2 a) { return make_float2(-a.x, -a.y); }
+
+// broadcast of a scalar constant
+template <typename V> __device__ __forceinline__ V vset(float c);
+template <> __device__ __forceinline__ float vset<float>(float c) { return c; }
+template <> __device__ __forceinline__ float2 vset<float2>(float c) { return make_float2(c, c); }
+
+// ---- lane-wise comparisons and selects ---------------------------------------------------
+__device__ __forceinline__ bool vgt(float a, float b) { return a > b; }
+__device__ __forceinline__ bool vge(float a, float b) { return a >= b; }
+__device__ __forceinline__ bool2 vgt(float2 a, float2 b) { return {a.x > b.x, a.y > b.y}; }
+__device__ __forceinline__ bool2 vge(float2 a, float2 b) { return {a.x >= b.x, a.y >= b.y}; }
+
+__device__ __forceinline__ bool vnot(bool a) { return !a; }
+__device__ __forceinline__ bool vor(bool a, bool b) { return a || b; }
+__device__ __forceinline__ bool vand(bool a, bool b) { return a && b; }
+__device__ __forceinline__ bool2 vnot(bool2 a) { return {!a.x, !a.y}; }
+__device__ __forceinline__ bool2 vor(bool2 a, bool2 b) { return {a.x || b.x, a.y || b.y}; }
+__device__ __forceinline__ bool2 vand(bool2 a, bool2 b) { return {a.x && b.x, a.y && b.y}; }
+
+__device__ __forceinline__ float vsel(bool c, float a, float b) { return c ? a : b; }
+__device__ __forceinline__ float2 vsel(bool2 c, float2 a, float2 b) {
+  return make_float2(c.x ? a.x : b.x, c.y ? a.y : b.y);
+}
+
+__device__ __forceinline__ float vabs(float a) { return fabsf(a); }
+__device__ __forceinline__ float2 vabs(float2 a) { return make_float2(fabsf(a.x), fabsf(a.y)); }
+
+// ---- hardware seeds (rcp.approx / rsqrt.approx, flush-to-zero) ----------------------------
+__device__ __forceinline__ float vrcp(float a) { return rcp_approx_f32(a); }
+__device__ __forceinline__ float vrsqrt(float a) { return rsqrt_approx_f32(a); }
+__device__ __forceinline__ float2 vrcp(float2 a) {
+  return make_float2(rcp_approx_f32(a.x), rcp_approx_f32(a.y));
+}
+__device__ __forceinline__ float2 vrsqrt(float2 a) {
+  return make_float2(rsqrt_approx_f32(a.x), rsqrt_approx_f32(a.y));
+}
+
+// lane type of a predicate
+template <typename V> struct lanes_of;
+template <> struct lanes_of<float> { using B = bool; };
+template <> struct lanes_of<float2> { using B = bool2; };
+
+}  // namespace ak

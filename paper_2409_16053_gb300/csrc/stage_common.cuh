@@ -1,0 +1,149 @@
+// Device building blocks shared by the stage kernels and the flux-correction kernel:
+// primitive recovery (Section 3.1, Eq. (4)), reconstruction edges, the direction
+// permutation around the Riemann solver, and the corrected coarse-face fluxes of
+// static refinement.
+#pragma once
+
+#include <type_traits>
+
+#include "ak_internal.cuh"
+#include "hydro_ops.cuh"
+
+namespace ak {
+
+struct Counters {
+  unsigned long long* floors;
+  unsigned long long* nonfinite;
+};
+
+__device__ __forceinline__ void count(unsigned long long* c) { atomicAdd(c, 1ull); }
+
+// Bit-level tests that keep comparisons of doubles off the FP64 pipe.
+__device__ __forceinline__ bool not_finite(double x) {
+  return ((unsigned)__double2hiint(x) & 0x7ff00000u) == 0x7ff00000u;
+}
+// x >= floor for a positive, finite `floor` (false for negative x and NaN-free x < floor)
+__device__ __forceinline__ bool at_least(double x, double floor) {
+  return __double_as_longlong(x) >= __double_as_longlong(floor);
+}
+
+// Conserved -> primitive (Section 3.1 Eq. (4)), FP64 form.
+__device__ __forceinline__ void c2p(const double* u, double* w, const Bg&, Counters cn) {
+  double rho = u[0];
+  if (not_finite(rho) || not_finite(u[4])) count(cn.nonfinite);
+  if (!at_least(rho, AK_RHO_FLOOR)) {
+    rho = AK_RHO_FLOOR;
+    count(cn.floors);
+  }
+  const double r = rcp64(rho);
+  const double v1 = u[1] * r, v2 = u[2] * r, v3 = u[3] * r;
+  double ug = fma(-0.5, fma(u[1], v1, fma(u[2], v2, u[3] * v3)), u[4]);
+  if (!at_least(ug, AK_UG_FLOOR)) {
+    ug = AK_UG_FLOOR;
+    count(cn.floors);
+  }
+  w[0] = rho;
+  w[1] = v1;
+  w[2] = v2;
+  w[3] = v3;
+  w[4] = ug;
+}
+
+// Conserved -> primitive, mixed form.  The internal-energy recovery runs in FP64 with
+// the cancellation done before any division: rho (u_g - u_g,b) = rho (E - u_g,b) -
+// |M|^2 / 2 is formed in FP64, rounded to FP32 and only then divided by rho (FP32
+// reciprocal), so u_g - u_g,b keeps FP32 relative precision whatever the Mach number,
+// without an FP64 reciprocal.  rho - rho_b is an FP64 difference; velocities come from
+// FP32 arithmetic; the deviations W' are rounded to FP32 on the integer pipe.
+__device__ __forceinline__ void c2p(const double* u, float* w, const Bg& bg, Counters cn) {
+  double rho = u[0];
+  if (not_finite(rho) || not_finite(u[4])) count(cn.nonfinite);
+  if (!at_least(rho, AK_RHO_FLOOR)) {
+    rho = AK_RHO_FLOOR;
+    count(cn.floors);
+  }
+  const float rhof = f64_to_f32(rho);
+  float rf = rcp_approx_f32(rhof);
+  rf = fmaf(rf, fmaf(-rhof, rf, 1.0f), rf);
+  const double m2 = fma(u[1], u[1], fma(u[2], u[2], u[3] * u[3]));
+  const double num = fma(u[4] - bg.ug, rho, -dscale_down(m2, 1, 0.5));  // rho (u_g - u_g,b)
+  float dugf = f64_to_f32(num) * rf;
+  if (!(dugf >= bg.ug_floor_f)) {           // u_g below its floor (FP32 resolution)
+    dugf = f64_to_f32(AK_UG_FLOOR - bg.ug);
+    count(cn.floors);
+  }
+  w[0] = f64_to_f32(rho - bg.rho);
+  w[1] = f64_to_f32(u[1]) * rf;
+  w[2] = f64_to_f32(u[2]) * rf;
+  w[3] = f64_to_f32(u[3]) * rf;
+  w[4] = dugf;
+}
+
+__device__ __forceinline__ void riemann(const double* wl, const double* wr, const Bg& bg,
+                                        double* f) {
+  hllc_fp64(wl, wr, bg, f);
+}
+__device__ __forceinline__ void riemann(const float* wl, const float* wr, const Bg& bg,
+                                        float* f) {
+  hllc_mixed(wl, wr, bg, f);
+}
+
+// Lower and upper edge values of the middle cell of q[0 .. 2NG-2].
+template <int NG, typename R>
+__device__ __forceinline__ void edges(const R* q, R& lo, R& hi) {
+  if constexpr (std::is_same<R, float>::value) {
+    if constexpr (NG == 2)
+      plm_edges_v(q[0], q[1], q[2], lo, hi);
+    else
+      ppm_edges_v(q[0], q[1], q[2], q[3], q[4], lo, hi);
+  } else if constexpr (NG == 2) {
+    const R h = plm_half_slope(q[0], q[1], q[2]);
+    lo = q[1] - h;
+    hi = q[1] + h;
+  } else {
+    ppm_edges(q[0], q[1], q[2], q[3], q[4], lo, hi);
+  }
+}
+
+// HLLC on one face of direction d from edge values in natural variable order; the
+// flux comes back in natural order (rho, M1, M2, M3, E).
+template <typename R>
+__device__ __forceinline__ void solve(int d, const R* l, const R* r, const Bg& bg, R* f) {
+  const int perm[5] = {0, 1 + d, 1 + (d + 1) % 3, 1 + (d + 2) % 3, 4};
+  R wl[5], wr[5], fn[5];
+#pragma unroll
+  for (int n = 0; n < 5; ++n) {
+    wl[n] = l[perm[n]];
+    wr[n] = r[perm[n]];
+  }
+  riemann(wl, wr, bg, fn);
+#pragma unroll
+  for (int n = 0; n < 5; ++n) f[perm[n]] = fn[n];
+}
+
+// 0.5 * x for a finite double, on the integer pipe (the multiply for zero and
+// numbers near the subnormal range)
+__device__ __forceinline__ double half(double x) {
+  const int hi = __double2hiint(x);
+  if ((hi & 0x7fe00000) == 0) return 0.5 * x;
+  if ((hi & 0x7ff00000) == 0x7ff00000) return x;  // inf, NaN
+  return __hiloint2double(hi - 0x00100000, __double2loint(x));
+}
+
+// The corrected (fine-mean) flux of one coarse face cell from the correction buffer.
+__device__ __forceinline__ void corrected_flux(const double* buf, int cell, double* f) {
+#pragma unroll
+  for (int v = 0; v < 5; ++v) f[v] = buf[(long long)cell * 5 + v];
+}
+__device__ __forceinline__ void corrected_flux(const double* buf, int cell, float* f) {
+#pragma unroll
+  for (int v = 0; v < 5; ++v) f[v] = f64_to_f32(buf[(long long)cell * 5 + v]);
+}
+
+// Mixed-form PLM stage with paired x1/x2 work (ak_stage_mx.cu); prepare_only sets the
+// kernel's shared-memory attribute.
+cudaError_t launch_stage_mx(const ak_mesh* m, const double* uin, const double* u0, double* uout,
+                            const Bg& bg, double a, double b, int form, int last_stage,
+                            bool prepare_only);
+
+}  // namespace ak

@@ -172,3 +172,24 @@ def test_smr_autotune_keeps_results_bitwise(ak):
     assert np.array_equal(a.download_packed(), b.download_packed())
     a.close()
     b.close()
+
+
+def test_smr_mixed_kernel_variants_bitwise(ak):
+    """Every mixed-form kernel variant gives the same bits on a refined mesh (16^3 and
+    8^3 leaves: tiles larger than the blocks)."""
+    t = pgen.nested_refinement_blocks(32, 8, 8, 2)
+    P = _smooth(t, 32)
+    ref = None
+    for tile, seg, order in [(2, 1, 0), (0, 1, 0), (0, 2, 1), (1, 1, 1)]:
+        m = _gpu_mesh(ak, t, 32, precision=1, ref_rho=1.0, ref_p=1.0)
+        m.schedule(tile, seg, order)
+        m.upload_packed(P)
+        dt = m.new_dt()
+        for _ in range(3):
+            m.step(dt, want_dt_next=False)
+        out = m.download_packed()
+        m.close()
+        if ref is None:
+            ref = out
+        else:
+            assert np.array_equal(out, ref), (tile, seg, order)

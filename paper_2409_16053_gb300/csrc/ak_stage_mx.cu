@@ -26,12 +26,15 @@ namespace ak {
 
 namespace {
 
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+// 16-byte copy global -> shared through L2 only
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
 }
-// waits for all of this thread's cp.async copies
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// waits until at most N of this thread's committed copy groups are still in flight
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 template <int NG, int T>
 struct MxCfg {
@@ -108,35 +111,70 @@ __global__ void __launch_bounds__(MxCfg<NG, T>::NTH, 2)
     }
   };
   constexpr int NMY = 1 + XPT;  // slot 0: the column threads' cell; slots 1..: spare threads'
-  int mycell[NMY], mypos[NMY], myoff[NMY];
+  // cross cell of slot m of this thread (or >= NCROSS: none)
+  auto cell_of = [&](int m) {
+    return tid < NOWN ? (m == 0 ? tid : NCROSS) : (m == 0 ? NCROSS : tid + NSPARE * (m - 1));
+  };
+  int mypos[NMY];  // ring position of the slot's cell, or -1 (none, or outside the block)
 #pragma unroll
   for (int m = 0; m < NMY; ++m) {
-    const int c = tid < NOWN ? (m == 0 ? tid : -1)
-                             : (m == 0 ? -1 : NOWN + (tid - NOWN) + NSPARE * (m - 1));
-    mycell[m] = (c >= 0 && c < NCROSS) ? c : -1;
+    const int c = cell_of(m);
     mypos[m] = -1;
-    myoff[m] = 0;
-    if (mycell[m] >= 0) {
+    if (c < NCROSS) {
       int x, y;
-      cross_xy(mycell[m], x, y);
-      const int ip = i0 + x, jp = j0 + y;  // padded indices (halo starts at i0 - NG)
+      cross_xy(c, x, y);
+      if (i0 + x < g.p1 && j0 + y < g.p2) mypos[m] = y * WX + x;
+    }
+  }
+  // ---- 16-byte copy chunks of this thread ----------------------------------------------
+  // The next plane's cross, two cells per chunk: every row starts 16-byte aligned (the
+  // interior of a row is 32-byte aligned, NG is even and tiles start at multiples of 16),
+  // and p1 is even, so a chunk is inside the block when its first cell is.
+  static_assert(NG % 2 == 0, "16-byte row chunks need an even ghost width");
+  constexpr int FULLC = (TX + 2 * NG) / 2;            // chunks of a row with its x1 halo
+  constexpr int HALOC = TX / 2;                       // chunks of an x2 halo row
+  constexpr int CPV = C::TY * FULLC + 2 * NG * HALOC;  // chunks per variable
+  constexpr int NSC = (5 * CPV + C::NTH - 1) / C::NTH;
+  int sc_s[NSC], sc_g[NSC];  // shared element index (-1: none), element offset at plane 0
+#pragma unroll
+  for (int m = 0; m < NSC; ++m) {
+    const int q = tid + C::NTH * m;
+    sc_s[m] = -1;
+    sc_g[m] = 0;
+    if (q < 5 * CPV) {
+      const int v = q / CPV;
+      int r = q % CPV, x, y, c;
+      if (r < C::TY * FULLC) {
+        y = NG + r / FULLC;
+        x = 2 * (r % FULLC);
+        c = NG * TX + (y - NG) * (TX + 2 * NG) + x;
+      } else {
+        r -= C::TY * FULLC;
+        const int hr = r / HALOC;
+        x = NG + 2 * (r % HALOC);
+        y = hr < NG ? hr : hr + C::TY;
+        c = y < NG ? y * TX + (x - NG)
+                   : NG * TX + C::TY * (TX + 2 * NG) + (y - NG - C::TY) * TX + (x - NG);
+      }
+      const int ip = i0 + x, jp = j0 + y;
       if (ip < g.p1 && jp < g.p2) {
-        mypos[m] = y * WX + x;
-        myoff[m] = (NG * g.p2 + jp) * g.s1 + ip;  // element of plane 0, variable 0
+        sc_s[m] = v * NCROSS + c;
+        sc_g[m] = v * (int)vst + (NG * g.p2 + jp) * g.s1 + ip;
       }
     }
   }
-  // stage plane kp of the slots [m0, m1) into shared memory
-  auto stage_cells = [&](int kp, int m0, int m1) {
+  auto stage_plane = [&](int kp) {
+    const long long po = (long long)kp * pst;
 #pragma unroll
-    for (int m = 0; m < NMY; ++m) {
-      if (m >= m0 && m < m1 && mypos[m] >= 0) {
-        const double* src = ub + myoff[m] + kp * pst;
-#pragma unroll
-        for (int v = 0; v < 5; ++v) cp_async8(&stg[v * NCROSS + mycell[m]], src + v * vst);
-      }
-    }
+    for (int m = 0; m < NSC; ++m)
+      if (sc_s[m] >= 0) cp_async16(&stg[sc_s[m]], ub + sc_g[m] + po);
   };
+  // The columns' U_in and U0: NOWN / 2 chunks (two cells of a tile row) per variable.
+  static_assert(NOWN % 2 == 0 && (NOWN / 2) % 32 == 0, "chunk rows per warp");
+  const int ocy = (tid % (NOWN / 2)) / (TX / 2), ocx = 2 * (tid % (TX / 2));
+  const int ocell = ocy * TX + ocx;
+  const bool ochunk = tid < NOWN && i0 + ocx < g.nx1 && j0 + ocy < g.nx2;
+  const int ooff = (NG * g.p2 + j0 + ocy + NG) * g.s1 + i0 + ocx + NG;  // from the block start
   // primitive recovery of staged cells of slots [m0, m1) into the ring slot of plane kp
   auto convert_staged = [&](int kp, int m0, int m1) {
     float* dst = ring + slot(kp) * 5 * NPL;
@@ -146,7 +184,7 @@ __global__ void __launch_bounds__(MxCfg<NG, T>::NTH, 2)
         double u[5];
         float wv[5];
 #pragma unroll
-        for (int v = 0; v < 5; ++v) u[v] = stg[v * NCROSS + mycell[m]];
+        for (int v = 0; v < 5; ++v) u[v] = stg[v * NCROSS + cell_of(m)];
         c2p(u, wv, bg, cn);
 #pragma unroll
         for (int v = 0; v < 5; ++v) dst[v * NPL + mypos[m]] = wv[v];
@@ -159,7 +197,8 @@ __global__ void __launch_bounds__(MxCfg<NG, T>::NTH, 2)
 #pragma unroll
     for (int m = 0; m < NMY; ++m) {
       if (mypos[m] >= 0) {
-        const double* src = ub + myoff[m] + kp * pst;
+        const int x = mypos[m] % WX, y = mypos[m] / WX;  // padded (i0 + x, j0 + y)
+        const double* src = ub + ((long long)(kp + NG) * g.p2 + j0 + y) * g.s1 + i0 + x;
         double u[5];
         float wv[5];
 #pragma unroll
@@ -220,15 +259,22 @@ __global__ void __launch_bounds__(MxCfg<NG, T>::NTH, 2)
   for (int k = k0; k < k1; ++k) {
     const bool more = k + 1 < k1;
     __syncthreads();  // A: the previous plane's phase U is complete
-    if (more) stage_cells(k + NG + 1, 0, NMY);
-    if (own) {
-      const long long e = ecol + k * pst;
+    if (more) stage_plane(k + NG + 1);
+    cp_async_commit();  // group: the next plane (needed from phase F on)
+    if (ochunk) {
+      // column thread t copies, for the row chunk (ocy, ocx), the arrays/variables
+      // vv = t / 128 + 2 m (U_in for vv < 5, U0 above): 5 x 2 x 128 chunks in all
+      const long long po = g.off + ooff + k * pst;
 #pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        cp_async8(&ucol[v * NOWN + tid], uin + e + v * vst);
-        if (need_u0) cp_async8(&ucol[(5 + v) * NOWN + tid], u0 + e + v * vst);
+      for (int m = 0; m < 10 * NOWN / 2 / NOWN; ++m) {
+        const int vv = tid / (NOWN / 2) + 2 * m;
+        if (vv < 5)
+          cp_async16(&ucol[vv * NOWN + ocell], uin + po + vv * vst);
+        else if (need_u0)
+          cp_async16(&ucol[vv * NOWN + ocell], u0 + po + (vv - 5) * vst);
       }
     }
+    cp_async_commit();  // group: the columns' U_in / U0 (needed in phase U)
 
     // ---- R: x1 and x2 edges of plane k, paired --------------------------------------
     const float* pl = ring + slot(k) * 5 * NPL;
@@ -250,8 +296,8 @@ __global__ void __launch_bounds__(MxCfg<NG, T>::NTH, 2)
         e2hi[v * NE + tid] = hi.y;
       }
     }
-    cp_async_wait_all();
-    __syncthreads();  // B: edges and staged data visible
+    cp_async_wait<1>();
+    __syncthreads();  // B: edges and the staged plane visible
 
     // ---- F: x3 edge and face of the column; x1/x2 faces, paired ---------------------
     if (column) {
@@ -290,7 +336,8 @@ __global__ void __launch_bounds__(MxCfg<NG, T>::NTH, 2)
       }
     }
     if (more && !column) convert_staged(k + NG + 1, 1, 1 + XF);
-    __syncthreads();  // C: fluxes complete
+    cp_async_wait<0>();
+    __syncthreads();  // C: fluxes and the columns' U_in / U0 complete
 
     // ---- U: divergence, RK update and CFL of the column's cell ------------------------
     if (own) {

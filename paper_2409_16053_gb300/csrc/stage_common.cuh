@@ -50,8 +50,8 @@ __device__ __forceinline__ void c2p(const double* u, double* w, const Bg&, Count
 }
 
 // Conserved -> primitive, mixed form.  The internal-energy recovery runs in FP64 with
-// the cancellation done before any division: rho (u_g - u_g,b) = rho (E - u_g,b) -
-// |M|^2 / 2 is formed in FP64, rounded to FP32 and only then divided by rho (FP32
+// the cancellation done before any division: 2 rho (u_g - u_g,b) = 2 rho (E - u_g,b) -
+// |M|^2 is formed in FP64, rounded to FP32 and only then divided by 2 rho (FP32
 // reciprocal), so u_g - u_g,b keeps FP32 relative precision whatever the Mach number,
 // without an FP64 reciprocal.  rho - rho_b is an FP64 difference; velocities come from
 // FP32 arithmetic; the deviations W' are rounded to FP32 on the integer pipe.
@@ -66,8 +66,9 @@ __device__ __forceinline__ void c2p(const double* u, float* w, const Bg& bg, Cou
   float rf = rcp_approx_f32(rhof);
   rf = fmaf(rf, fmaf(-rhof, rf, 1.0f), rf);
   const double m2 = fma(u[1], u[1], fma(u[2], u[2], u[3] * u[3]));
-  const double num = fma(u[4] - bg.ug, rho, -dscale_down(m2, 1, 0.5));  // rho (u_g - u_g,b)
-  float dugf = f64_to_f32(num) * rf;
+  // 2 rho (u_g - u_g,b); rho >= its floor is normal, so 2 rho is an exponent increment
+  const double num2 = fma(u[4] - bg.ug, dscale(rho, 1), -m2);
+  float dugf = f64_to_f32(num2) * (0.5f * rf);
   if (!(dugf >= bg.ug_floor_f)) {           // u_g below its floor (FP32 resolution)
     dugf = f64_to_f32(AK_UG_FLOOR - bg.ug);
     count(cn.floors);

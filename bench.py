@@ -357,6 +357,88 @@ def run_profile_case(args):
     return 0 if c[:2] == [0, 0] else 1
 
 
+def run_large_case(args):
+    """The large configurations, timed like the main line (device-resident dt,
+    graph-replayed ak_step, CUDA events on the mesh's stream):
+      c3: 512^3 in 64 MeshBlocks of 128^3, PPM4 + HLLC + RK3, k^-2 turbulence Mach 0.5,
+          FP64 and mixed;
+      c5: 768^3 in 512 MeshBlocks of 96^3, PLM + HLLC + RK2, mixed, solenoidal k^-2
+          (2 <= |k| <= 16) turbulence, rms Mach 2, 50 steps.
+    Inputs come from the torch form of the turbulence recipe, generated on the GPU.  Each
+    form also reports the L1 difference from the FP64 oracle after one step on a 64^3
+    sub-box replay (the interior beyond the step's stencil reach), sqrt(sum_k L1_k^2)
+    with L1_k the mean |U_k(GPU) - U_k(oracle)|."""
+    import torch
+    import oracle
+    import pgen
+    from paper_2409_16053_gb300 import ak
+    oracle.build()
+    c3 = args.case == "c3"
+    root = 512 if c3 else 768
+    nblk = 128 if c3 else 96
+    rk = 3 if c3 else 2
+    recon = ak.AK_PPM4 if c3 else ak.AK_PLM
+    reach = 9 if c3 else 4
+    steps = args.steps if c3 else max(args.steps, 50)
+    forms = [("fp64", ak.AK_FP64), ("mixed", ak.AK_MIXED)] if c3 else [("mixed", ak.AK_MIXED)]
+    gen = dict(seed=3, kmin=2, kmax=8, mach=0.5) if c3 else \
+        dict(seed=5, kmin=2, kmax=16, mach=2.0, solenoidal=True)
+    lo = (100, 100, 100) if c3 else (90, 300, 700)
+    cells = root ** 3
+    peaks, peak_kind = load_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    bytes_cu = 320.0 if rk == 3 else 200.0
+    out = {"case": args.case, "workload": (
+        f"{root}^3 periodic in {(root // nblk) ** 3} MeshBlocks of {nblk}^3, "
+        + ("PPM4+HLLC+RK3, k^-2 turbulence Mach 0.5" if c3 else
+           "PLM+HLLC+RK2, solenoidal k^-2 turbulence (2<=|k|<=16) Mach 2")),
+        "metric": "cell-updates/s", "steps": steps, "warmup": args.warmup, "forms": {}}
+    clocks = ClockSampler(0)
+    for name, prec in forms:
+        U0 = pgen.turbulence_device((root,) * 3, **gen)
+        sub = U0[:, lo[2]:lo[2] + 64, lo[1]:lo[1] + 64, lo[0]:lo[0] + 64].cpu().numpy()
+        m = ak.Mesh((root,) * 3, (nblk,) * 3, recon=recon, rk=rk, precision=prec,
+                    ref_rho=1.0, ref_p=1.0)
+        m.upload_device(U0)
+        del U0
+        torch.cuda.empty_cache()
+        dt = m.new_dt()
+        m.step(dt, want_dt_next=False)  # one step from the initial state: the replay
+        got = m.download_box(lo, (64,) * 3)
+        grid = oracle.Grid((64,) * 3, length=(64 / root,) * 3,
+                           recon=oracle.PPM4 if c3 else oracle.PLM)
+        ref, _ = oracle.rk_step(sub, grid, dt, rk)
+        c = slice(reach, 64 - reach)
+        l1 = float(np.sqrt(sum(np.mean(np.abs(got[k, c, c, c] - ref[k, c, c, c])) ** 2
+                               for k in range(5))))
+        for _ in range(args.warmup):
+            m.step(0.0, want_dt_next=False)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        clocks.start()
+        a.record(m.stream)
+        for _ in range(steps):
+            m.step(0.0, want_dt_next=False)
+        b.record(m.stream)
+        b.synchronize()
+        clk = clocks.stop()
+        ms = a.elapsed_time(b)
+        value = cells * steps / (ms * 1e-3)
+        gbs = value * bytes_cu / 1e9
+        out["forms"][name] = {
+            "value": value, "ms_per_step": ms / steps,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                         "frac": gbs / hbm, "bytes_per_cell_update": bytes_cu,
+                         "peak_source": f"{peak_kind} hbm_gbs"},
+            "l1_vs_oracle_subbox": l1, "dt0": dt, "dt_after": m.new_dt(),
+            "counters": m.counters(), "clocks": clk}
+        m.close()
+        del m
+        torch.cuda.empty_cache()
+    print(json.dumps(out), flush=True)
+    return 0 if all(f["counters"][:2] == [0, 0] for f in out["forms"].values()) else 1
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -364,13 +446,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--case", default="bench", choices=["bench", "profile", "profile-smr"])
+    ap.add_argument("--case", default="bench",
+                    choices=["bench", "profile", "profile-smr", "c3", "c5"])
     ap.add_argument("--form", default="fp64", choices=["fp64", "mixed"])
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.case in ("profile", "profile-smr"):
         return run_profile_case(args)
+    if args.case in ("c3", "c5"):
+        return run_large_case(args)
 
     ws, rank, local = dist_env()
     import torch

@@ -300,6 +300,48 @@ class Mesh:
     def download(self, reg=0):
         return self.unpack(self.download_packed(reg))
 
+    def upload_device(self, U, reg=0):
+        """Global (5, n3, n2, n1) float64 torch tensor on the mesh's device (uniform
+        mesh): each block's interior is copied device to device."""
+        torch = self.torch
+        assert self.uniform and tuple(U.shape) == (5, self.root_nx[2], self.root_nx[1],
+                                                   self.root_nx[0])
+        g = self.ng
+        n1, n2, n3 = self.block_nx
+        R = self.register_view(reg)
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+        with torch.cuda.stream(self.stream):
+            for b, row in enumerate(self.table):
+                lx, ly, lz = int(row[1]), int(row[2]), int(row[3])
+                R[b, :, g:g + n3, g:g + n2, g:g + n1].copy_(U[:, lz:lz + n3, ly:ly + n2,
+                                                            lx:lx + n1])
+        self.stream.synchronize()
+
+    def download_box(self, lo, size, reg=0):
+        """Interior cells lo <= (i, j, k) < lo + size of the global grid of a uniform mesh
+        (no periodic wrap), as a numpy (5, s3, s2, s1) array."""
+        torch = self.torch
+        g = self.ng
+        lo = [int(v) for v in lo]
+        size = [int(v) for v in size]
+        assert all(lo[d] >= 0 and lo[d] + size[d] <= self.root_nx[d] for d in range(3))
+        out = torch.empty((5, size[2], size[1], size[0]), dtype=torch.float64,
+                          device=self.device)
+        R = self.register_view(reg)
+        self.stream.synchronize()
+        for b, row in enumerate(self.table):
+            org = [int(row[1]), int(row[2]), int(row[3])]
+            n = [int(row[4]), int(row[5]), int(row[6])]
+            a = [max(lo[d], org[d]) for d in range(3)]
+            e = [min(lo[d] + size[d], org[d] + n[d]) for d in range(3)]
+            if any(a[d] >= e[d] for d in range(3)):
+                continue
+            src = R[b, :, g + a[2] - org[2]:g + e[2] - org[2], g + a[1] - org[1]:g + e[1] - org[1],
+                    g + a[0] - org[0]:g + e[0] - org[0]]
+            out[:, a[2] - lo[2]:e[2] - lo[2], a[1] - lo[1]:e[1] - lo[1],
+                a[0] - lo[0]:e[0] - lo[0]].copy_(src)
+        return out.cpu().numpy()
+
     def fill_ghosts(self, reg=0):
         ak_fill_ghosts(self.handle, reg)
 

@@ -107,6 +107,55 @@ def turbulence(n, seed, kmin=2, kmax=8, mach=0.5, solenoidal=False, rho=1.0, p=1
     return _cons(rho * ones, v[0], v[1], v[2], p * ones, gamma)
 
 
+def turbulence_device(n, seed, kmin=2, kmax=8, mach=0.5, solenoidal=False, rho=1.0, p=1.0,
+                      gamma=5.0 / 3.0, device="cuda"):
+    """The recipe of `turbulence` generated with torch on a GPU, for grids whose FFT is too
+    large for the host (512^3, 768^3): random-phase Gaussian modes with per-mode rms
+    k^-2 on kmin <= |k| <= kmax, optional solenoidal projection, mean removed, scaled to
+    rms Mach `mach`.  Its random stream (torch's, seeded with SEED_BASE + seed) differs
+    from the numpy one.  Returns a float64 torch tensor (5, n3, n2, n1) on `device`."""
+    import torch
+    n1, n2, n3 = n
+    f64 = torch.float64
+    gen = torch.Generator(device=device)
+    gen.manual_seed(SEED_BASE + int(seed))
+    k3 = torch.fft.fftfreq(n3, d=1.0 / n3, dtype=f64, device=device).view(-1, 1, 1)
+    k2 = torch.fft.fftfreq(n2, d=1.0 / n2, dtype=f64, device=device).view(1, -1, 1)
+    k1 = torch.fft.rfftfreq(n1, d=1.0 / n1, dtype=f64, device=device).view(1, 1, -1)
+    kk = torch.sqrt(k1 * k1 + k2 * k2 + k3 * k3)
+    band = (kk >= kmin) & (kk <= kmax)
+    amp = torch.where(band, kk.clamp(min=1.0) ** -2.0, torch.zeros_like(kk))
+    shp = amp.shape
+    vh = []
+    for _ in range(3):
+        re = torch.randn(shp, generator=gen, dtype=f64, device=device)
+        im = torch.randn(shp, generator=gen, dtype=f64, device=device)
+        vh.append(amp * torch.complex(re, im))
+        del re, im
+    if solenoidal:
+        kd = torch.where(kk == 0, torch.ones_like(kk), kk)
+        kdotv = (k1 * vh[0] + k2 * vh[1] + k3 * vh[2]) / (kd * kd)
+        vh = [vh[0] - k1 * kdotv, vh[1] - k2 * kdotv, vh[2] - k3 * kdotv]
+        del kdotv
+    U = torch.empty((5, n3, n2, n1), dtype=f64, device=device)
+    for c in range(3):
+        v = torch.fft.irfftn(vh[c], s=(n3, n2, n1), dim=(0, 1, 2))
+        vh[c] = None
+        U[1 + c] = v - v.mean()
+        del v
+    vrms = torch.sqrt((U[1] ** 2 + U[2] ** 2 + U[3] ** 2).mean())
+    cs = (gamma * p / rho) ** 0.5
+    scale = mach * cs / vrms
+    U[0].fill_(rho)
+    for c in range(3):
+        U[1 + c] *= scale
+    # conserved: M = rho v, E = p / (gamma - 1) + rho |v|^2 / 2
+    U[4] = 0.5 * rho * (U[1] ** 2 + U[2] ** 2 + U[3] ** 2) + p / (gamma - 1.0)
+    for c in range(3):
+        U[1 + c] *= rho
+    return U
+
+
 def shock_tube(n, direction=0, left=(1.0, 0.0, 1.0), right=(0.125, 0.0, 0.1),
                gamma=1.4, x0=0.25, x1=0.75):
     """Riemann problem along `direction`: state `left` (rho, u, p) for x0 <= x < x1,

@@ -322,3 +322,31 @@ def test_sod_converges_to_exact_solution():
         errs.append(np.mean(np.abs(U[0, 0, 0, sel] - rho_ex)))
     assert errs[2] < 6e-3, errs
     assert errs[0] / errs[1] > 1.4 and errs[1] / errs[2] > 1.4, errs
+
+
+def test_device_turbulence_recipe_on_cpu():
+    """The torch form of the turbulence recipe (used for 512^3 / 768^3 inputs), run on
+    the CPU: rms Mach, zero mean momentum, the spectral band, and a divergence-free
+    field when projected."""
+    import torch
+    n = (24, 20, 16)
+    for sol in (False, True):
+        U = pgen.turbulence_device(n, seed=2, kmin=2, kmax=5, mach=2.0, solenoidal=sol,
+                                   device="cpu").numpy()
+        v = U[1:4] / U[0]
+        assert abs(np.sqrt((v ** 2).sum(axis=0).mean()) / np.sqrt(5.0 / 3.0) - 2.0) < 1e-12
+        assert np.abs(U[1:4].mean(axis=(1, 2, 3))).max() < 1e-12
+        e_kin = 0.5 * (U[1] ** 2 + U[2] ** 2 + U[3] ** 2) / U[0]
+        assert np.allclose(U[4] - e_kin, 1.0 / (5.0 / 3.0 - 1.0), rtol=0, atol=1e-12)
+        vh = [np.fft.fftn(c) for c in v]
+        k3 = np.fft.fftfreq(n[2], 1.0 / n[2])[:, None, None]
+        k2 = np.fft.fftfreq(n[1], 1.0 / n[1])[None, :, None]
+        k1 = np.fft.fftfreq(n[0], 1.0 / n[0])[None, None, :]
+        kk = np.sqrt(k1 ** 2 + k2 ** 2 + k3 ** 2)
+        power = sum(np.abs(c) ** 2 for c in vh)
+        assert power[(kk < 2) | (kk > 5)].max() < 1e-18 * power.max()
+        div = np.abs(k1 * vh[0] + k2 * vh[1] + k3 * vh[2])
+        if sol:
+            assert div.max() < 1e-9 * np.sqrt(power.max()) * kk.max()
+        else:
+            assert div.max() > 1e-3 * np.sqrt(power.max())

@@ -4,7 +4,7 @@
 // f64<->f32 conversion instructions run on that same unit.  The helpers below move
 // conversions to the integer pipe and replace IEEE double division and square root
 // (several FP64 instructions each) by a single-precision hardware seed refined with
-// one Newton-Raphson step in FP64:
+// one Newton-Raphson step, evaluated without the FP64 unit (see below):
 //   reciprocal:       r' = r + r (1 - x r)                (Newton on f(r) = 1/r - x)
 //   reciprocal sqrt:  y' = y + y (1 - x y^2) / 2          (Newton on f(y) = 1/y^2 - x)
 // A seed with relative error e becomes e^2 (reciprocal) or ~1.5 e^2 (rsqrt) after the
@@ -45,7 +45,7 @@ __device__ __forceinline__ double f32_to_f64(float f) {
   return __hiloint2double((int)(hi | (b & 0x80000000u)), (int)(b << 29));
 }
 
-// ---- reciprocal, rsqrt, sqrt with one FP64 Newton step ------------------------------
+// ---- hardware seeds ----------------------------------------------------------------
 __device__ __forceinline__ float rcp_approx_f32(float x) {
   float r;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -57,23 +57,57 @@ __device__ __forceinline__ float rsqrt_approx_f32(float x) {
   return r;
 }
 
-// 1/x for finite normal x.  x = m 2^e with m in [1, 2): the seed is the float
-// reciprocal of m, refined once in FP64, then scaled by 2^-e on the integer pipe.
+// ---- Newton steps without the FP64 unit ----------------------------------------------
+// For a seed r0 (a float) of 1/m or 1/sqrt(m), m = mh + ml in [1, 4) with mh its leading
+// 24 bits, the residual of one Newton step is small (|e| < 2^-21), so FP32 fused
+// multiply-adds on the split m give it to ~2^-46, and the correction d = c r0 e (c = 1 or
+// 1/2) to ~2^-46 r0.  r0 + d then has bits from 2^-1 down to ~2^-46 only: it is exact
+// in a double and is formed by adding d, in units of 2^-53 (the last place of doubles in
+// [1/2, 1)), to the bit pattern of r0.  A sum that leaves [1/2, 1) lies within ~2^-44 of
+// the binade edge, where the changed unit only adds an error of that size.
+
+// d * 2^53 as a 64-bit integer, from the bits of the float d (|d| < 2^-20; bits below
+// 2^-53 are dropped)
+__device__ __forceinline__ long long f32_times_2p53(float d) {
+  const unsigned b = __float_as_uint(d);
+  const int ex = (int)((b >> 23) & 0xffu);
+  const unsigned long long mant = (unsigned long long)((b & 0x7fffffu) | 0x800000u);
+  const int sh = ex - 97;  // d 2^53 = mant 2^(ex - 127 - 23 + 53)
+  long long v = sh >= 0 ? (long long)(mant << (sh & 63)) : (long long)(mant >> ((-sh) & 63));
+  v = (ex < 40) ? 0ll : v;  // |d| < 2^-87 (or zero): nothing at or above 2^-53
+  return (b >> 31) ? -v : v;
+}
+
+// bit pattern of the double nearest r0 + d for a positive normal float r0 and |d| < 2^-20 r0
+__device__ __forceinline__ long long f32_plus_small_bits(float r0, float d) {
+  const unsigned b = __float_as_uint(r0);
+  const long long widened = ((long long)((b >> 3) + (896u << 20)) << 32) | (long long)(b << 29);
+  return widened + f32_times_2p53(d);
+}
+
+// mantissa m in [1, 2) of a double (hi/lo words) split into its leading 24 bits (exact
+// float) and the remaining 29 bits (rounded down to 23 bits, a float)
+__device__ __forceinline__ void split_mantissa(unsigned hi, unsigned lo, float& mh, float& ml) {
+  mh = __uint_as_float(0x3f800000u | ((hi & 0x000fffffu) << 3) | (lo >> 29));
+  ml = (__uint_as_float(0x4b000000u | ((lo & 0x1fffffffu) >> 6)) - 8388608.0f) * 0x1p-46f;
+}
+
+// 1/x for finite normal x.  x = +-m 2^(ex-1023), m in [1, 2): r0 = seed of 1/mh in
+// (1/2, 1], e = 1 - m r0, 1/m ~ r0 + r0 e; then scaled by 2^(1023-ex) and signed.
+// Relative error below 2^-43.
 __device__ __forceinline__ double rcp64(double x) {
   const unsigned hi = (unsigned)__double2hiint(x);
   const unsigned lo = (unsigned)__double2loint(x);
   const unsigned ex = (hi >> 20) & 0x7ffu;
   if (ex == 0u || ex >= 2045u) return 1.0 / x;  // zero, subnormal, huge, inf, NaN
-  const unsigned mhi = (hi & 0x800fffffu) | 0x3ff00000u;  // m in +-[1, 2)
-  const double m = __hiloint2double((int)mhi, (int)lo);
-  const float mf = __uint_as_float(((mhi & 0x80000000u) | 0x3f800000u) |
-                                   (((mhi & 0x000fffffu) << 3) | (lo >> 29)));
-  double r = f32_to_f64(rcp_approx_f32(mf));
-  const double t = fma(-m, r, 1.0);
-  r = fma(r, t, r);
-  // scale by 2^(1023 - ex): add to the exponent field of r (|r| in (1/2, 1])
-  const int rhi = __double2hiint(r) + (int)((1023u - ex) << 20);
-  return __hiloint2double(rhi, __double2loint(r));
+  float mh, ml;
+  split_mantissa(hi, lo, mh, ml);
+  const float r0 = rcp_approx_f32(mh);
+  const float e = fmaf(-ml, r0, fmaf(-mh, r0, 1.0f));
+  long long bits = f32_plus_small_bits(r0, r0 * e);
+  bits += (long long)(1023 - (int)ex) << 52;
+  bits |= (long long)(hi & 0x80000000u) << 32;
+  return __longlong_as_double(bits);
 }
 
 // ---- comparisons and exact scalings of doubles on the integer pipe --------------------
@@ -102,26 +136,31 @@ __device__ __forceinline__ double dscale_down(double x, int n, double two_pow_mi
   return __hiloint2double(hi - (n << 20), __double2loint(x));
 }
 
-// 1/sqrt(x) for finite normal x > 0: x = m 4^k with m in [1, 4).
+// 1/sqrt(x) for finite normal x > 0: x = m 4^k with m in [1, 4).  y0 = seed of
+// 1/sqrt(mh) in (1/2, 1]; y0^2 = p + pe exactly (pe = fma(y0, y0, -p)), so
+// e = 1 - m y0^2 = 1 - mh p - mh pe - ml p to ~2^-46, and 1/sqrt(m) ~ y0 + y0 e / 2.
+// Relative error below 2^-42.
 __device__ __forceinline__ double rsqrt64(double x) {
   const unsigned hi = (unsigned)__double2hiint(x);
   const unsigned lo = (unsigned)__double2loint(x);
   const unsigned ex = (hi >> 20) & 0x7ffu;
   if (ex == 0u || ex >= 2046u || (hi & 0x80000000u)) return 1.0 / sqrt(x);
   // even part of the unbiased exponent goes into the scale, the rest stays in m
-  const int e = (int)ex - 1023;
-  const int k = e >> 1;                 // floor(e / 2)
-  const unsigned mex = (unsigned)(1023 + (e - 2 * k));  // m in [1, 4)
-  const unsigned mhi = (hi & 0x000fffffu) | (mex << 20);
-  const double m = __hiloint2double((int)mhi, (int)lo);
-  const float mf = __uint_as_float(((mex - 896u) << 23) |
-                                   (((mhi & 0x000fffffu) << 3) | (lo >> 29)));
-  double y = f32_to_f64(rsqrt_approx_f32(mf));
-  const double t = fma(-m * y, y, 1.0);  // 1 - m y^2
-  y = fma(dscale(y, -1), t, y);          // y + (y/2) t
-  // scale by 2^-k
-  const int yhi = __double2hiint(y) - (k << 20);
-  return __hiloint2double(yhi, __double2loint(y));
+  const int e2 = (int)ex - 1023;
+  const int k = e2 >> 1;  // floor(e2 / 2)
+  float mh, ml;
+  split_mantissa(hi, lo, mh, ml);
+  if (e2 - 2 * k) {       // m in [2, 4): exact doubling of both parts
+    mh *= 2.0f;
+    ml *= 2.0f;
+  }
+  const float y0 = rsqrt_approx_f32(mh);
+  const float p = y0 * y0;
+  const float pe = fmaf(y0, y0, -p);
+  const float e = fmaf(-mh, pe, fmaf(-ml, p, fmaf(-mh, p, 1.0f)));
+  long long bits = f32_plus_small_bits(y0, 0.5f * y0 * e);
+  bits -= (long long)k << 52;  // scale by 2^-k
+  return __longlong_as_double(bits);
 }
 
 __device__ __forceinline__ double sqrt64(double x) {

@@ -21,7 +21,7 @@ def lib(tmp_path_factory):
     from paper_2409_16053_gb300 import build
     so = str(tmp_path_factory.mktemp("fm") / "fastmath_check.so")
     subprocess.run([build.nvcc(), "-gencode", "arch=compute_103a,code=sm_103a", "-O3",
-                    "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
+                    "-std=c++17", "-fmad=false", "-shared", "-Xcompiler", "-fPIC",
                     os.path.join(HERE, "fastmath_check.cu"), "-o", so], check=True)
     L = ctypes.CDLL(so)
     L.fastmath_eval.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
@@ -35,6 +35,10 @@ def test_fastmath_against_ieee(lib):
         10.0 ** rng.uniform(-300, 300, 20000) * rng.choice([-1, 1], 20000),
         10.0 ** rng.uniform(-30, 30, 20000),
         np.array([1.0, 2.0, 0.5, 3.0, 1e-12, 1e12, 1.0 - 2 ** -52, 1.0 + 2 ** -52]),
+        # mantissas next to the binade edges of 1/m and 1/sqrt(m), and with large low parts
+        2.0 - rng.uniform(0, 2 ** -20, 5000), 1.0 + rng.uniform(0, 2 ** -20, 5000),
+        4.0 - rng.uniform(0, 2 ** -18, 5000), 1.0 + (2 ** 23 - 1) * 2 ** -23 + rng.uniform(0, 2 ** -23, 5000),
+        2.0 ** rng.integers(-1000, 1000, 5000) * (2.0 - 2.0 ** -52),
     ]).astype(np.float64)
     out = np.empty((x.size, 9))
     assert lib.fastmath_eval(x.ctypes.data, x.size, out.ctypes.data) == 0

@@ -342,7 +342,10 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
         } else {
           const double L = -fma(d1, idx1, fma(d2, idx2, d3 * idx3));
           r = fma(dt, L, uin[e + v * g.var_stride]);
-          if (form != 0) r = fma(a, u0[e + v * g.var_stride], b * r);
+          if (form == 1)  // RK2 final stage: (U0 + U + dt L) / 2
+            r = half(u0[e + v * g.var_stride] + r);
+          else if (form == 2)
+            r = fma(a, u0[e + v * g.var_stride], b * r);
         }
         un[v] = r;
         if constexpr (TMA_OUT)

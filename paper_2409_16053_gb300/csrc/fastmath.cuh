@@ -128,12 +128,13 @@ __device__ __forceinline__ bool dgt_pos(double a, double b) {
 __device__ __forceinline__ double dscale(double x, int n) {
   return __hiloint2double(__double2hiint(x) + (n << 20), __double2loint(x));
 }
-// x * 2^-n (n > 0) for any finite x: exponent arithmetic, or the multiply when x is
-// zero or so small that the result would leave the normal range
-__device__ __forceinline__ double dscale_down(double x, int n, double two_pow_minus_n) {
+// x * 2^-n (n > 0) for finite x by exponent arithmetic; a result that would leave the
+// normal range (|x| < 2^(n-1022), zero included) becomes a signed zero
+__device__ __forceinline__ double dscale_down(double x, int n) {
   const int hi = __double2hiint(x);
-  if ((hi & 0x7ff00000) <= (n << 20)) return x * two_pow_minus_n;
-  return __hiloint2double(hi - (n << 20), __double2loint(x));
+  const bool tiny = (hi & 0x7ff00000) <= (n << 20);
+  return __hiloint2double(tiny ? (hi & (int)0x80000000) : hi - (n << 20),
+                          tiny ? 0 : __double2loint(x));
 }
 
 // 1/sqrt(x) for finite normal x > 0: x = m 4^k with m in [1, 4).  y0 = seed of

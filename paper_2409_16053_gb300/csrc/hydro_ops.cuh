@@ -126,8 +126,7 @@ __device__ __forceinline__ void hllc_fp64(const double* wl, const double* wr, co
   const double cr = gpr * rsqrt64(gpr * rr);
 
   // pressure estimate of the linearised (PVRS) solver, then shock-aware speeds
-  double ps = fma(-dscale_down((ur - ul) * (rl + rr), 3, 0.125), cl + cr,
-                  dscale_down(pl + pr, 1, 0.5));
+  double ps = fma(-dscale_down((ur - ul) * (rl + rr), 3), cl + cr, dscale_down(pl + pr, 1));
   ps = dpos(ps) ? ps : 0.0;
   const double kq = bg.kq;
   double ql = 1.0, qr = 1.0;

@@ -122,13 +122,15 @@ __device__ __forceinline__ void solve(int d, const R* l, const R* r, const Bg& b
   for (int n = 0; n < 5; ++n) f[perm[n]] = fn[n];
 }
 
-// 0.5 * x for a finite double, on the integer pipe (the multiply for zero and
-// numbers near the subnormal range)
+// 0.5 * x on the integer pipe: exact for normal results; a result below the normal
+// range (|x| < 2^-1021) becomes a signed zero, inf and NaN stay
 __device__ __forceinline__ double half(double x) {
   const int hi = __double2hiint(x);
-  if ((hi & 0x7fe00000) == 0) return 0.5 * x;
-  if ((hi & 0x7ff00000) == 0x7ff00000) return x;  // inf, NaN
-  return __hiloint2double(hi - 0x00100000, __double2loint(x));
+  const int sub = (hi & 0x7fe00000) == 0;
+  const int special = (hi & 0x7ff00000) == 0x7ff00000;
+  const int h = special ? hi : (sub ? (hi & (int)0x80000000) : hi - 0x00100000);
+  const int l = (special || !sub) ? __double2loint(x) : 0;
+  return __hiloint2double(h, l);
 }
 
 // The corrected (fine-mean) flux of one coarse face cell from the correction buffer.

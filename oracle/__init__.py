@@ -40,6 +40,9 @@ _lib = None
 
 PLM = 0
 PPM4 = 1
+HLLC = 0
+HLLE = 1
+LLF = 2
 
 
 def build(force: bool = False) -> str:
@@ -60,7 +63,7 @@ def build(force: bool = False) -> str:
 class _Grid(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64 * 3), ("dx", ctypes.c_double * 3),
                 ("gamma", ctypes.c_double), ("recon", ctypes.c_int32),
-                ("pad", ctypes.c_int32)]
+                ("riemann", ctypes.c_int32)]
 
 
 class _Smr(ctypes.Structure):
@@ -68,7 +71,8 @@ class _Smr(ctypes.Structure):
                 ("recon", ctypes.c_int32), ("flux_correction", ctypes.c_int32),
                 ("blocks", ctypes.POINTER(ctypes.c_int32)),
                 ("root_nx", ctypes.c_int32 * 3), ("length", ctypes.c_double * 3),
-                ("gamma", ctypes.c_double)]
+                ("gamma", ctypes.c_double), ("riemann", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
 
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -87,6 +91,8 @@ def _load():
             lib.orc_plm_slope.restype = ctypes.c_double
             lib.orc_ppm4_edges.argtypes = [_dp, _dp, _dp]
             lib.orc_hllc.argtypes = [_dp, _dp, ctypes.c_double, _dp]
+            lib.orc_hlle.argtypes = [_dp, _dp, ctypes.c_double, _dp]
+            lib.orc_llf.argtypes = [_dp, _dp, ctypes.c_double, _dp]
             lib.orc_rhs.argtypes = [G, _dp, _dp]
             lib.orc_rhs.restype = ctypes.c_int64
             lib.orc_rk_step.argtypes = [G, _dp, ctypes.c_double, ctypes.c_int]
@@ -125,7 +131,8 @@ def _ptr(a: np.ndarray):
 class Grid:
     """Periodic uniform grid: n = (n1, n2, n3) cells on a box of side lengths `length`."""
 
-    def __init__(self, n, length=(1.0, 1.0, 1.0), gamma=5.0 / 3.0, recon=PLM):
+    def __init__(self, n, length=(1.0, 1.0, 1.0), gamma=5.0 / 3.0, recon=PLM, riemann=HLLC):
+        self.riemann = int(riemann)
         self.n = tuple(int(v) for v in n)
         self.length = tuple(float(v) for v in length)
         self.dx = tuple(self.length[d] / self.n[d] for d in range(3))
@@ -139,6 +146,7 @@ class Grid:
             g.dx[d] = self.dx[d]
         g.gamma = self.gamma
         g.recon = self.recon
+        g.riemann = self.riemann
         return ctypes.byref(g)
 
     @property
@@ -176,13 +184,27 @@ def ppm4_edges(q5):
     return lo.value, hi.value
 
 
-def hllc(wl, wr, gamma):
-    """HLLC flux; w = (rho, u_normal, v_t1, v_t2, u_g)."""
+def _flux(name, wl, wr, gamma):
     wl = np.ascontiguousarray(wl, dtype=np.float64)
     wr = np.ascontiguousarray(wr, dtype=np.float64)
     f = np.empty(5)
-    _load().orc_hllc(_ptr(wl), _ptr(wr), float(gamma), _ptr(f))
+    getattr(_load(), name)(_ptr(wl), _ptr(wr), float(gamma), _ptr(f))
     return f
+
+
+def hllc(wl, wr, gamma):
+    """HLLC flux; w = (rho, u_normal, v_t1, v_t2, u_g)."""
+    return _flux("orc_hllc", wl, wr, gamma)
+
+
+def hlle(wl, wr, gamma):
+    """HLLE flux (HLL with Einfeldt's Roe-average speeds)."""
+    return _flux("orc_hlle", wl, wr, gamma)
+
+
+def llf(wl, wr, gamma):
+    """LLF (Rusanov) flux."""
+    return _flux("orc_llf", wl, wr, gamma)
 
 
 def rhs(U, grid: Grid):
@@ -278,7 +300,7 @@ class SmrMesh:
     periodic box; storage = padded arrays block after block (see ak_oracle_smr.c)."""
 
     def __init__(self, table, root_nx, length=(1.0, 1.0, 1.0), gamma=5.0 / 3.0,
-                 recon=PLM, flux_correction=True):
+                 recon=PLM, flux_correction=True, riemann=HLLC):
         self.table = np.ascontiguousarray(np.asarray(table, dtype=np.int32))
         self.root_nx = tuple(int(v) for v in root_nx)
         self.length = tuple(float(v) for v in length)
@@ -295,6 +317,7 @@ class SmrMesh:
             c.root_nx[d] = self.root_nx[d]
             c.length[d] = self.length[d]
         c.gamma = self.gamma
+        c.riemann = int(riemann)
         self._c = c
         g = self.ng
         self.shapes = [(5, r[6] + 2 * g, r[5] + 2 * g, r[4] + 2 * g) for r in self.table]

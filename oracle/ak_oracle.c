@@ -25,6 +25,11 @@
  *   - HLLC: Toro (2009) ch. 10, PVRS wave-speed estimate bounded outward by the
  *     Davis speeds, star states of the standard form, ties at S_L = 0 / S* = 0
  *     resolved to the left.
+ *   - LLF (Rusanov): Toro (2009) Sec. 10.5.1 with the single speed
+ *     S+ = max(|u_L| + c_L, |u_R| + c_R).
+ *   - HLLE: the HLL flux (Toro Eq. 10.21) with Einfeldt's speeds
+ *     S_L = min(u_L - c_L, u~ - c~), S_R = max(u_R + c_R, u~ + c~) from the Roe averages
+ *     (Toro Sec. 10.5.1, Eqs. 10.49-10.53), taken as b- = min(S_L, 0), b+ = max(S_R, 0).
  *   - SSP-RK2 (Heun) and SSP-RK3 (Shu-Osher) coefficients, each stage evaluated as
  *     a*U0 + b*(U + dt*L(U)).
  *   - Floors: rho < 1e-12 or u_g < 1e-15 in the primitive recovery are clamped and
@@ -42,12 +47,16 @@
 #define ORC_PLM 0
 #define ORC_PPM4 1
 
+#define ORC_HLLC 0
+#define ORC_HLLE 1
+#define ORC_LLF 2
+
 typedef struct {
   int64_t n[3];     /* cells per dimension of the periodic grid */
   double dx[3];     /* uniform cell widths (Section 2: uniform Cartesian only) */
   double gamma;     /* ratio of specific heats of the gamma-law EOS */
   int32_t recon;    /* ORC_PLM or ORC_PPM4 */
-  int32_t pad;
+  int32_t riemann;  /* ORC_HLLC, ORC_HLLE or ORC_LLF */
 } orc_grid;
 
 static int64_t wrap(int64_t i, int64_t n) {
@@ -227,11 +236,81 @@ void orc_hllc(const double wl[5], const double wr[5], double gamma, double f[5])
   for (int n = 0; n < NVAR; ++n) f[n] = fk[n] + s * (ustar[n] - uk5[n]);
 }
 
+/* Conserved state of a primitive face state (same layout as the flux). */
+static void face_cons(const double w[5], double e, double u[5]) {
+  u[0] = w[0];
+  u[1] = w[0] * w[1];
+  u[2] = w[0] * w[2];
+  u[3] = w[0] * w[3];
+  u[4] = e;
+}
+
+/* LLF (Rusanov): F = (F_L + F_R) / 2 - S+ (U_R - U_L) / 2. */
+void orc_llf(const double wl[5], const double wr[5], double gamma, double f[5]) {
+  double pl = (gamma - 1.0) * wl[4];
+  double pr = (gamma - 1.0) * wr[4];
+  double el = wl[4] + 0.5 * wl[0] * (wl[1] * wl[1] + wl[2] * wl[2] + wl[3] * wl[3]);
+  double er = wr[4] + 0.5 * wr[0] * (wr[1] * wr[1] + wr[2] * wr[2] + wr[3] * wr[3]);
+  double cl = sqrt(gamma * pl / wl[0]);
+  double cr = sqrt(gamma * pr / wr[0]);
+  double al = fabs(wl[1]) + cl, ar = fabs(wr[1]) + cr;
+  double smax = al > ar ? al : ar;
+  double fl[5], fr[5], ul[5], ur[5];
+  phys_flux(wl, pl, el, fl);
+  phys_flux(wr, pr, er, fr);
+  face_cons(wl, el, ul);
+  face_cons(wr, er, ur);
+  for (int n = 0; n < NVAR; ++n) f[n] = 0.5 * (fl[n] + fr[n]) - 0.5 * smax * (ur[n] - ul[n]);
+}
+
+/* HLLE: HLL flux with Einfeldt's wave speeds from the Roe averages. */
+void orc_hlle(const double wl[5], const double wr[5], double gamma, double f[5]) {
+  double rl = wl[0], rr = wr[0];
+  double pl = (gamma - 1.0) * wl[4];
+  double pr = (gamma - 1.0) * wr[4];
+  double el = wl[4] + 0.5 * rl * (wl[1] * wl[1] + wl[2] * wl[2] + wl[3] * wl[3]);
+  double er = wr[4] + 0.5 * rr * (wr[1] * wr[1] + wr[2] * wr[2] + wr[3] * wr[3]);
+  double cl = sqrt(gamma * pl / rl);
+  double cr = sqrt(gamma * pr / rr);
+  /* Roe averages (Toro Eq. 10.50): weights sqrt(rho), enthalpy H = (E + p) / rho */
+  double sl = sqrt(rl), sr = sqrt(rr);
+  double ub[3], hb, q2 = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    ub[a] = (sl * wl[1 + a] + sr * wr[1 + a]) / (sl + sr);
+    q2 += ub[a] * ub[a];
+  }
+  hb = (sl * (el + pl) / rl + sr * (er + pr) / rr) / (sl + sr);
+  double cb2 = (gamma - 1.0) * (hb - 0.5 * q2);
+  double cb = cb2 > 0.0 ? sqrt(cb2) : 0.0;
+  double sL = wl[1] - cl, sR = wr[1] + cr;
+  if (ub[0] - cb < sL) sL = ub[0] - cb;
+  if (ub[0] + cb > sR) sR = ub[0] + cb;
+  double bm = sL < 0.0 ? sL : 0.0;
+  double bp = sR > 0.0 ? sR : 0.0;
+  double fl[5], fr[5], ul[5], ur[5];
+  phys_flux(wl, pl, el, fl);
+  phys_flux(wr, pr, er, fr);
+  face_cons(wl, el, ul);
+  face_cons(wr, er, ur);
+  for (int n = 0; n < NVAR; ++n)
+    f[n] = (bp * fl[n] - bm * fr[n] + bp * bm * (ur[n] - ul[n])) / (bp - bm);
+}
+
+void orc_riemann(int solver, const double wl[5], const double wr[5], double gamma,
+                 double f[5]) {
+  if (solver == ORC_LLF)
+    orc_llf(wl, wr, gamma, f);
+  else if (solver == ORC_HLLE)
+    orc_hlle(wl, wr, gamma, f);
+  else
+    orc_hllc(wl, wr, gamma, f);
+}
+
 /* ---------------------------------------------------------------------------------
  * Right-hand side L(U) = -div F of Section 3 Eq. (1) (S = 0) on the periodic grid.
  * For each direction d, the face between cells c - e_d and c gets its left state from
- * the reconstruction in cell c - e_d and its right state from that in cell c; HLLC
- * gives the flux; then L -= (F(c + e_d) - F(c)) / dx_d, summed x1, x2, x3 in turn.
+ * the reconstruction in cell c - e_d and its right state from that in cell c; the
+ * Riemann solver (HLLC, HLLE or LLF) gives the flux; then L -= (F(c + e_d) - F(c)) / dx_d, summed x1, x2, x3 in turn.
  * ------------------------------------------------------------------------------- */
 static void face_states(const orc_grid* g, const double* W, int d, int64_t i, int64_t j,
                         int64_t k, double wl[5], double wr[5]) {
@@ -296,7 +375,7 @@ int64_t orc_rhs(const orc_grid* g, const double* U, double* L) {
         for (int64_t i = 0; i < g->n[0]; ++i) {
           double wl[5], wr[5], f[5];
           face_states(g, W, d, i, j, k, wl, wr);
-          orc_hllc(wl, wr, g->gamma, f);
+          orc_riemann(g->riemann, wl, wr, g->gamma, f);
           int64_t c = cell(g, i, j, k);
           for (int n = 0; n < NVAR; ++n) F[(int64_t)perm[n] * N + c] = f[n];
         }

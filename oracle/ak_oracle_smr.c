@@ -36,7 +36,8 @@
 void orc_cons_to_prim(const double u[5], double w[5], int64_t* nfloor);
 double orc_plm_slope(double qm, double q0, double qp);
 void orc_ppm4_edges(const double q[5], double* qlo, double* qhi);
-void orc_hllc(const double wl[5], const double wr[5], double gamma, double f[5]);
+void orc_riemann(int solver, const double wl[5], const double wr[5], double gamma,
+                 double f[5]);
 
 typedef struct {
   int32_t nblocks, ng, recon, flux_correction;
@@ -44,6 +45,8 @@ typedef struct {
   int32_t root_nx[3];
   double length[3]; /* domain side lengths */
   double gamma;
+  int32_t riemann;   /* 0 HLLC, 1 HLLE, 2 LLF */
+  int32_t pad;
 } orc_smr;
 
 typedef struct {
@@ -291,7 +294,7 @@ static void block_fluxes(const smr_index* x, int b, const double* U, double* F[3
               wr[q] = lo2;
             }
           }
-          orc_hllc(wl, wr, m->gamma, f);
+          orc_riemann(m->riemann, wl, wr, m->gamma, f);
           int64_t fi = ((int64_t)k * n[1] + j) * n[0] + i;
           int64_t fn = (int64_t)n[0] * n[1] * n[2];
           for (int q = 0; q < NV; ++q) F[d][(int64_t)perm[q] * fn + fi] = f[q];

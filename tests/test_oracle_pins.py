@@ -350,3 +350,96 @@ def test_device_turbulence_recipe_on_cpu():
             assert div.max() < 1e-9 * np.sqrt(power.max()) * kk.max()
         else:
             assert div.max() > 1e-3 * np.sqrt(power.max())
+
+
+# ---------------------------------------------------------------------------------
+# LLF and HLLE (the other Riemann solvers of the hydro module)
+# ---------------------------------------------------------------------------------
+@pytest.mark.parametrize("solver", ["hlle", "llf"])
+def test_llf_hlle_consistency_and_reflection_symmetry(solver):
+    rng = np.random.default_rng(11)
+    fn = getattr(oracle, solver)
+    g = G53
+    flip = np.array([1, -1, 1, 1, 1])
+    for _ in range(300):
+        wl = np.array([rng.uniform(0.2, 3), *rng.normal(0, 1, 3), rng.uniform(0.1, 3)])
+        wr = np.array([rng.uniform(0.2, 3), *rng.normal(0, 1, 3), rng.uniform(0.1, 3)])
+        fw = _phys_flux(wl, g)
+        sc = np.max(np.abs(fw)) + 1
+        assert np.allclose(fn(wl, wl, g), fw, rtol=0, atol=1e-14 * sc)
+        f = fn(wl, wr, g)
+        fm = fn(wr * flip, wl * flip, g)
+        sc = np.max(np.abs(f)) + 1
+        assert np.allclose(fm, f * np.array([-1, 1, -1, -1, -1]), rtol=0, atol=1e-13 * sc)
+
+
+def test_llf_stationary_contact_closed_form():
+    # u = 0 on both sides and equal p: F = (F_L + F_R)/2 - S+ (U_R - U_L)/2 with
+    # S+ = max(c_L, c_R), F_K = (0, p, 0, 0, 0) and E_L = E_R = p/(gamma-1)
+    g = G53
+    p = 0.7
+    wl = np.array([2.0, 0.0, 0.3, -0.1, p / (g - 1)])
+    wr = np.array([0.5, 0.0, -0.2, 0.6, p / (g - 1)])
+    smax = max(math.sqrt(g * p / 2.0), math.sqrt(g * p / 0.5))
+    f = oracle.llf(wl, wr, g)
+    ke_l, ke_r = 0.5 * 2.0 * (0.3 ** 2 + 0.1 ** 2), 0.5 * 0.5 * (0.2 ** 2 + 0.6 ** 2)
+    expect = [-0.5 * smax * (0.5 - 2.0), p, -0.5 * smax * (0.5 * -0.2 - 2.0 * 0.3),
+              -0.5 * smax * (0.5 * 0.6 - 2.0 * -0.1), -0.5 * smax * (ke_r - ke_l)]
+    assert np.allclose(f, expect, rtol=1e-14, atol=1e-15)
+
+
+def test_hlle_contact_dissipation_between_hllc_and_llf():
+    # a stationary contact: HLLC carries no mass, HLLE diffuses it, LLF (the largest
+    # single speed) diffuses it more; HLLE's flux is an average of the two sides'
+    g = G53
+    p = 0.7
+    wl = np.array([2.0, 0.0, 0.0, 0.0, p / (g - 1)])
+    wr = np.array([0.5, 0.0, 0.0, 0.0, p / (g - 1)])
+    fc, fe, fl = oracle.hllc(wl, wr, g), oracle.hlle(wl, wr, g), oracle.llf(wl, wr, g)
+    assert fc[0] == 0.0 and fe[0] > 0.0 and fl[0] > fe[0]
+    assert math.isclose(fe[1], p, rel_tol=1e-14)
+
+
+def test_hlle_supersonic_is_upwind_flux():
+    g = 1.4
+    wl = np.array([1.0, 5.0, 0.3, -0.2, 2.5])
+    wr = np.array([0.5, 4.0, 0.1, 0.4, 1.0])
+    assert np.allclose(oracle.hlle(wl, wr, g), _phys_flux(wl, g), rtol=1e-14, atol=0)
+    flip = np.array([1, -1, 1, 1, 1])
+    assert np.allclose(oracle.hlle(wr * flip, wl * flip, g), _phys_flux(wl * flip, g),
+                       rtol=1e-14, atol=0)
+
+
+@pytest.mark.parametrize("riemann", [oracle.HLLE, oracle.LLF])
+def test_sod_converges_with_hlle_and_llf(riemann):
+    wl, wr, g = (1.0, 0.0, 1.0), (0.125, 0.0, 0.1), 1.4
+    errs = []
+    t_end = 0.1
+    for N in (64, 128, 256):
+        grid = oracle.Grid((N, 1, 1), gamma=g, riemann=riemann)
+        U0 = pgen.shock_tube((N, 1, 1), direction=0, left=wl, right=wr, gamma=g)
+        U, t, _, nf = oracle.run(U0, grid, 0.4, t_end=t_end)
+        assert nf == 0
+        x = pgen.cell_centres(N)
+        sel = (x > 0.5)
+        rho_ex = oracle.exact_sample(np.array(wl), np.array(wr), g, (x[sel] - 0.75) / t)[0]
+        errs.append(np.mean(np.abs(U[0, 0, 0, sel] - rho_ex)))
+    assert errs[2] < 8e-3, errs
+    assert errs[0] / errs[1] > 1.4 and errs[1] / errs[2] > 1.4, errs
+
+
+def test_sod_error_ordered_hllc_hlle_llf():
+    # the contact is what separates the solvers: at a fixed resolution the density L1
+    # error grows from HLLC to HLLE to LLF
+    wl, wr, g = (1.0, 0.0, 1.0), (0.125, 0.0, 0.1), 1.4
+    N, t_end = 128, 0.1
+    err = {}
+    for rs in (oracle.HLLC, oracle.HLLE, oracle.LLF):
+        grid = oracle.Grid((N, 1, 1), gamma=g, riemann=rs)
+        U0 = pgen.shock_tube((N, 1, 1), direction=0, left=wl, right=wr, gamma=g)
+        U, t, _, _ = oracle.run(U0, grid, 0.4, t_end=t_end)
+        x = pgen.cell_centres(N)
+        sel = (x > 0.5)
+        rho_ex = oracle.exact_sample(np.array(wl), np.array(wr), g, (x[sel] - 0.75) / t)[0]
+        err[rs] = np.mean(np.abs(U[0, 0, 0, sel] - rho_ex))
+    assert err[oracle.HLLC] < err[oracle.HLLE] < err[oracle.LLF], err

@@ -93,11 +93,12 @@ def test_composite_conservation_and_negative_control():
     assert res[False].max() > 1e-7, res[False]
 
 
-def test_single_level_equals_uniform_oracle():
+@pytest.mark.parametrize("riemann", [oracle.HLLC, oracle.HLLE, oracle.LLF])
+def test_single_level_equals_uniform_oracle(riemann):
     # every block on level 0: the SMR oracle must reproduce the uniform-grid oracle
     t = pgen.nested_refinement_blocks(16, 8, 8, 0)
     P = _smooth_blocks(t, 16)
-    m = oracle.SmrMesh(t, (16, 16, 16))
+    m = oracle.SmrMesh(t, (16, 16, 16), riemann=riemann)
     U = m.from_packed(P)
     # global array from the blocks
     G = np.zeros((5, 16, 16, 16))
@@ -105,7 +106,7 @@ def test_single_level_equals_uniform_oracle():
     for b, r in enumerate(t):
         G[:, r[3]:r[3] + 8, r[2]:r[2] + 8, r[1]:r[1] + 8] = P[o:o + 5 * 512].reshape(5, 8, 8, 8)
         o += 5 * 512
-    grid = oracle.Grid((16, 16, 16))
+    grid = oracle.Grid((16, 16, 16), riemann=riemann)
     dt = oracle.new_dt(G, grid, 0.3)
     assert dt == m.new_dt(U, 0.3)
     Gn, _ = oracle.rk_step(G, grid, dt, 2)

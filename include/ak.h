@@ -66,6 +66,7 @@ typedef enum {
 
 enum { AK_PLM = 0, AK_PPM4 = 1 };     /* reconstruction (Section 3) */
 enum { AK_FP64 = 0, AK_MIXED = 1 };   /* arithmetic form of the stage */
+enum { AK_HLLC = 0, AK_HLLE = 1, AK_LLF = 2 };  /* Riemann solver (Section 3) */
 
 /* Number of int32 entries per block in ak_mesh_desc.blocks. */
 #define AK_BLOCK_INTS 7
@@ -87,6 +88,9 @@ typedef struct {
   int32_t recon;            /* AK_PLM or AK_PPM4 */
   int32_t rk;               /* SSP-RK order: 2 (Heun) or 3 (Shu-Osher) */
   int32_t precision;        /* AK_FP64 or AK_MIXED */
+  int32_t riemann;          /* AK_HLLC (0: HLLC with PVRS speeds bounded by the Davis
+                               speeds), AK_HLLE (HLL with Einfeldt's Roe-average speeds)
+                               or AK_LLF (Rusanov) */
   double gamma;             /* gamma-law EOS, > 1 */
   double cfl;               /* Courant number of Eq. (3), in (0, 1] */
   double ref_rho, ref_p;    /* AK_MIXED only: background density and pressure that are

@@ -26,6 +26,7 @@ AK_OK, AK_EINVAL, AK_ENOMEM, AK_ECUDA, AK_ENEGATIVE, AK_ETIMEOUT, AK_ESTATE = \
     0, -1, -2, -3, -4, -5, -6
 AK_PLM, AK_PPM4 = 0, 1
 AK_FP64, AK_MIXED = 0, 1
+AK_HLLC, AK_HLLE, AK_LLF = 0, 1, 2
 AK_BLOCK_INTS = 7
 
 _STATUS_NAMES = {0: "AK_OK", -1: "AK_EINVAL", -2: "AK_ENOMEM", -3: "AK_ECUDA",
@@ -45,6 +46,7 @@ class ak_mesh_desc(ctypes.Structure):
         ("xmin", ctypes.c_double * 3), ("xmax", ctypes.c_double * 3),
         ("root_nx", ctypes.c_int32 * 3),
         ("recon", ctypes.c_int32), ("rk", ctypes.c_int32), ("precision", ctypes.c_int32),
+        ("riemann", ctypes.c_int32),
         ("gamma", ctypes.c_double), ("cfl", ctypes.c_double),
         ("ref_rho", ctypes.c_double), ("ref_p", ctypes.c_double),
     ]
@@ -211,7 +213,8 @@ class Mesh:
     statically refined mesh (table)."""
 
     def __init__(self, root_nx, block_nx=None, *, table=None, recon=AK_PLM, rk=2,
-                 precision=AK_FP64, gamma=5.0 / 3.0, cfl=0.3, xmin=(0.0, 0.0, 0.0),
+                 precision=AK_FP64, riemann=0, gamma=5.0 / 3.0, cfl=0.3,
+                 xmin=(0.0, 0.0, 0.0),
                  xmax=(1.0, 1.0, 1.0), ref_rho=1.0, ref_p=1.0, device="cuda", stream=None):
         import torch
         self.torch = torch
@@ -240,6 +243,7 @@ class Mesh:
             d.xmax[a] = float(xmax[a])
             d.root_nx[a] = self.root_nx[a]
         d.recon, d.rk, d.precision = int(recon), int(rk), int(precision)
+        d.riemann = int(riemann)
         d.gamma, d.cfl = float(gamma), float(cfl)
         d.ref_rho, d.ref_p = float(ref_rho), float(ref_p)
         self.desc = d

@@ -76,6 +76,8 @@ extern "C" ak_status ak_mesh_create(const ak_mesh_desc* d, void* cuda_stream, ak
   if (d->rk != 2 && d->rk != 3) return einval("ak_mesh_create: rk must be 2 or 3");
   if (d->precision != AK_FP64 && d->precision != AK_MIXED)
     return einval("ak_mesh_create: precision must be AK_FP64 or AK_MIXED");
+  if (d->riemann != AK_HLLC && d->riemann != AK_HLLE && d->riemann != AK_LLF)
+    return einval("ak_mesh_create: riemann must be AK_HLLC, AK_HLLE or AK_LLF");
   if (!(d->gamma > 1.0)) return einval("ak_mesh_create: gamma must be > 1");
   if (!(d->cfl > 0.0 && d->cfl <= 1.0)) return einval("ak_mesh_create: cfl must be in (0, 1]");
   if (d->precision == AK_MIXED && !(d->ref_rho > 0.0 && d->ref_p > 0.0))

@@ -547,6 +547,7 @@ static Bg make_bg(const ak_mesh* m) {
   bg.gg_f = (float)(gamma / (gamma - 1.0));
   bg.kq_f = (float)bg.kq;
   bg.pb_f = bg.gm1_f * bg.ug_f;
+  bg.rsolver = m->desc.riemann;
   return bg;
 }
 

@@ -320,7 +320,24 @@ __global__ void __launch_bounds__(MxCfg<NG, T>::NTH, 2)
         wl[n] = make_float2(e1hi[n * NE + l1], e2hi[P2[n] * NE + l2]);
         wr[n] = make_float2(e1lo[n * NE + l1 + 1], e2lo[P2[n] * NE + l2 + TX]);
       }
-      hllc_mixed(wl, wr, bg, fn);
+      if (bg.rsolver == AK_HLLC) {
+        hllc_mixed(wl, wr, bg, fn);  // both faces in the two lanes
+      } else {
+        // HLLE / LLF: one face at a time (their packed form did not reproduce the
+        // scalar bits of the flux-correction and unpaired kernels)
+        float la[5], ra[5], lb[5], rb[5], ga[5], gb[5];
+#pragma unroll
+        for (int n = 0; n < 5; ++n) {
+          la[n] = wl[n].x;
+          ra[n] = wr[n].x;
+          lb[n] = wl[n].y;
+          rb[n] = wr[n].y;
+        }
+        riemann(la, ra, bg, ga);
+        riemann(lb, rb, bg, gb);
+#pragma unroll
+        for (int n = 0; n < 5; ++n) fn[n] = make_float2(ga[n], gb[n]);
+      }
       float fa[5], fb[5];
 #pragma unroll
       for (int n = 0; n < 5; ++n) {

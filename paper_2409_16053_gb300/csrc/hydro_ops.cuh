@@ -12,8 +12,9 @@
 //
 // Sources: Section 3, Eq. (1) and Section 3.1, Eq. (4) of AthenaK (arXiv 2409.16053)
 // for the equations; PLM with the van Leer harmonic limiter, PPM4 after Colella &
-// Woodward (1984) and HLLC after Toro (2009) ch. 10 (PVRS wave-speed estimate bounded
-// outward by the Davis speeds), as readings of the methods the paper names.
+// Woodward (1984), HLLC after Toro (2009) ch. 10 (PVRS wave-speed estimate bounded
+// outward by the Davis speeds), HLLE (HLL with Einfeldt's Roe-average speeds, Toro
+// Sec. 10.5.1) and LLF (Rusanov), as readings of the methods the paper names.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -36,6 +37,7 @@ struct Bg {
   float gg_f;            // p_b = (gamma - 1) u_g,b, rounded (mixed form)
   float kq_f;
   float pb_f;
+  int rsolver;           // AK_HLLC, AK_HLLE or AK_LLF
 };
 
 // ------------------------------------------------------------------------------
@@ -179,6 +181,68 @@ __device__ __forceinline__ void hllc_fp64(const double* wl, const double* wr, co
 }
 
 // ------------------------------------------------------------------------------
+// LLF (Rusanov), FP64 form: F = (F_L + F_R)/2 - S+ (U_R - U_L)/2,
+// S+ = max(|u_L| + c_L, |u_R| + c_R).
+// ------------------------------------------------------------------------------
+__device__ __forceinline__ void llf_fp64(const double* wl, const double* wr, const Bg& bg,
+                                         double* f) {
+  const double gamma = bg.gamma, gm1 = bg.gm1;
+  const double rl = wl[0], ul = wl[1], rr = wr[0], ur = wr[1];
+  const double pl = gm1 * wl[4], pr = gm1 * wr[4];
+  const double gpl = gamma * pl, gpr = gamma * pr;
+  const double cl = gpl * rsqrt64(gpl * rl), cr = gpr * rsqrt64(gpr * rr);
+  const double al = fabs(ul) + cl, ar = fabs(ur) + cr;
+  const double sm = -(dgt_pos(al, ar) ? al : ar);
+  const double el = fma(dscale(rl, -1), fma(ul, ul, fma(wl[2], wl[2], wl[3] * wl[3])), wl[4]);
+  const double er = fma(dscale(rr, -1), fma(ur, ur, fma(wr[2], wr[2], wr[3] * wr[3])), wr[4]);
+  const double ml = rl * ul, mr = rr * ur;
+  f[0] = dscale_down(fma(sm, rr - rl, ml + mr), 1);
+  f[1] = dscale_down(fma(sm, mr - ml, fma(ml, ul, pl) + fma(mr, ur, pr)), 1);
+  f[2] = dscale_down(fma(sm, fma(rr, wr[2], -(rl * wl[2])), fma(ml, wl[2], mr * wr[2])), 1);
+  f[3] = dscale_down(fma(sm, fma(rr, wr[3], -(rl * wl[3])), fma(ml, wl[3], mr * wr[3])), 1);
+  f[4] = dscale_down(fma(sm, er - el, fma(el + pl, ul, (er + pr) * ur)), 1);
+}
+
+// ------------------------------------------------------------------------------
+// HLLE, FP64 form: the HLL flux (b+ F_L - b- F_R + b+ b- (U_R - U_L)) / (b+ - b-) with
+// b- = min(S_L, 0), b+ = max(S_R, 0), S_L = min(u_L - c_L, u~ - c~),
+// S_R = max(u_R + c_R, u~ + c~) from the Roe averages (weights sqrt(rho)).
+// ------------------------------------------------------------------------------
+__device__ __forceinline__ void hlle_fp64(const double* wl, const double* wr, const Bg& bg,
+                                          double* f) {
+  const double gamma = bg.gamma, gm1 = bg.gm1;
+  const double rl = wl[0], ul = wl[1], rr = wr[0], ur = wr[1];
+  const double pl = gm1 * wl[4], pr = gm1 * wr[4];
+  const double gpl = gamma * pl, gpr = gamma * pr;
+  const double cl = gpl * rsqrt64(gpl * rl), cr = gpr * rsqrt64(gpr * rr);
+  const double el = fma(dscale(rl, -1), fma(ul, ul, fma(wl[2], wl[2], wl[3] * wl[3])), wl[4]);
+  const double er = fma(dscale(rr, -1), fma(ur, ur, fma(wr[2], wr[2], wr[3] * wr[3])), wr[4]);
+  const double isl = rsqrt64(rl), isr = rsqrt64(rr);  // 1 / sqrt(rho)
+  const double sl = rl * isl, sr = rr * isr;          // sqrt(rho)
+  const double iw = rcp64(sl + sr);
+  const double ub = fma(sl, ul, sr * ur) * iw;
+  const double vb = fma(sl, wl[2], sr * wr[2]) * iw;
+  const double wb = fma(sl, wl[3], sr * wr[3]) * iw;
+  const double hb = fma(el + pl, isl, (er + pr) * isr) * iw;  // Roe-averaged (E + p)/rho
+  const double cb2 = gm1 * fma(-0.5, fma(ub, ub, fma(vb, vb, wb * wb)), hb);
+  const double cb = dpos(cb2) ? sqrt64(cb2) : 0.0;
+  double sL = ul - cl, sR = ur + cr;
+  const double ea = ub - cb, eb = ub + cb;
+  sL = dgt(sL, ea) ? ea : sL;
+  sR = dgt(eb, sR) ? eb : sR;
+  const double bm = dnonneg(sL) ? 0.0 : sL;
+  const double bp = dpos(sR) ? sR : 0.0;
+  const double ib = rcp64(bp - bm);
+  const double bpm = bp * bm;
+  const double ml = rl * ul, mr = rr * ur;
+  f[0] = fma(bp, ml, fma(-bm, mr, bpm * (rr - rl))) * ib;
+  f[1] = fma(bp, fma(ml, ul, pl), fma(-bm, fma(mr, ur, pr), bpm * (mr - ml))) * ib;
+  f[2] = fma(bp, ml * wl[2], fma(-bm, mr * wr[2], bpm * fma(rr, wr[2], -(rl * wl[2])))) * ib;
+  f[3] = fma(bp, ml * wl[3], fma(-bm, mr * wr[3], bpm * fma(rr, wr[3], -(rl * wl[3])))) * ib;
+  f[4] = fma(bp, (el + pl) * ul, fma(-bm, (er + pr) * ur, bpm * (er - el))) * ib;
+}
+
+// ------------------------------------------------------------------------------
 // Mixed form, FP32 on deviations, written once over the lane-generic operations of
 // lanes.cuh: V = float solves one problem, V = float2 two at once with the same bits.
 // ------------------------------------------------------------------------------
@@ -306,5 +370,101 @@ __device__ __forceinline__ void hllc_mixed(const V* wl, const V* wr, const Bg& b
 }
 
 __device__ __forceinline__ float sqrt_fast(float x) { return x * rsqrt_approx_f32(x); }
+
+// State jumps U_R - U_L of the mixed form from the deviations, each written so that no
+// O(1) quantities are subtracted: M_R - M_L = rho_R (v_R - v_L) + (rho_R - rho_L) v_L and
+// E_R - E_L = (k_R - k_L) + (u_g,R - u_g,L), k_R - k_L = (rho_R (|v_R|^2 - |v_L|^2) +
+// (rho_R - rho_L) |v_L|^2) / 2.
+template <typename V>
+__device__ __forceinline__ void jumps_mixed(const V* wl, const V* wr, V rr, V* d) {
+  d[0] = vsub(wr[0], wl[0]);
+  V dv2 = vset<V>(0.0f), vl2 = vset<V>(0.0f);
+#pragma unroll
+  for (int a = 1; a < 4; ++a) {
+    const V dv = vsub(wr[a], wl[a]);
+    d[a] = vfma(rr, dv, vmul(d[0], wl[a]));
+    dv2 = vfma(dv, vadd(wr[a], wl[a]), dv2);
+    vl2 = vfma(wl[a], wl[a], vl2);
+  }
+  d[4] = vadd(vmul(vset<V>(0.5f), vfma(rr, dv2, vmul(d[0], vl2))), vsub(wr[4], wl[4]));
+}
+
+// Physical fluxes of one face state in the mixed form (background pressure left out of
+// the normal momentum flux): (m, m u + dp, m v, m w, h u) with m = rho u, h = E + p.
+template <typename V>
+__device__ __forceinline__ void pflux_mixed(const V* w, V rho, V dp, V h, V* f) {
+  const V m = vmul(rho, w[1]);
+  f[0] = m;
+  f[1] = vfma(m, w[1], dp);
+  f[2] = vmul(m, w[2]);
+  f[3] = vmul(m, w[3]);
+  f[4] = vmul(h, w[1]);
+}
+
+// LLF, mixed form.  Returns F - (0, p_b, 0, 0, 0).
+template <typename V>
+__device__ __forceinline__ void llf_mixed(const V* wl, const V* wr, const Bg& bg, V* f) {
+  const V half = vset<V>(0.5f);
+  const V g = vset<V>(bg.gamma_f), gm1 = vset<V>(bg.gm1_f), gg = vset<V>(bg.gg_f);
+  const V pb = vset<V>(bg.pb_f);
+  const V rl = vadd(vset<V>(bg.rho_f), wl[0]), rr = vadd(vset<V>(bg.rho_f), wr[0]);
+  const V dpl = vmul(gm1, wl[4]), dpr = vmul(gm1, wr[4]);
+  const V pl = vadd(pb, dpl), pr = vadd(pb, dpr);
+  const V kel = vmul(vmul(half, rl), vfma(wl[1], wl[1], vfma(wl[2], wl[2], vmul(wl[3], wl[3]))));
+  const V ker = vmul(vmul(half, rr), vfma(wr[1], wr[1], vfma(wr[2], wr[2], vmul(wr[3], wr[3]))));
+  const V gpl = vmul(g, pl), gpr = vmul(g, pr);
+  const V cl = vmul(gpl, vrsqrt(vmul(gpl, rl)));
+  const V cr = vmul(gpr, vrsqrt(vmul(gpr, rr)));
+  const V al = vadd(vabs(wl[1]), cl), ar = vadd(vabs(wr[1]), cr);
+  const V sm = vneg(vsel(vgt(al, ar), al, ar));
+  V fl[5], fr[5], d[5];
+  pflux_mixed(wl, rl, dpl, vfma(gg, pl, kel), fl);
+  pflux_mixed(wr, rr, dpr, vfma(gg, pr, ker), fr);
+  jumps_mixed(wl, wr, rr, d);
+#pragma unroll
+  for (int n = 0; n < 5; ++n) f[n] = vmul(half, vfma(sm, d[n], vadd(fl[n], fr[n])));
+}
+
+// HLLE, mixed form (Roe averages and wave speeds in FP32).  Returns F - (0, p_b, 0, 0, 0).
+template <typename V>
+__device__ __forceinline__ void hlle_mixed(const V* wl, const V* wr, const Bg& bg, V* f) {
+  const V zero = vset<V>(0.0f), half = vset<V>(0.5f);
+  const V g = vset<V>(bg.gamma_f), gm1 = vset<V>(bg.gm1_f), gg = vset<V>(bg.gg_f);
+  const V pb = vset<V>(bg.pb_f);
+  const V rl = vadd(vset<V>(bg.rho_f), wl[0]), rr = vadd(vset<V>(bg.rho_f), wr[0]);
+  const V ul = wl[1], ur = wr[1];
+  const V dpl = vmul(gm1, wl[4]), dpr = vmul(gm1, wr[4]);
+  const V pl = vadd(pb, dpl), pr = vadd(pb, dpr);
+  const V kel = vmul(vmul(half, rl), vfma(ul, ul, vfma(wl[2], wl[2], vmul(wl[3], wl[3]))));
+  const V ker = vmul(vmul(half, rr), vfma(ur, ur, vfma(wr[2], wr[2], vmul(wr[3], wr[3]))));
+  const V hl = vfma(gg, pl, kel), hr = vfma(gg, pr, ker);  // E + p
+  const V gpl = vmul(g, pl), gpr = vmul(g, pr);
+  const V cl = vmul(gpl, vrsqrt(vmul(gpl, rl)));
+  const V cr = vmul(gpr, vrsqrt(vmul(gpr, rr)));
+  const V isl = vrsqrt(rl), isr = vrsqrt(rr);              // 1 / sqrt(rho)
+  const V iw = vrcp(vadd(vmul(rl, isl), vmul(rr, isr)));   // 1 / (sqrt(rho_L) + sqrt(rho_R))
+  const V sl = vmul(rl, isl), sr = vmul(rr, isr);
+  const V ub = vmul(vfma(sl, ul, vmul(sr, ur)), iw);
+  const V vb = vmul(vfma(sl, wl[2], vmul(sr, wr[2])), iw);
+  const V wb = vmul(vfma(sl, wl[3], vmul(sr, wr[3])), iw);
+  const V hb = vmul(vfma(hl, isl, vmul(hr, isr)), iw);
+  const V cb2 = vmul(gm1, vfma(vset<V>(-0.5f), vfma(ub, ub, vfma(vb, vb, vmul(wb, wb))), hb));
+  const V cb = vsel(vgt(cb2, zero), vmul(cb2, vrsqrt(cb2)), zero);
+  V sL = vsub(ul, cl), sR = vadd(ur, cr);
+  const V ea = vsub(ub, cb), eb = vadd(ub, cb);
+  sL = vsel(vgt(sL, ea), ea, sL);
+  sR = vsel(vgt(eb, sR), eb, sR);
+  const V bm = vsel(vge(sL, zero), zero, sL);
+  const V bp = vsel(vgt(sR, zero), sR, zero);
+  const V ib = vrcp(vsub(bp, bm));
+  const V bpm = vmul(bp, bm);
+  V fl[5], fr[5], d[5];
+  pflux_mixed(wl, rl, dpl, hl, fl);
+  pflux_mixed(wr, rr, dpr, hr, fr);
+  jumps_mixed(wl, wr, rr, d);
+#pragma unroll
+  for (int n = 0; n < 5; ++n)
+    f[n] = vmul(vfma(bp, fl[n], vfma(vneg(bm), fr[n], vmul(bpm, d[n]))), ib);
+}
 
 }  // namespace ak

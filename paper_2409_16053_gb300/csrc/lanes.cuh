@@ -1,6 +1,6 @@
 // Lane-generic FP32 arithmetic for the mixed form: every function below exists for a
 // scalar `float` and for a `float2` that carries two independent problems in its two
-// lanes (GB300's packed FP32x2 add, multiply and fused multiply-add issue one
+// lanes (GB300's packed FP32x2 add, subtract, multiply and fused multiply-add issue one
 // instruction for both).  Each lane of a float2 operation rounds exactly like the
 // scalar operation, so code written once over these functions gives the same bits for a
 // problem solved alone or paired with another one.  Comparisons, selects and the
@@ -18,18 +18,41 @@ struct bool2 {
 };
 
 // ---- arithmetic ------------------------------------------------------------------------
-__device__ __forceinline__ float vadd(float a, float b) { return a + b; }
-__device__ __forceinline__ float vsub(float a, float b) { return a - b; }
-__device__ __forceinline__ float vmul(float a, float b) { return a * b; }
-__device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
+// scalar forms through the round-to-nearest intrinsics, which are never fused
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float vsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 
-__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
-// a - b = fma(b, -1, a): the product is exact, so this rounds like the subtraction
-__device__ __forceinline__ float2 vsub(float2 a, float2 b) {
-  return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+// The packed operations are issued as PTX so that the compiler cannot fuse a packed
+// multiply into a following add (the library builds without implicit contraction, and
+// the packed lanes must round exactly like the scalar code).
+__device__ __forceinline__ unsigned long long f2_bits(float2 a) {
+  return ((unsigned long long)__float_as_uint(a.y) << 32) | __float_as_uint(a.x);
 }
-__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 bits_f2(unsigned long long r) {
+  return make_float2(__uint_as_float((unsigned)r), __uint_as_float((unsigned)(r >> 32)));
+}
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) {
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+  return bits_f2(r);
+}
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+  return bits_f2(r);
+}
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) {
+  unsigned long long r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+  return bits_f2(r);
+}
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) {
+  unsigned long long r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(f2_bits(a)), "l"(f2_bits(b)), "l"(f2_bits(c)));
+  return bits_f2(r);
+}
 
 __device__ __forceinline__ float vneg(float a) { return -a; }
 __device__ __forceinline__ float2 vneg(float2 a) { return make_float2(-a.x, -a.y); }

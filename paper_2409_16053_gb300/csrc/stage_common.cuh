@@ -80,13 +80,24 @@ __device__ __forceinline__ void c2p(const double* u, float* w, const Bg& bg, Cou
   w[4] = dugf;
 }
 
+// The Riemann solver of the mesh (one choice per launch, a uniform branch)
 __device__ __forceinline__ void riemann(const double* wl, const double* wr, const Bg& bg,
                                         double* f) {
-  hllc_fp64(wl, wr, bg, f);
+  if (bg.rsolver == AK_HLLE)
+    hlle_fp64(wl, wr, bg, f);
+  else if (bg.rsolver == AK_LLF)
+    llf_fp64(wl, wr, bg, f);
+  else
+    hllc_fp64(wl, wr, bg, f);
 }
-__device__ __forceinline__ void riemann(const float* wl, const float* wr, const Bg& bg,
-                                        float* f) {
-  hllc_mixed(wl, wr, bg, f);
+template <typename V>
+__device__ __forceinline__ void riemann(const V* wl, const V* wr, const Bg& bg, V* f) {
+  if (bg.rsolver == AK_HLLE)
+    hlle_mixed(wl, wr, bg, f);
+  else if (bg.rsolver == AK_LLF)
+    llf_mixed(wl, wr, bg, f);
+  else
+    hllc_mixed(wl, wr, bg, f);
 }
 
 // Lower and upper edge values of the middle cell of q[0 .. 2NG-2].

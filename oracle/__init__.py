@@ -63,7 +63,7 @@ def build(force: bool = False) -> str:
 class _Grid(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64 * 3), ("dx", ctypes.c_double * 3),
                 ("gamma", ctypes.c_double), ("recon", ctypes.c_int32),
-                ("riemann", ctypes.c_int32)]
+                ("riemann", ctypes.c_int32), ("fofc", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 class _Smr(ctypes.Structure):
@@ -97,6 +97,8 @@ def _load():
             lib.orc_rhs.restype = ctypes.c_int64
             lib.orc_rk_step.argtypes = [G, _dp, ctypes.c_double, ctypes.c_int]
             lib.orc_rk_step.restype = ctypes.c_int64
+            lib.orc_rk_step_fofc.argtypes = [G, _dp, ctypes.c_double, ctypes.c_int, _i64p]
+            lib.orc_rk_step_fofc.restype = ctypes.c_int64
             lib.orc_new_dt.argtypes = [G, _dp, ctypes.c_double]
             lib.orc_new_dt.restype = ctypes.c_double
             lib.orc_exact_star.argtypes = [_dp, _dp, ctypes.c_double, _dp, _dp]
@@ -131,8 +133,10 @@ def _ptr(a: np.ndarray):
 class Grid:
     """Periodic uniform grid: n = (n1, n2, n3) cells on a box of side lengths `length`."""
 
-    def __init__(self, n, length=(1.0, 1.0, 1.0), gamma=5.0 / 3.0, recon=PLM, riemann=HLLC):
+    def __init__(self, n, length=(1.0, 1.0, 1.0), gamma=5.0 / 3.0, recon=PLM, riemann=HLLC,
+                 fofc=False):
         self.riemann = int(riemann)
+        self.fofc = bool(fofc)
         self.n = tuple(int(v) for v in n)
         self.length = tuple(float(v) for v in length)
         self.dx = tuple(self.length[d] / self.n[d] for d in range(3))
@@ -147,6 +151,7 @@ class Grid:
         g.gamma = self.gamma
         g.recon = self.recon
         g.riemann = self.riemann
+        g.fofc = 1 if self.fofc else 0
         return ctypes.byref(g)
 
     @property
@@ -225,6 +230,18 @@ def rk_step(U, grid: Grid, dt: float, rk: int = 2):
     if nf < 0:
         raise MemoryError("oracle rk_step allocation failed")
     return Un, int(nf)
+
+
+def rk_step_fofc(U, grid: Grid, dt: float, rk: int = 2):
+    """One full SSP-RK step; returns (U_new, floors, cells flagged by FOFC over its
+    stages)."""
+    Un = np.array(U, dtype=np.float64, order="C", copy=True)
+    assert Un.shape == grid.shape
+    nfl = ctypes.c_int64(0)
+    nf = _load().orc_rk_step_fofc(grid._c(), _ptr(Un), float(dt), int(rk), ctypes.byref(nfl))
+    if nf < 0:
+        raise MemoryError("oracle rk_step allocation failed")
+    return Un, int(nf), int(nfl.value)
 
 
 def new_dt(U, grid: Grid, cfl: float) -> float:

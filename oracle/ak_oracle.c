@@ -34,6 +34,9 @@
  *     a*U0 + b*(U + dt*L(U)).
  *   - Floors: rho < 1e-12 or u_g < 1e-15 in the primitive recovery are clamped and
  *     counted (the paper gives no hydro floor values).
+ *   - FOFC (Section 3, first-order flux correction): after a stage's update, a cell
+ *     whose density or internal energy is not positive gets LLF fluxes of the
+ *     piecewise-constant states on all its faces, and the stage is recomputed with them.
  */
 #include <math.h>
 #include <stdint.h>
@@ -57,6 +60,8 @@ typedef struct {
   double gamma;     /* ratio of specific heats of the gamma-law EOS */
   int32_t recon;    /* ORC_PLM or ORC_PPM4 */
   int32_t riemann;  /* ORC_HLLC, ORC_HLLE or ORC_LLF */
+  int32_t fofc;     /* 1: first-order flux correction in every RK stage */
+  int32_t pad;
 } orc_grid;
 
 static int64_t wrap(int64_t i, int64_t n) {
@@ -347,7 +352,10 @@ static void face_states(const orc_grid* g, const double* W, int d, int64_t i, in
   }
 }
 
-int64_t orc_rhs(const orc_grid* g, const double* U, double* L) {
+/* flag != NULL: a face with a flagged cell on either side gets the LLF flux of the two
+ * cells' own (piecewise-constant) states instead of the reconstructed one (FOFC). */
+static int64_t rhs_impl(const orc_grid* g, const double* U, double* L,
+                        const unsigned char* flag) {
   int64_t N = g->n[0] * g->n[1] * g->n[2];
   int64_t nfloor = 0;
   double* W = (double*)malloc(sizeof(double) * NVAR * N);
@@ -374,9 +382,18 @@ int64_t orc_rhs(const orc_grid* g, const double* U, double* L) {
       for (int64_t j = 0; j < g->n[1]; ++j)
         for (int64_t i = 0; i < g->n[0]; ++i) {
           double wl[5], wr[5], f[5];
-          face_states(g, W, d, i, j, k, wl, wr);
-          orc_riemann(g->riemann, wl, wr, g->gamma, f);
           int64_t c = cell(g, i, j, k);
+          int64_t cm = cell(g, i - (d == 0), j - (d == 1), k - (d == 2));
+          if (flag && (flag[c] || flag[cm])) {
+            for (int n = 0; n < NVAR; ++n) {
+              wl[n] = W[(int64_t)perm[n] * N + cm];
+              wr[n] = W[(int64_t)perm[n] * N + c];
+            }
+            orc_llf(wl, wr, g->gamma, f);
+          } else {
+            face_states(g, W, d, i, j, k, wl, wr);
+            orc_riemann(g->riemann, wl, wr, g->gamma, f);
+          }
           for (int n = 0; n < NVAR; ++n) F[(int64_t)perm[n] * N + c] = f[n];
         }
 #pragma omp parallel for
@@ -394,27 +411,34 @@ int64_t orc_rhs(const orc_grid* g, const double* U, double* L) {
   return nfloor;
 }
 
+int64_t orc_rhs(const orc_grid* g, const double* U, double* L) {
+  return rhs_impl(g, U, L, NULL);
+}
+
 /* ---------------------------------------------------------------------------------
  * One SSP-RK step (Section 3, method of lines with SSP-RK; reading of the standard
  * coefficients).  Stage s: U <- a_s*U0 + b_s*(U + dt*L(U)).  Returns the number of
  * floors applied, or -1 on allocation failure.
  * ------------------------------------------------------------------------------- */
-int64_t orc_rk_step(const orc_grid* g, double* U, double dt, int rk) {
+int64_t orc_rk_step_fofc(const orc_grid* g, double* U, double dt, int rk, int64_t* nfofc) {
   static const double a2[2] = {0.0, 0.5}, b2[2] = {1.0, 0.5};
   static const double a3[3] = {0.0, 0.75, 1.0 / 3.0}, b3[3] = {1.0, 0.25, 2.0 / 3.0};
   const double* a = (rk == 3) ? a3 : a2;
   const double* b = (rk == 3) ? b3 : b2;
   int ns = (rk == 3) ? 3 : 2;
-  int64_t N = NVAR * g->n[0] * g->n[1] * g->n[2];
+  int64_t NC = g->n[0] * g->n[1] * g->n[2];
+  int64_t N = NVAR * NC;
   double* U0 = (double*)malloc(sizeof(double) * N);
   double* L = (double*)malloc(sizeof(double) * N);
-  if (!U0 || !L) {
+  unsigned char* flag = g->fofc ? (unsigned char*)malloc(NC) : NULL;
+  if (!U0 || !L || (g->fofc && !flag)) {
     free(U0);
     free(L);
+    free(flag);
     return -1;
   }
   memcpy(U0, U, sizeof(double) * N);
-  int64_t nfloor = 0;
+  int64_t nfloor = 0, nflag = 0;
   for (int s = 0; s < ns; ++s) {
     int64_t nf = orc_rhs(g, U, L);
     if (nf < 0) {
@@ -422,12 +446,38 @@ int64_t orc_rk_step(const orc_grid* g, double* U, double dt, int rk) {
       break;
     }
     nfloor += nf;
+    if (g->fofc) {
+      /* tentative update; flag cells whose density or internal energy is not positive */
+      int64_t nst = 0;
+#pragma omp parallel for reduction(+ : nst)
+      for (int64_t c = 0; c < NC; ++c) {
+        double u[5];
+        for (int n = 0; n < NVAR; ++n)
+          u[n] = a[s] * U0[n * NC + c] + b[s] * (U[n * NC + c] + dt * L[n * NC + c]);
+        double ug = u[4] - 0.5 * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) / u[0];
+        flag[c] = !(u[0] > 0.0) || !(ug > 0.0);
+        nst += flag[c];
+      }
+      if (nst) {
+        nflag += nst;
+        if (rhs_impl(g, U, L, flag) < 0) {
+          nfloor = -1;
+          break;
+        }
+      }
+    }
 #pragma omp parallel for
     for (int64_t c = 0; c < N; ++c) U[c] = a[s] * U0[c] + b[s] * (U[c] + dt * L[c]);
   }
   free(U0);
   free(L);
+  free(flag);
+  if (nfofc) *nfofc = nflag;
   return nfloor;
+}
+
+int64_t orc_rk_step(const orc_grid* g, double* U, double dt, int rk) {
+  return orc_rk_step_fofc(g, U, dt, rk, NULL);
 }
 
 /* ---------------------------------------------------------------------------------

@@ -443,3 +443,44 @@ def test_sod_error_ordered_hllc_hlle_llf():
         rho_ex = oracle.exact_sample(np.array(wl), np.array(wr), g, (x[sel] - 0.75) / t)[0]
         err[rs] = np.mean(np.abs(U[0, 0, 0, sel] - rho_ex))
     assert err[oracle.HLLC] < err[oracle.HLLE] < err[oracle.LLF], err
+
+
+# ---------------------------------------------------------------------------------
+# FOFC: first-order flux correction (Section 3)
+# ---------------------------------------------------------------------------------
+def test_fofc_is_identity_when_nothing_goes_negative():
+    n = (16, 12, 8)
+    U0 = pgen.turbulence(n, seed=5, kmin=1, kmax=4, mach=0.5)
+    g, gf = oracle.Grid(n), oracle.Grid(n, fofc=True)
+    dt = oracle.new_dt(U0, g, 0.3)
+    Ua, fa = oracle.rk_step(U0, g, dt, 2)
+    Ub, fb, nflag = oracle.rk_step_fofc(U0, gf, dt, 2)
+    assert nflag == 0 and fa == fb == 0
+    assert np.array_equal(Ua, Ub)
+
+
+def _mach5_run(fofc, steps=15):
+    n = (24, 24, 24)
+    U = pgen.turbulence(n, seed=3, kmin=1, kmax=6, mach=5.0)
+    g = oracle.Grid(n, fofc=fofc)
+    tot0 = U.reshape(5, -1).sum(axis=1)
+    floors = flagged = 0
+    for _ in range(steps):
+        dt = oracle.new_dt(U, g, 0.3)
+        U, nf, nfl = oracle.rk_step_fofc(U, g, dt, 2)
+        floors += nf
+        flagged += nfl
+    return U, tot0, floors, flagged
+
+
+def test_fofc_keeps_mach5_turbulence_positive_and_conservative():
+    # the plain PLM + HLLC step drives cells to negative internal energy (floors);
+    # FOFC replaces those cells' fluxes and no floor is needed
+    _, _, floors_plain, flagged_plain = _mach5_run(False)
+    assert floors_plain > 0 and flagged_plain == 0
+    U, tot0, floors, flagged = _mach5_run(True)
+    assert floors == 0 and flagged > 0
+    # the correction exchanges fluxes, so the totals are conserved to round-off
+    tot = U.reshape(5, -1).sum(axis=1)
+    scale = np.abs(U).reshape(5, -1).sum(axis=1)
+    assert np.all(np.abs(tot - tot0) <= 1e-13 * scale), (tot - tot0)

@@ -91,6 +91,11 @@ typedef struct {
   int32_t riemann;          /* AK_HLLC (0: HLLC with PVRS speeds bounded by the Davis
                                speeds), AK_HLLE (HLL with Einfeldt's Roe-average speeds)
                                or AK_LLF (Rusanov) */
+  int32_t fofc;             /* 1: first-order flux correction (Section 3): in every RK
+                               stage, a cell whose density or internal energy would not
+                               be positive gets first-order (piecewise-constant) LLF
+                               fluxes on all its faces.  Uniform meshes only (AK_EINVAL
+                               with several levels).  0: off. */
   double gamma;             /* gamma-law EOS, > 1 */
   double cfl;               /* Courant number of Eq. (3), in (0, 1] */
   double ref_rho, ref_p;    /* AK_MIXED only: background density and pressure that are
@@ -199,7 +204,8 @@ ak_status ak_upload(ak_mesh* mesh, int32_t reg, const double* host_interior);
 ak_status ak_download(ak_mesh* mesh, int32_t reg, double* host_interior);
 
 /* Device counters (synchronizes): out[0] floors applied, out[1] non-finite cells seen,
- * out[2] bounded waits that timed out, out[3] reserved (0). */
+ * out[2] bounded waits that timed out, out[3] cells corrected by FOFC (summed over
+ * stages). */
 ak_status ak_status_counters(ak_mesh* mesh, int64_t out[4]);
 
 /* Largest number of MeshBlocks ak_cfl_dt_noalloc accepts: the size of its static

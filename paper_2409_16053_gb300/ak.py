@@ -46,7 +46,7 @@ class ak_mesh_desc(ctypes.Structure):
         ("xmin", ctypes.c_double * 3), ("xmax", ctypes.c_double * 3),
         ("root_nx", ctypes.c_int32 * 3),
         ("recon", ctypes.c_int32), ("rk", ctypes.c_int32), ("precision", ctypes.c_int32),
-        ("riemann", ctypes.c_int32),
+        ("riemann", ctypes.c_int32), ("fofc", ctypes.c_int32),
         ("gamma", ctypes.c_double), ("cfl", ctypes.c_double),
         ("ref_rho", ctypes.c_double), ("ref_p", ctypes.c_double),
     ]
@@ -213,7 +213,7 @@ class Mesh:
     statically refined mesh (table)."""
 
     def __init__(self, root_nx, block_nx=None, *, table=None, recon=AK_PLM, rk=2,
-                 precision=AK_FP64, riemann=0, gamma=5.0 / 3.0, cfl=0.3,
+                 precision=AK_FP64, riemann=0, fofc=False, gamma=5.0 / 3.0, cfl=0.3,
                  xmin=(0.0, 0.0, 0.0),
                  xmax=(1.0, 1.0, 1.0), ref_rho=1.0, ref_p=1.0, device="cuda", stream=None):
         import torch
@@ -244,6 +244,7 @@ class Mesh:
             d.root_nx[a] = self.root_nx[a]
         d.recon, d.rk, d.precision = int(recon), int(rk), int(precision)
         d.riemann = int(riemann)
+        d.fofc = 1 if fofc else 0
         d.gamma, d.cfl = float(gamma), float(cfl)
         d.ref_rho, d.ref_p = float(ref_rho), float(ref_p)
         self.desc = d

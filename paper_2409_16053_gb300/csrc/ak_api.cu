@@ -78,6 +78,7 @@ extern "C" ak_status ak_mesh_create(const ak_mesh_desc* d, void* cuda_stream, ak
     return einval("ak_mesh_create: precision must be AK_FP64 or AK_MIXED");
   if (d->riemann != AK_HLLC && d->riemann != AK_HLLE && d->riemann != AK_LLF)
     return einval("ak_mesh_create: riemann must be AK_HLLC, AK_HLLE or AK_LLF");
+  if (d->fofc != 0 && d->fofc != 1) return einval("ak_mesh_create: fofc must be 0 or 1");
   if (!(d->gamma > 1.0)) return einval("ak_mesh_create: gamma must be > 1");
   if (!(d->cfl > 0.0 && d->cfl <= 1.0)) return einval("ak_mesh_create: cfl must be in (0, 1]");
   if (d->precision == AK_MIXED && !(d->ref_rho > 0.0 && d->ref_p > 0.0))
@@ -202,6 +203,10 @@ extern "C" ak_status ak_mesh_create(const ak_mesh_desc* d, void* cuda_stream, ak
   m->nlev = X.nlev;
   m->multilevel = X.nlev > 1;
   m->nblocks = nb;
+  if (d->fofc && m->multilevel) {
+    free(m);
+    return einval("ak_mesh_create: FOFC is built for uniform meshes only (one level)");
+  }
   m->h_blocks = (int32_t*)malloc(sizeof(int32_t) * AK_BLOCK_INTS * nb);
   m->h_offsets = (int64_t*)malloc(sizeof(int64_t) * nb);
   m->h_blk = (ak_block*)calloc(nb, sizeof(ak_block));
@@ -397,6 +402,18 @@ extern "C" ak_status ak_mesh_create(const ak_mesh_desc* d, void* cuda_stream, ak
   m->md.xb = m->d_xb;
   m->md.nxa = (long long)xa.size();
   m->md.nxb = (long long)xb.size();
+  m->md.cell_off = m->d_pack_off;
+  if (d->fofc) {
+    // flagged cells are rare: a list of cells/64 entries (at least 65536)
+    const long long cap = std::max(65536ll, m->interior_cells / 64);
+    m->md.fcap = (int)std::min(cap, (long long)INT32_MAX);
+    m->md.fofc = 1;
+    dmalloc((void**)&m->d_fflag, (size_t)m->interior_cells);
+    dmalloc((void**)&m->d_flist, sizeof(int4) * (size_t)m->md.fcap);
+    if (e == cudaSuccess) e = cudaMemset(m->d_fflag, 0, (size_t)m->interior_cells);
+    m->md.fflag = m->d_fflag;
+    m->md.flist = m->d_flist;
+  }
   if (e == cudaSuccess) e = ak_build_work(m, 0, seg, 0);
   if (e == cudaSuccess) e = ak_stage_prepare(m);
   if (e == cudaSuccess) {
@@ -473,6 +490,8 @@ extern "C" void ak_mesh_destroy(ak_mesh* m) {
   cudaFree(m->d_pad_off);
   cudaFree(m->d_xa);
   cudaFree(m->d_xb);
+  cudaFree(m->d_fflag);
+  cudaFree(m->d_flist);
   cudaFree(m->d_work);
   cudaFree(m->d_sc);
   cudaFree(m->d_staging);
@@ -573,6 +592,8 @@ static ak_status enqueue_stage(ak_mesh* m, int stage) {
   const int rk = m->desc.rk;
   const int in = stage_in_reg(rk, stage), outr = stage_out_reg(rk, stage);
   AK_CUDA_TRY(ak_launch_stage(m, stage, m->reg[in], m->reg[0], m->reg[outr], outr, stage == rk));
+  if (m->md.fofc)
+    AK_CUDA_TRY(ak_launch_fofc(m, stage, m->reg[in], m->reg[outr], stage == rk));
   return AK_OK;
 }
 
@@ -696,6 +717,8 @@ extern "C" ak_status ak_mesh_autotune(ak_mesh* m, int32_t result[4]) {
   int best_tile = m->tile, best_seg = m->nseg, best_order = m->order;
   float best = 1e30f;
   cudaError_t e = cudaSuccess;
+  const int fofc = m->md.fofc;
+  m->md.fofc = 0;  // the timed launches flag no cells (their output is discarded)
   for (int tile = 0; tile < ntile && e == cudaSuccess; ++tile)
     for (int seg = 1; seg <= 16 && e == cudaSuccess; seg *= 2)
       for (int order = 0; order < 2 && e == cudaSuccess; ++order) {
@@ -719,6 +742,7 @@ extern "C" ak_status ak_mesh_autotune(ak_mesh* m, int32_t result[4]) {
       }
   cudaEventDestroy(ev[0]);
   cudaEventDestroy(ev[1]);
+  m->md.fofc = fofc;
   if (e == cudaSuccess) e = ak_build_work(m, best_tile, best_seg, best_order);
   if (e != cudaSuccess) {
     ak_set_error("ak_mesh_autotune: %s", cudaGetErrorString(e));
@@ -796,6 +820,5 @@ extern "C" ak_status ak_status_counters(ak_mesh* m, int64_t out[4]) {
   AK_CUDA_TRY(cudaMemcpyAsync(&s, m->d_sc, sizeof(s), cudaMemcpyDeviceToHost, m->stream));
   AK_CUDA_TRY(cudaStreamSynchronize(m->stream));
   for (int i = 0; i < 4; ++i) out[i] = (int64_t)s.counters[i];
-  out[3] = 0;
   return AK_OK;
 }

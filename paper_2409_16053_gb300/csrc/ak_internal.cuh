@@ -23,8 +23,11 @@ struct ak_dev_scalars {
   double dt;                        // dt used by the stage kernels
   double dt_next;                   // cfl * min(dx / (|v| + c_s)) of the last reduction
   unsigned long long dtmin_bits;    // running min of dx / (|v| + c_s), as bits (>= 0)
-  unsigned long long counters[4];   // floors, non-finite cells, timeouts, reserved
+  unsigned long long counters[4];   // floors, non-finite cells, timeouts, FOFC cells
   unsigned long long reported[4];   // counters already reported to the host
+  unsigned int fofc_n;              // cells flagged by FOFC in the current stage
+  unsigned int fofc_dropped;        // flagged cells beyond the list's capacity
+  unsigned long long sink[2];       // counts nobody reads (recomputations)
 };
 
 // One leaf MeshBlock (device table entry).
@@ -77,6 +80,11 @@ struct ak_meshdev {
   const ak_xfer* xa;    // exchange plan, pass 1: copies and restrictions
   const ak_xfer* xb;    // exchange plan, pass 2: prolongations
   long long nxa, nxb;
+  const long long* cell_off;  // first interior cell of each block in the global count
+  unsigned char* fflag; // FOFC: 1 for a flagged interior cell (global count), else 0
+  int4* flist;          // FOFC: flagged cells (block, i, j, k) of the current stage
+  int fcap;             // capacity of flist
+  int fofc;             // FOFC on
   int nblocks, nlev, ng, nfc;
   double gamma;
 };
@@ -103,6 +111,8 @@ struct ak_mesh {
   double* d_fcbuf;
   long long* d_pack_off;        // interior prefix sums per block (nblocks + 1)
   long long* d_pad_off;         // padded-cell prefix sums per block (nblocks + 1)
+  unsigned char* d_fflag;       // FOFC flags and list (see ak_meshdev)
+  int4* d_flist;
   ak_xfer* d_xa;                // exchange plan (see ak_xfer)
   ak_xfer* d_xb;
   ak_work* d_work;
@@ -132,6 +142,10 @@ cudaError_t ak_launch_unpack(const ak_mesh* m, const double* packed, double* reg
 cudaError_t ak_launch_stage(const ak_mesh* m, int stage, const double* u_in, const double* u0,
                             double* u_out, int out_reg, int last_stage);
 cudaError_t ak_launch_cfl(const ak_mesh* m, const double* reg);
+// First-order flux correction after a stage launch (FOFC meshes): corrects the stage's
+// output for the cells it flagged and their neighbours, then clears the flags.
+cudaError_t ak_launch_fofc(const ak_mesh* m, int stage, const double* u_in, double* u_out,
+                           int last_stage);
 cudaError_t ak_launch_finalize_dt(const ak_mesh* m, int use_next_as_dt);
 cudaError_t ak_launch_set_dt(const ak_mesh* m, double dt);
 cudaError_t ak_stage_prepare(const ak_mesh* m);

@@ -354,6 +354,7 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
           uout[e + v * g.var_stride] = r;
         f3m[v] = f3p[v];
       }
+      if (md.fofc) fofc_flag(un, md, sc, blk, g, ci, cj, k);
       if constexpr (TMA_OUT) fence_proxy_async_smem();
       if (last_stage) {
         if constexpr (MIXED) {
@@ -530,6 +531,8 @@ __global__ void flux_correction_kernel(const double* __restrict__ reg, ak_meshde
       out[v] = R(0.25) * sum[v];
   }
 }
+
+Bg stage_bg(const ak_mesh* m) { return make_bg(m); }
 
 static Bg make_bg(const ak_mesh* m) {
   Bg bg;

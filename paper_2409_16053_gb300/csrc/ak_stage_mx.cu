@@ -378,6 +378,7 @@ __global__ void __launch_bounds__(MxCfg<NG, T>::NTH, 2)
         un[v] = r;
         uout[e + v * vst] = r;
       }
+      if (md.fofc) fofc_flag(un, md, sc, w.block, g, ci, cj, k);
       if (last_stage) {
         // CFL ratio in FP32: it only sets the next step's dt
         const float rho = fmaxf(f64_to_f32(un[0]), (float)AK_RHO_FLOOR);

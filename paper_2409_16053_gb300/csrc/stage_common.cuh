@@ -154,6 +154,27 @@ __device__ __forceinline__ void corrected_flux(const double* buf, int cell, floa
   for (int v = 0; v < 5; ++v) f[v] = f64_to_f32(buf[(long long)cell * 5 + v]);
 }
 
+// FOFC flag of an updated cell (Section 3): density or internal energy not positive,
+// i.e. rho <= 0 or rho (2E) - |M|^2 <= 0.  Flagged cells go to the mesh's list and
+// flag array for the correction kernel (cells beyond the list's capacity are counted
+// and left to the floors).
+__device__ __forceinline__ void fofc_flag(const double* un, const ak_meshdev& md,
+                                          ak_dev_scalars* sc, int blk, const ak_block& g,
+                                          int i, int j, int k) {
+  const double m2 = fma(un[1], un[1], fma(un[2], un[2], un[3] * un[3]));
+  if (dpos(un[0]) && dpos(fma(un[0], un[4] + un[4], -m2))) return;
+  const unsigned idx = atomicAdd(&sc->fofc_n, 1u);
+  if (idx < (unsigned)md.fcap) {
+    md.flist[idx] = make_int4(blk, i, j, k);
+    md.fflag[md.cell_off[blk] + ((long long)k * g.nx2 + j) * g.nx1 + i] = 1;
+  } else {
+    atomicAdd(&sc->fofc_dropped, 1u);
+  }
+}
+
+// The stage kernels' background state and EOS constants of a mesh (ak_stage.cu).
+Bg stage_bg(const ak_mesh* m);
+
 // Mixed-form PLM stage with paired x1/x2 work (ak_stage_mx.cu); prepare_only sets the
 // kernel's shared-memory attribute.
 cudaError_t launch_stage_mx(const ak_mesh* m, const double* uin, const double* u0, double* uout,

@@ -1,0 +1,91 @@
+"""First-order flux correction (FOFC) on the GPU against the oracle: Mach-5 turbulence,
+where the plain scheme needs floors, on a mesh of 8 MeshBlocks (corrections cross block
+boundaries), FP64 parity step by step with the oracle's dt sequence and the same number
+of corrected cells, PPM4 + RK3, the mixed form, and refused on refined meshes."""
+import numpy as np
+import pytest
+
+import oracle
+import pgen
+from _helpers import max_norm_diff
+
+pytestmark = pytest.mark.gpu
+G53 = 5.0 / 3.0
+N = (24, 24, 24)
+
+
+@pytest.fixture(scope="module")
+def ak():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_2409_16053_gb300 import build
+    build.build()
+    from paper_2409_16053_gb300 import ak as mod
+    oracle.build()
+    return mod
+
+
+def _run(ak, precision, recon, rk, steps, tol):
+    U = pgen.turbulence(N, seed=3, kmin=1, kmax=6, mach=5.0)
+    g = oracle.Grid(N, recon=recon, fofc=True)
+    m = ak.Mesh(N, (12, 12, 12), recon=recon, rk=rk, precision=precision, fofc=True,
+                ref_rho=1.0, ref_p=1.0)
+    m.upload(U)
+    tot0 = U.reshape(5, -1).sum(axis=1)
+    flagged = 0
+    errs = []
+    for _ in range(steps):
+        dt = oracle.new_dt(U, g, 0.3)
+        U, nf, nfl = oracle.rk_step_fofc(U, g, dt, rk)
+        assert nf == 0
+        flagged += nfl
+        m.step(dt, want_dt_next=False)
+        errs.append(max_norm_diff(m.download(), U, G53))
+    out = m.download()
+    c = m.counters()
+    m.close()
+    assert max(errs) <= tol, errs
+    assert c[0] == 0 and c[1] == 0, c       # no floors, no non-finite cells
+    # FP64: conservation to round-off; mixed: to the FP32 rounding of the divergence
+    tot = out.reshape(5, -1).sum(axis=1)
+    scale = np.abs(out).reshape(5, -1).sum(axis=1)
+    ctol = 1e-12 if precision == 0 else 1e-8
+    assert np.all(np.abs(tot - tot0) <= ctol * scale), (tot - tot0)
+    return c[3], flagged
+
+
+def test_fp64_plm_rk2_mach5_step_parity(ak):
+    gpu_cells, oracle_cells = _run(ak, 0, 0, 2, 15, 1e-10)
+    assert oracle_cells > 0
+    assert gpu_cells == oracle_cells, (gpu_cells, oracle_cells)
+
+
+def test_fp64_ppm4_rk3_mach5_step_parity(ak):
+    gpu_cells, oracle_cells = _run(ak, 0, 1, 3, 4, 1e-10)
+    assert oracle_cells > 0
+    assert gpu_cells == oracle_cells, (gpu_cells, oracle_cells)
+
+
+def test_mixed_mach5_positive_and_close(ak):
+    gpu_cells, oracle_cells = _run(ak, 1, 0, 2, 15, 5e-3)
+    assert gpu_cells > 0 and oracle_cells > 0
+
+
+def test_plain_scheme_needs_floors_on_the_gpu(ak):
+    U = pgen.turbulence(N, seed=3, kmin=1, kmax=6, mach=5.0)
+    g = oracle.Grid(N)
+    m = ak.Mesh(N, (12, 12, 12))
+    m.upload(U)
+    for _ in range(15):
+        dt = oracle.new_dt(U, g, 0.3)
+        U, _ = oracle.rk_step(U, g, dt, 2)
+        m.step(dt, want_dt_next=False)
+    assert m.counters()[0] > 0 and m.counters()[3] == 0
+    m.close()
+
+
+def test_fofc_refused_on_refined_mesh(ak):
+    t = pgen.nested_refinement_blocks(32, 8, 8, 2)
+    with pytest.raises(ak.AkError):
+        ak.Mesh((32,) * 3, table=t, fofc=True)

@@ -40,6 +40,7 @@ _lib = None
 
 PLM = 0
 PPM4 = 1
+WENOZ = 2
 HLLC = 0
 HLLE = 1
 LLF = 2
@@ -90,6 +91,7 @@ def _load():
             lib.orc_plm_slope.argtypes = [ctypes.c_double] * 3
             lib.orc_plm_slope.restype = ctypes.c_double
             lib.orc_ppm4_edges.argtypes = [_dp, _dp, _dp]
+            lib.orc_wenoz_edges.argtypes = [_dp, _dp, _dp]
             lib.orc_hllc.argtypes = [_dp, _dp, ctypes.c_double, _dp]
             lib.orc_hlle.argtypes = [_dp, _dp, ctypes.c_double, _dp]
             lib.orc_llf.argtypes = [_dp, _dp, ctypes.c_double, _dp]
@@ -186,6 +188,14 @@ def ppm4_edges(q5):
     q = np.ascontiguousarray(q5, dtype=np.float64)
     lo, hi = ctypes.c_double(), ctypes.c_double()
     _load().orc_ppm4_edges(_ptr(q), ctypes.byref(lo), ctypes.byref(hi))
+    return lo.value, hi.value
+
+
+def wenoz_edges(q5):
+    """WENO-Z values at x_{i-1/2} and x_{i+1/2} of the middle cell of q5."""
+    q = np.ascontiguousarray(q5, dtype=np.float64)
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    _load().orc_wenoz_edges(_ptr(q), ctypes.byref(lo), ctypes.byref(hi))
     return lo.value, hi.value
 
 

@@ -22,6 +22,10 @@
  *   - PLM limiter: van Leer harmonic mean of the one-sided differences.
  *   - PPM4: Colella & Woodward (1984) uniform-grid interface values and limiter,
  *     no flattening, no contact steepening.
+ *   - WENO-Z: Borges, Carmona, Costa & Don (2008): the three third-order candidate
+ *     interface values of Jiang & Shu (1996) with their smoothness indicators, weights
+ *     alpha_k = d_k (1 + tau5 / (beta_k + eps)), tau5 = |beta_0 - beta_2|, ideal weights
+ *     (1, 6, 3)/10, eps = 1e-40; on primitives, 3 ghost cells.
  *   - HLLC: Toro (2009) ch. 10, PVRS wave-speed estimate bounded outward by the
  *     Davis speeds, star states of the standard form, ties at S_L = 0 / S* = 0
  *     resolved to the left.
@@ -49,6 +53,7 @@
 
 #define ORC_PLM 0
 #define ORC_PPM4 1
+#define ORC_WENOZ 2
 
 #define ORC_HLLC 0
 #define ORC_HLLE 1
@@ -162,6 +167,34 @@ void orc_ppm4_edges(const double q[5], double* qlo, double* qhi) {
   }
   *qlo = alo;
   *qhi = ahi;
+}
+
+/* ---------------------------------------------------------------------------------
+ * WENO-Z (Section 3: one of the reconstructions of the hydro module).  Given
+ * q(i-2..i+2) returns the values at x_{i-1/2} (from the right) and x_{i+1/2} (from the
+ * left) in cell i.
+ * ------------------------------------------------------------------------------- */
+static double wenoz_value(double a, double b, double c, double d, double e) {
+  /* value at the interface between c and d from cells a, b, c, d, e (c is the cell) */
+  double p0 = (2.0 * a - 7.0 * b + 11.0 * c) / 6.0;
+  double p1 = (-b + 5.0 * c + 2.0 * d) / 6.0;
+  double p2 = (2.0 * c + 5.0 * d - e) / 6.0;
+  double b0 = 13.0 / 12.0 * (a - 2.0 * b + c) * (a - 2.0 * b + c) +
+              0.25 * (a - 4.0 * b + 3.0 * c) * (a - 4.0 * b + 3.0 * c);
+  double b1 = 13.0 / 12.0 * (b - 2.0 * c + d) * (b - 2.0 * c + d) + 0.25 * (b - d) * (b - d);
+  double b2 = 13.0 / 12.0 * (c - 2.0 * d + e) * (c - 2.0 * d + e) +
+              0.25 * (3.0 * c - 4.0 * d + e) * (3.0 * c - 4.0 * d + e);
+  double tau = fabs(b0 - b2);
+  const double eps = 1e-40;
+  double a0 = 0.1 * (1.0 + tau / (b0 + eps));
+  double a1 = 0.6 * (1.0 + tau / (b1 + eps));
+  double a2 = 0.3 * (1.0 + tau / (b2 + eps));
+  return (a0 * p0 + a1 * p1 + a2 * p2) / (a0 + a1 + a2);
+}
+
+void orc_wenoz_edges(const double q[5], double* qlo, double* qhi) {
+  *qhi = wenoz_value(q[0], q[1], q[2], q[3], q[4]);
+  *qlo = wenoz_value(q[4], q[3], q[2], q[1], q[0]);
 }
 
 /* ---------------------------------------------------------------------------------
@@ -342,8 +375,13 @@ static void face_states(const orc_grid* g, const double* W, int d, int64_t i, in
         s[m] = q[cell(g, i + o * e[0], j + o * e[1], k + o * e[2])];
       }
       double lo, hi, lo2, hi2;
-      orc_ppm4_edges(&s[0], &lo, &hi);  /* cell c - e_d, stencil c-3e..c+e */
-      orc_ppm4_edges(&s[1], &lo2, &hi2); /* cell c, stencil c-2e..c+2e */
+      if (g->recon == ORC_WENOZ) {
+        orc_wenoz_edges(&s[0], &lo, &hi);  /* cell c - e_d, stencil c-3e..c+e */
+        orc_wenoz_edges(&s[1], &lo2, &hi2); /* cell c, stencil c-2e..c+2e */
+      } else {
+        orc_ppm4_edges(&s[0], &lo, &hi);
+        orc_ppm4_edges(&s[1], &lo2, &hi2);
+      }
       (void)lo;
       (void)hi2;
       wl[n] = hi;

@@ -36,6 +36,7 @@
 void orc_cons_to_prim(const double u[5], double w[5], int64_t* nfloor);
 double orc_plm_slope(double qm, double q0, double qp);
 void orc_ppm4_edges(const double q[5], double* qlo, double* qhi);
+void orc_wenoz_edges(const double q[5], double* qlo, double* qhi);
 void orc_riemann(int solver, const double wl[5], const double wr[5], double gamma,
                  double f[5]);
 
@@ -288,8 +289,13 @@ static void block_fluxes(const smr_index* x, int b, const double* U, double* F[3
             } else {
               double s[6], lo, hi, lo2, hi2;
               for (int t = 0; t < 6; ++t) s[t] = w[c0 + (t - 3) * st[d]];
-              orc_ppm4_edges(&s[0], &lo, &hi);
-              orc_ppm4_edges(&s[1], &lo2, &hi2);
+              if (m->recon == 2) {
+                orc_wenoz_edges(&s[0], &lo, &hi);
+                orc_wenoz_edges(&s[1], &lo2, &hi2);
+              } else {
+                orc_ppm4_edges(&s[0], &lo, &hi);
+                orc_ppm4_edges(&s[1], &lo2, &hi2);
+              }
               wl[q] = hi;
               wr[q] = lo2;
             }

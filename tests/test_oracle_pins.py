@@ -12,6 +12,7 @@ import pytest
 
 import oracle
 import pgen
+from _helpers import l1_wave_error
 
 G53 = 5.0 / 3.0
 
@@ -484,3 +485,54 @@ def test_fofc_keeps_mach5_turbulence_positive_and_conservative():
     tot = U.reshape(5, -1).sum(axis=1)
     scale = np.abs(U).reshape(5, -1).sum(axis=1)
     assert np.all(np.abs(tot - tot0) <= 1e-13 * scale), (tot - tot0)
+
+
+# ---------------------------------------------------------------------------------
+# WENO-Z reconstruction
+# ---------------------------------------------------------------------------------
+def test_wenoz_exact_for_quadratic_cell_averages():
+    # every third-order candidate is exact for a quadratic, so any convex weights are
+    rng = np.random.default_rng(6)
+    for _ in range(50):
+        c0, c1, c2 = rng.normal(size=3)
+        q = lambda x: c0 + c1 * x + c2 * x * x
+        avg = [q(i) + c2 / 12.0 for i in range(-2, 3)]   # cell averages over [i-1/2, i+1/2]
+        lo, hi = oracle.wenoz_edges(avg)
+        sc = 1 + abs(c0) + abs(c1) + abs(c2)
+        assert abs(lo - q(-0.5)) < 1e-14 * sc and abs(hi - q(0.5)) < 1e-14 * sc
+
+
+def test_wenoz_fifth_order_on_smooth_data():
+    errs = []
+    for h in (0.1, 0.05, 0.025):
+        avg = [(np.cos(h * (i - 0.5)) - np.cos(h * (i + 0.5))) / h for i in range(-2, 3)]
+        lo, hi = oracle.wenoz_edges(avg)
+        errs.append(abs(hi - np.sin(0.5 * h)) + abs(lo - np.sin(-0.5 * h)))
+    assert errs[0] / errs[1] > 28 and errs[1] / errs[2] > 28, errs
+
+
+def test_wenoz_mirror_symmetry_and_step():
+    rng = np.random.default_rng(7)
+    for _ in range(100):
+        q = rng.normal(size=5)
+        lo, hi = oracle.wenoz_edges(q)
+        lo_r, hi_r = oracle.wenoz_edges(q[::-1])
+        assert lo == hi_r and hi == lo_r
+    # a step next to the cell: the weight of the stencil across it vanishes
+    lo, hi = oracle.wenoz_edges([0.0, 0.0, 0.0, 1.0, 1.0])
+    assert abs(hi) < 1e-30 and abs(lo) < 1e-30
+
+
+def test_wenoz_rk3_sound_wave_converges_faster_than_ppm4():
+    errs = {}
+    for recon in (oracle.PPM4, oracle.WENOZ):
+        e = []
+        for n in (16, 32, 64):
+            U0, T = pgen.linear_wave((n, 1, 1))
+            U, _, _, nf = oracle.run(U0, oracle.Grid((n, 1, 1), recon=recon), 0.3, t_end=T, rk=3)
+            assert nf == 0
+            e.append(l1_wave_error(U, U0))
+        errs[recon] = e
+    w = errs[oracle.WENOZ]
+    assert w[0] / w[1] > 8 and w[1] / w[2] > 8, w
+    assert all(a < b for a, b in zip(w, errs[oracle.PPM4])), errs

@@ -64,7 +64,7 @@ typedef enum {
   AK_ESTATE = -6      /* call out of order (e.g. a register not bound) */
 } ak_status;
 
-enum { AK_PLM = 0, AK_PPM4 = 1 };     /* reconstruction (Section 3) */
+enum { AK_PLM = 0, AK_PPM4 = 1, AK_WENOZ = 2 };  /* reconstruction (Section 3) */
 enum { AK_FP64 = 0, AK_MIXED = 1 };   /* arithmetic form of the stage */
 enum { AK_HLLC = 0, AK_HLLE = 1, AK_LLF = 2 };  /* Riemann solver (Section 3) */
 
@@ -75,7 +75,7 @@ typedef struct ak_mesh ak_mesh;
 
 typedef struct {
   int32_t nblocks;        /* number of MeshBlocks (Section 2), >= 1 */
-  int32_t nghost;         /* ghost cells per side: 2 for PLM, 3 for PPM4 */
+  int32_t nghost;         /* ghost cells per side: 2 for PLM, 3 for PPM4 and WENO-Z */
   const int32_t* blocks;  /* host array, AK_BLOCK_INTS ints per leaf block:
                              level, lx1, lx2, lx3, nx1, nx2, nx3 -- (lx1, lx2, lx3) is the
                              block's first cell in the cell index space of its level
@@ -85,7 +85,7 @@ typedef struct {
                              create time; the caller keeps ownership. */
   double xmin[3], xmax[3];  /* domain, periodic in all three directions */
   int32_t root_nx[3];       /* level-0 cells per direction; the blocks must tile it */
-  int32_t recon;            /* AK_PLM or AK_PPM4 */
+  int32_t recon;            /* AK_PLM, AK_PPM4 or AK_WENOZ */
   int32_t rk;               /* SSP-RK order: 2 (Heun) or 3 (Shu-Osher) */
   int32_t precision;        /* AK_FP64 or AK_MIXED */
   int32_t riemann;          /* AK_HLLC (0: HLLC with PVRS speeds bounded by the Davis

@@ -70,9 +70,10 @@ extern "C" ak_status ak_mesh_create(const ak_mesh_desc* d, void* cuda_stream, ak
   if (!d || !out) return einval("ak_mesh_create: NULL argument");
   *out = nullptr;
   if (d->nblocks < 1 || !d->blocks) return einval("ak_mesh_create: need nblocks >= 1 and a block table");
-  if (d->recon != AK_PLM && d->recon != AK_PPM4) return einval("ak_mesh_create: recon must be AK_PLM or AK_PPM4");
+  if (d->recon != AK_PLM && d->recon != AK_PPM4 && d->recon != AK_WENOZ)
+    return einval("ak_mesh_create: recon must be AK_PLM, AK_PPM4 or AK_WENOZ");
   const int ng = d->recon == AK_PLM ? 2 : 3;
-  if (d->nghost != ng) return einval("ak_mesh_create: nghost must be 2 for PLM and 3 for PPM4");
+  if (d->nghost != ng) return einval("ak_mesh_create: nghost must be 2 for PLM and 3 for PPM4 / WENO-Z");
   if (d->rk != 2 && d->rk != 3) return einval("ak_mesh_create: rk must be 2 or 3");
   if (d->precision != AK_FP64 && d->precision != AK_MIXED)
     return einval("ak_mesh_create: precision must be AK_FP64 or AK_MIXED");

@@ -75,8 +75,8 @@ __device__ void face_change(const double* uin, const ak_meshdev& md, const Bg& b
       qa[m] = W[m][v];
       qb[m] = W[m + 1][v];
     }
-    edges<NG>(qa, lo_a[v], hi_a[v]);
-    edges<NG>(qb, lo_b[v], hi_b[v]);
+    edges<NG>(qa, lo_a[v], hi_a[v], bg.wenoz);
+    edges<NG>(qb, lo_b[v], hi_b[v], bg.wenoz);
   }
   R fh[5], fl[5];
   solve(d, hi_a, lo_b, bg, fh);

@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
       R q[2 * NG - 1];
 #pragma unroll
       for (int m = 0; m < 2 * NG - 1; ++m) q[m] = ring[slot(kc - NG + 1 + m) * 5 * NPL + v * NPL + oc];
-      edges<NG>(q, lo[v], hi[v]);
+      edges<NG>(q, lo[v], hi[v], bg.wenoz);
     }
   };
   auto x1_edges = [&](const R* pl) {  // cells i0-1 .. i0+TX of the tile's rows
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
           R q[2 * NG - 1];
 #pragma unroll
           for (int m = 0; m < 2 * NG - 1; ++m) q[m] = pl[v * NPL + base + m];
-          edges<NG>(q, e1lo[(v * TY + r) * C1 + c], e1hi[(v * TY + r) * C1 + c]);
+          edges<NG>(q, e1lo[(v * TY + r) * C1 + c], e1hi[(v * TY + r) * C1 + c], bg.wenoz);
         }
       }
     }
@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
           R q[2 * NG - 1];
 #pragma unroll
           for (int m = 0; m < 2 * NG - 1; ++m) q[m] = pl[v * NPL + base + m * WX];
-          edges<NG>(q, e2lo[(v * (TY + 2) + r) * TX + c], e2hi[(v * (TY + 2) + r) * TX + c]);
+          edges<NG>(q, e2lo[(v * (TY + 2) + r) * TX + c], e2hi[(v * (TY + 2) + r) * TX + c], bg.wenoz);
         }
       }
     }
@@ -514,8 +514,8 @@ __global__ void flux_correction_kernel(const double* __restrict__ reg, ak_meshde
           qa[mm] = W[mm][v];
           qb[mm] = W[mm + 1][v];
         }
-        edges<NG>(qa, lo_a[v], hi_a[v]);
-        edges<NG>(qb, lo_b[v], hi_b[v]);
+        edges<NG>(qa, lo_a[v], hi_a[v], bg.wenoz);
+        edges<NG>(qb, lo_b[v], hi_b[v], bg.wenoz);
       }
       R f[5];
       solve(d, hi_a, lo_b, bg, f);
@@ -551,6 +551,7 @@ static Bg make_bg(const ak_mesh* m) {
   bg.kq_f = (float)bg.kq;
   bg.pb_f = bg.gm1_f * bg.ug_f;
   bg.rsolver = m->desc.riemann;
+  bg.wenoz = m->desc.recon == AK_WENOZ;
   return bg;
 }
 

@@ -38,6 +38,7 @@ struct Bg {
   float kq_f;
   float pb_f;
   int rsolver;           // AK_HLLC, AK_HLLE or AK_LLF
+  int wenoz;             // 3-ghost reconstruction: 1 WENO-Z, 0 PPM4
 };
 
 // ------------------------------------------------------------------------------
@@ -107,6 +108,49 @@ __device__ __forceinline__ void ppm_edges(R q0, R q1, R q2, R q3, R q4, R& lo, R
   }
   lo = a_lo;
   hi = a_hi;
+}
+
+// WENO-Z (Borges et al. 2008) values at both faces of the middle cell of q0..q4: the
+// three third-order candidates of Jiang & Shu (1996), their smoothness indicators
+// beta_k, tau5 = |beta_0 - beta_2| and weights alpha_k = d_k (1 + tau5 / (beta_k + eps))
+// with d = (1, 6, 3)/10.  The lower face uses the mirrored stencil, whose indicators are
+// beta_2, beta_1, beta_0.  eps = 1e-40 in FP64; 1e-30 in FP32, where 1e-40 would be
+// subnormal (and flushed by the hardware reciprocal).
+__device__ __forceinline__ double rcp_w(double x) { return rcp64(x); }
+__device__ __forceinline__ float rcp_w(float x) {
+  float r = rcp_approx_f32(x);
+  return fmaf(r, fmaf(-x, r, 1.0f), r);
+}
+template <typename R>
+__device__ __forceinline__ void wenoz_edges(R a, R b, R c, R d, R e, R& lo, R& hi) {
+  const R sixth = R(1) / R(6), c13 = R(13) / R(12), q = R(0.25);
+  const R eps = sizeof(R) == 8 ? R(1e-40) : R(1e-30);
+  const R t0 = fmar(R(-2), b, a + c), u0 = fmar(R(-4), b, fmar(R(3), c, a));
+  const R t1 = fmar(R(-2), c, b + d), u1 = b - d;
+  const R t2 = fmar(R(-2), d, c + e), u2 = fmar(R(3), c, fmar(R(-4), d, e));
+  const R b0 = fmar(c13, t0 * t0, q * (u0 * u0));
+  const R b1 = fmar(c13, t1 * t1, q * (u1 * u1));
+  const R b2 = fmar(c13, t2 * t2, q * (u2 * u2));
+  const R tau = fabs(b0 - b2);
+  const R r0 = tau * rcp_w(b0 + eps), r1 = tau * rcp_w(b1 + eps), r2 = tau * rcp_w(b2 + eps);
+  // upper face (candidates toward d, e)
+  {
+    const R p0 = fmar(R(2), a, fmar(R(-7), b, R(11) * c)) * sixth;
+    const R p1 = fmar(R(5), c, fmar(R(2), d, -b)) * sixth;
+    const R p2 = fmar(R(2), c, fmar(R(5), d, -e)) * sixth;
+    const R a0 = fmar(R(0.1), r0, R(0.1)), a1 = fmar(R(0.6), r1, R(0.6)),
+            a2 = fmar(R(0.3), r2, R(0.3));
+    hi = fmar(a0, p0, fmar(a1, p1, a2 * p2)) * rcp_w(a0 + a1 + a2);
+  }
+  // lower face: the mirrored stencil e, d, c, b, a
+  {
+    const R p0 = fmar(R(2), e, fmar(R(-7), d, R(11) * c)) * sixth;
+    const R p1 = fmar(R(5), c, fmar(R(2), b, -d)) * sixth;
+    const R p2 = fmar(R(2), c, fmar(R(5), b, -a)) * sixth;
+    const R a0 = fmar(R(0.1), r2, R(0.1)), a1 = fmar(R(0.6), r1, R(0.6)),
+            a2 = fmar(R(0.3), r0, R(0.3));
+    lo = fmar(a0, p0, fmar(a1, p1, a2 * p2)) * rcp_w(a0 + a1 + a2);
+  }
 }
 
 // ------------------------------------------------------------------------------

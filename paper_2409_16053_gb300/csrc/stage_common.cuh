@@ -100,9 +100,16 @@ __device__ __forceinline__ void riemann(const V* wl, const V* wr, const Bg& bg, 
     hllc_mixed(wl, wr, bg, f);
 }
 
-// Lower and upper edge values of the middle cell of q[0 .. 2NG-2].
+// Lower and upper edge values of the middle cell of q[0 .. 2NG-2] (NG = 3: WENO-Z if
+// wz, else PPM4).
 template <int NG, typename R>
-__device__ __forceinline__ void edges(const R* q, R& lo, R& hi) {
+__device__ __forceinline__ void edges(const R* q, R& lo, R& hi, bool wz) {
+  if constexpr (NG == 3) {
+    if (wz) {
+      wenoz_edges(q[0], q[1], q[2], q[3], q[4], lo, hi);
+      return;
+    }
+  }
   if constexpr (std::is_same<R, float>::value) {
     if constexpr (NG == 2)
       plm_edges_v(q[0], q[1], q[2], lo, hi);

@@ -9,14 +9,14 @@
 // FP32x2 arithmetic (lanes.cuh), which gives the same bits as solving each alone.  The
 // first T^2 threads also own one column: its x3 reconstruction, x3 face and update.
 //
-// Per plane k, between three barriers:
-//   R  x1/x2 edges of plane k (paired);
-//   F  the column's x3 edge of cell k+1 and x3 face, x1/x2 faces (paired), and part of
-//      the primitive recovery of plane k+NG+1 on the threads without a column;
-//   U  divergence and RK update of the column's cell, CFL, and the rest of the
-//      primitive recovery of plane k+NG+1.
-// The conserved state of plane k+NG+1 and the column's U_in / U0 arrive in shared
-// memory by cp.async issued at the top of the plane, so no register holds data in
+// Per plane k, between two barriers:
+//   P1  x1/x2 edges of plane k (paired); the column's x3 edge of cell k, the x3 face below
+//       it, and the divergence, RK update and CFL of cell k-1 (whose x1/x2 fluxes the
+//       previous P2 left in shared memory); primitive recovery of plane k+NG.  The FP64
+//       work of the update and the recovery overlaps the FP32 reconstruction;
+//   P2  x1/x2 faces of plane k (paired).
+// The conserved state of plane k+NG+1 and the columns' U_in / U0 of plane k arrive in
+// shared memory by cp.async issued at the start of P2, so no register holds data in
 // flight across the phases.
 #include "ak_internal.cuh"
 #include "hydro_ops.cuh"
@@ -48,7 +48,6 @@ struct MxCfg {
   static constexpr int NCROSS = TX * TY + 2 * NG * (TX + TY);  // converted cells per plane
   static constexpr int NSPARE = NTH - NOWN;         // threads without a column
   static constexpr int XPT = (NCROSS - NOWN + NSPARE - 1) / NSPARE;  // their cells
-  static constexpr int XF = XPT / 2;                // of which converted in phase F
   static_assert(NE == (TY + 2) * TX && NF == (TY + 1) * TX, "square tiles");
   static_assert(NSPARE > 0, "threads without a column take the extra cells");
   static constexpr size_t bytes = sizeof(double) * (5 * NCROSS + 2 * 5 * NOWN) +
@@ -65,7 +64,7 @@ __global__ void __launch_bounds__(MxCfg<NG, T>::NTH, 2)
   using C = MxCfg<NG, T>;
   constexpr int TX = C::TX, WX = C::WX, NPL = C::NPL, NR = C::NR, NE = C::NE, NF = C::NF;
   constexpr int C1 = C::C1, NOWN = C::NOWN, NCROSS = C::NCROSS, NSPARE = C::NSPARE;
-  constexpr int XPT = C::XPT, XF = C::XF;
+  constexpr int XPT = C::XPT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* stg = reinterpret_cast<double*>(smem_raw);          // [5][NCROSS] next plane
   double* ucol = stg + 5 * NCROSS;                              // [2][5][NOWN] U_in, U0
@@ -239,46 +238,27 @@ __global__ void __launch_bounds__(MxCfg<NG, T>::NTH, 2)
     }
   };
 
-  // ---- prologue: planes k0-NG .. k0+NG-1, the x3 face below k0, then plane k0+NG --------
+  // ---- prologue: plane k0+NG staged, planes k0-NG .. k0+NG-1 loaded and converted, the
+  //      upper x3 edge of cell k0-1 -----------------------------------------------------
+  stage_plane(k0 + NG);
+  cp_async_commit();
   for (int kp = k0 - NG; kp < k0 + NG; ++kp) load_plane(kp);
   __syncthreads();
-  float hi3[5], f3m[5], f3p[5];
+  float hi3[5], f3lo[5];  // upper x3 edge of cell k-1; flux through the face below cell k-1
   if (column) {
-    float lo_a[5], hi_a[5], lo_b[5];
-    x3_edges(k0 - 1, lo_a, hi_a);
-    x3_edges(k0, lo_b, hi3);
-    if (k0 == 0 && g.ovr[4] >= 0)
-      corrected_flux(md.fcbuf, g.ovr[4] + cj * g.nx1 + ci, f3m);
-    else
-      solve(2, hi_a, lo_b, bg, f3m);
+    float lo_a[5];
+    x3_edges(k0 - 1, lo_a, hi3);
   }
+  cp_async_wait<0>();
   __syncthreads();
-  load_plane(k0 + NG);
 
   float dtmin_f = __int_as_float(0x7f800000);
-  for (int k = k0; k < k1; ++k) {
-    const bool more = k + 1 < k1;
-    __syncthreads();  // A: the previous plane's phase U is complete
-    if (more) stage_plane(k + NG + 1);
-    cp_async_commit();  // group: the next plane (needed from phase F on)
-    if (ochunk) {
-      // column thread t copies, for the row chunk (ocy, ocx), the arrays/variables
-      // vv = t / 128 + 2 m (U_in for vv < 5, U0 above): 5 x 2 x 128 chunks in all
-      const long long po = g.off + ooff + k * pst;
-#pragma unroll
-      for (int m = 0; m < 10 * NOWN / 2 / NOWN; ++m) {
-        const int vv = tid / (NOWN / 2) + 2 * m;
-        if (vv < 5)
-          cp_async16(&ucol[vv * NOWN + ocell], uin + po + vv * vst);
-        else if (need_u0)
-          cp_async16(&ucol[vv * NOWN + ocell], u0 + po + (vv - 5) * vst);
-      }
-    }
-    cp_async_commit();  // group: the columns' U_in / U0 (needed in phase U)
-
-    // ---- R: x1 and x2 edges of plane k, paired --------------------------------------
-    const float* pl = ring + slot(k) * 5 * NPL;
-    if (tid < NE) {
+  for (int k = k0;; ++k) {
+    const bool plane = k < k1;  // plane k is in this CTA's segment
+    // ---- P1: x1/x2 edges of plane k (paired); x3 edge of cell k and the face below it;
+    //      update of plane k-1; primitive recovery of plane k+NG --------------------------
+    if (plane && tid < NE) {
+      const float* pl = ring + slot(k) * 5 * NPL;
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
         float2 q[2 * NG - 1];
@@ -296,20 +276,80 @@ __global__ void __launch_bounds__(MxCfg<NG, T>::NTH, 2)
         e2hi[v * NE + tid] = hi.y;
       }
     }
-    cp_async_wait<1>();
-    __syncthreads();  // B: edges and the staged plane visible
-
-    // ---- F: x3 edge and face of the column; x1/x2 faces, paired ---------------------
     if (column) {
-      float lo3[5], hi3n[5];
-      x3_edges(k + 1, lo3, hi3n);
-      if (k + 1 == g.nx3 && g.ovr[5] >= 0)
-        corrected_flux(md.fcbuf, g.ovr[5] + cj * g.nx1 + ci, f3p);
+      float lo3[5], hi3k[5], f3hi[5];  // f3hi: the face between cells k-1 and k
+      x3_edges(k, lo3, hi3k);
+      if (k == 0 && g.ovr[4] >= 0)
+        corrected_flux(md.fcbuf, g.ovr[4] + cj * g.nx1 + ci, f3hi);
+      else if (k == g.nx3 && g.ovr[5] >= 0)
+        corrected_flux(md.fcbuf, g.ovr[5] + cj * g.nx1 + ci, f3hi);
       else
-        solve(2, hi3, lo3, bg, f3p);
+        solve(2, hi3, lo3, bg, f3hi);
 #pragma unroll
-      for (int v = 0; v < 5; ++v) hi3[v] = hi3n[v];
+      for (int v = 0; v < 5; ++v) hi3[v] = hi3k[v];
+      // ---- divergence, RK update and CFL of cell k-1 (fluxes of the previous P2) -----
+      if (own && k > k0) {
+        const int kc = k - 1;
+        const long long e = ecol + kc * pst;
+        double un[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          const float d1 = f1[v * NF + ty * (TX + 1) + tx + 1] - f1[v * NF + ty * (TX + 1) + tx];
+          const float d2 = f2[v * NF + (ty + 1) * TX + tx] - f2[v * NF + ty * TX + tx];
+          const float d3 = f3hi[v] - f3lo[v];
+          const float L = -fmaf(d1, idx1f, fmaf(d2, idx2f, d3 * idx3f));
+          const double Ld = f32_to_f64(L);
+          const double uik = ucol[v * NOWN + tid];
+          double r;
+          if (form == 1)
+            r = half(ucol[(5 + v) * NOWN + tid] + fma(dt, Ld, uik));
+          else if (form == 0)
+            r = fma(dt, Ld, uik);
+          else
+            r = fma(b, fma(dt, Ld, uik), a * ucol[(5 + v) * NOWN + tid]);
+          un[v] = r;
+          uout[e + v * vst] = r;
+        }
+        if (md.fofc) fofc_flag(un, md, sc, w.block, g, ci, cj, kc);
+        if (last_stage) {
+          // CFL ratio in FP32: it only sets the next step's dt
+          const float rho = fmaxf(f64_to_f32(un[0]), (float)AK_RHO_FLOOR);
+          const float ir = rcp_approx_f32(rho);
+          const float m1 = f64_to_f32(un[1]), m2 = f64_to_f32(un[2]), m3 = f64_to_f32(un[3]);
+          const float ug = fmaxf(fmaf(-0.5f * ir, fmaf(m1, m1, fmaf(m2, m2, m3 * m3)),
+                                      f64_to_f32(un[4])), (float)AK_UG_FLOOR);
+          const float cs = sqrt_fast(bg.gamma_f * (bg.gamma_f - 1.0f) * ug * ir);
+          float lam = fmaf(fabsf(m1), ir, cs) * idx1f;
+          lam = fmaxf(lam, fmaf(fabsf(m2), ir, cs) * idx2f);
+          lam = fmaxf(lam, fmaf(fabsf(m3), ir, cs) * idx3f);
+          dtmin_f = fminf(dtmin_f, rcp_approx_f32(lam));
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < 5; ++v) f3lo[v] = f3hi[v];
     }
+    if (!plane) break;
+    convert_staged(k + NG, 0, NMY);  // staged during the previous P2 (or the prologue)
+    __syncthreads();  // Y: edges, plane k+NG; the update's reads of fluxes and U_in / U0
+
+    if (k + 1 < k1) stage_plane(k + NG + 1);
+    cp_async_commit();
+    if (ochunk) {
+      // column thread t copies, for the row chunk (ocy, ocx), the arrays/variables
+      // vv = t / 128 + 2 m (U_in for vv < 5, U0 above): 5 x 2 x 128 chunks in all
+      const long long po = g.off + ooff + k * pst;
+#pragma unroll
+      for (int m = 0; m < 10 * NOWN / 2 / NOWN; ++m) {
+        const int vv = tid / (NOWN / 2) + 2 * m;
+        if (vv < 5)
+          cp_async16(&ucol[vv * NOWN + ocell], uin + po + vv * vst);
+        else if (need_u0)
+          cp_async16(&ucol[vv * NOWN + ocell], u0 + po + (vv - 5) * vst);
+      }
+    }
+    cp_async_commit();
+
+    // ---- P2: x1/x2 faces of plane k, paired --------------------------------------------
     if (tid < NF) {
       // x1 face: (rho, v1; v2, v3, u_g); x2 face: (rho, v2; v3, v1, u_g)
       constexpr int P2[5] = {0, 2, 3, 1, 4};
@@ -352,57 +392,8 @@ __global__ void __launch_bounds__(MxCfg<NG, T>::NTH, 2)
         f2[v * NF + tid] = fb[v];
       }
     }
-    if (more && !column) convert_staged(k + NG + 1, 1, 1 + XF);
     cp_async_wait<0>();
-    __syncthreads();  // C: fluxes and the columns' U_in / U0 complete
-
-    // ---- U: divergence, RK update and CFL of the column's cell ------------------------
-    if (own) {
-      const long long e = ecol + k * pst;
-      double un[5];
-#pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        const float d1 = f1[v * NF + ty * (TX + 1) + tx + 1] - f1[v * NF + ty * (TX + 1) + tx];
-        const float d2 = f2[v * NF + (ty + 1) * TX + tx] - f2[v * NF + ty * TX + tx];
-        const float d3 = f3p[v] - f3m[v];
-        const float L = -fmaf(d1, idx1f, fmaf(d2, idx2f, d3 * idx3f));
-        const double Ld = f32_to_f64(L);
-        const double uik = ucol[v * NOWN + tid];
-        double r;
-        if (form == 1)
-          r = half(ucol[(5 + v) * NOWN + tid] + fma(dt, Ld, uik));
-        else if (form == 0)
-          r = fma(dt, Ld, uik);
-        else
-          r = fma(b, fma(dt, Ld, uik), a * ucol[(5 + v) * NOWN + tid]);
-        un[v] = r;
-        uout[e + v * vst] = r;
-      }
-      if (md.fofc) fofc_flag(un, md, sc, w.block, g, ci, cj, k);
-      if (last_stage) {
-        // CFL ratio in FP32: it only sets the next step's dt
-        const float rho = fmaxf(f64_to_f32(un[0]), (float)AK_RHO_FLOOR);
-        const float ir = rcp_approx_f32(rho);
-        const float m1 = f64_to_f32(un[1]), m2 = f64_to_f32(un[2]), m3 = f64_to_f32(un[3]);
-        const float ug = fmaxf(fmaf(-0.5f * ir, fmaf(m1, m1, fmaf(m2, m2, m3 * m3)),
-                                    f64_to_f32(un[4])), (float)AK_UG_FLOOR);
-        const float cs = sqrt_fast(bg.gamma_f * (bg.gamma_f - 1.0f) * ug * ir);
-        float lam = fmaf(fabsf(m1), ir, cs) * idx1f;
-        lam = fmaxf(lam, fmaf(fabsf(m2), ir, cs) * idx2f);
-        lam = fmaxf(lam, fmaf(fabsf(m3), ir, cs) * idx3f);
-        dtmin_f = fminf(dtmin_f, rcp_approx_f32(lam));
-      }
-    }
-    if (column) {
-#pragma unroll
-      for (int v = 0; v < 5; ++v) f3m[v] = f3p[v];
-    }
-    if (more) {
-      if (column)
-        convert_staged(k + NG + 1, 0, 1);
-      else
-        convert_staged(k + NG + 1, 1 + XF, NMY);
-    }
+    __syncthreads();  // X: fluxes, the staged plane and the columns' U_in / U0
   }
 
   if (last_stage) {

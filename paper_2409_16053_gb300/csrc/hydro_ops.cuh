@@ -68,44 +68,46 @@ __device__ __forceinline__ double plm_half_slope(double qm, double q0, double qp
   return dpos(prod) ? prod * rcp64(dl + dr) : 0.0;
 }
 
-template <typename R>
-__device__ __forceinline__ R ppm_slope(R qm, R q0, R qp) {
-  // centred difference limited to twice the one-sided ones, zero at extrema (CW84)
-  R dl = q0 - qm;
-  R dr = qp - q0;
-  if (dl * dr <= R(0)) return R(0);
-  R d = R(0.5) * (qp - qm);
-  R m = fabs(d);
-  R tl = R(2) * fabs(dl);
-  R tr = R(2) * fabs(dr);
-  m = tl < m ? tl : m;
-  m = tr < m ? tr : m;
-  return d > R(0) ? m : -m;
+// FP64 PPM4 with the sign tests, minima and exact halvings on the integer pipe.  The
+// limited slope is carried as half its value,
+//   h = sgn(dq) min(|qp - qm| / 4, |q0 - qm|, |qp - q0|)  (0 at extrema),
+// so the interface value 0.5 (q_i + q_i+1) - (S_i+1 - S_i) / 6 is
+// fma(h_i - h_i+1, 1/3, 0.5 (q_i + q_i+1)); the monotonization keeps the products of CW84.
+__device__ __forceinline__ double ppm_half_slope_fp64(double qm, double q0, double qp) {
+  const double dl = q0 - qm, dr = qp - q0;
+  const long long bl = __double_as_longlong(dl), br = __double_as_longlong(dr);
+  if ((bl ^ br) < 0 || (bl << 1) == 0 || (br << 1) == 0) return 0.0;  // extremum or flat
+  const double s = qp - qm;
+  const long long mask = 0x7fffffffffffffffll;
+  long long m = __double_as_longlong(dscale_down(s, 2)) & mask;       // |qp - qm| / 4
+  m = (bl & mask) < m ? (bl & mask) : m;
+  m = (br & mask) < m ? (br & mask) : m;
+  return __longlong_as_double(m | (bl & ~mask));                       // sign of dl (= dr)
 }
 
-// Edge values (lower, upper) of the monotonized parabola of the middle cell of
-// q[0..4] (CW84 interface values on a uniform grid and their monotonization).
-template <typename R>
-__device__ __forceinline__ void ppm_edges(R q0, R q1, R q2, R q3, R q4, R& lo, R& hi) {
-  R sm = ppm_slope(q0, q1, q2);
-  R sc = ppm_slope(q1, q2, q3);
-  R sp = ppm_slope(q2, q3, q4);
-  const R sixth = R(1) / R(6);
-  R a_lo = fmar(sm - sc, sixth, R(0.5) * (q1 + q2));
-  R a_hi = fmar(sc - sp, sixth, R(0.5) * (q2 + q3));
-  R a = q2;
-  if ((a_hi - a) * (a - a_lo) <= R(0)) {
-    a_lo = a;
-    a_hi = a;
-  } else {
-    R da = a_hi - a_lo;
-    R a6 = R(6) * fmar(R(-0.5), a_lo + a_hi, a);
-    if (da * a6 > da * da) {
-      a_lo = fmar(R(3), a, R(-2) * a_hi);
-    } else if (-da * da > da * a6) {
-      a_hi = fmar(R(3), a, R(-2) * a_lo);
-    }
+__device__ __forceinline__ void ppm_edges_fp64(double q0, double q1, double q2, double q3,
+                                               double q4, double& lo, double& hi) {
+  const double third = 1.0 / 3.0;
+  const double hm = ppm_half_slope_fp64(q0, q1, q2);
+  const double hc = ppm_half_slope_fp64(q1, q2, q3);
+  const double hp = ppm_half_slope_fp64(q2, q3, q4);
+  double a_lo = fma(hm - hc, third, dscale_down(q1 + q2, 1));
+  double a_hi = fma(hc - hp, third, dscale_down(q2 + q3, 1));
+  const double a = q2;
+  const double dh = a_hi - a, dlo = a - a_lo;
+  const long long bh = __double_as_longlong(dh), bo = __double_as_longlong(dlo);
+  if ((bh ^ bo) < 0 || (bh << 1) == 0 || (bo << 1) == 0) {  // (a_hi - a)(a - a_lo) <= 0
+    lo = a;
+    hi = a;
+    return;
   }
+  const double da = a_hi - a_lo;
+  const double a6 = 6.0 * fma(-0.5, a_lo + a_hi, a);
+  const double p = da * a6, q = da * da;
+  if (dgt(p, q))
+    a_lo = fma(3.0, a, -(a_hi + a_hi));
+  else if (dgt(-q, p))
+    a_hi = fma(3.0, a, -(a_lo + a_lo));
   lo = a_lo;
   hi = a_hi;
 }

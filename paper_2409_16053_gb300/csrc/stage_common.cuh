@@ -120,7 +120,7 @@ __device__ __forceinline__ void edges(const R* q, R& lo, R& hi, bool wz) {
     lo = q[1] - h;
     hi = q[1] + h;
   } else {
-    ppm_edges(q[0], q[1], q[2], q[3], q[4], lo, hi);
+    ppm_edges_fp64(q[0], q[1], q[2], q[3], q[4], lo, hi);
   }
 }
 

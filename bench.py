@@ -164,6 +164,8 @@ def time_form(ak, torch, precision, U0, steps, warmup):
     """Times `steps` RK2 steps of one form.  Returns a dict of measurements."""
     mesh = ak.Mesh(ROOT_NX, BLOCK_NX, precision=precision, ref_rho=1.0, ref_p=1.0)
     mesh.upload(U0)
+    schedule = mesh.autotune()  # library autotuner, outside the timed region
+    mesh.upload(U0)
     mesh.new_dt()
     h = mesh.handle
     stream = mesh.stream
@@ -203,7 +205,9 @@ def time_form(ak, torch, precision, U0, steps, warmup):
     del mesh
     torch.cuda.empty_cache()
     return {"total_ms": total_ms, "stage1_ms": statistics.mean(st1),
-            "stage2_ms": statistics.mean(st2), "dt_after": dt_next, "counters": counters}
+            "stage2_ms": statistics.mean(st2), "dt_after": dt_next, "counters": counters,
+            "schedule": {"tile": schedule[0], "x3_segments": schedule[1],
+                         "order": schedule[2]}}
 
 
 def e2e_form(ak, torch, precision, U0, steps):
@@ -214,7 +218,9 @@ def e2e_form(ak, torch, precision, U0, steps):
     mesh = ak.Mesh(ROOT_NX, BLOCK_NX, precision=precision, ref_rho=1.0, ref_p=1.0)
     packed = torch.from_numpy(mesh.pack(U0)).pin_memory()
     out = torch.empty_like(packed).pin_memory()
-    ak.ak_upload(mesh.handle, 0, packed.data_ptr())      # warm-up: graph capture etc.
+    ak.ak_upload(mesh.handle, 0, packed.data_ptr())      # warm-up: schedule, graph capture
+    ak.ak_mesh_autotune(mesh.handle)
+    ak.ak_upload(mesh.handle, 0, packed.data_ptr())
     dt, _ = ak.ak_new_dt(mesh.handle, 0)
     ak.ak_step(mesh.handle, dt, True)
     torch.cuda.synchronize()
@@ -248,6 +254,8 @@ def time_smr(ak, torch, precision, steps, warmup):
     m = ak.Mesh((128, 128, 128), table=t, precision=precision, xmin=(-0.5,) * 3,
                 xmax=(0.5,) * 3, ref_rho=1.0, ref_p=1e-5)
     m.upload_packed(P)
+    schedule = m.autotune()
+    m.upload_packed(P)
     m.new_dt()
     for _ in range(warmup):
         m.step(0.0, want_dt_next=False)
@@ -264,7 +272,8 @@ def time_smr(ak, torch, precision, steps, warmup):
     m.close()
     torch.cuda.empty_cache()
     return {"value": cells * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
-            "counters": c}
+            "counters": c, "schedule": {"tile": schedule[0], "x3_segments": schedule[1],
+                                        "order": schedule[2]}}
 
 
 def cpu_baseline(sample_n=96, budget_s=12.0, steps_max=None):
@@ -521,6 +530,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": t64 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "form": "FP64", "cells": cells,
+                   "schedule": r64["schedule"], "schedule_mixed": rmx["schedule"],
                    "l2": "inputs larger than L2: 2 registers x 805 MB",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "roofline": {"bound": "alu", "achieved": ach64, "peak": FP64_PEAK_TFLOPS,

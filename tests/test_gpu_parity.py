@@ -79,6 +79,7 @@ CASES = [
     ((32, 32, 32), (32, 32, 32), "sound"),     # one block, x3 split in segments
     ((12, 40, 10), (6, 20, 10), "tube_x2"),    # discontinuities across block faces
     ((33, 18, 21), (11, 9, 7), "turb"),        # odd sizes, 27 blocks
+    ((8, 8, 8), (2, 2, 2), "turb"),            # blocks as thin as the ghost zone
 ]
 
 
@@ -407,3 +408,9 @@ def test_schedule_rejects_bad_arguments(ak):
             m.schedule(*args)
     m.schedule(0, 2, 1)
     m.close()
+
+
+@pytest.mark.parametrize("recon,block", [(0, (16, 1, 1)), (1, (2, 2, 2)), (2, (4, 2, 4))])
+def test_blocks_thinner_than_the_ghost_zone_are_refused(ak, recon, block):
+    with pytest.raises(ak.AkError, match="nghost"):
+        _mesh(ak, (16, 8, 8), block, recon=recon, rk=3 if recon else 2)

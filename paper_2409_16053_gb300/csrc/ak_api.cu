@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <unordered_map>
 #include <vector>
 
 #include <cudaTypedefs.h>
@@ -298,6 +299,7 @@ extern "C" ak_status ak_mesh_create(const ak_mesh_desc* d, void* cuda_stream, ak
     auto el0 = [&](const ak_block& B, long long i, long long j, long long k) {
       return B.off + ((k + ng) * B.p2 + (j + ng)) * (long long)B.s1 + (i + ng);
     };
+    std::unordered_map<long long, size_t> pro;  // coarse cell -> its entry (one block)
     for (int b = 0; b < nb; ++b) {
       const ak_block& B = m->h_blk[b];
       const int l = B.level;
@@ -332,12 +334,21 @@ extern "C" ak_status ak_mesh_create(const ak_mesh_desc* d, void* cuda_stream, ak
               ak_mesh_destroy(m);
               return einval("ak_mesh_create: ghost cell without a source");
             }
+            // one entry per (fine block, coarse cell): the ghost children form a mask and
+            // dst is the element of the child with the lower half in every direction
             const ak_block& C = m->h_blk[coarse];
             t.src = el0(C, (gx >> 1) - C.lx1, (gy >> 1) - C.lx2, (gz >> 1) - C.lx3);
-            t.info = 2 | (l << 2) | ((l - 1) << 10) |
-                     (int)(((gx & 1) | ((gy & 1) << 1) | ((gz & 1) << 2)) << 18);
-            xb.push_back(t);
+            const int child = (int)((gx & 1) | ((gy & 1) << 1) | ((gz & 1) << 2));
+            auto it = pro.find(t.src);
+            if (it == pro.end()) {
+              t.dst = el0(B, i - (gx & 1), j - (gy & 1), k - (gz & 1));
+              t.info = 2 | (l << 2) | ((l - 1) << 10);
+              it = pro.emplace(t.src, xb.size()).first;
+              xb.push_back(t);
+            }
+            xb[it->second].info |= 1 << (18 + child);
           }
+      pro.clear();
     }
   }
   // level table

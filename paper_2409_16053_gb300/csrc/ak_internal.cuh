@@ -55,10 +55,13 @@ struct ak_level {
   int row, plane;        // (row = s1, plane = s1 * p2)
 };
 
-// One ghost cell of the exchange plan (built once per mesh on the host): the element of
-// variable 0 of the ghost cell, the element of variable 0 of its source (same-level
-// cell, first of the 2x2x2 fine cells, or the coarse cell), and
-// info = kind | dst level << 2 | src level << 10 | upper-half bits << 18
+// One entry of the exchange plan (built once per mesh on the host).  Copies and
+// restrictions (pass 1): one ghost cell -- the element of variable 0 of the ghost cell and
+// of its source (same-level cell, or the first of the 2x2x2 fine cells).  Prolongations
+// (pass 2): one coarse cell and a fine block -- the coarse element, and the element of the
+// fine child with the lower half in every direction (it may itself lie outside the
+// ghost zone); bits 18..25 of info mark the children (x | y << 1 | z << 2) that are ghost
+// cells of that block.  info = kind | dst level << 2 | src level << 10 | ...
 // (kind 0 copy, 1 restriction, 2 prolongation).
 struct ak_xfer {
   long long dst, src;

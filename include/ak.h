@@ -138,7 +138,10 @@ ak_status ak_mesh_bind(ak_mesh* mesh, int32_t reg, double* dev_ptr);
  * 2x2x2 cells of a finer neighbour, or prolonged from a coarser neighbour (coarse value
  * plus minmod-limited slopes of the conserved variables, +-1/4 of a coarse slope per
  * direction; done after the copies and restrictions).  One launch per pass covers all
- * blocks.  Edge and corner ghosts are filled too. */
+ * blocks.  Edge and corner ghosts are filled too.
+ * On a uniform mesh (one level) without FOFC the stage kernels read halo cells straight
+ * from the neighbouring blocks' interiors, so ak_stage needs no filled ghost cells there
+ * and ak_step does not fill them; this call still fills them (e.g. for output). */
 ak_status ak_fill_ghosts(ak_mesh* mesh, int32_t reg);
 
 /* One RK stage s in [1, rk] with time step dt (Section 3); dt <= 0 uses the

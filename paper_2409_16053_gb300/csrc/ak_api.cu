@@ -415,6 +415,7 @@ extern "C" ak_status ak_mesh_create(const ak_mesh_desc* d, void* cuda_stream, ak
   m->md.nxa = (long long)xa.size();
   m->md.nxb = (long long)xb.size();
   m->md.cell_off = m->d_pack_off;
+  m->md.direct = !m->multilevel && !d->fofc;
   if (d->fofc) {
     // flagged cells are rare: a list of cells/64 entries (at least 65536)
     const long long cap = std::max(65536ll, m->interior_cells / 64);
@@ -659,7 +660,7 @@ extern "C" ak_status ak_new_dt(ak_mesh* m, int32_t reg, double* dt_out) {
 static ak_status enqueue_step(ak_mesh* m) {
   for (int st = 1; st <= m->desc.rk; ++st) {
     double* in = m->reg[stage_in_reg(m->desc.rk, st)];
-    AK_CUDA_TRY(ak_launch_fill_ghosts(m, in));
+    if (!m->md.direct) AK_CUDA_TRY(ak_launch_fill_ghosts(m, in));
     if (m->nfc) AK_CUDA_TRY(ak_launch_flux_correction(m, in));
     ak_status s = enqueue_stage(m, st);
     if (s != AK_OK) return s;

@@ -88,6 +88,8 @@ struct ak_meshdev {
   int4* flist;          // FOFC: flagged cells (block, i, j, k) of the current stage
   int fcap;             // capacity of flist
   int fofc;             // FOFC on
+  int direct;           // stage kernels read halo cells from the neighbour blocks (uniform
+                        // meshes without FOFC): no ghost fill before a stage
   int nblocks, nlev, ng, nfc;
   double gamma;
 };

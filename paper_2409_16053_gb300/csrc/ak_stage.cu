@@ -73,11 +73,14 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
   R* f1 = e1hi + C::EB;                      // [5][TY][TX+1]
   R* f2 = f1 + C::F1;                        // [5][TY+1][TX]
   __shared__ double red[NT / 32];
+  __shared__ long long nbr[27];  // direct halo reads: the neighbour blocks
 
   const int tid = threadIdx.x;
   // this CTA's column tile of one MeshBlock, and that block's geometry
   const ak_work w = work[blockIdx.x];
   const ak_block g = md.blocks[w.block];
+  if (md.direct) neighbour_table(md, w.block, nbr);
+  __syncthreads();
   const int blk = w.block;
   const int i0 = w.i0, j0 = w.j0, k0 = w.k0, k1 = w.k1;
   int kcur = k0;  // the plane whose x1/x2 faces are being solved
@@ -117,9 +120,13 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
         cross_xy(c, x, y);
         const int ip = i0 + x, jp = j0 + y;  // padded indices (halo starts at i0 - NG)
         if (ip < g.p1 && jp < g.p2) {
-          const long long e = ((long long)(kp + NG) * g.p2 + jp) * g.s1 + ip;
+          const bool halo = ip < NG || ip >= NG + g.nx1 || jp < NG || jp >= NG + g.nx2 ||
+                            kp < 0 || kp >= g.nx3;
+          const double* src = (md.direct && halo)
+                                  ? uin + halo_elem(g, nbr, NG, ip, jp, kp)
+                                  : ub + ((long long)(kp + NG) * g.p2 + jp) * g.s1 + ip;
 #pragma unroll
-          for (int v = 0; v < 5; ++v) u[m][v] = ub[e + v * g.var_stride];
+          for (int v = 0; v < 5; ++v) u[m][v] = src[v * g.var_stride];
           pos[m] = y * WX + x;
         }
       }

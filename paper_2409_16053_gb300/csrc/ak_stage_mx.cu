@@ -76,10 +76,12 @@ __global__ void __launch_bounds__(MxCfg<NG, T>::NTH, 2)
   float* f1 = e2hi + 5 * NE;                                    // [5][NF]
   float* f2 = f1 + 5 * NF;
   __shared__ double red[C::NTH / 32];
+  __shared__ long long nbr[27];  // direct halo reads: the neighbour blocks
 
   const int tid = threadIdx.x;
   const ak_work w = work[blockIdx.x];
   const ak_block g = md.blocks[w.block];
+  if (md.direct) neighbour_table(md, w.block, nbr);
   const int i0 = w.i0, j0 = w.j0, k0 = w.k0, k1 = w.k1;
   const double* ub = uin + g.off;
   const Counters cn{&sc->counters[0], &sc->counters[1]};
@@ -134,7 +136,9 @@ __global__ void __launch_bounds__(MxCfg<NG, T>::NTH, 2)
   constexpr int HALOC = TX / 2;                       // chunks of an x2 halo row
   constexpr int CPV = C::TY * FULLC + 2 * NG * HALOC;  // chunks per variable
   constexpr int NSC = (5 * CPV + C::NTH - 1) / C::NTH;
-  int sc_s[NSC], sc_g[NSC];  // shared element index (-1: none), element offset at plane 0
+  // shared element index (-1: none) with, for direct halo reads, the x/y neighbour
+  // (dx + 1) + 3 (dy + 1) in bits 16..19; element offset at plane 0 in the source block
+  int sc_s[NSC], sc_g[NSC];
 #pragma unroll
   for (int m = 0; m < NSC; ++m) {
     const int q = tid + C::NTH * m;
@@ -155,18 +159,32 @@ __global__ void __launch_bounds__(MxCfg<NG, T>::NTH, 2)
         c = y < NG ? y * TX + (x - NG)
                    : NG * TX + C::TY * (TX + 2 * NG) + (y - NG - C::TY) * TX + (x - NG);
       }
-      const int ip = i0 + x, jp = j0 + y;
+      int ip = i0 + x, jp = j0 + y;
       if (ip < g.p1 && jp < g.p2) {
-        sc_s[m] = v * NCROSS + c;
+        int code = 4;
+        if (md.direct) {  // a halo chunk comes from the x/y neighbour block
+          const int dx = ip < NG ? -1 : (ip >= NG + g.nx1 ? 1 : 0);
+          const int dy = jp < NG ? -1 : (jp >= NG + g.nx2 ? 1 : 0);
+          ip -= dx * g.nx1;
+          jp -= dy * g.nx2;
+          code = (dx + 1) + 3 * (dy + 1);
+        }
+        sc_s[m] = (v * NCROSS + c) | (code << 16);
         sc_g[m] = v * (int)vst + (NG * g.p2 + jp) * g.s1 + ip;
       }
     }
   }
   auto stage_plane = [&](int kp) {
-    const long long po = (long long)kp * pst;
+    // direct halo reads: ghost planes come from the x3 neighbour blocks
+    const int dz = md.direct ? (kp < 0 ? -1 : (kp >= g.nx3 ? 1 : 0)) : 0;
+    const long long po = (long long)(kp - dz * g.nx3) * pst;
 #pragma unroll
-    for (int m = 0; m < NSC; ++m)
-      if (sc_s[m] >= 0) cp_async16(&stg[sc_s[m]], ub + sc_g[m] + po);
+    for (int m = 0; m < NSC; ++m) {
+      if (sc_s[m] >= 0) {
+        const long long base = md.direct ? nbr[(sc_s[m] >> 16) + 9 * (dz + 1)] : g.off;
+        cp_async16(&stg[sc_s[m] & 0xffff], uin + base + sc_g[m] + po);
+      }
+    }
   };
   // The columns' U_in and U0: NOWN / 2 chunks (two cells of a tile row) per variable.
   static_assert(NOWN % 2 == 0 && (NOWN / 2) % 32 == 0, "chunk rows per warp");
@@ -197,7 +215,12 @@ __global__ void __launch_bounds__(MxCfg<NG, T>::NTH, 2)
     for (int m = 0; m < NMY; ++m) {
       if (mypos[m] >= 0) {
         const int x = mypos[m] % WX, y = mypos[m] / WX;  // padded (i0 + x, j0 + y)
-        const double* src = ub + ((long long)(kp + NG) * g.p2 + j0 + y) * g.s1 + i0 + x;
+        const int ip = i0 + x, jp = j0 + y;
+        const bool halo = ip < NG || ip >= NG + g.nx1 || jp < NG || jp >= NG + g.nx2 || kp < 0 ||
+                          kp >= g.nx3;
+        const double* src = (md.direct && halo)
+                                ? uin + halo_elem(g, nbr, NG, ip, jp, kp)
+                                : ub + ((long long)(kp + NG) * g.p2 + jp) * g.s1 + ip;
         double u[5];
         float wv[5];
 #pragma unroll
@@ -240,6 +263,7 @@ __global__ void __launch_bounds__(MxCfg<NG, T>::NTH, 2)
 
   // ---- prologue: plane k0+NG staged, planes k0-NG .. k0+NG-1 loaded and converted, the
   //      upper x3 edge of cell k0-1 -----------------------------------------------------
+  __syncthreads();  // the neighbour table
   stage_plane(k0 + NG);
   cp_async_commit();
   for (int kp = k0 - NG; kp < k0 + NG; ++kp) load_plane(kp);

@@ -90,6 +90,21 @@ def linear_wave_l1(ak, precision, n=32):
     return float(np.sqrt(sum(np.mean(np.abs(U[k] - U0[k])) ** 2 for k in range(5))))
 
 
+def max_over_ranks(dist, v, device="cuda"):
+    """The slowest rank's time: the job's time (v itself without a process group)."""
+    if not dist:
+        return v
+    import torch
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(ws, cells_per_rank, steps, t_ms):
+    """Whole-job cell-updates/s: every rank advances its own replica (weak scaling)."""
+    return ws * cells_per_rank * steps / (t_ms * 1e-3)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -495,11 +510,7 @@ def main():
         dist.barrier()
 
     def tmax(v):
-        if not dist:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks(dist, v)
 
     smr = None
     if rank == 0:
@@ -510,8 +521,8 @@ def main():
     t64 = tmax(r64["total_ms"])
     tmx = tmax(rmx["total_ms"])
     cells = ROOT_NX[0] * ROOT_NX[1] * ROOT_NX[2]
-    value64 = ws * cells * args.steps / (t64 * 1e-3)
-    valuemx = ws * cells * args.steps / (tmx * 1e-3)
+    value64 = job_rate(ws, cells, args.steps, t64)
+    valuemx = job_rate(ws, cells, args.steps, tmx)
 
     e2e = e2e_form(ak, torch, ak.AK_FP64, U0, max(2, args.steps // 2)) if rank == 0 else None
     e2e_mx = e2e_form(ak, torch, ak.AK_MIXED, U0, max(2, args.steps // 2)) if rank == 0 else None

@@ -12,6 +12,8 @@ Parity status of each function (what pins it, see tests/test_oracle_*.py):
   cons_to_prim / prim_to_cons   round trip; Section 3.1 Eq. (4) closed forms
   plm_slope                     linear data, extrema, translation invariance
   ppm4_edges                    parabola reproduction, monotonicity
+  ppmx_edges                    cubic / smooth-extremum reproduction, spike and step
+                                cases by hand, mirror symmetry, 1D wave convergence
   hllc                          supersonic upwinding, stationary contact, symmetry,
                                 consistency, entropy-wave/sound-wave convergence
   rhs / rk_step                 2nd-order sound and entropy wave convergence,
@@ -41,6 +43,7 @@ _lib = None
 PLM = 0
 PPM4 = 1
 WENOZ = 2
+PPMX = 3
 HLLC = 0
 HLLE = 1
 LLF = 2
@@ -92,6 +95,7 @@ def _load():
             lib.orc_plm_slope.restype = ctypes.c_double
             lib.orc_ppm4_edges.argtypes = [_dp, _dp, _dp]
             lib.orc_wenoz_edges.argtypes = [_dp, _dp, _dp]
+            lib.orc_ppmx_edges.argtypes = [_dp, _dp, _dp]
             lib.orc_hllc.argtypes = [_dp, _dp, ctypes.c_double, _dp]
             lib.orc_hlle.argtypes = [_dp, _dp, ctypes.c_double, _dp]
             lib.orc_llf.argtypes = [_dp, _dp, ctypes.c_double, _dp]
@@ -188,6 +192,14 @@ def ppm4_edges(q5):
     q = np.ascontiguousarray(q5, dtype=np.float64)
     lo, hi = ctypes.c_double(), ctypes.c_double()
     _load().orc_ppm4_edges(_ptr(q), ctypes.byref(lo), ctypes.byref(hi))
+    return lo.value, hi.value
+
+
+def ppmx_edges(q5):
+    """PPMX (extremum-preserving PPM) edge values of the middle cell of q5."""
+    q = np.ascontiguousarray(q5, dtype=np.float64)
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    _load().orc_ppmx_edges(_ptr(q), ctypes.byref(lo), ctypes.byref(hi))
     return lo.value, hi.value
 
 

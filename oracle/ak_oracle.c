@@ -22,6 +22,11 @@
  *   - PLM limiter: van Leer harmonic mean of the one-sided differences.
  *   - PPM4: Colella & Woodward (1984) uniform-grid interface values and limiter,
  *     no flattening, no contact steepening.
+ *   - PPMX: the fourth-order interface values of PPM with the extremum-preserving
+ *     interface limiter of Colella & Sekora (2008) and the cell limiter of
+ *     McCorquodale & Colella (2011), curvature constant C = 1.25, on the five-cell
+ *     stencil (3 ghost cells): the third-derivative smoothness test of the latter,
+ *     which needs seven cells, is not applied.
  *   - WENO-Z: Borges, Carmona, Costa & Don (2008): the three third-order candidate
  *     interface values of Jiang & Shu (1996) with their smoothness indicators, weights
  *     alpha_k = d_k (1 + tau5 / (beta_k + eps)), tau5 = |beta_0 - beta_2|, ideal weights
@@ -54,6 +59,7 @@
 #define ORC_PLM 0
 #define ORC_PPM4 1
 #define ORC_WENOZ 2
+#define ORC_PPMX 3
 
 #define ORC_HLLC 0
 #define ORC_HLLE 1
@@ -63,7 +69,7 @@ typedef struct {
   int64_t n[3];     /* cells per dimension of the periodic grid */
   double dx[3];     /* uniform cell widths (Section 2: uniform Cartesian only) */
   double gamma;     /* ratio of specific heats of the gamma-law EOS */
-  int32_t recon;    /* ORC_PLM or ORC_PPM4 */
+  int32_t recon;    /* ORC_PLM, ORC_PPM4, ORC_WENOZ or ORC_PPMX */
   int32_t riemann;  /* ORC_HLLC, ORC_HLLE or ORC_LLF */
   int32_t fofc;     /* 1: first-order flux correction in every RK stage */
   int32_t pad;
@@ -164,6 +170,85 @@ void orc_ppm4_edges(const double q[5], double* qlo, double* qhi) {
     } else if (-da * da > da * a6) {
       ahi = 3.0 * a - 2.0 * alo;
     }
+  }
+  *qlo = alo;
+  *qhi = ahi;
+}
+
+/* ---------------------------------------------------------------------------------
+ * PPMX (Section 3: PPM with extremum-preserving limiters).  Given q(i-2..i+2) returns
+ * the left (x_{i-1/2}) and right (x_{i+1/2}) edge values of cell i.
+ * ------------------------------------------------------------------------------- */
+#define PPMX_C 1.25
+
+static int ppmx_same_sign3(double x, double y, double z) {
+  return (x > 0.0 && y > 0.0 && z > 0.0) || (x < 0.0 && y < 0.0 && z < 0.0);
+}
+
+/* Interface value between cells b and c of the four cells a, b, c, d.  The fourth-order
+ * value; if it does not lie between b and c, its second difference is limited by those
+ * of the neighbouring cells (Colella & Sekora 2008). */
+static double ppmx_interface(double a, double b, double c, double d) {
+  double f = 7.0 / 12.0 * (b + c) - 1.0 / 12.0 * (a + d);
+  if ((f - b) * (c - f) < 0.0) {
+    double d2 = 3.0 * ((b + c) - 2.0 * f); /* the interface's own second difference */
+    double d2l = (a + c) - 2.0 * b;        /* second difference of cell b */
+    double d2r = (b + d) - 2.0 * c;        /* second difference of cell c */
+    double lim = 0.0;
+    if (ppmx_same_sign3(d2, d2l, d2r)) {
+      double m = fabs(d2);
+      if (PPMX_C * fabs(d2l) < m) m = PPMX_C * fabs(d2l);
+      if (PPMX_C * fabs(d2r) < m) m = PPMX_C * fabs(d2r);
+      lim = d2 > 0.0 ? m : -m;
+    }
+    f = 0.5 * (b + c) - lim / 6.0;
+  }
+  return f;
+}
+
+void orc_ppmx_edges(const double q[5], double* qlo, double* qhi) {
+  /* q[0..4] = q(i-2), q(i-1), q(i), q(i+1), q(i+2) */
+  double alo = ppmx_interface(q[0], q[1], q[2], q[3]);
+  double ahi = ppmx_interface(q[1], q[2], q[3], q[4]);
+  double a = q[2];
+  double dp = ahi - a; /* rise of the parabola from the mean to the right edge */
+  double dm = a - alo; /* rise from the left edge to the mean */
+  if (dp * dm <= 0.0 || (q[3] - a) * (a - q[1]) <= 0.0) {
+    /* An extremum: of the parabola inside the cell, or of the cell means.  Compare
+     * the parabola's second derivative, 6 (a_lo + a_hi - 2 a), with the second
+     * differences of cells i-1, i, i+1 (McCorquodale & Colella 2011). */
+    double d2 = 6.0 * ((alo + ahi) - 2.0 * a);
+    double d2c = (q[1] + q[3]) - 2.0 * a;
+    double d2l = (q[0] + a) - 2.0 * q[1];
+    double d2r = (a + q[4]) - 2.0 * q[3];
+    double r = 0.0; /* ratio of the limited to the parabola's second derivative */
+    int limit = 1;
+    if (ppmx_same_sign3(d2, d2c, d2l) && ppmx_same_sign3(d2, d2c, d2r)) {
+      double m = PPMX_C * fabs(d2c);
+      if (PPMX_C * fabs(d2l) < m) m = PPMX_C * fabs(d2l);
+      if (PPMX_C * fabs(d2r) < m) m = PPMX_C * fabs(d2r);
+      if (m >= fabs(d2))
+        limit = 0; /* the curvature is consistent with the neighbours' */
+      else
+        r = m / fabs(d2);
+    }
+    if (limit) {
+      if (dp * dm < 0.0) {
+        /* extremum inside the cell: scale the curvature by r */
+        alo = a - r * dm;
+        ahi = a + r * dp;
+      } else if (fabs(dm) >= 2.0 * fabs(dp)) {
+        alo = a - 2.0 * (1.0 - r) * dp - r * dm;
+      } else if (fabs(dp) >= 2.0 * fabs(dm)) {
+        ahi = a + 2.0 * (1.0 - r) * dm + r * dp;
+      }
+    }
+  } else {
+    /* monotone: keep the parabola's extremum out of the cell (Colella & Woodward) */
+    if (fabs(dm) >= 2.0 * fabs(dp))
+      alo = a - 2.0 * dp;
+    else if (fabs(dp) >= 2.0 * fabs(dm))
+      ahi = a + 2.0 * dm;
   }
   *qlo = alo;
   *qhi = ahi;
@@ -378,6 +463,9 @@ static void face_states(const orc_grid* g, const double* W, int d, int64_t i, in
       if (g->recon == ORC_WENOZ) {
         orc_wenoz_edges(&s[0], &lo, &hi);  /* cell c - e_d, stencil c-3e..c+e */
         orc_wenoz_edges(&s[1], &lo2, &hi2); /* cell c, stencil c-2e..c+2e */
+      } else if (g->recon == ORC_PPMX) {
+        orc_ppmx_edges(&s[0], &lo, &hi);
+        orc_ppmx_edges(&s[1], &lo2, &hi2);
       } else {
         orc_ppm4_edges(&s[0], &lo, &hi);
         orc_ppm4_edges(&s[1], &lo2, &hi2);

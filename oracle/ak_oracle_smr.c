@@ -37,6 +37,7 @@ void orc_cons_to_prim(const double u[5], double w[5], int64_t* nfloor);
 double orc_plm_slope(double qm, double q0, double qp);
 void orc_ppm4_edges(const double q[5], double* qlo, double* qhi);
 void orc_wenoz_edges(const double q[5], double* qlo, double* qhi);
+void orc_ppmx_edges(const double q[5], double* qlo, double* qhi);
 void orc_riemann(int solver, const double wl[5], const double wr[5], double gamma,
                  double f[5]);
 
@@ -292,6 +293,9 @@ static void block_fluxes(const smr_index* x, int b, const double* U, double* F[3
               if (m->recon == 2) {
                 orc_wenoz_edges(&s[0], &lo, &hi);
                 orc_wenoz_edges(&s[1], &lo2, &hi2);
+              } else if (m->recon == 3) {
+                orc_ppmx_edges(&s[0], &lo, &hi);
+                orc_ppmx_edges(&s[1], &lo2, &hi2);
               } else {
                 orc_ppm4_edges(&s[0], &lo, &hi);
                 orc_ppm4_edges(&s[1], &lo2, &hi2);

@@ -226,7 +226,7 @@ def test_exact_riemann_fan_is_self_similar_isentrope():
 # ----------------------------------------------------------------------------------
 # Whole scheme: invariants.
 # ----------------------------------------------------------------------------------
-@pytest.mark.parametrize("recon", [oracle.PLM, oracle.PPM4])
+@pytest.mark.parametrize("recon", [oracle.PLM, oracle.PPM4, oracle.PPMX])
 def test_uniform_state_stays_bitwise_uniform(recon):
     g = oracle.Grid((8, 6, 5), recon=recon)
     U = pgen.uniform((8, 6, 5), rho=1.3, p=0.7, v=(0.4, -0.25, 0.6))
@@ -236,7 +236,7 @@ def test_uniform_state_stays_bitwise_uniform(recon):
     assert not np.any(L)
 
 
-@pytest.mark.parametrize("rk,recon", [(2, oracle.PLM), (3, oracle.PPM4)])
+@pytest.mark.parametrize("rk,recon", [(2, oracle.PLM), (3, oracle.PPM4), (3, oracle.PPMX)])
 def test_periodic_conservation_to_round_off(rk, recon):
     n = (16, 12, 8)
     g = oracle.Grid(n, recon=recon)
@@ -252,7 +252,7 @@ def test_periodic_conservation_to_round_off(rk, recon):
     assert np.max(np.abs(U1 - U)) > 1e-4
 
 
-@pytest.mark.parametrize("recon", [oracle.PLM, oracle.PPM4])
+@pytest.mark.parametrize("recon", [oracle.PLM, oracle.PPM4, oracle.PPMX])
 def test_shock_tube_bitwise_permutation_of_axes(recon):
     outs = []
     for d in range(3):
@@ -536,3 +536,95 @@ def test_wenoz_rk3_sound_wave_converges_faster_than_ppm4():
     w = errs[oracle.WENOZ]
     assert w[0] / w[1] > 8 and w[1] / w[2] > 8, w
     assert all(a < b for a, b in zip(w, errs[oracle.PPM4])), errs
+
+
+# ---------------------------------------------------------------------------------
+# PPMX reconstruction (extremum-preserving PPM)
+# ---------------------------------------------------------------------------------
+def _cubic_averages(c, cells):
+    """Cell averages over [i-1/2, i+1/2] of c0 + c1 x + c2 x^2 + c3 x^3."""
+    return [c[0] + c[1] * i + c[2] * (i * i + 1.0 / 12.0) + c[3] * (i ** 3 + 0.25 * i)
+            for i in cells]
+
+
+def test_ppmx_exact_for_monotone_cubic():
+    # the fourth-order interface value is exact for cubics; on monotone data no limiter
+    # acts, so both edges are the cubic's point values
+    rng = np.random.default_rng(8)
+    for _ in range(50):
+        c = [rng.normal(), 1.0 + rng.random(), 0.05 * rng.normal(), 0.05 * rng.normal()]
+        sgn = rng.choice([-1.0, 1.0])
+        c = [c[0], sgn * c[1], sgn * c[2], sgn * c[3]]
+        f = lambda x: c[0] + c[1] * x + c[2] * x * x + c[3] * x ** 3
+        lo, hi = oracle.ppmx_edges(_cubic_averages(c, range(-2, 3)))
+        sc = 1 + sum(abs(v) for v in c)
+        assert abs(lo - f(-0.5)) < 1e-14 * sc and abs(hi - f(0.5)) < 1e-14 * sc
+
+
+def test_ppmx_keeps_smooth_extremum_that_ppm4_clips():
+    # a parabola with its vertex in or next to the cell: every second difference is the
+    # same, so the limiters leave the exact edge values; PPM4 flattens the cell
+    rng = np.random.default_rng(9)
+    for _ in range(50):
+        s, c2, c0 = rng.uniform(-0.45, 0.45), rng.choice([-1, 1]) * rng.uniform(0.5, 2), rng.normal()
+        avg = [c0 + c2 * ((i - s) ** 2 + 1.0 / 12.0) for i in range(-2, 3)]
+        lo, hi = oracle.ppmx_edges(avg)
+        sc = 1 + abs(c0) + abs(c2)
+        assert abs(lo - (c0 + c2 * (-0.5 - s) ** 2)) < 1e-14 * sc
+        assert abs(hi - (c0 + c2 * (0.5 - s) ** 2)) < 1e-14 * sc
+        if abs(s) < 0.1:
+            lo4, hi4 = oracle.ppm4_edges(avg)
+            assert lo4 == hi4 == avg[2]
+
+
+def test_ppmx_spike_and_step_cases():
+    # an isolated spike: the neighbours' curvatures disagree in sign -> flat cell
+    assert oracle.ppmx_edges([0.0, 0.0, 1.0, 0.0, 0.0]) == (1.0, 1.0)
+    assert oracle.ppmx_edges([2.0, 2.0, -1.0, 2.0, 2.0]) == (-1.0, -1.0)
+    # the cells at the foot and the top of a step stay flat: no new extremum
+    assert oracle.ppmx_edges([0.0, 0.0, 0.0, 1.0, 1.0]) == (0.0, 0.0)
+    assert oracle.ppmx_edges([0.0, 0.0, 1.0, 1.0, 1.0]) == (1.0, 1.0)
+    # a cell inside a ramp next to a step keeps edges between its neighbours
+    lo, hi = oracle.ppmx_edges([0.0, 0.0, 0.5, 1.0, 1.0])
+    assert 0.0 <= lo <= 0.5 <= hi <= 1.0
+
+
+def test_ppmx_mirror_symmetry_and_limited_curvature():
+    rng = np.random.default_rng(10)
+    for _ in range(200):
+        q = rng.normal(size=5)
+        lo, hi = oracle.ppmx_edges(q)
+        lo_r, hi_r = oracle.ppmx_edges(q[::-1])
+        assert lo == hi_r and hi == lo_r
+    # valleys sharper in the middle cell than in its neighbours: where the cell keeps
+    # an interior extremum, the limited parabola's second derivative 6 (lo + hi - 2 q_i)
+    # is at most 1.25 x the smallest neighbour second difference, and equal to it when
+    # the limiter scaled it down (Colella & Sekora's limited curvature)
+    scaled = 0
+    for _ in range(400):
+        q = np.array([4.0, 1.0, 0.0, 1.0, 4.0]) + 0.3 * rng.normal(size=5)
+        q[2] -= rng.uniform(0.0, 1.5)
+        lo, hi = oracle.ppmx_edges(q)
+        d2 = [q[k - 1] - 2 * q[k] + q[k + 1] for k in (1, 2, 3)]
+        if (hi - q[2]) * (q[2] - lo) < 0 and all(v > 0 for v in d2):
+            curv = 6 * (lo + hi - 2 * q[2])
+            target = 1.25 * min(d2)
+            assert 0 < curv <= target * (1 + 1e-12), (q, curv, target)
+            scaled += math.isclose(curv, target, rel_tol=1e-12)
+    assert scaled > 50, scaled
+
+
+def test_ppmx_rk3_sound_wave_fourth_order():
+    # Section 3.1: PPMX converges at fourth order on 1D linear waves (PPM4 at second)
+    errs = {}
+    for recon in (oracle.PPM4, oracle.PPMX):
+        e = []
+        for n in (16, 32, 64):
+            U0, T = pgen.linear_wave((n, 1, 1))
+            U, _, _, nf = oracle.run(U0, oracle.Grid((n, 1, 1), recon=recon), 0.3, t_end=T, rk=3)
+            assert nf == 0
+            e.append(l1_wave_error(U, U0))
+        errs[recon] = e
+    x = errs[oracle.PPMX]
+    assert x[0] / x[1] > 12 and x[1] / x[2] > 12, x
+    assert all(a < 0.1 * b for a, b in zip(x, errs[oracle.PPM4])), errs

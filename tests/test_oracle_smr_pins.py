@@ -93,12 +93,14 @@ def test_composite_conservation_and_negative_control():
     assert res[False].max() > 1e-7, res[False]
 
 
-@pytest.mark.parametrize("riemann", [oracle.HLLC, oracle.HLLE, oracle.LLF])
-def test_single_level_equals_uniform_oracle(riemann):
+@pytest.mark.parametrize("riemann,recon", [
+    (oracle.HLLC, oracle.PLM), (oracle.HLLE, oracle.PLM), (oracle.LLF, oracle.PLM),
+    (oracle.HLLC, oracle.PPMX), (oracle.HLLC, oracle.WENOZ)])
+def test_single_level_equals_uniform_oracle(riemann, recon):
     # every block on level 0: the SMR oracle must reproduce the uniform-grid oracle
     t = pgen.nested_refinement_blocks(16, 8, 8, 0)
     P = _smooth_blocks(t, 16)
-    m = oracle.SmrMesh(t, (16, 16, 16), riemann=riemann)
+    m = oracle.SmrMesh(t, (16, 16, 16), riemann=riemann, recon=recon)
     U = m.from_packed(P)
     # global array from the blocks
     G = np.zeros((5, 16, 16, 16))
@@ -106,7 +108,7 @@ def test_single_level_equals_uniform_oracle(riemann):
     for b, r in enumerate(t):
         G[:, r[3]:r[3] + 8, r[2]:r[2] + 8, r[1]:r[1] + 8] = P[o:o + 5 * 512].reshape(5, 8, 8, 8)
         o += 5 * 512
-    grid = oracle.Grid((16, 16, 16), riemann=riemann)
+    grid = oracle.Grid((16, 16, 16), riemann=riemann, recon=recon)
     dt = oracle.new_dt(G, grid, 0.3)
     assert dt == m.new_dt(U, 0.3)
     Gn, _ = oracle.rk_step(G, grid, dt, 2)

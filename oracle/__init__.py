@@ -76,7 +76,7 @@ class _Smr(ctypes.Structure):
                 ("blocks", ctypes.POINTER(ctypes.c_int32)),
                 ("root_nx", ctypes.c_int32 * 3), ("length", ctypes.c_double * 3),
                 ("gamma", ctypes.c_double), ("riemann", ctypes.c_int32),
-                ("pad", ctypes.c_int32)]
+                ("fofc", ctypes.c_int32)]
 
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -121,6 +121,8 @@ def _load():
             lib.orc_smr_rhs.restype = ctypes.c_int64
             lib.orc_smr_rk_step.argtypes = [S, _dp, ctypes.c_double, ctypes.c_int]
             lib.orc_smr_rk_step.restype = ctypes.c_int64
+            lib.orc_smr_rk_step_fofc.argtypes = [S, _dp, ctypes.c_double, ctypes.c_int, _i64p]
+            lib.orc_smr_rk_step_fofc.restype = ctypes.c_int64
             lib.orc_smr_new_dt.argtypes = [S, _dp, ctypes.c_double]
             lib.orc_smr_new_dt.restype = ctypes.c_double
             lib.orc_prolong.argtypes = [ctypes.c_double, _dp, _dp, ctypes.POINTER(ctypes.c_int)]
@@ -339,7 +341,7 @@ class SmrMesh:
     periodic box; storage = padded arrays block after block (see ak_oracle_smr.c)."""
 
     def __init__(self, table, root_nx, length=(1.0, 1.0, 1.0), gamma=5.0 / 3.0,
-                 recon=PLM, flux_correction=True, riemann=HLLC):
+                 recon=PLM, flux_correction=True, riemann=HLLC, fofc=False):
         self.table = np.ascontiguousarray(np.asarray(table, dtype=np.int32))
         self.root_nx = tuple(int(v) for v in root_nx)
         self.length = tuple(float(v) for v in length)
@@ -357,6 +359,7 @@ class SmrMesh:
             c.length[d] = self.length[d]
         c.gamma = self.gamma
         c.riemann = int(riemann)
+        c.fofc = 1 if fofc else 0
         self._c = c
         g = self.ng
         self.shapes = [(5, r[6] + 2 * g, r[5] + 2 * g, r[4] + 2 * g) for r in self.table]
@@ -402,6 +405,16 @@ class SmrMesh:
         if _load().orc_smr_rk_step(self._ref(), _ptr(Un), float(dt), int(rk)) != 0:
             raise ValueError("inconsistent SMR mesh")
         return Un
+
+    def rk_step_fofc(self, U, dt, rk=2):
+        """One RK step with FOFC (the mesh must be built with fofc=True); returns the new
+        state and the number of flagged cells summed over the stages."""
+        Un = np.array(U, dtype=np.float64, copy=True)
+        n = ctypes.c_int64(0)
+        if _load().orc_smr_rk_step_fofc(self._ref(), _ptr(Un), float(dt), int(rk),
+                                        ctypes.byref(n)) != 0:
+            raise ValueError("inconsistent SMR mesh")
+        return Un, int(n.value)
 
     def new_dt(self, U, cfl):
         return float(_load().orc_smr_new_dt(self._ref(), _ptr(U), float(cfl)))

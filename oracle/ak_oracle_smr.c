@@ -16,7 +16,13 @@
  *   - flux correction: on a coarse face whose neighbour region is refined, the coarse
  *     flux is replaced by the mean of the 2x2 fine fluxes computed by the fine block
  *     on the same face (before the coarse update, so the update is conservative);
- *   - one global dt: min over all leaves of CFL dx_l / (|v| + c_s).
+ *   - one global dt: min over all leaves of CFL dx_l / (|v| + c_s);
+ *   - FOFC (Section 3: applied before the level flux correction): a face of a leaf
+ *     takes the LLF flux of the piecewise-constant states when the cell on either
+ *     side is flagged; a ghost cell carries the flag of the same-level or coarser leaf
+ *     cell it lies in, so a fine face at a level boundary turns first-order when the
+ *     fine cell or the coarse cell across is flagged.  The coarse side of such a face
+ *     then takes the mean of the fine fluxes, as without FOFC.
  * Ghost zones are filled in two passes: same-level copies and restrictions first, then
  * prolongations level by level from coarse to fine, so that every coarse value a
  * prolongation reads (including coarse ghost cells) is already final.
@@ -48,7 +54,7 @@ typedef struct {
   double length[3]; /* domain side lengths */
   double gamma;
   int32_t riemann;   /* 0 HLLC, 1 HLLE, 2 LLF */
-  int32_t pad;
+  int32_t fofc;      /* 1: first-order flux correction in every RK stage */
 } orc_smr;
 
 typedef struct {
@@ -80,7 +86,10 @@ static int64_t wrapl(int64_t i, int64_t n) {
   return r < 0 ? r + n : r;
 }
 
-/* builds the leaf maps; returns 0 or -1 on an inconsistent mesh */
+static int leaf_at(const smr_index* x, int l, const int64_t G[3]);
+
+/* builds the leaf maps; returns 0 or -1 on an inconsistent mesh (blocks of one level of
+ * different sizes, two leaves in one slot, or a leaf overlapping a coarser one) */
 static int index_build(const orc_smr* m, smr_index* x) {
   memset(x, 0, sizeof(*x));
   x->m = m;
@@ -119,7 +128,21 @@ static int index_build(const orc_smr* m, smr_index* x) {
     int64_t c[3];
     for (int d = 0; d < 3; ++d) c[d] = e[1 + d] / x->bs[3 * l + d];
     int64_t id = x->mapoff[l] + (c[2] * x->mapdim[3 * l + 1] + c[1]) * x->mapdim[3 * l] + c[0];
+    if (x->map[id] >= 0) return -1; /* two leaves in one slot */
     x->map[id] = b;
+  }
+  /* leaves must not overlap: no cell of a leaf lies in a leaf of a coarser level */
+  for (int b = 0; b < m->nblocks; ++b) {
+    const int32_t* e = m->blocks + 7 * b;
+    for (int l = e[0] - 1; l >= 0; --l) {
+      int sh = e[0] - l;
+      for (int64_t k = e[3]; k < e[3] + e[6]; ++k)
+        for (int64_t j = e[2]; j < e[2] + e[5]; ++j)
+          for (int64_t i = e[1]; i < e[1] + e[4]; ++i) {
+            int64_t G[3] = {i >> sh, j >> sh, k >> sh};
+            if (x->bs[3 * l] && leaf_at(x, l, G) >= 0) return -1;
+          }
+    }
   }
   return 0;
 }
@@ -256,7 +279,8 @@ int orc_smr_fill_ghosts(const orc_smr* m, double* U) {
 
 /* Face fluxes of one block: F[d] has (n_d + 1) faces along d, full extent in the other
  * directions, layout [v][k][j][i] with the face index along d. */
-static void block_fluxes(const smr_index* x, int b, const double* U, double* F[3]) {
+static void block_fluxes(const smr_index* x, int b, const double* U, double* F[3],
+                         const unsigned char* flag) {
   const orc_smr* m = x->m;
   const int32_t* e = m->blocks + 7 * b;
   int g = m->ng;
@@ -281,6 +305,19 @@ static void block_fluxes(const smr_index* x, int b, const double* U, double* F[3
           /* face below cell (i,j,k) along d */
           int64_t c0 = ((int64_t)(k + g) * p2 + j + g) * p1 + i + g;
           double wl[5], wr[5], f[5];
+          const unsigned char* fb = flag ? flag + x->off[b] / NV : NULL;
+          if (fb && (fb[c0 - st[d]] || fb[c0])) {
+            /* FOFC: LLF flux of the two cells' own states */
+            for (int q = 0; q < NV; ++q) {
+              wl[q] = W[(int64_t)perm[q] * np + c0 - st[d]];
+              wr[q] = W[(int64_t)perm[q] * np + c0];
+            }
+            orc_riemann(2, wl, wr, m->gamma, f);
+            int64_t fi = ((int64_t)k * n[1] + j) * n[0] + i;
+            int64_t fn = (int64_t)n[0] * n[1] * n[2];
+            for (int q = 0; q < NV; ++q) F[d][(int64_t)perm[q] * fn + fi] = f[q];
+            continue;
+          }
           for (int q = 0; q < NV; ++q) {
             const double* w = W + (int64_t)perm[q] * np;
             if (m->recon == 0) {
@@ -313,9 +350,41 @@ static void block_fluxes(const smr_index* x, int b, const double* U, double* F[3
   free(W);
 }
 
+/* FOFC flags of the ghost cells of every leaf: the flag of the same-level leaf cell, or
+ * of the coarser leaf cell, the ghost cell lies in; 0 over a finer region (those ghost
+ * cells only border level-boundary faces, whose coarse flux the fine mean replaces).
+ * flag: one byte per padded cell, block b from off[b] / NV. */
+static void fill_flag_ghosts(const smr_index* x, unsigned char* flag) {
+  const orc_smr* m = x->m;
+  int g = m->ng;
+  for (int b = 0; b < m->nblocks; ++b) {
+    const int32_t* e = m->blocks + 7 * b;
+    int l = e[0];
+    int64_t p1 = e[4] + 2 * g, p2 = e[5] + 2 * g;
+    for (int k = -g; k < e[6] + g; ++k)
+      for (int j = -g; j < e[5] + g; ++j)
+        for (int i = -g; i < e[4] + g; ++i) {
+          if (i >= 0 && i < e[4] && j >= 0 && j < e[5] && k >= 0 && k < e[6]) continue;
+          int64_t G[3] = {e[1] + i, e[2] + j, e[3] + k};
+          for (int d = 0; d < 3; ++d) G[d] = wrapl(G[d], lvl_n(m, l, d));
+          unsigned char f = 0;
+          int same = leaf_at(x, l, G);
+          if (same >= 0) {
+            f = flag[x->off[same] / NV + (elem(x, same, 0, G) - x->off[same])];
+          } else {
+            int64_t C[3] = {G[0] >> 1, G[1] >> 1, G[2] >> 1};
+            int coarse = leaf_at(x, l - 1, C);
+            if (coarse >= 0) f = flag[x->off[coarse] / NV + (elem(x, coarse, 0, C) - x->off[coarse])];
+          }
+          flag[x->off[b] / NV + ((int64_t)(k + g) * p2 + j + g) * p1 + i + g] = f;
+        }
+  }
+}
+
 /* L(U) for every leaf (interior cells, layout of U; ghost entries of L are zero).
- * Returns the floors applied. */
-int64_t orc_smr_rhs(const orc_smr* m, const double* U, double* L) {
+ * flag != NULL: FOFC flags (ghosts filled) select first-order LLF faces. */
+static int64_t smr_rhs_impl(const orc_smr* m, const double* U, double* L,
+                            const unsigned char* flag) {
   smr_index x;
   if (index_build(m, &x) != 0) {
     index_free(&x);
@@ -331,7 +400,7 @@ int64_t orc_smr_rhs(const orc_smr* m, const double* U, double* L) {
     }
   }
 #pragma omp parallel for schedule(dynamic)
-  for (int b = 0; b < m->nblocks; ++b) block_fluxes(&x, b, U, &Fb[3 * b]);
+  for (int b = 0; b < m->nblocks; ++b) block_fluxes(&x, b, U, &Fb[3 * b], flag);
 
   /* flux correction: coarse faces next to a refined region take the fine mean */
   if (m->flux_correction) {
@@ -414,9 +483,17 @@ int64_t orc_smr_rhs(const orc_smr* m, const double* U, double* L) {
   return 0;
 }
 
+int64_t orc_smr_rhs(const orc_smr* m, const double* U, double* L) {
+  return smr_rhs_impl(m, U, L, NULL);
+}
+
 /* One SSP-RK step of every leaf with one dt: ghost fill, then U <- a U0 + b (U + dt L)
- * on interior cells, for each stage. */
-int64_t orc_smr_rk_step(const orc_smr* m, double* U, double dt, int rk) {
+ * on interior cells, for each stage.  With m->fofc, each stage first makes the update
+ * tentatively, flags the cells whose density or internal energy would not be positive,
+ * and recomputes L with first-order LLF faces around them; *nfofc (if given) receives
+ * the number of flagged cells summed over the stages. */
+int64_t orc_smr_rk_step_fofc(const orc_smr* m, double* U, double dt, int rk,
+                             int64_t* nfofc) {
   static const double a2[2] = {0.0, 0.5}, b2[2] = {1.0, 0.5};
   static const double a3[3] = {0.0, 0.75, 1.0 / 3.0}, b3[3] = {1.0, 0.25, 2.0 / 3.0};
   const double* a = rk == 3 ? a3 : a2;
@@ -425,14 +502,47 @@ int64_t orc_smr_rk_step(const orc_smr* m, double* U, double dt, int rk) {
   int64_t n = orc_smr_storage(m);
   double* U0 = (double*)malloc(sizeof(double) * n);
   double* L = (double*)malloc(sizeof(double) * n);
+  unsigned char* flag = m->fofc ? (unsigned char*)calloc(n / NV, 1) : NULL;
   memcpy(U0, U, sizeof(double) * n);
-  int64_t rc = 0;
+  int64_t rc = 0, nflag = 0;
+  smr_index x;
+  if (index_build(m, &x) != 0) rc = -1;
+  int g = m->ng;
   for (int s = 0; s < ns && rc == 0; ++s) {
-    if (orc_smr_fill_ghosts(m, U) != 0 || orc_smr_rhs(m, U, L) != 0) {
+    if (orc_smr_fill_ghosts(m, U) != 0 || smr_rhs_impl(m, U, L, NULL) != 0) {
       rc = -1;
       break;
     }
-    int g = m->ng;
+    if (m->fofc) {
+      int64_t nst = 0;
+      memset(flag, 0, n / NV);
+      for (int b = 0; b < m->nblocks; ++b) {
+        const int32_t* e = m->blocks + 7 * b;
+        int64_t p1 = e[4] + 2 * g, p2 = e[5] + 2 * g, p3 = e[6] + 2 * g, np = p1 * p2 * p3;
+        for (int k = 0; k < e[6]; ++k)
+          for (int j = 0; j < e[5]; ++j)
+            for (int i = 0; i < e[4]; ++i) {
+              int64_t c = ((int64_t)(k + g) * p2 + j + g) * p1 + i + g;
+              double u[5];
+              for (int v = 0; v < NV; ++v) {
+                int64_t cv = x.off[b] + v * np + c;
+                u[v] = a[s] * U0[cv] + bb[s] * (U[cv] + dt * L[cv]);
+              }
+              double ug = u[4] - 0.5 * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) / u[0];
+              unsigned char f = !(u[0] > 0.0) || !(ug > 0.0);
+              flag[x.off[b] / NV + c] = f;
+              nst += f;
+            }
+      }
+      if (nst) {
+        nflag += nst;
+        fill_flag_ghosts(&x, flag);
+        if (smr_rhs_impl(m, U, L, flag) != 0) {
+          rc = -1;
+          break;
+        }
+      }
+    }
     int64_t o = 0;
     for (int b = 0; b < m->nblocks; ++b) {
       const int32_t* e = m->blocks + 7 * b;
@@ -447,9 +557,16 @@ int64_t orc_smr_rk_step(const orc_smr* m, double* U, double dt, int rk) {
       o += block_elems(m, b);
     }
   }
+  index_free(&x);
   free(U0);
   free(L);
+  free(flag);
+  if (nfofc) *nfofc = nflag;
   return rc;
+}
+
+int64_t orc_smr_rk_step(const orc_smr* m, double* U, double dt, int rk) {
+  return orc_smr_rk_step_fofc(m, U, dt, rk, NULL);
 }
 
 /* Global CFL dt over every leaf's interior (Section 3 Eq. (3), uniform across levels). */

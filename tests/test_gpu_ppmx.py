@@ -1,0 +1,133 @@
+"""PPMX (extremum-preserving PPM) on the GPU against the oracle: FP64 parity after one
+RK3 step (uniform and refined meshes, HLLC and HLLE), after 100 steps, on a shock tube,
+the mixed form within its tolerance, and the sound-wave L1 of the mixed form within 1%
+of the FP64 one."""
+import numpy as np
+import pytest
+
+import oracle
+import pgen
+from _helpers import l1_wave_error, max_norm_diff
+
+pytestmark = pytest.mark.gpu
+G53 = 5.0 / 3.0
+
+
+@pytest.fixture(scope="module")
+def ak():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_2409_16053_gb300 import build
+    build.build()
+    from paper_2409_16053_gb300 import ak as mod
+    oracle.build()
+    return mod
+
+
+@pytest.mark.parametrize("rs,ors", [(0, oracle.HLLC), (1, oracle.HLLE)])
+def test_fp64_one_step_parity(ak, rs, ors):
+    root, block = (36, 24, 18), (18, 12, 9)
+    U0 = pgen.turbulence(root, seed=41, kmin=1, kmax=5, mach=1.5)
+    g = oracle.Grid(root, recon=oracle.PPMX, riemann=ors)
+    dt = oracle.new_dt(U0, g, 0.3)
+    ref, nf = oracle.rk_step(U0, g, dt, 3)
+    assert nf == 0
+    m = ak.Mesh(root, block, recon=ak.AK_PPMX, rk=3, riemann=rs)
+    m.upload(U0)
+    m.step(dt)
+    err = max_norm_diff(m.download(), ref, G53)
+    assert err <= 1e-12, err
+    assert m.counters()[:2] == [0, 0]
+    m.close()
+
+
+def test_fp64_hundred_steps(ak):
+    root, block = (16, 16, 16), (8, 8, 8)
+    U = pgen.turbulence(root, seed=43, kmin=1, kmax=4, mach=0.8)
+    g = oracle.Grid(root, recon=oracle.PPMX)
+    m = ak.Mesh(root, block, recon=ak.AK_PPMX, rk=3)
+    m.upload(U)
+    for _ in range(100):
+        dt = oracle.new_dt(U, g, 0.3)
+        U, nf = oracle.rk_step(U, g, dt, 3)
+        assert nf == 0
+        m.step(dt, want_dt_next=False)
+    err = max_norm_diff(m.download(), U, G53)
+    assert err <= 1e-9, err
+    m.close()
+
+
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_fp64_shock_tube_parity(ak, d):
+    n = [8, 8, 8]
+    n[d] = 64
+    n = tuple(n)
+    U = pgen.shock_tube(n, direction=d)
+    g = oracle.Grid(n, gamma=1.4, recon=oracle.PPMX)
+    blk = tuple(v // 2 for v in n)
+    m = ak.Mesh(n, blk, recon=ak.AK_PPMX, rk=3, gamma=1.4)
+    m.upload(U)
+    for _ in range(10):
+        dt = oracle.new_dt(U, g, 0.3)
+        U, _ = oracle.rk_step(U, g, dt, 3)
+        m.step(dt, want_dt_next=False)
+    err = max_norm_diff(m.download(), U, 1.4)
+    assert err <= 1e-11, err
+    m.close()
+
+
+def test_mixed_close_to_oracle(ak):
+    root, block = (32, 32, 32), (16, 16, 16)
+    U0 = pgen.turbulence(root, seed=47, kmin=2, kmax=8, mach=0.5)
+    g = oracle.Grid(root, recon=oracle.PPMX)
+    dt = oracle.new_dt(U0, g, 0.3)
+    ref, _ = oracle.rk_step(U0, g, dt, 3)
+    m = ak.Mesh(root, block, recon=ak.AK_PPMX, rk=3, precision=1, ref_rho=1.0, ref_p=1.0)
+    m.upload(U0)
+    m.step(dt)
+    err = max_norm_diff(m.download(), ref, G53)
+    assert err <= 2e-6, err
+    m.close()
+
+
+def test_mixed_sound_wave_l1_within_one_percent(ak):
+    n = (32, 32, 32)
+    U0, T = pgen.linear_wave(n)
+    errs = []
+    for prec in (0, 1):
+        m = ak.Mesh(n, n, recon=ak.AK_PPMX, rk=3, precision=prec, ref_rho=1.0, ref_p=0.6)
+        m.upload(U0)
+        t, dt = 0.0, m.new_dt()
+        while t < T:
+            dt = min(dt, T - t)
+            dn = m.step(dt)
+            t += dt
+            dt = dn
+        errs.append(l1_wave_error(m.download(), U0))
+        m.close()
+    e64, e32 = errs
+    assert abs(e32 - e64) <= 0.01 * e64, (e32, e64)
+
+
+def test_refined_mesh_parity(ak):
+    t = pgen.nested_refinement_blocks(32, 8, 8, 2)
+
+    def fn(x, y, z):
+        tp = 2 * np.pi
+        return (1.0 + 0.3 * np.sin(tp * x) * np.cos(tp * y), 0.5 * np.sin(tp * y + 0.3),
+                0.4 * np.cos(tp * z), 0.3 * np.sin(tp * x + tp * z),
+                1.0 + 0.2 * np.cos(tp * (x + y + z)))
+    P = pgen.field_blocks(t, 32, fn)
+    om = oracle.SmrMesh(t, (32, 32, 32), recon=oracle.PPMX)
+    U = om.from_packed(P)
+    dt = om.new_dt(U, 0.3)
+    m = ak.Mesh((32,) * 3, table=t, recon=ak.AK_PPMX, rk=3, xmin=(-0.5,) * 3, xmax=(0.5,) * 3)
+    m.upload_packed(P)
+    for _ in range(2):
+        U = om.rk_step(U, dt, 3)
+        m.step(dt, want_dt_next=False)
+    ref = om.to_packed(U)
+    err = np.abs(m.download_packed() - ref).max() / np.abs(ref).max()
+    assert err <= 1e-12, err
+    m.close()

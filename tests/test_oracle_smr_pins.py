@@ -155,3 +155,92 @@ def test_sedov_taylor_radius_across_levels():
     R_st = 1.15 * (1.0 * t_end ** 2 / 1.0) ** 0.2  # Sedov-Taylor, gamma = 5/3
     dx2 = 1.0 / 128
     assert abs(R - R_st) < 1.0 * dx2, (R, R_st)
+
+
+def test_overlapping_leaves_refused():
+    # root blocks of 8 cells cannot leave out the central half of a 16-cell root grid:
+    # the refined blocks would overlap root leaves
+    t = pgen.nested_refinement_blocks(16, 8, 8, 1)
+    m = oracle.SmrMesh(t, (16, 16, 16))
+    with pytest.raises(ValueError):
+        m.fill_ghosts(np.ones(m.size))
+
+
+# ---------------------------------------------------------------------------------
+# FOFC on refined meshes (Section 3: before the level flux correction)
+# ---------------------------------------------------------------------------------
+def _cold_shear_blocks(t, root, p):
+    """A cold (low-pressure) diverging/shearing flow across the level boundaries."""
+    def fn(x, y, z):
+        tp = 2 * np.pi
+        return (1.0 + 0.5 * np.cos(tp * (x + y)),
+                np.sin(tp * (x - 0.25)) * (1 + 0.3 * np.cos(tp * y)),
+                0.5 * np.sin(tp * (y + 0.1)) * np.cos(tp * z), 0.3 * np.cos(tp * x), p)
+    return pgen.field_blocks(t, root, fn)
+
+
+def _bad_cells(m, t, U):
+    """Leaf cells with rho <= 0 or u_g <= 0."""
+    P, o, bad = m.to_packed(U), 0, 0
+    for r in t:
+        n = int(r[4] * r[5] * r[6])
+        u = P[o:o + 5 * n].reshape(5, n)
+        o += 5 * n
+        ug = u[4] - 0.5 * (u[1] ** 2 + u[2] ** 2 + u[3] ** 2) / u[0]
+        bad += int(np.sum((u[0] <= 0) | (ug <= 0)))
+    return bad
+
+
+def test_smr_fofc_is_identity_without_flags():
+    t = pgen.nested_refinement_blocks(16, 4, 8, 1)
+    P = _cold_shear_blocks(t, 16, 1.0)
+    a = oracle.SmrMesh(t, (16, 16, 16))
+    b = oracle.SmrMesh(t, (16, 16, 16), fofc=True)
+    U = a.from_packed(P)
+    dt = a.new_dt(U, 0.3)
+    Ub, nflag = b.rk_step_fofc(U, dt, 2)
+    assert nflag == 0 and np.array_equal(a.rk_step(U, dt), Ub)
+
+
+def test_smr_fofc_single_level_equals_uniform_oracle():
+    # every block on level 0: the SMR FOFC step must reproduce the uniform-grid FOFC step
+    n = (24, 24, 24)
+    G = pgen.turbulence(n, seed=3, kmin=1, kmax=6, mach=5.0)
+    t = pgen.nested_refinement_blocks(24, 8, 8, 0)
+    m = oracle.SmrMesh(t, n, fofc=True)
+    U = m.from_packed(np.concatenate(
+        [G[:, r[3]:r[3] + 8, r[2]:r[2] + 8, r[1]:r[1] + 8].reshape(-1) for r in t]))
+    grid = oracle.Grid(n, fofc=True)
+    total = 0
+    for _ in range(15):
+        dt = oracle.new_dt(G, grid, 0.3)
+        G, _, nfl = oracle.rk_step_fofc(G, grid, dt, 2)
+        U, nfl2 = m.rk_step_fofc(U, dt, 2)
+        assert nfl == nfl2
+        total += nfl
+        P, o = m.to_packed(U), 0
+        for r in t:
+            blk = P[o:o + 5 * 512].reshape(5, 8, 8, 8)
+            assert np.array_equal(blk, G[:, r[3]:r[3] + 8, r[2]:r[2] + 8, r[1]:r[1] + 8])
+            o += 5 * 512
+    assert total > 0
+
+
+def test_smr_fofc_two_levels_positive_and_conservative():
+    t = pgen.nested_refinement_blocks(16, 4, 8, 1)
+    P = _cold_shear_blocks(t, 16, 0.003)
+    res = {}
+    for fofc in (False, True):
+        m = oracle.SmrMesh(t, (16, 16, 16), fofc=fofc)
+        U = m.from_packed(P)
+        tot0 = m.totals(U)
+        flagged = 0
+        for _ in range(6):
+            U, nfl = m.rk_step_fofc(U, m.new_dt(U, 0.3), 2)
+            flagged += nfl
+        res[fofc] = (flagged, _bad_cells(m, t, U), np.abs(m.totals(U) - tot0))
+    # the plain scheme leaves cells with negative internal energy; FOFC flags and
+    # corrects them, conserving the totals to round-off
+    assert res[False][0] == 0 and res[False][1] > 0
+    assert res[True][0] > 0 and res[True][1] == 0
+    assert res[True][2].max() < 1e-14, res[True][2]

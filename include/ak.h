@@ -7,8 +7,9 @@
  *   - conservation law dU/dt + div F(W) = 0 ............ Section 3, Eq. (1) (S = 0)
  *   - U = (rho, rho v, E), F, W = (rho, v, u_g),
  *     E = u_g + rho v^2/2, p = (gamma-1) u_g ............ Section 3.1, Eq. (4)
- *   - reconstruction on primitives (PLM, PPM4) ......... Section 3
- *   - HLLC Riemann solver .............................. Section 3
+ *   - reconstruction on primitives (PLM, PPM4, PPMX,
+ *     WENO-Z) ........................................ Section 3
+ *   - HLLC, HLLE and LLF Riemann solvers ............... Section 3
  *   - method of lines with SSP Runge-Kutta ............. Section 3
  *   - CFL time step, min over all cells and dims ....... Section 3, Eq. (3)
  *   - MeshBlocks aggregated per device, one launch
@@ -64,7 +65,7 @@ typedef enum {
   AK_ESTATE = -6      /* call out of order (e.g. a register not bound) */
 } ak_status;
 
-enum { AK_PLM = 0, AK_PPM4 = 1, AK_WENOZ = 2 };  /* reconstruction (Section 3) */
+enum { AK_PLM = 0, AK_PPM4 = 1, AK_WENOZ = 2, AK_PPMX = 3 };  /* reconstruction (Section 3) */
 enum { AK_FP64 = 0, AK_MIXED = 1 };   /* arithmetic form of the stage */
 enum { AK_HLLC = 0, AK_HLLE = 1, AK_LLF = 2 };  /* Riemann solver (Section 3) */
 
@@ -75,7 +76,7 @@ typedef struct ak_mesh ak_mesh;
 
 typedef struct {
   int32_t nblocks;        /* number of MeshBlocks (Section 2), >= 1 */
-  int32_t nghost;         /* ghost cells per side: 2 for PLM, 3 for PPM4 and WENO-Z */
+  int32_t nghost;         /* ghost cells per side: 2 for PLM, 3 for PPM4, WENO-Z, PPMX */
   const int32_t* blocks;  /* host array, AK_BLOCK_INTS ints per leaf block:
                              level, lx1, lx2, lx3, nx1, nx2, nx3 -- (lx1, lx2, lx3) is the
                              block's first cell in the cell index space of its level
@@ -85,7 +86,9 @@ typedef struct {
                              create time; the caller keeps ownership. */
   double xmin[3], xmax[3];  /* domain, periodic in all three directions */
   int32_t root_nx[3];       /* level-0 cells per direction; the blocks must tile it */
-  int32_t recon;            /* AK_PLM, AK_PPM4 or AK_WENOZ */
+  int32_t recon;            /* AK_PLM (van Leer), AK_PPM4 (Colella & Woodward limiters),
+                               AK_WENOZ (Borges et al.) or AK_PPMX (extremum-preserving
+                               limiters of Colella & Sekora / McCorquodale & Colella) */
   int32_t rk;               /* SSP-RK order: 2 (Heun) or 3 (Shu-Osher) */
   int32_t precision;        /* AK_FP64 or AK_MIXED */
   int32_t riemann;          /* AK_HLLC (0: HLLC with PVRS speeds bounded by the Davis
@@ -94,8 +97,10 @@ typedef struct {
   int32_t fofc;             /* 1: first-order flux correction (Section 3): in every RK
                                stage, a cell whose density or internal energy would not
                                be positive gets first-order (piecewise-constant) LLF
-                               fluxes on all its faces.  Uniform meshes only (AK_EINVAL
-                               with several levels).  0: off. */
+                               fluxes on all its faces, before the level flux correction
+                               on refined meshes (a fine face at a level boundary turns
+                               first-order when the fine or the coarse cell is flagged;
+                               the coarse side takes the fine mean).  0: off. */
   double gamma;             /* gamma-law EOS, > 1 */
   double cfl;               /* Courant number of Eq. (3), in (0, 1] */
   double ref_rho, ref_p;    /* AK_MIXED only: background density and pressure that are

@@ -24,7 +24,7 @@ from . import build as _build
 
 AK_OK, AK_EINVAL, AK_ENOMEM, AK_ECUDA, AK_ENEGATIVE, AK_ETIMEOUT, AK_ESTATE = \
     0, -1, -2, -3, -4, -5, -6
-AK_PLM, AK_PPM4, AK_WENOZ = 0, 1, 2
+AK_PLM, AK_PPM4, AK_WENOZ, AK_PPMX = 0, 1, 2, 3
 AK_FP64, AK_MIXED = 0, 1
 AK_HLLC, AK_HLLE, AK_LLF = 0, 1, 2
 AK_BLOCK_INTS = 7

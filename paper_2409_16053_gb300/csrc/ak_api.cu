@@ -71,10 +71,10 @@ extern "C" ak_status ak_mesh_create(const ak_mesh_desc* d, void* cuda_stream, ak
   if (!d || !out) return einval("ak_mesh_create: NULL argument");
   *out = nullptr;
   if (d->nblocks < 1 || !d->blocks) return einval("ak_mesh_create: need nblocks >= 1 and a block table");
-  if (d->recon != AK_PLM && d->recon != AK_PPM4 && d->recon != AK_WENOZ)
-    return einval("ak_mesh_create: recon must be AK_PLM, AK_PPM4 or AK_WENOZ");
+  if (d->recon != AK_PLM && d->recon != AK_PPM4 && d->recon != AK_WENOZ && d->recon != AK_PPMX)
+    return einval("ak_mesh_create: recon must be AK_PLM, AK_PPM4, AK_WENOZ or AK_PPMX");
   const int ng = d->recon == AK_PLM ? 2 : 3;
-  if (d->nghost != ng) return einval("ak_mesh_create: nghost must be 2 for PLM and 3 for PPM4 / WENO-Z");
+  if (d->nghost != ng) return einval("ak_mesh_create: nghost must be 2 for PLM and 3 for PPM4 / WENO-Z / PPMX");
   if (d->rk != 2 && d->rk != 3) return einval("ak_mesh_create: rk must be 2 or 3");
   if (d->precision != AK_FP64 && d->precision != AK_MIXED)
     return einval("ak_mesh_create: precision must be AK_FP64 or AK_MIXED");
@@ -205,10 +205,6 @@ extern "C" ak_status ak_mesh_create(const ak_mesh_desc* d, void* cuda_stream, ak
   m->nlev = X.nlev;
   m->multilevel = X.nlev > 1;
   m->nblocks = nb;
-  if (d->fofc && m->multilevel) {
-    free(m);
-    return einval("ak_mesh_create: FOFC is built for uniform meshes only (one level)");
-  }
   m->h_blocks = (int32_t*)malloc(sizeof(int32_t) * AK_BLOCK_INTS * nb);
   m->h_offsets = (int64_t*)malloc(sizeof(int64_t) * nb);
   m->h_blk = (ak_block*)calloc(nb, sizeof(ak_block));

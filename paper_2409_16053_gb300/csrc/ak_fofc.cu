@@ -4,13 +4,19 @@
 //
 // The stage kernels flag such cells (fofc_flag) while they write the stage's output.
 // This kernel then corrects that output: every cell with a flagged cell among itself
-// and its six face neighbours changes by b dt (the stage's weight of dt L) times the
+// and the cells across its faces changes by b dt (the stage's weight of dt L) times the
 // change of L(U) from its corrected faces, dL = sum_faces -+ (F_LLF - F_high) / dx_d.
 // F_high is recomputed from the stage's input with the stage kernels' own device code,
 // so it equals the flux the stage used.  Each affected cell is corrected by exactly
-// one thread -- the one holding the lowest-numbered flagged cell next to it -- so the
-// result does not depend on thread order.  One CTA runs it; flagged cells are rare.
-// Uniform meshes only (faces of one level, no level flux correction).
+// one thread -- the one holding the lowest-numbered flagged cell that touches it -- so
+// the result does not depend on thread order.  One CTA runs it; flagged cells are rare.
+//
+// Refined meshes (the paper applies FOFC before the level flux correction): a face
+// between a fine cell and a coarser leaf is the fine block's face, computed from the
+// fine block's data (its ghost cell there is the prolongated coarse value); it turns
+// first-order when the fine cell or the coarse cell is flagged.  The coarse side of
+// that face carries the mean of its four fine faces' fluxes, so a coarse cell next to a
+// finer region changes by the mean of those fine faces' flux changes.
 #include "ak_internal.cuh"
 #include "hydro_ops.cuh"
 #include "stage_common.cuh"
@@ -26,18 +32,70 @@ __device__ __forceinline__ long long cell_id(const ak_meshdev& md, int4 c) {
   return md.cell_off[c.x] + ((long long)c.w * B.nx2 + c.z) * B.nx1 + c.y;
 }
 
-// face neighbour of interior cell c = (block, i, j, k) across direction d, dir = -1 / +1
-// (periodic; the level's leaf map gives the neighbour block)
-__device__ __forceinline__ int4 neighbour(const ak_meshdev& md, int4 c, int d, int dir) {
-  const ak_block& B = md.blocks[c.x];
+// leaf of level l holding the level-l cell (q0, q1, q2) (periodic), or -1
+__device__ __forceinline__ int leaf_at(const ak_meshdev& md, int l, int q0, int q1, int q2) {
+  if (l < 0 || l >= md.nlev) return -1;
+  const ak_level& L = md.levels[l];
+  if (L.bs1 == 0) return -1;
+  q0 = q0 < 0 ? q0 + L.n1 : (q0 >= L.n1 ? q0 - L.n1 : q0);
+  q1 = q1 < 0 ? q1 + L.n2 : (q1 >= L.n2 ? q1 - L.n2 : q1);
+  q2 = q2 < 0 ? q2 + L.n3 : (q2 >= L.n3 ? q2 - L.n3 : q2);
+  return md.map[L.map_off + ((q2 / L.bs3) * L.md2 + q1 / L.bs2) * L.md1 + q0 / L.bs1];
+}
+
+// interior cell of leaf `blk` at the level-l cell q (periodic)
+__device__ __forceinline__ int4 local_cell(const ak_meshdev& md, int blk, int q0, int q1, int q2) {
+  const ak_block& B = md.blocks[blk];
   const ak_level& L = md.levels[B.level];
+  int r0 = q0 - B.lx1, r1 = q1 - B.lx2, r2 = q2 - B.lx3;
+  r0 = r0 < 0 ? r0 + L.n1 : (r0 >= L.n1 ? r0 - L.n1 : r0);
+  r1 = r1 < 0 ? r1 + L.n2 : (r1 >= L.n2 ? r1 - L.n2 : r1);
+  r2 = r2 < 0 ? r2 + L.n3 : (r2 >= L.n3 ? r2 - L.n3 : r2);
+  return make_int4(blk, r0, r1, r2);
+}
+
+// The cells across one face of interior cell c (direction d, dir = -1 / +1): one cell of
+// the same level (kind 0) or of the coarser level (kind 1), or the four cells of the
+// finer level that share the face (kind 2).
+struct Across {
+  int kind, n;
+  int4 c[4];
+};
+__device__ __noinline__ Across across(const ak_meshdev& md, int4 c, int d, int dir) {
+  const ak_block& B = md.blocks[c.x];
+  const int l = B.level;
+  const ak_level& L = md.levels[l];
+  const int n[3] = {L.n1, L.n2, L.n3};
   int q[3] = {B.lx1 + c.y, B.lx2 + c.z, B.lx3 + c.w};
-  const int n[3] = {L.n1, L.n2, L.n3}, bs[3] = {L.bs1, L.bs2, L.bs3};
   q[d] += dir;
   q[d] = q[d] < 0 ? q[d] + n[d] : (q[d] >= n[d] ? q[d] - n[d] : q[d]);
-  const int b0 = q[0] / bs[0], b1 = q[1] / bs[1], b2 = q[2] / bs[2];
-  const int blk = md.map[L.map_off + (b2 * L.md2 + b1) * L.md1 + b0];
-  return make_int4(blk, q[0] - b0 * bs[0], q[1] - b1 * bs[1], q[2] - b2 * bs[2]);
+  Across a;
+  int b = leaf_at(md, l, q[0], q[1], q[2]);
+  if (b >= 0) {
+    a.kind = 0;
+    a.n = 1;
+    a.c[0] = local_cell(md, b, q[0], q[1], q[2]);
+    return a;
+  }
+  b = leaf_at(md, l - 1, q[0] >> 1, q[1] >> 1, q[2] >> 1);
+  if (b >= 0) {
+    a.kind = 1;
+    a.n = 1;
+    a.c[0] = local_cell(md, b, q[0] >> 1, q[1] >> 1, q[2] >> 1);
+    return a;
+  }
+  a.kind = 2;
+  a.n = 0;
+  const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+  for (int u = 0; u < 4; ++u) {
+    int Q[3];
+    Q[d] = 2 * q[d] + (dir > 0 ? 0 : 1);  // the fine layer next to the face
+    Q[t1] = 2 * q[t1] + (u & 1);
+    Q[t2] = 2 * q[t2] + (u >> 1);
+    const int f = leaf_at(md, l + 1, Q[0], Q[1], Q[2]);
+    if (f >= 0) a.c[a.n++] = local_cell(md, f, Q[0], Q[1], Q[2]);
+  }
+  return a;
 }
 
 __device__ __forceinline__ bool flagged(const ak_meshdev& md, int4 c) {
@@ -75,8 +133,8 @@ __device__ void face_change(const double* uin, const ak_meshdev& md, const Bg& b
       qa[m] = W[m][v];
       qb[m] = W[m + 1][v];
     }
-    edges<NG>(qa, lo_a[v], hi_a[v], bg.wenoz);
-    edges<NG>(qb, lo_b[v], hi_b[v], bg.wenoz);
+    edges<NG>(qa, lo_a[v], hi_a[v], bg.recon);
+    edges<NG>(qb, lo_b[v], hi_b[v], bg.recon);
   }
   R fh[5], fl[5];
   solve(d, hi_a, lo_b, bg, fh);
@@ -100,31 +158,70 @@ __global__ void __launch_bounds__(kFofcThreads)
   for (unsigned idx = threadIdx.x; idx < n; idx += blockDim.x) {
     const int4 f = md.flist[idx];
     const long long gf = cell_id(md, f);
-    for (int c7 = 0; c7 < 7; ++c7) {
-      const int4 c = c7 == 0 ? f : neighbour(md, f, (c7 - 1) >> 1, (c7 & 1) ? -1 : 1);
-      // owner of c: the lowest-numbered flagged cell among c and its neighbours
-      long long owner = flagged(md, c) ? cell_id(md, c) : 0x7fffffffffffffffll;
-      bool nb_flag[6];
-#pragma unroll
+    // the cells f touches: itself and the cells across its faces (each once)
+    int4 cand[1 + 6 * 4];
+    long long cid[1 + 6 * 4];
+    int nc = 0;
+    cand[nc] = f;
+    cid[nc++] = gf;
+    for (int q = 0; q < 6; ++q) {
+      const Across a = across(md, f, q >> 1, (q & 1) ? 1 : -1);
+      for (int u = 0; u < a.n; ++u) {
+        const long long g = cell_id(md, a.c[u]);
+        bool seen = false;
+        for (int t = 0; t < nc; ++t) seen |= cid[t] == g;
+        if (!seen) {
+          cand[nc] = a.c[u];
+          cid[nc++] = g;
+        }
+      }
+    }
+    for (int ci = 0; ci < nc; ++ci) {
+      const int4 c = cand[ci];
+      // owner of c: the lowest-numbered flagged cell among c and the cells across its
+      // faces
+      const bool cf = flagged(md, c);
+      long long owner = cf ? cid[ci] : 0x7fffffffffffffffll;
       for (int q = 0; q < 6; ++q) {
-        const int4 nq = neighbour(md, c, q >> 1, (q & 1) ? 1 : -1);
-        nb_flag[q] = flagged(md, nq);
-        const long long gq = cell_id(md, nq);
-        if (nb_flag[q] && gq < owner) owner = gq;
+        const Across a = across(md, c, q >> 1, (q & 1) ? 1 : -1);
+        for (int u = 0; u < a.n; ++u)
+          if (flagged(md, a.c[u])) {
+            const long long g = cell_id(md, a.c[u]);
+            owner = g < owner ? g : owner;
+          }
       }
       if (owner != gf) continue;
-      const bool cf = flagged(md, c);
       const ak_block& B = md.blocks[c.x];
       const double idx_d[3] = {1.0 / B.dx1, 1.0 / B.dx2, 1.0 / B.dx3};
       double dl[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
       for (int q = 0; q < 6; ++q) {  // face q: direction q/2, lower (q even) or upper
-        if (!cf && !nb_flag[q]) continue;
         const int d = q >> 1, side = q & 1;
-        double df[5];
-        face_change<NG, MIXED>(uin, md, bg, cn, c, d, side, df);
+        const Across a = across(md, c, d, side ? 1 : -1);
+        double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        bool any = false;
+        if (a.kind != 2) {
+          // a face of c's own block (same level, or fine side of a level boundary)
+          if (cf || flagged(md, a.c[0])) {
+            face_change<NG, MIXED>(uin, md, bg, cn, c, d, side, acc);
+            any = true;
+          }
+        } else {
+          // coarse side of a level boundary: the mean of the four fine faces' changes
+          for (int u = 0; u < a.n; ++u) {
+            if (!cf && !flagged(md, a.c[u])) continue;
+            double df[5];
+            face_change<NG, MIXED>(uin, md, bg, cn, a.c[u], d, 1 - side, df);
+#pragma unroll
+            for (int v = 0; v < 5; ++v) acc[v] += df[v];
+            any = true;
+          }
+#pragma unroll
+          for (int v = 0; v < 5; ++v) acc[v] *= 0.25;
+        }
+        if (!any) continue;
         // L = -(F_upper - F_lower) / dx: a lower face adds, an upper face subtracts
 #pragma unroll
-        for (int v = 0; v < 5; ++v) dl[v] += (side ? -df[v] : df[v]) * idx_d[d];
+        for (int v = 0; v < 5; ++v) dl[v] += (side ? -acc[v] : acc[v]) * idx_d[d];
       }
       const long long e = B.off + ((long long)(c.w + NG) * B.p2 + (c.z + NG)) * B.s1 + c.y + NG;
       double un[5];

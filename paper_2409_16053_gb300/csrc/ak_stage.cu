@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
       R q[2 * NG - 1];
 #pragma unroll
       for (int m = 0; m < 2 * NG - 1; ++m) q[m] = ring[slot(kc - NG + 1 + m) * 5 * NPL + v * NPL + oc];
-      edges<NG>(q, lo[v], hi[v], bg.wenoz);
+      edges<NG>(q, lo[v], hi[v], bg.recon);
     }
   };
   auto x1_edges = [&](const R* pl) {  // cells i0-1 .. i0+TX of the tile's rows
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
           R q[2 * NG - 1];
 #pragma unroll
           for (int m = 0; m < 2 * NG - 1; ++m) q[m] = pl[v * NPL + base + m];
-          edges<NG>(q, e1lo[(v * TY + r) * C1 + c], e1hi[(v * TY + r) * C1 + c], bg.wenoz);
+          edges<NG>(q, e1lo[(v * TY + r) * C1 + c], e1hi[(v * TY + r) * C1 + c], bg.recon);
         }
       }
     }
@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
           R q[2 * NG - 1];
 #pragma unroll
           for (int m = 0; m < 2 * NG - 1; ++m) q[m] = pl[v * NPL + base + m * WX];
-          edges<NG>(q, e2lo[(v * (TY + 2) + r) * TX + c], e2hi[(v * (TY + 2) + r) * TX + c], bg.wenoz);
+          edges<NG>(q, e2lo[(v * (TY + 2) + r) * TX + c], e2hi[(v * (TY + 2) + r) * TX + c], bg.recon);
         }
       }
     }
@@ -521,8 +521,8 @@ __global__ void flux_correction_kernel(const double* __restrict__ reg, ak_meshde
           qa[mm] = W[mm][v];
           qb[mm] = W[mm + 1][v];
         }
-        edges<NG>(qa, lo_a[v], hi_a[v], bg.wenoz);
-        edges<NG>(qb, lo_b[v], hi_b[v], bg.wenoz);
+        edges<NG>(qa, lo_a[v], hi_a[v], bg.recon);
+        edges<NG>(qb, lo_b[v], hi_b[v], bg.recon);
       }
       R f[5];
       solve(d, hi_a, lo_b, bg, f);
@@ -558,7 +558,7 @@ static Bg make_bg(const ak_mesh* m) {
   bg.kq_f = (float)bg.kq;
   bg.pb_f = bg.gm1_f * bg.ug_f;
   bg.rsolver = m->desc.riemann;
-  bg.wenoz = m->desc.recon == AK_WENOZ;
+  bg.recon = m->desc.recon;
   return bg;
 }
 

@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(MxCfg<NG, T>::NTH, 2)
       float q[2 * NG - 1];
 #pragma unroll
       for (int m = 0; m < 2 * NG - 1; ++m) q[m] = ring[slot(kc - NG + 1 + m) * 5 * NPL + v * NPL + oc];
-      edges<NG>(q, lo[v], hi[v], bg.wenoz);
+      edges<NG>(q, lo[v], hi[v], bg.recon);
     }
   };
 

@@ -12,7 +12,7 @@
 //
 // Sources: Section 3, Eq. (1) and Section 3.1, Eq. (4) of AthenaK (arXiv 2409.16053)
 // for the equations; PLM with the van Leer harmonic limiter, PPM4 after Colella &
-// Woodward (1984), HLLC after Toro (2009) ch. 10 (PVRS wave-speed estimate bounded
+// Woodward (1984), PPMX after Colella & Sekora (2008) and McCorquodale & Colella (2011), HLLC after Toro (2009) ch. 10 (PVRS wave-speed estimate bounded
 // outward by the Davis speeds), HLLE (HLL with Einfeldt's Roe-average speeds, Toro
 // Sec. 10.5.1) and LLF (Rusanov), as readings of the methods the paper names.
 #pragma once
@@ -38,7 +38,7 @@ struct Bg {
   float kq_f;
   float pb_f;
   int rsolver;           // AK_HLLC, AK_HLLE or AK_LLF
-  int wenoz;             // 3-ghost reconstruction: 1 WENO-Z, 0 PPM4
+  int recon;             // AK_PLM, AK_PPM4, AK_WENOZ or AK_PPMX
 };
 
 // ------------------------------------------------------------------------------
@@ -110,6 +110,77 @@ __device__ __forceinline__ void ppm_edges_fp64(double q0, double q1, double q2, 
     a_hi = fma(3.0, a, -(a_lo + a_lo));
   lo = a_lo;
   hi = a_hi;
+}
+
+// PPMX: PPM with extremum-preserving limiters.  The fourth-order interface value
+//   f = 7/12 (q_i + q_i+1) - 1/12 (q_i-1 + q_i+2);
+// if f is not between q_i and q_i+1, its second difference 3 (q_i + q_i+1 - 2 f) is
+// limited by those of cells i and i+1 (Colella & Sekora 2008) and
+// f = (q_i + q_i+1) / 2 - lim / 6.  In a cell at an extremum (of the parabola, or of the
+// cell values) the parabola's second derivative 6 (lo + hi - 2 q) is compared with
+// C x the second differences of cells i-1, i, i+1 (C = 1.25) and its deviations from the
+// mean are scaled by their ratio r (McCorquodale & Colella 2011); elsewhere the
+// overshooting edge is pulled in as in Colella & Woodward.  Five-cell stencil: the
+// seven-cell third-derivative test of the latter paper is not applied.  Same
+// operations and order in both precisions; -fmad=false keeps each rounding as written.
+template <typename R>
+__device__ __forceinline__ bool same_sign3(R x, R y, R z) {
+  return (x > R(0) && y > R(0) && z > R(0)) || (x < R(0) && y < R(0) && z < R(0));
+}
+template <typename R>
+__device__ __forceinline__ R ppmx_interface(R a, R b, R c, R d) {
+  const R C = R(1.25);
+  R f = R(7.0 / 12.0) * (b + c) - R(1.0 / 12.0) * (a + d);
+  if ((f - b) * (c - f) < R(0)) {
+    const R d2 = R(3) * ((b + c) - R(2) * f);
+    const R d2l = (a + c) - R(2) * b;
+    const R d2r = (b + d) - R(2) * c;
+    R lim = R(0);
+    if (same_sign3(d2, d2l, d2r)) {
+      const R m = fmin(fabs(d2), fmin(C * fabs(d2l), C * fabs(d2r)));
+      lim = d2 > R(0) ? m : -m;
+    }
+    f = R(0.5) * (b + c) - lim / R(6);
+  }
+  return f;
+}
+template <typename R>
+__device__ __forceinline__ void ppmx_edges(R q0, R q1, R q2, R q3, R q4, R& lo, R& hi) {
+  const R C = R(1.25);
+  R alo = ppmx_interface(q0, q1, q2, q3);
+  R ahi = ppmx_interface(q1, q2, q3, q4);
+  const R a = q2, dp = ahi - a, dm = a - alo;
+  if (dp * dm <= R(0) || (q3 - a) * (a - q1) <= R(0)) {
+    const R d2 = R(6) * ((alo + ahi) - R(2) * a);
+    const R d2c = (q1 + q3) - R(2) * a;
+    const R d2l = (q0 + a) - R(2) * q1;
+    const R d2r = (a + q4) - R(2) * q3;
+    R r = R(0);
+    bool limit = true;
+    if (same_sign3(d2, d2c, d2l) && same_sign3(d2, d2c, d2r)) {
+      const R m = C * fmin(fabs(d2c), fmin(fabs(d2l), fabs(d2r)));
+      if (m >= fabs(d2))
+        limit = false;
+      else
+        r = m / fabs(d2);
+    }
+    if (limit) {
+      if (dp * dm < R(0)) {
+        alo = a - r * dm;
+        ahi = a + r * dp;
+      } else if (fabs(dm) >= R(2) * fabs(dp)) {
+        alo = a - R(2) * (R(1) - r) * dp - r * dm;
+      } else if (fabs(dp) >= R(2) * fabs(dm)) {
+        ahi = a + R(2) * (R(1) - r) * dm + r * dp;
+      }
+    }
+  } else if (fabs(dm) >= R(2) * fabs(dp)) {
+    alo = a - R(2) * dp;
+  } else if (fabs(dp) >= R(2) * fabs(dm)) {
+    ahi = a + R(2) * dm;
+  }
+  lo = alo;
+  hi = ahi;
 }
 
 // WENO-Z (Borges et al. 2008) values at both faces of the middle cell of q0..q4: the

@@ -100,13 +100,17 @@ __device__ __forceinline__ void riemann(const V* wl, const V* wr, const Bg& bg, 
     hllc_mixed(wl, wr, bg, f);
 }
 
-// Lower and upper edge values of the middle cell of q[0 .. 2NG-2] (NG = 3: WENO-Z if
-// wz, else PPM4).
+// Lower and upper edge values of the middle cell of q[0 .. 2NG-2] (NG = 3: PPM4,
+// WENO-Z or PPMX by `recon`).
 template <int NG, typename R>
-__device__ __forceinline__ void edges(const R* q, R& lo, R& hi, bool wz) {
+__device__ __forceinline__ void edges(const R* q, R& lo, R& hi, int recon) {
   if constexpr (NG == 3) {
-    if (wz) {
+    if (recon == AK_WENOZ) {
       wenoz_edges(q[0], q[1], q[2], q[3], q[4], lo, hi);
+      return;
+    }
+    if (recon == AK_PPMX) {
+      ppmx_edges(q[0], q[1], q[2], q[3], q[4], lo, hi);
       return;
     }
   }

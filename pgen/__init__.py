@@ -281,3 +281,16 @@ def field_blocks(table, root_nx, fn, gamma=5.0 / 3.0, lo=-0.5, length=1.0):
         parts.append(_cons(rho * np.ones(shape), v1 * np.ones(shape), v2 * np.ones(shape),
                            v3 * np.ones(shape), p * np.ones(shape), gamma).reshape(-1))
     return np.concatenate(parts)
+
+
+def cold_shear_blocks(table, root_nx, p, gamma=5.0 / 3.0):
+    """A cold (pressure p) diverging and shearing flow of unit-order speed on leaf blocks
+    of several levels, with its divergence centred on a level boundary of the nested
+    refinement; at p ~ 1e-3 the plain scheme drives cells to negative internal energy.
+    Packed block after block as [block][var][k][j][i]."""
+    def fn(x, y, z):
+        tp = 2 * np.pi
+        return (1.0 + 0.5 * np.cos(tp * (x + y)),
+                np.sin(tp * (x - 0.25)) * (1 + 0.3 * np.cos(tp * y)),
+                0.5 * np.sin(tp * (y + 0.1)) * np.cos(tp * z), 0.3 * np.cos(tp * x), p)
+    return field_blocks(table, root_nx, fn, gamma)

@@ -1,7 +1,8 @@
 """First-order flux correction (FOFC) on the GPU against the oracle: Mach-5 turbulence,
 where the plain scheme needs floors, on a mesh of 8 MeshBlocks (corrections cross block
 boundaries), FP64 parity step by step with the oracle's dt sequence and the same number
-of corrected cells, PPM4 + RK3, the mixed form, and refused on refined meshes."""
+of corrected cells, PPM4 + RK3, the mixed form, and a two-level refined mesh whose
+flagged cells sit on both levels and next to the level boundaries."""
 import numpy as np
 import pytest
 
@@ -85,7 +86,36 @@ def test_plain_scheme_needs_floors_on_the_gpu(ak):
     m.close()
 
 
-def test_fofc_refused_on_refined_mesh(ak):
-    t = pgen.nested_refinement_blocks(32, 8, 8, 2)
-    with pytest.raises(ak.AkError):
-        ak.Mesh((32,) * 3, table=t, fofc=True)
+@pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 5e-3)])
+def test_refined_mesh_cold_shear_parity(ak, precision, tol):
+    t = pgen.nested_refinement_blocks(16, 4, 8, 1)
+    # p = 1e-3: flagged cells on both levels, coarse and fine ones next to the level
+    # boundary among them
+    P = pgen.cold_shear_blocks(t, 16, 0.001)
+    om = oracle.SmrMesh(t, (16, 16, 16), fofc=True)
+    U = om.from_packed(P)
+    m = ak.Mesh((16,) * 3, table=t, fofc=True, precision=precision, xmin=(-0.5,) * 3,
+                xmax=(0.5,) * 3, ref_rho=1.0, ref_p=0.001)
+    m.upload_packed(P)
+    tot0 = om.totals(U)
+    flagged, errs = 0, []
+    for _ in range(4):
+        dt = om.new_dt(U, 0.3)
+        U, nfl = om.rk_step_fofc(U, dt, 2)
+        flagged += nfl
+        m.step(dt, want_dt_next=False)
+        ref = om.to_packed(U)
+        errs.append(np.abs(m.download_packed() - ref).max() / np.abs(ref).max())
+    out = om.from_packed(m.download_packed())
+    c = m.counters()
+    m.close()
+    assert flagged > 0
+    assert max(errs) <= tol, errs
+    assert c[0] == 0 and c[1] == 0, c
+    tot = om.totals(out)
+    ctol = 1e-13 if precision == 0 else 1e-8
+    assert np.all(np.abs(tot - tot0) <= ctol * (np.abs(tot0) + 1.0)), tot - tot0
+    if precision == 0:
+        assert c[3] == flagged, (c[3], flagged)
+    else:
+        assert c[3] > 0

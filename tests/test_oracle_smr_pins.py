@@ -169,16 +169,6 @@ def test_overlapping_leaves_refused():
 # ---------------------------------------------------------------------------------
 # FOFC on refined meshes (Section 3: before the level flux correction)
 # ---------------------------------------------------------------------------------
-def _cold_shear_blocks(t, root, p):
-    """A cold (low-pressure) diverging/shearing flow across the level boundaries."""
-    def fn(x, y, z):
-        tp = 2 * np.pi
-        return (1.0 + 0.5 * np.cos(tp * (x + y)),
-                np.sin(tp * (x - 0.25)) * (1 + 0.3 * np.cos(tp * y)),
-                0.5 * np.sin(tp * (y + 0.1)) * np.cos(tp * z), 0.3 * np.cos(tp * x), p)
-    return pgen.field_blocks(t, root, fn)
-
-
 def _bad_cells(m, t, U):
     """Leaf cells with rho <= 0 or u_g <= 0."""
     P, o, bad = m.to_packed(U), 0, 0
@@ -193,7 +183,7 @@ def _bad_cells(m, t, U):
 
 def test_smr_fofc_is_identity_without_flags():
     t = pgen.nested_refinement_blocks(16, 4, 8, 1)
-    P = _cold_shear_blocks(t, 16, 1.0)
+    P = pgen.cold_shear_blocks(t, 16, 1.0)
     a = oracle.SmrMesh(t, (16, 16, 16))
     b = oracle.SmrMesh(t, (16, 16, 16), fofc=True)
     U = a.from_packed(P)
@@ -228,7 +218,7 @@ def test_smr_fofc_single_level_equals_uniform_oracle():
 
 def test_smr_fofc_two_levels_positive_and_conservative():
     t = pgen.nested_refinement_blocks(16, 4, 8, 1)
-    P = _cold_shear_blocks(t, 16, 0.003)
+    P = pgen.cold_shear_blocks(t, 16, 0.003)
     res = {}
     for fofc in (False, True):
         m = oracle.SmrMesh(t, (16, 16, 16), fofc=fofc)

@@ -294,3 +294,19 @@ def cold_shear_blocks(table, root_nx, p, gamma=5.0 / 3.0):
                 np.sin(tp * (x - 0.25)) * (1 + 0.3 * np.cos(tp * y)),
                 0.5 * np.sin(tp * (y + 0.1)) * np.cos(tp * z), 0.3 * np.cos(tp * x), p)
     return field_blocks(table, root_nx, fn, gamma)
+
+
+def blocks_from_fine(table, Uf):
+    """Leaf-block data of a nested mesh from a uniform field Uf (5, n3, n2, n1) given at
+    the resolution of the finest level: each leaf of level l takes the means of the
+    2^(L-l)-cubes of fine cells it covers (L the finest level), so the totals are those
+    of Uf.  Packed block after block as [block][var][k][j][i]."""
+    tab = np.asarray(table)
+    top = int(tab[:, 0].max())
+    parts = []
+    for r in tab:
+        f = 1 << (top - int(r[0]))
+        lx, ly, lz, nx, ny, nz = (int(v) for v in r[1:7])
+        sub = Uf[:, f * lz:f * (lz + nz), f * ly:f * (ly + ny), f * lx:f * (lx + nx)]
+        parts.append(sub.reshape(5, nz, f, ny, f, nx, f).mean(axis=(2, 4, 6)).reshape(-1))
+    return np.concatenate(parts)

@@ -234,3 +234,12 @@ def test_smr_fofc_two_levels_positive_and_conservative():
     assert res[False][0] == 0 and res[False][1] > 0
     assert res[True][0] > 0 and res[True][1] == 0
     assert res[True][2].max() < 1e-14, res[True][2]
+
+
+def test_blocks_from_fine_keeps_totals():
+    t = pgen.nested_refinement_blocks(16, 4, 8, 1)
+    Uf = pgen.turbulence((32, 32, 32), seed=53, kmin=1, kmax=6, mach=1.0)
+    m = oracle.SmrMesh(t, (16, 16, 16))
+    tot = m.totals(m.from_packed(pgen.blocks_from_fine(t, Uf)))
+    ref = Uf.reshape(5, -1).sum(axis=1) / 32 ** 3
+    assert np.allclose(tot, ref, rtol=0, atol=1e-14)

@@ -294,7 +294,7 @@ def time_smr(ak, torch, precision, steps, warmup):
     torch.cuda.empty_cache()
     return {"value": cells * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
             "counters": c, "schedule": {"tile": schedule[0], "x3_segments": schedule[1],
-                                        "order": schedule[2]}}
+                                        "order": schedule[2], "fused": schedule[4]}}
 
 
 def cpu_baseline(sample_n=96, budget_s=12.0, steps_max=None):

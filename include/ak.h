@@ -189,9 +189,24 @@ ak_status ak_step(ak_mesh* mesh, double dt, double* dt_next);
  * cut into GPU work.  Results are bitwise independent of the choice.  Registers 0 and 1
  * must be bound and register 0 must hold a valid state (its ghosts are refilled);
  * register 1 is overwritten.  Synchronizes the stream; do not call during a stream
- * capture.  result (may be NULL): tile, segments, order (as for ak_mesh_schedule), and
- * the chosen schedule's stage time in microseconds. */
-ak_status ak_mesh_autotune(ak_mesh* mesh, int32_t result[4]);
+ * capture.  On a mesh with a ghost fill (static refinement, or FOFC) it then times a
+ * stage as separate fill / flux-correction / stage launches against the persistent fused
+ * launch (ak_mesh_fuse) and keeps the faster.  result (may be NULL): tile, segments,
+ * order (as for ak_mesh_schedule), the chosen stage time in microseconds (with the fill
+ * and flux correction on such meshes), and 1 if the fused launch was chosen. */
+ak_status ak_mesh_autotune(ak_mesh* mesh, int32_t result[5]);
+
+/* Fused stage for meshes with a ghost fill (Section 2: static refinement; or FOFC).
+ *   fused = 1: each stage is ONE persistent cooperative launch of at most one resident
+ *              wave of CTAs: the ghost fill (copies / restrictions, then prolongations)
+ *              and the flux correction run first, spread over the whole grid and
+ *              separated by grid barriers (bounded waits: a barrier that times out counts
+ *              in ak_status_counters' timeouts, AK_ETIMEOUT), then the CTAs loop over
+ *              the stage work list;
+ *   fused = 0: separate fill, flux-correction and stage launches (default).
+ * Results are bitwise the same either way.  AK_EINVAL for fused = 1 on a mesh without
+ * a ghost fill (one level, no FOFC: its stage reads halos from the neighbour blocks). */
+ak_status ak_mesh_fuse(ak_mesh* mesh, int32_t fused);
 
 /* Sets the stage kernel's schedule explicitly (what ak_mesh_autotune picks by timing).
  *   tile:  0 = 16x16 column tiles (for the mixed PLM form: the variant with paired

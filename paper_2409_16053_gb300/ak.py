@@ -8,7 +8,7 @@ CUDA stream.
 Low level (same names and arguments as the C functions):
     ak_mesh_create, ak_mesh_destroy, ak_mesh_layout, ak_mesh_bind, ak_fill_ghosts,
     ak_stage, ak_new_dt, ak_step, ak_upload, ak_download, ak_status_counters,
-    ak_mesh_autotune, ak_mesh_schedule, ak_cfl_dt_noalloc, ak_last_error
+    ak_mesh_autotune, ak_mesh_schedule, ak_mesh_fuse, ak_cfl_dt_noalloc, ak_last_error
 High level: ``Mesh`` builds a uniform mesh of equal MeshBlocks, allocates and binds
 its registers as torch tensors, and converts between a global (5, n3, n2, n1) array
 and the library's block layout.
@@ -76,6 +76,8 @@ def _load_lib():
     lib.ak_mesh_autotune.restype = ctypes.c_int
     lib.ak_mesh_schedule.argtypes = [vp, i32, i32, i32]
     lib.ak_mesh_schedule.restype = ctypes.c_int
+    lib.ak_mesh_fuse.argtypes = [vp, i32]
+    lib.ak_mesh_fuse.restype = ctypes.c_int
     lib.ak_cfl_dt_noalloc.argtypes = [vp, i32, ctypes.POINTER(i32), i32, dp, ctypes.c_double,
                                       ctypes.c_double, vp, dp]
     lib.ak_cfl_dt_noalloc.restype = ctypes.c_int
@@ -90,7 +92,7 @@ def _load_lib():
 _lib = _load_lib()
 EXPORTED = ("ak_mesh_create", "ak_mesh_destroy", "ak_mesh_layout", "ak_mesh_bind",
             "ak_fill_ghosts", "ak_stage", "ak_new_dt", "ak_step", "ak_upload",
-            "ak_download", "ak_status_counters", "ak_mesh_autotune", "ak_mesh_schedule",
+            "ak_download", "ak_status_counters", "ak_mesh_autotune", "ak_mesh_schedule", "ak_mesh_fuse",
             "ak_cfl_dt_noalloc", "ak_last_error")
 
 
@@ -170,9 +172,10 @@ def ak_status_counters(mesh):
 
 
 def ak_mesh_autotune(mesh):
-    """Times stage-kernel schedules on this mesh and keeps the fastest.  Returns
-    (tile, segments, order, microseconds per stage launch)."""
-    out = (ctypes.c_int32 * 4)()
+    """Times stage-kernel schedules on this mesh and keeps the fastest (and, on meshes
+    with a ghost fill, the separate or the fused stage launch).  Returns (tile, segments,
+    order, microseconds per stage, fused)."""
+    out = (ctypes.c_int32 * 5)()
     _check(_lib.ak_mesh_autotune(mesh, out))
     return tuple(int(v) for v in out)
 
@@ -180,6 +183,11 @@ def ak_mesh_autotune(mesh):
 def ak_mesh_schedule(mesh, tile: int, nseg: int, order: int):
     """Sets the stage kernel's schedule (tile variant, x3 segments, CTA order)."""
     _check(_lib.ak_mesh_schedule(mesh, tile, nseg, order))
+
+
+def ak_mesh_fuse(mesh, fused: bool):
+    """Fill, flux correction and stage in one persistent cooperative launch per stage."""
+    _check(_lib.ak_mesh_fuse(mesh, 1 if fused else 0))
 
 
 def ak_cfl_dt_noalloc(reg_ptr: int, nblocks: int, nx, nghost: int, dx, gamma: float,
@@ -370,6 +378,9 @@ class Mesh:
 
     def schedule(self, tile, nseg=1, order=0):
         ak_mesh_schedule(self.handle, tile, nseg, order)
+
+    def fuse(self, fused=True):
+        ak_mesh_fuse(self.handle, fused)
 
     def register_view(self, reg=0):
         """Torch view (nblocks, 5, p3, p2, p1) of a register, ghosts included."""

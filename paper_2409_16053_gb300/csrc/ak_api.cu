@@ -405,6 +405,7 @@ extern "C" ak_status ak_mesh_create(const ak_mesh_desc* d, void* cuda_stream, ak
   m->md.nlev = X.nlev;
   m->md.ng = ng;
   m->md.nfc = m->nfc;
+  m->md.fc_cells = m->fc_cells;
   m->md.gamma = d->gamma;
   m->md.xa = m->d_xa;
   m->md.xb = m->d_xb;
@@ -615,7 +616,8 @@ extern "C" ak_status ak_stage(ak_mesh* m, int32_t stage, double dt) {
     if (s != AK_OK) return s;
   }
   if (dt > 0.0) AK_CUDA_TRY(ak_launch_set_dt(m, dt));
-  if (m->nfc) AK_CUDA_TRY(ak_launch_flux_correction(m, m->reg[stage_in_reg(m->desc.rk, stage)]));
+  if (m->nfc && !m->fused)
+    AK_CUDA_TRY(ak_launch_flux_correction(m, m->reg[stage_in_reg(m->desc.rk, stage)]));
   ak_status s = enqueue_stage(m, stage);
   if (s != AK_OK) return s;
   if (stage == m->desc.rk) AK_CUDA_TRY(ak_launch_finalize_dt(m, 0));
@@ -656,8 +658,8 @@ extern "C" ak_status ak_new_dt(ak_mesh* m, int32_t reg, double* dt_out) {
 static ak_status enqueue_step(ak_mesh* m) {
   for (int st = 1; st <= m->desc.rk; ++st) {
     double* in = m->reg[stage_in_reg(m->desc.rk, st)];
-    if (!m->md.direct) AK_CUDA_TRY(ak_launch_fill_ghosts(m, in));
-    if (m->nfc) AK_CUDA_TRY(ak_launch_flux_correction(m, in));
+    if (!m->md.direct && !m->fused) AK_CUDA_TRY(ak_launch_fill_ghosts(m, in));
+    if (m->nfc && !m->fused) AK_CUDA_TRY(ak_launch_flux_correction(m, in));
     ak_status s = enqueue_stage(m, st);
     if (s != AK_OK) return s;
   }
@@ -711,12 +713,14 @@ extern "C" ak_status ak_step(ak_mesh* m, double dt, double* dt_next) {
   return AK_OK;
 }
 
-extern "C" ak_status ak_mesh_autotune(ak_mesh* m, int32_t result[4]) {
+extern "C" ak_status ak_mesh_autotune(ak_mesh* m, int32_t result[5]) {
   if (!m) return einval("ak_mesh_autotune: NULL mesh");
   for (int r = 0; r < 2; ++r) {
     ak_status s = need_reg(m, r, "ak_mesh_autotune");
     if (s != AK_OK) return s;
   }
+  const int fused0 = m->fused;
+  m->fused = 0;
   AK_CUDA_TRY(ak_launch_fill_ghosts(m, m->reg[0]));
   if (m->nfc) AK_CUDA_TRY(ak_launch_flux_correction(m, m->reg[0]));
   cudaEvent_t ev[2];
@@ -749,10 +753,33 @@ extern "C" ak_status ak_mesh_autotune(ak_mesh* m, int32_t result[4]) {
           best_order = order;
         }
       }
+  // meshes with a ghost fill: separate fill / flux-correction / stage launches against
+  // the persistent fused launch, with the chosen schedule
+  int best_fused = 0;
+  if (e == cudaSuccess) e = ak_build_work(m, best_tile, best_seg, best_order);
+  if (!m->md.direct && e == cudaSuccess) {
+    float tf[2] = {1e30f, 1e30f};
+    for (int fu = 0; fu < 2 && e == cudaSuccess; ++fu) {
+      m->fused = fu;
+      for (int rep = 0; rep < 5 && e == cudaSuccess; ++rep) {
+        e = cudaEventRecord(ev[0], m->stream);
+        if (e == cudaSuccess && !fu) e = ak_launch_fill_ghosts(m, m->reg[0]);
+        if (e == cudaSuccess && !fu && m->nfc) e = ak_launch_flux_correction(m, m->reg[0]);
+        if (e == cudaSuccess) e = ak_launch_stage(m, 1, m->reg[0], m->reg[0], m->reg[1], 1, 0);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[1], m->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+        if (rep >= 2 && ms < tf[fu]) tf[fu] = ms;
+      }
+    }
+    best_fused = tf[1] < tf[0];
+    best = tf[best_fused];
+  }
+  m->fused = e == cudaSuccess ? best_fused : fused0;
   cudaEventDestroy(ev[0]);
   cudaEventDestroy(ev[1]);
   m->md.fofc = fofc;
-  if (e == cudaSuccess) e = ak_build_work(m, best_tile, best_seg, best_order);
   if (e != cudaSuccess) {
     ak_set_error("ak_mesh_autotune: %s", cudaGetErrorString(e));
     return AK_ECUDA;
@@ -763,7 +790,18 @@ extern "C" ak_status ak_mesh_autotune(ak_mesh* m, int32_t result[4]) {
     result[1] = best_seg;
     result[2] = best_order;
     result[3] = (int32_t)(best * 1000.0f);
+    result[4] = m->fused;
   }
+  return AK_OK;
+}
+
+extern "C" ak_status ak_mesh_fuse(ak_mesh* m, int32_t fused) {
+  if (!m) return einval("ak_mesh_fuse: NULL mesh");
+  if (fused != 0 && fused != 1) return einval("ak_mesh_fuse: fused must be 0 or 1");
+  if (fused && m->md.direct)
+    return einval("ak_mesh_fuse: this mesh has no ghost fill to fuse (uniform, no FOFC)");
+  m->fused = fused;
+  invalidate_graph(m);
   return AK_OK;
 }
 

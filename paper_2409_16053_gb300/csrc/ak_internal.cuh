@@ -28,6 +28,9 @@ struct ak_dev_scalars {
   unsigned int fofc_n;              // cells flagged by FOFC in the current stage
   unsigned int fofc_dropped;        // flagged cells beyond the list's capacity
   unsigned long long sink[2];       // counts nobody reads (recomputations)
+  unsigned int bar_count;           // grid barrier of the fused stage kernel: arrivals
+  unsigned int bar_gen;             //   and generation
+  unsigned int work_next;           // next stage tile of the fused kernel's loop
 };
 
 // One leaf MeshBlock (device table entry).
@@ -91,6 +94,7 @@ struct ak_meshdev {
   int direct;           // stage kernels read halo cells from the neighbour blocks (uniform
                         // meshes without FOFC): no ghost fill before a stage
   int nblocks, nlev, ng, nfc;
+  long long fc_cells;   // face cells of all flux-correction faces
   double gamma;
 };
 
@@ -125,6 +129,9 @@ struct ak_mesh {
   int tile;                     // stage tile: 0 = 16x16 columns, 1 = 32x8
   int nseg;                     // x3 segments per block (upper bound)
   int order;                    // 0 = block order, 1 = longest work first
+  int fused;                    // 1: meshes with a ghost fill run each stage as one
+                                // persistent cooperative launch (fill, flux correction
+                                // and stage fused); 0: separate launches
   int nfc;
   long long fc_cells;
   ak_meshdev md;

@@ -9,6 +9,7 @@
 // minmod-limited slopes of the conserved variables, U_f = U_c + sum_d (+-1/4) s_d, so the
 // eight fine cells average back to U_c.
 #include "ak_internal.cuh"
+#include "exchange.cuh"
 
 namespace {
 
@@ -18,19 +19,7 @@ __device__ __forceinline__ long long elem(const ak_block& B, int ng, int v, int 
   return B.off + v * B.var_stride + ((long long)(k + ng) * B.p2 + (j + ng)) * B.s1 + (i + ng);
 }
 
-// minmod of two differences with its sign and magnitude tests on the integer pipe:
-// 0 unless a and b are nonzero with one sign, else the one of smaller magnitude
-__device__ __forceinline__ double minmod(double a, double b) {
-  const long long ba = __double_as_longlong(a), bb = __double_as_longlong(b);
-  if ((ba ^ bb) < 0 || (ba << 1) == 0 || (bb << 1) == 0) return 0.0;
-  return (ba & 0x7fffffffffffffffll) < (bb & 0x7fffffffffffffffll) ? a : b;
-}
-
-// Ghost fill, pass 1 of the exchange plan: same-level copies and restrictions (mean of
-// the 2x2x2 fine cells).  One thread per pair of plan entries: the plan lists ghost
-// cells row by row (x fastest) in runs of even length, so two consecutive copies whose
-// destinations and sources are both contiguous and 16-byte aligned move as one 16-byte
-// load and store per variable; anything else goes cell by cell.
+// Ghost fill, pass 1 of the exchange plan: one thread per pair of plan entries.
 __global__ void fill_copy_restrict_kernel(double* reg, ak_meshdev md) {
   __shared__ long long vstride[AK_MAX_LEVELS];
   __shared__ int srow[AK_MAX_LEVELS], splane[AK_MAX_LEVELS];
@@ -40,73 +29,15 @@ __global__ void fill_copy_restrict_kernel(double* reg, ak_meshdev md) {
     splane[threadIdx.x] = md.levels[threadIdx.x].plane;
   }
   __syncthreads();
-  const long long t0 = 2 * (blockIdx.x * (long long)blockDim.x + threadIdx.x);
-  if (t0 >= md.nxa) return;
-  const ak_xfer x = md.xa[t0];
-  if (t0 + 1 < md.nxa) {
-    const ak_xfer y = md.xa[t0 + 1];
-    if ((x.info & 3) == 0 && (y.info & 3) == 0 && y.dst == x.dst + 1 && y.src == x.src + 1 &&
-        ((x.dst | x.src) & 1) == 0 && x.info == y.info) {
-      const long long vd = vstride[(x.info >> 2) & 0xff], vs = vstride[(x.info >> 10) & 0xff];
-#pragma unroll
-      for (int v = 0; v < AK_NVAR; ++v)
-        *reinterpret_cast<double2*>(reg + x.dst + v * vd) =
-            *reinterpret_cast<const double2*>(reg + x.src + v * vs);
-      return;
-    }
-  }
-  for (long long t = t0; t < t0 + 2 && t < md.nxa; ++t) {
-    const ak_xfer z = t == t0 ? x : md.xa[t];
-    const int ld = (z.info >> 2) & 0xff, ls = (z.info >> 10) & 0xff;
-    const long long vd = vstride[ld], vs = vstride[ls];
-    if ((z.info & 3) == 0) {
-#pragma unroll
-      for (int v = 0; v < AK_NVAR; ++v) reg[z.dst + v * vd] = reg[z.src + v * vs];
-    } else {
-      const int row = srow[ls], plane = splane[ls];
-#pragma unroll
-      for (int v = 0; v < AK_NVAR; ++v) {
-        const double* f = reg + z.src + v * vs;
-        double s = 0.0;
-        for (int dz = 0; dz < 2; ++dz)
-          for (int dy = 0; dy < 2; ++dy)
-            for (int dx = 0; dx < 2; ++dx) s += f[dz * plane + dy * row + dx];
-        reg[z.dst + v * vd] = s / 8.0;
-      }
-    }
-  }
+  ak::xfer_pass1_pair(reg, md, blockIdx.x * (long long)blockDim.x + threadIdx.x, vstride, srow,
+                      splane);
 }
 
 // Ghost fill, pass 2 of the exchange plan: prolongation, after pass 1 has made every
-// coarse value it reads final (proper nesting).  One thread per coarse cell: its three
-// minmod slopes once, then every fine ghost child it owns, U_f = U_c + sum_d (+-1/4) s_d
-// (added in the order x, y, z).
+// coarse value it reads final (proper nesting).  One thread per coarse cell.
 __global__ void fill_prolong_kernel(double* reg, ak_meshdev md) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= md.nxb) return;
-  const ak_xfer x = md.xb[t];
-  const ak_level D = md.levels[(x.info >> 2) & 0xff];
-  const ak_level C = md.levels[(x.info >> 10) & 0xff];
-  const int mask = (x.info >> 18) & 0xff;
-  const long long st[3] = {1, C.row, C.plane};
-#pragma unroll
-  for (int v = 0; v < AK_NVAR; ++v) {
-    const double* c = reg + x.src + v * C.var_stride;
-    const double uc = c[0];
-    double s[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) s[d] = 0.25 * minmod(c[st[d]] - uc, uc - c[-st[d]]);
-    double* f = reg + x.dst + v * D.var_stride;
-#pragma unroll
-    for (int ch = 0; ch < 8; ++ch) {
-      if (!((mask >> ch) & 1)) continue;
-      double u = uc;
-      u += (ch & 1) ? s[0] : -s[0];
-      u += (ch & 2) ? s[1] : -s[1];
-      u += (ch & 4) ? s[2] : -s[2];
-      f[(ch & 1) + ((ch >> 1) & 1) * (long long)D.row + ((ch >> 2) & 1) * (long long)D.plane] = u;
-    }
-  }
+  if (t < md.nxb) ak::xfer_prolong(reg, md, t);
 }
 
 // packed[pack_off[b]*5 + (v*nx3 + k)*nx2*nx1 + j*nx1 + i] <-> register layout

@@ -51,12 +51,15 @@ struct StageCfg {
       sizeof(double) * (size_t)OUT + sizeof(R) * (size_t)(NR * 5 * NPL + 2 * EB + F1 + F2);
 };
 
-template <int NG, bool MIXED, int TX, int TY, bool TMA_OUT>
+// PERSIST: the persistent fused form for meshes that need a ghost fill (static
+// refinement, FOFC): a cooperative launch of at most one resident wave of CTAs first runs
+// the fill and the flux correction (fused_prologue), then loops over the work list.
+template <int NG, bool MIXED, int TX, int TY, bool TMA_OUT, bool PERSIST = false>
 __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
-    stage_kernel(const double* __restrict__ uin, const double* u0, double* uout, ak_meshdev md,
-                 const ak_work* __restrict__ work, Bg bg, double a, double b, int form,
-                 ak_dev_scalars* sc, int last_stage,
-                 const __grid_constant__ CUtensorMap tmap_out) {
+    stage_kernel(const double* __restrict__ uin_arg, const double* u0, double* uout,
+                 ak_meshdev md, const ak_work* __restrict__ work, Bg bg, double a, double b,
+                 int form, ak_dev_scalars* sc, int last_stage,
+                 const __grid_constant__ CUtensorMap tmap_out, int nwork) {
   // form: 0 = first stage U + dt L; 1 = RK2 final (U0 + U + dt L) / 2;
   //       2 = a U0 + b (U + dt L)
   using C = StageCfg<NG, MIXED, TX, TY, TMA_OUT>;
@@ -75,9 +78,20 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
   __shared__ double red[NT / 32];
   __shared__ long long nbr[27];  // direct halo reads: the neighbour blocks
 
+  if constexpr (PERSIST) {
+    constexpr int KB = C::bytes / (NT * 80) < 8 ? (int)(C::bytes / (NT * 80)) : 8;
+    static_assert(KB >= 1, "no room to stage the fill");
+    fused_prologue<NG, MIXED, KB>(launder(const_cast<double*>(uin_arg)), md, bg, sc, smem_raw);
+  }
+  // one tile per CTA, or (persistent) tiles taken from the list until it runs out
+  __shared__ int wslot;
+  for (int it = 0; it < (PERSIST ? 0x7fffffff : 1); ++it) {
+  const int wi = PERSIST ? next_tile(sc, &wslot) : (int)blockIdx.x;
+  if (PERSIST && wi >= nwork) break;
+  const double* __restrict__ uin = PERSIST ? launder(uin_arg) : uin_arg;
   const int tid = threadIdx.x;
   // this CTA's column tile of one MeshBlock, and that block's geometry
-  const ak_work w = work[blockIdx.x];
+  const ak_work w = work[wi];
   const ak_block g = md.blocks[w.block];
   if (md.direct) neighbour_table(md, w.block, nbr);
   __syncthreads();
@@ -433,6 +447,8 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
         atomicMin(&sc->dtmin_bits, (unsigned long long)__double_as_longlong(v));
     }
   }
+  if constexpr (PERSIST) __syncthreads();  // the next tile reuses the shared memory
+  }
 }
 
 static Bg make_bg(const ak_mesh* m);
@@ -443,100 +459,35 @@ static cudaError_t launch(const ak_mesh* m, const double* uin, const double* u0,
                           bool prepare_only) {
   const size_t smem = StageCfg<NG, MIXED, TX, TY, TMA_OUT>::bytes;
   auto kern = stage_kernel<NG, MIXED, TX, TY, TMA_OUT>;
-  if (prepare_only)
-    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (prepare_only) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if constexpr (!TMA_OUT) {
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(stage_kernel<NG, MIXED, TX, TY, false, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    }
+    return e;
+  }
   const Bg bg = make_bg(m);
   const int form = rk2_final ? 1 : (a == 0.0 ? 0 : 2);
+  if (m->fused) {
+    if constexpr (!TMA_OUT) {
+      auto pk = stage_kernel<NG, MIXED, TX, TY, false, true>;
+      return launch_persistent(m, pk, TX * TY, smem, uin, u0, uout, m->md, m->d_work, bg, a, b,
+                               form, m->d_sc, last_stage, m->tmap[out_reg], m->nwork);
+    }
+  }
   kern<<<(unsigned)m->nwork, TX * TY, smem, m->stream>>>(uin, u0, uout, m->md, m->d_work, bg, a,
                                                           b, form, m->d_sc, last_stage,
-                                                          m->tmap[out_reg]);
+                                                          m->tmap[out_reg], m->nwork);
   return cudaGetLastError();
 }
 
-// Flux correction at level boundaries (Section 2): for every coarse face cell next to a
-// refined region, the mean of the 2x2 fine fluxes through it, computed from the fine
-// block's cells (interior and prolonged ghosts) with the same reconstruction and HLLC
-// code the stage kernel runs, so the fine block's own update sees the same fluxes.
 template <int NG, bool MIXED>
 __global__ void flux_correction_kernel(const double* __restrict__ reg, ak_meshdev md, Bg bg,
                                        ak_dev_scalars* sc, long long ncells) {
-  using R = typename std::conditional<MIXED, float, double>::type;
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= ncells) return;
-  int lo = 0, hi = md.nfc - 1;  // face entry holding cell t
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (md.fc[mid].z <= t) lo = mid; else hi = mid - 1;
-  }
-  const int4 F = md.fc[lo];
-  const int cell = (int)(t - F.z);
-  const ak_block B = md.blocks[F.x];
-  const int d = F.y >> 1, side = F.y & 1;
-  const int n[3] = {B.nx1, B.nx2, B.nx3};
-  const int org[3] = {B.lx1, B.lx2, B.lx3};
-  const int a1 = d == 0 ? 1 : 0, a2 = d == 2 ? 1 : 2;
-  int loc[3];
-  loc[d] = side ? n[d] - 1 : 0;
-  loc[a1] = cell % n[a1];
-  loc[a2] = cell / n[a1];
-  const ak_level LV = md.levels[B.level];
-  const int nl[3] = {LV.n1, LV.n2, LV.n3};
-  int N[3];
-  for (int q = 0; q < 3; ++q) {
-    int v = org[q] + loc[q] + (q == d ? (side ? 1 : -1) : 0);
-    N[q] = v < 0 ? v + nl[q] : (v >= nl[q] ? v - nl[q] : v);
-  }
-  const ak_level LF = md.levels[B.level + 1];
-  const int fine = md.map[LF.map_off + ((2 * N[2] / LF.bs3) * LF.md2 + 2 * N[1] / LF.bs2) * LF.md1 +
-                          2 * N[0] / LF.bs1];
-  const ak_block Fb = md.blocks[fine];
-  const int forg[3] = {Fb.lx1, Fb.lx2, Fb.lx3};
-  const Counters cn{&sc->counters[0], &sc->counters[1]};
-  R sum[5] = {R(0), R(0), R(0), R(0), R(0)};
-  for (int u2 = 0; u2 < 2; ++u2)
-    for (int u1 = 0; u1 < 2; ++u1) {
-      int q[3];
-      q[d] = (side ? 2 * N[d] : 2 * N[d] + 1) - forg[d];
-      q[a1] = 2 * N[a1] + u1 - forg[a1];
-      q[a2] = 2 * N[a2] + u2 - forg[a2];
-      const int fi = q[d] + (side ? 0 : 1);  // the face between fine cells fi-1 and fi
-      R W[2 * NG][5];
-#pragma unroll
-      for (int mm = 0; mm < 2 * NG; ++mm) {
-        int c[3] = {q[0], q[1], q[2]};
-        c[d] = fi - NG + mm;
-        const long long e = Fb.off + ((long long)(c[2] + NG) * Fb.p2 + (c[1] + NG)) * Fb.s1 +
-                            (c[0] + NG);
-        double u[5];
-#pragma unroll
-        for (int v = 0; v < 5; ++v) u[v] = reg[e + v * Fb.var_stride];
-        c2p(u, W[mm], bg, cn);
-      }
-      R lo_a[5], hi_a[5], lo_b[5], hi_b[5];
-#pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        R qa[2 * NG - 1], qb[2 * NG - 1];
-#pragma unroll
-        for (int mm = 0; mm < 2 * NG - 1; ++mm) {
-          qa[mm] = W[mm][v];
-          qb[mm] = W[mm + 1][v];
-        }
-        edges<NG>(qa, lo_a[v], hi_a[v], bg.recon);
-        edges<NG>(qb, lo_b[v], hi_b[v], bg.recon);
-      }
-      R f[5];
-      solve(d, hi_a, lo_b, bg, f);
-#pragma unroll
-      for (int v = 0; v < 5; ++v) sum[v] += f[v];
-    }
-  double* out = md.fcbuf + (long long)(B.ovr[F.y] + cell) * 5;
-#pragma unroll
-  for (int v = 0; v < 5; ++v) {
-    if constexpr (MIXED)
-      out[v] = f32_to_f64(R(0.25) * sum[v]);
-    else
-      out[v] = R(0.25) * sum[v];
-  }
+  if (t < ncells) flux_correction_cell<NG, MIXED>(reg, md, bg, sc, t);
 }
 
 Bg stage_bg(const ak_mesh* m) { return make_bg(m); }

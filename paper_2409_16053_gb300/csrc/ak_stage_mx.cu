@@ -54,11 +54,13 @@ struct MxCfg {
                                   sizeof(float) * (NR * 5 * NPL + 4 * 5 * NE + 2 * 5 * NF);
 };
 
-template <int NG, int T>
+// PERSIST: the persistent fused form (see stage_kernel): ghost fill and flux correction
+// in a cooperative prologue, then a loop over the work list.
+template <int NG, int T, bool PERSIST = false>
 __global__ void __launch_bounds__(MxCfg<NG, T>::NTH, 2)
-    stage_mx_kernel(const double* __restrict__ uin, const double* u0, double* uout,
+    stage_mx_kernel(const double* __restrict__ uin_arg, const double* u0, double* uout,
                     ak_meshdev md, const ak_work* __restrict__ work, Bg bg, double a, double b,
-                    int form, ak_dev_scalars* sc, int last_stage) {
+                    int form, ak_dev_scalars* sc, int last_stage, int nwork) {
   // form: 0 = first stage U + dt L; 1 = RK2 final (U0 + U + dt L) / 2;
   //       2 = a U0 + b (U + dt L)
   using C = MxCfg<NG, T>;
@@ -78,8 +80,19 @@ __global__ void __launch_bounds__(MxCfg<NG, T>::NTH, 2)
   __shared__ double red[C::NTH / 32];
   __shared__ long long nbr[27];  // direct halo reads: the neighbour blocks
 
+  if constexpr (PERSIST) {
+    constexpr int KB = C::bytes / (C::NTH * 80) < 8 ? (int)(C::bytes / (C::NTH * 80)) : 8;
+    static_assert(KB >= 1, "no room to stage the fill");
+    fused_prologue<NG, true, KB>(launder(const_cast<double*>(uin_arg)), md, bg, sc, smem_raw);
+  }
+  // one tile per CTA, or (persistent) tiles taken from the list until it runs out
+  __shared__ int wslot;
+  for (int it = 0; it < (PERSIST ? 0x7fffffff : 1); ++it) {
+  const int wi = PERSIST ? next_tile(sc, &wslot) : (int)blockIdx.x;
+  if (PERSIST && wi >= nwork) break;
+  const double* __restrict__ uin = PERSIST ? launder(uin_arg) : uin_arg;
   const int tid = threadIdx.x;
-  const ak_work w = work[blockIdx.x];
+  const ak_work w = work[wi];
   const ak_block g = md.blocks[w.block];
   if (md.direct) neighbour_table(md, w.block, nbr);
   const int i0 = w.i0, j0 = w.j0, k0 = w.k0, k1 = w.k1;
@@ -434,6 +447,8 @@ __global__ void __launch_bounds__(MxCfg<NG, T>::NTH, 2)
       if (tid == 0) atomicMin(&sc->dtmin_bits, (unsigned long long)__double_as_longlong(v));
     }
   }
+  if constexpr (PERSIST) __syncthreads();  // the next tile reuses the shared memory
+  }
 }
 
 }  // namespace
@@ -443,10 +458,19 @@ cudaError_t launch_stage_mx(const ak_mesh* m, const double* uin, const double* u
                             bool prepare_only) {
   using C = MxCfg<2, 16>;
   auto kern = stage_mx_kernel<2, 16>;
-  if (prepare_only)
-    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::bytes);
+  auto pk = stage_mx_kernel<2, 16, true>;
+  if (prepare_only) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::bytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(pk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::bytes);
+    return e;
+  }
+  if (m->fused)
+    return launch_persistent(m, pk, C::NTH, C::bytes, uin, u0, uout, m->md, m->d_work, bg, a, b,
+                             form, m->d_sc, last_stage, m->nwork);
   kern<<<(unsigned)m->nwork, C::NTH, C::bytes, m->stream>>>(uin, u0, uout, m->md, m->d_work, bg,
-                                                            a, b, form, m->d_sc, last_stage);
+                                                            a, b, form, m->d_sc, last_stage,
+                                                            m->nwork);
   return cudaGetLastError();
 }
 

@@ -5,9 +5,11 @@
 #pragma once
 
 #include <type_traits>
+#include <utility>
 
 #include "ak_internal.cuh"
 #include "hydro_ops.cuh"
+#include "exchange.cuh"
 
 namespace ak {
 
@@ -158,11 +160,178 @@ __device__ __forceinline__ double half(double x) {
 // The corrected (fine-mean) flux of one coarse face cell from the correction buffer.
 __device__ __forceinline__ void corrected_flux(const double* buf, int cell, double* f) {
 #pragma unroll
-  for (int v = 0; v < 5; ++v) f[v] = buf[(long long)cell * 5 + v];
+  for (int v = 0; v < 5; ++v) f[v] = __ldcg(buf + (long long)cell * 5 + v);
 }
 __device__ __forceinline__ void corrected_flux(const double* buf, int cell, float* f) {
 #pragma unroll
-  for (int v = 0; v < 5; ++v) f[v] = f64_to_f32(buf[(long long)cell * 5 + v]);
+  for (int v = 0; v < 5; ++v) f[v] = f64_to_f32(__ldcg(buf + (long long)cell * 5 + v));
+}
+
+// Flux correction at level boundaries (Section 2): for every coarse face cell next to a
+// refined region, the mean of the 2x2 fine fluxes through it, computed from the fine
+// block's cells (interior and prolonged ghosts) with the same reconstruction and HLLC
+// code the stage kernel runs (register reads through L2 only, as the fused stage kernel
+// needs), so the fine block's own update sees the same fluxes.
+template <int NG, bool MIXED>
+__device__ __forceinline__ void flux_correction_cell(const double* reg, const ak_meshdev& md,
+                                                     const Bg& bg, ak_dev_scalars* sc,
+                                                     long long t) {
+  using R = typename std::conditional<MIXED, float, double>::type;
+  int lo = 0, hi = md.nfc - 1;  // face entry holding cell t
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (md.fc[mid].z <= t) lo = mid; else hi = mid - 1;
+  }
+  const int4 F = md.fc[lo];
+  const int cell = (int)(t - F.z);
+  const ak_block B = md.blocks[F.x];
+  const int d = F.y >> 1, side = F.y & 1;
+  const int n[3] = {B.nx1, B.nx2, B.nx3};
+  const int org[3] = {B.lx1, B.lx2, B.lx3};
+  const int a1 = d == 0 ? 1 : 0, a2 = d == 2 ? 1 : 2;
+  int loc[3];
+  loc[d] = side ? n[d] - 1 : 0;
+  loc[a1] = cell % n[a1];
+  loc[a2] = cell / n[a1];
+  const ak_level LV = md.levels[B.level];
+  const int nl[3] = {LV.n1, LV.n2, LV.n3};
+  int N[3];
+  for (int q = 0; q < 3; ++q) {
+    int v = org[q] + loc[q] + (q == d ? (side ? 1 : -1) : 0);
+    N[q] = v < 0 ? v + nl[q] : (v >= nl[q] ? v - nl[q] : v);
+  }
+  const ak_level LF = md.levels[B.level + 1];
+  const int fine = md.map[LF.map_off + ((2 * N[2] / LF.bs3) * LF.md2 + 2 * N[1] / LF.bs2) * LF.md1 +
+                          2 * N[0] / LF.bs1];
+  const ak_block Fb = md.blocks[fine];
+  const int forg[3] = {Fb.lx1, Fb.lx2, Fb.lx3};
+  const Counters cn{&sc->counters[0], &sc->counters[1]};
+  R sum[5] = {R(0), R(0), R(0), R(0), R(0)};
+  for (int u2 = 0; u2 < 2; ++u2)
+    for (int u1 = 0; u1 < 2; ++u1) {
+      int q[3];
+      q[d] = (side ? 2 * N[d] : 2 * N[d] + 1) - forg[d];
+      q[a1] = 2 * N[a1] + u1 - forg[a1];
+      q[a2] = 2 * N[a2] + u2 - forg[a2];
+      const int fi = q[d] + (side ? 0 : 1);  // the face between fine cells fi-1 and fi
+      R W[2 * NG][5];
+#pragma unroll
+      for (int mm = 0; mm < 2 * NG; ++mm) {
+        int c[3] = {q[0], q[1], q[2]};
+        c[d] = fi - NG + mm;
+        const long long e = Fb.off + ((long long)(c[2] + NG) * Fb.p2 + (c[1] + NG)) * Fb.s1 +
+                            (c[0] + NG);
+        double u[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) u[v] = __ldcg(reg + e + v * Fb.var_stride);
+        c2p(u, W[mm], bg, cn);
+      }
+      R lo_a[5], hi_a[5], lo_b[5], hi_b[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        R qa[2 * NG - 1], qb[2 * NG - 1];
+#pragma unroll
+        for (int mm = 0; mm < 2 * NG - 1; ++mm) {
+          qa[mm] = W[mm][v];
+          qb[mm] = W[mm + 1][v];
+        }
+        edges<NG>(qa, lo_a[v], hi_a[v], bg.recon);
+        edges<NG>(qb, lo_b[v], hi_b[v], bg.recon);
+      }
+      R f[5];
+      solve(d, hi_a, lo_b, bg, f);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) sum[v] += f[v];
+    }
+  double* out = md.fcbuf + (long long)(B.ovr[F.y] + cell) * 5;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    if constexpr (MIXED)
+      out[v] = f32_to_f64(R(0.25) * sum[v]);
+    else
+      out[v] = R(0.25) * sum[v];
+  }
+}
+
+// A pointer the compiler cannot relate to any other (so no restrict promise of a kernel
+// parameter carries over to the accesses made through it).
+template <typename T>
+__device__ __forceinline__ T* launder(T* p) {
+  T* q;
+  asm volatile("mov.b64 %0, %1;" : "=l"(q) : "l"(p) : "memory");
+  return q;
+}
+
+// Prologue of the persistent fused stage kernel (static refinement, Section 2): the
+// ghost fill of the stage's input register (pass 1, then pass 2) and the flux
+// correction, each spread over all threads of the cooperative grid and separated by
+// grid barriers; a last barrier makes everything visible to the stage tiles.
+// smem: the kernel's dynamic shared memory, idle until the stage tiles start; KB
+// 16-byte-pair slots per thread of it (5 x 16 B each) stage the pass-1 copies.
+template <int NG, bool MIXED, int KB>
+__device__ __forceinline__ void fused_prologue(double* reg, const ak_meshdev& md, const Bg& bg,
+                                               ak_dev_scalars* sc, unsigned char* smem) {
+  __shared__ long long vstride[AK_MAX_LEVELS];
+  __shared__ int srow[AK_MAX_LEVELS], splane[AK_MAX_LEVELS];
+  if (threadIdx.x < md.nlev) {
+    vstride[threadIdx.x] = md.levels[threadIdx.x].var_stride;
+    srow[threadIdx.x] = md.levels[threadIdx.x].row;
+    splane[threadIdx.x] = md.levels[threadIdx.x].plane;
+  }
+  __syncthreads();
+  const long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long gs = (long long)gridDim.x * blockDim.x;
+  double2* buf = reinterpret_cast<double2*>(smem) + (long long)threadIdx.x * KB * AK_NVAR;
+  for (long long p = gt; p < (md.nxa + 1) / 2; p += KB * gs)
+    xfer_pass1_staged<KB>(reg, md, p, gs, buf, vstride, srow, splane);
+  // the prolongations and the face cells of the flux correction are few: spread them
+  // across the CTAs (item t to CTA t mod grid), not over the first CTAs' threads
+  const long long gi = (long long)threadIdx.x * gridDim.x + blockIdx.x;
+  if (md.nxb) {
+    grid_barrier(sc);
+    for (long long t = gi; t < md.nxb; t += gs) xfer_prolong(reg, md, t);
+  }
+  if (md.nfc) {
+    grid_barrier(sc);
+    for (long long t = gi; t < md.fc_cells; t += gs) flux_correction_cell<NG, MIXED>(reg, md, bg, sc, t);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) sc->work_next = 0u;  // tiles are handed out next
+  grid_barrier(sc);
+}
+
+// Cooperative launch of a persistent stage kernel over the mesh's work list: at most
+// one resident wave of CTAs (the occupancy of `kern` times the SM count), so that the
+// grid barriers of its prologue are met by every CTA.
+template <typename... P, typename... A>
+inline cudaError_t launch_persistent(const ak_mesh* m, void (*kern)(P...), int threads,
+                                     size_t smem, A&&... args) {
+  int dev = 0, nsm = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+  const long long cap = (long long)per_sm * nsm;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(m->nwork < cap ? m->nwork : cap));
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = m->stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<A>(args)...);
+}
+
+// Index of the next stage tile of a persistent kernel: handed out one by one from a
+// device counter (reset by the prologue), so CTAs that finish early take more tiles.
+__device__ __forceinline__ int next_tile(ak_dev_scalars* sc, int* slot) {
+  if (threadIdx.x == 0) *slot = (int)atomicAdd(&sc->work_next, 1u);
+  __syncthreads();
+  return *slot;
 }
 
 // FOFC flag of an updated cell (Section 3): density or internal energy not positive,

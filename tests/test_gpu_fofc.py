@@ -122,3 +122,22 @@ def test_refined_mesh_cold_shear_parity(ak, precision, tol):
         assert c[3] == flagged, (c[3], flagged)
     else:
         assert c[3] > 0
+
+
+def test_fused_launch_bitwise_with_fofc(ak):
+    # a uniform FOFC mesh needs a ghost fill: the fused stage launch gives the same bits
+    outs = []
+    for fused in (False, True):
+        U = pgen.turbulence(N, seed=3, kmin=1, kmax=6, mach=5.0)
+        g = oracle.Grid(N)
+        m = ak.Mesh(N, (12, 12, 12), fofc=True)
+        m.fuse(fused)
+        m.upload(U)
+        for _ in range(12):
+            dt = oracle.new_dt(U, g, 0.3)
+            U, _ = oracle.rk_step(U, g, dt, 2)
+            m.step(dt, want_dt_next=False)
+        outs.append((m.download(), m.counters()))
+        m.close()
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert outs[0][1] == outs[1][1] and outs[0][1][3] > 0

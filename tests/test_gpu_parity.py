@@ -357,7 +357,7 @@ def test_autotune_keeps_results_bitwise(ak, precision):
     U0 = pgen.turbulence(root, seed=4, kmin=1, kmax=6, mach=0.8)
     a = _mesh(ak, root, block, precision=precision, ref_rho=1.0, ref_p=1.0)
     a.upload(U0)
-    tile, seg, order, us = a.autotune()
+    tile, seg, order, us, fused = a.autotune()
     assert tile in (0, 1, 2) and seg >= 1 and order in (0, 1) and us > 0
     b = _mesh(ak, root, block, precision=precision, ref_rho=1.0, ref_p=1.0)
     b.upload(U0)

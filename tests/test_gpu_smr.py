@@ -193,3 +193,31 @@ def test_smr_mixed_kernel_variants_bitwise(ak):
             ref = out
         else:
             assert np.array_equal(out, ref), (tile, seg, order)
+
+
+@pytest.mark.parametrize("precision,recon", [(0, 0), (1, 0), (0, 1), (1, 3)])
+def test_smr_fused_launch_bitwise(ak, precision, recon):
+    """The persistent fused stage (fill, flux correction and stage in one cooperative
+    launch) gives the bits of the separate launches."""
+    t = pgen.nested_refinement_blocks(32, 8, 8, 2)
+    P = _smooth(t, 32)
+    outs = []
+    for fused in (False, True):
+        m = _gpu_mesh(ak, t, 32, precision=precision, recon=recon, rk=3 if recon else 2,
+                      ref_rho=1.0, ref_p=1.0)
+        m.fuse(fused)
+        m.upload_packed(P)
+        dt = m.new_dt()
+        for _ in range(3):
+            m.step(dt, want_dt_next=False)
+        outs.append(m.download_packed())
+        assert m.counters()[:3] == [0, 0, 0]   # no floors, non-finite cells or timeouts
+        m.close()
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_fuse_refused_without_ghost_fill(ak):
+    m = ak.Mesh((32, 32, 32), (16, 16, 16))
+    with pytest.raises(ak.AkError):
+        m.fuse(True)
+    m.close()

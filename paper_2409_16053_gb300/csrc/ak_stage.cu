@@ -353,13 +353,7 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
         double r;
         if constexpr (MIXED) {
           const float L = -fmaf(d1, (float)idx1, fmaf(d2, (float)idx2, d3 * (float)idx3));
-          const double Ld = f32_to_f64(L);
-          if (form == 1)
-            r = half(u0k[v] + fma(dt, Ld, uik[v]));
-          else if (form == 0)
-            r = fma(dt, Ld, uik[v]);
-          else
-            r = fma(b, fma(dt, Ld, uik[v]), a * u0k[v]);
+          r = rk_update_mixed(form, a, b, dt, L, uik[v], u0k[v]);
         } else {
           const double L = -fma(d1, idx1, fma(d2, idx2, d3 * idx3));
           r = fma(dt, L, uin[e + v * g.var_stride]);

@@ -335,15 +335,8 @@ __global__ void __launch_bounds__(MxCfg<NG, T>::NTH, 2)
           const float d2 = f2[v * NF + (ty + 1) * TX + tx] - f2[v * NF + ty * TX + tx];
           const float d3 = f3hi[v] - f3lo[v];
           const float L = -fmaf(d1, idx1f, fmaf(d2, idx2f, d3 * idx3f));
-          const double Ld = f32_to_f64(L);
-          const double uik = ucol[v * NOWN + tid];
-          double r;
-          if (form == 1)
-            r = half(ucol[(5 + v) * NOWN + tid] + fma(dt, Ld, uik));
-          else if (form == 0)
-            r = fma(dt, Ld, uik);
-          else
-            r = fma(b, fma(dt, Ld, uik), a * ucol[(5 + v) * NOWN + tid]);
+          const double r =
+              rk_update_mixed(form, a, b, dt, L, ucol[v * NOWN + tid], ucol[(5 + v) * NOWN + tid]);
           un[v] = r;
           uout[e + v * vst] = r;
         }

@@ -169,4 +169,5 @@ __device__ __forceinline__ double sqrt64(double x) {
   return x * rsqrt64(x);
 }
 
+
 }  // namespace ak

@@ -334,6 +334,16 @@ __device__ __forceinline__ int next_tile(ak_dev_scalars* sc, int* slot) {
   return *slot;
 }
 
+// RK stage update of one conserved value in the mixed form (Section 3), in FP64 from
+// the FP32 L:  form 0: u + dt L;  form 1: (u0 + u + dt L) / 2;  form 2: a u0 + b (u + dt L)
+__device__ __forceinline__ double rk_update_mixed(int form, double a, double b, double dt,
+                                                  float L, double u, double u0) {
+  const double Ld = f32_to_f64(L);
+  if (form == 0) return fma(dt, Ld, u);
+  if (form == 1) return half(u0 + fma(dt, Ld, u));
+  return fma(b, fma(dt, Ld, u), a * u0);
+}
+
 // FOFC flag of an updated cell (Section 3): density or internal energy not positive,
 // i.e. rho <= 0 or rho (2E) - |M|^2 <= 0.  Flagged cells go to the mesh's list and
 // flag array for the correction kernel (cells beyond the list's capacity are counted

@@ -46,8 +46,8 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes per cell of the stage kernels (dram__bytes_read.sum + dram__bytes_write.sum
 # of one ncu capture, 192^3 in 64^3 blocks; the per-cell figure carries over to 256^3 in
 # the same blocks), valid for the kernel sources with this hash (else traffic = null)
-TRAFFIC_SRC_HASH = "1028413cfd19e8b8b420486e8e922075b3ac0670"
-TRAFFIC_B_PER_CELL = {"fp64": (85.76, 128.76), "mixed": (83.92, 126.94)}
+TRAFFIC_SRC_HASH = "cdb5446cc3fb2ec2213eb5cda6f36cf86c51eae3"
+TRAFFIC_B_PER_CELL = {"fp64": (85.87, 128.78), "mixed": (83.94, 126.99)}
 
 
 def kernel_source_hash():

@@ -55,8 +55,8 @@ def kernel_source_hash():
     import hashlib
     d = os.path.join(ROOT, "paper_2409_16053_gb300", "csrc")
     lines = ""
-    for f in ("ak_stage.cu", "ak_stage_mx.cu", "stage_common.cuh", "hydro_ops.cuh", "lanes.cuh",
-              "fastmath.cuh", "exchange.cuh"):
+    for f in ("stage_kernel.cuh", "ak_stage_plm.cu", "ak_stage_mx.cu", "stage_common.cuh",
+              "hydro_ops.cuh", "lanes.cuh", "fastmath.cuh", "exchange.cuh"):
         h = hashlib.sha1(open(os.path.join(d, f), "rb").read()).hexdigest()
         lines += f"{h}  ../paper_2409_16053_gb300/csrc/{f}\n"
     return hashlib.sha1(lines.encode()).hexdigest()

@@ -32,7 +32,8 @@ struct Bg {
   float gamma_f;
   double kq;             // (gamma + 1) / (2 gamma), for the shock speed factor
   double gm1;            // gamma - 1
-  float ug_floor_f;      // u_g floor minus u_g,b, rounded (mixed form)
+  float ug_floor_f;      // mixed form: u_g floor minus u_g,b, rounded
+  double rho_min;        // mixed form: density floor
   float gm1_f;           // gamma - 1, gamma / (gamma - 1), (gamma + 1) / (2 gamma) and
   float gg_f;            // p_b = (gamma - 1) u_g,b, rounded (mixed form)
   float kq_f;
@@ -419,19 +420,6 @@ __device__ __forceinline__ void ppm_edges_v(V q0, V q1, V q2, V q3, V q4, V& lo,
   hi = vsel(flat, a, n_hi);
 }
 
-// Full density and pressure of a mixed-form face state, kept positive.  A floored cell
-// has deviations that cancel the background to within FP32 rounding, so rho_b + rho' or
-// p_b + p' can come out zero or slightly negative; they are raised to tiny positive
-// values (and p' with p) so the sound speed stays finite.  Other states are untouched.
-template <typename V>
-__device__ __forceinline__ void positive_rp(V& r, V& p, V& dp, const V& pb) {
-  const V rmin = vset<V>(1.0e-30f), pmin = vset<V>(1.0e-30f);
-  r = vsel(vgt(r, rmin), r, rmin);
-  const auto ok = vgt(p, pmin);
-  dp = vsel(ok, dp, vsub(pmin, pb));
-  p = vsel(ok, p, pmin);
-}
-
 // HLLC, mixed form.  w = (rho - rho_b, u_n, u_t1, u_t2, u_g - u_g,b) in FP32.  Returns
 // F - (0, p_b, 0, 0, 0).  Every difference of two O(1) quantities is formed from the
 // deviations, so that a perturbation of relative size 1e-6 keeps ~7 digits.  Without
@@ -444,10 +432,8 @@ __device__ __forceinline__ void hllc_mixed(const V* wl, const V* wr, const Bg& b
   const V pb = vset<V>(bg.pb_f);
   V rl = vadd(vset<V>(bg.rho_f), wl[0]), rr = vadd(vset<V>(bg.rho_f), wr[0]);
   const V ul = wl[1], ur = wr[1];
-  V dpl = vmul(gm1, wl[4]), dpr = vmul(gm1, wr[4]);  // p - p_b
-  V pl = vadd(pb, dpl), pr = vadd(pb, dpr);          // full pressures
-  positive_rp(rl, pl, dpl, pb);
-  positive_rp(rr, pr, dpr, pb);
+  const V dpl = vmul(gm1, wl[4]), dpr = vmul(gm1, wr[4]);  // p - p_b
+  const V pl = vadd(pb, dpl), pr = vadd(pb, dpr);          // full pressures
   const V kel = vmul(vmul(half, rl), vfma(ul, ul, vfma(wl[2], wl[2], vmul(wl[3], wl[3]))));
   const V ker = vmul(vmul(half, rr), vfma(ur, ur, vfma(wr[2], wr[2], vmul(wr[3], wr[3]))));
   const V hl = vfma(gg, pl, kel);                          // E + p
@@ -540,10 +526,8 @@ __device__ __forceinline__ void llf_mixed(const V* wl, const V* wr, const Bg& bg
   const V g = vset<V>(bg.gamma_f), gm1 = vset<V>(bg.gm1_f), gg = vset<V>(bg.gg_f);
   const V pb = vset<V>(bg.pb_f);
   V rl = vadd(vset<V>(bg.rho_f), wl[0]), rr = vadd(vset<V>(bg.rho_f), wr[0]);
-  V dpl = vmul(gm1, wl[4]), dpr = vmul(gm1, wr[4]);
-  V pl = vadd(pb, dpl), pr = vadd(pb, dpr);
-  positive_rp(rl, pl, dpl, pb);
-  positive_rp(rr, pr, dpr, pb);
+  const V dpl = vmul(gm1, wl[4]), dpr = vmul(gm1, wr[4]);
+  const V pl = vadd(pb, dpl), pr = vadd(pb, dpr);
   const V kel = vmul(vmul(half, rl), vfma(wl[1], wl[1], vfma(wl[2], wl[2], vmul(wl[3], wl[3]))));
   const V ker = vmul(vmul(half, rr), vfma(wr[1], wr[1], vfma(wr[2], wr[2], vmul(wr[3], wr[3]))));
   const V gpl = vmul(g, pl), gpr = vmul(g, pr);
@@ -567,10 +551,8 @@ __device__ __forceinline__ void hlle_mixed(const V* wl, const V* wr, const Bg& b
   const V pb = vset<V>(bg.pb_f);
   V rl = vadd(vset<V>(bg.rho_f), wl[0]), rr = vadd(vset<V>(bg.rho_f), wr[0]);
   const V ul = wl[1], ur = wr[1];
-  V dpl = vmul(gm1, wl[4]), dpr = vmul(gm1, wr[4]);
-  V pl = vadd(pb, dpl), pr = vadd(pb, dpr);
-  positive_rp(rl, pl, dpl, pb);
-  positive_rp(rr, pr, dpr, pb);
+  const V dpl = vmul(gm1, wl[4]), dpr = vmul(gm1, wr[4]);
+  const V pl = vadd(pb, dpl), pr = vadd(pb, dpr);
   const V kel = vmul(vmul(half, rl), vfma(ul, ul, vfma(wl[2], wl[2], vmul(wl[3], wl[3]))));
   const V ker = vmul(vmul(half, rr), vfma(ur, ur, vfma(wr[2], wr[2], vmul(wr[3], wr[3]))));
   const V hl = vfma(gg, pl, kel), hr = vfma(gg, pr, ker);  // E + p

@@ -51,7 +51,8 @@ __device__ __forceinline__ void c2p(const double* u, double* w, const Bg&, Count
   w[4] = ug;
 }
 
-// Conserved -> primitive, mixed form.  The internal-energy recovery runs in FP64 with
+// Conserved -> primitive, mixed form (floors: bg.rho_min and bg.ug_floor_f, the
+// absolute floors raised to 2^-20 of the background).  The internal-energy recovery runs in FP64 with
 // the cancellation done before any division: 2 rho (u_g - u_g,b) = 2 rho (E - u_g,b) -
 // |M|^2 is formed in FP64, rounded to FP32 and only then divided by 2 rho (FP32
 // reciprocal), so u_g - u_g,b keeps FP32 relative precision whatever the Mach number,
@@ -60,8 +61,8 @@ __device__ __forceinline__ void c2p(const double* u, double* w, const Bg&, Count
 __device__ __forceinline__ void c2p(const double* u, float* w, const Bg& bg, Counters cn) {
   double rho = u[0];
   if (not_finite(rho) || not_finite(u[4])) count(cn.nonfinite);
-  if (!at_least(rho, AK_RHO_FLOOR)) {
-    rho = AK_RHO_FLOOR;
+  if (!at_least(rho, bg.rho_min)) {
+    rho = bg.rho_min;
     count(cn.floors);
   }
   const float rhof = f64_to_f32(rho);
@@ -72,7 +73,7 @@ __device__ __forceinline__ void c2p(const double* u, float* w, const Bg& bg, Cou
   const double num2 = fma(u[4] - bg.ug, dscale(rho, 1), -m2);
   float dugf = f64_to_f32(num2) * (0.5f * rf);
   if (!(dugf >= bg.ug_floor_f)) {           // u_g below its floor (FP32 resolution)
-    dugf = f64_to_f32(AK_UG_FLOOR - bg.ug);
+    dugf = bg.ug_floor_f;
     count(cn.floors);
   }
   w[0] = f64_to_f32(rho - bg.rho);
@@ -102,21 +103,15 @@ __device__ __forceinline__ void riemann(const V* wl, const V* wr, const Bg& bg, 
     hllc_mixed(wl, wr, bg, f);
 }
 
-// Lower and upper edge values of the middle cell of q[0 .. 2NG-2] (NG = 3: PPM4,
-// WENO-Z or PPMX by `recon`).
-template <int NG, typename R>
-__device__ __forceinline__ void edges(const R* q, R& lo, R& hi, int recon) {
-  if constexpr (NG == 3) {
-    if (recon == AK_WENOZ) {
-      wenoz_edges(q[0], q[1], q[2], q[3], q[4], lo, hi);
-      return;
-    }
-    if (recon == AK_PPMX) {
-      ppmx_edges(q[0], q[1], q[2], q[3], q[4], lo, hi);
-      return;
-    }
-  }
-  if constexpr (std::is_same<R, float>::value) {
+// Lower and upper edge values of the middle cell of q[0 .. 2NG-2] for the
+// reconstruction RC (NG = 2: PLM; NG = 3: AK_PPM4, AK_WENOZ or AK_PPMX).
+template <int NG, int RC, typename R>
+__device__ __forceinline__ void edges_t(const R* q, R& lo, R& hi) {
+  if constexpr (NG == 3 && RC == AK_WENOZ) {
+    wenoz_edges(q[0], q[1], q[2], q[3], q[4], lo, hi);
+  } else if constexpr (NG == 3 && RC == AK_PPMX) {
+    ppmx_edges(q[0], q[1], q[2], q[3], q[4], lo, hi);
+  } else if constexpr (std::is_same<R, float>::value) {
     if constexpr (NG == 2)
       plm_edges_v(q[0], q[1], q[2], lo, hi);
     else
@@ -127,6 +122,22 @@ __device__ __forceinline__ void edges(const R* q, R& lo, R& hi, int recon) {
     hi = q[1] + h;
   } else {
     ppm_edges_fp64(q[0], q[1], q[2], q[3], q[4], lo, hi);
+  }
+}
+
+// The same with the reconstruction chosen at run time (the flux-correction and FOFC
+// kernels, which serve every reconstruction).
+template <int NG, typename R>
+__device__ __forceinline__ void edges(const R* q, R& lo, R& hi, int recon) {
+  if constexpr (NG == 3) {
+    if (recon == AK_WENOZ)
+      edges_t<3, AK_WENOZ>(q, lo, hi);
+    else if (recon == AK_PPMX)
+      edges_t<3, AK_PPMX>(q, lo, hi);
+    else
+      edges_t<3, AK_PPM4>(q, lo, hi);
+  } else {
+    edges_t<2, AK_PLM>(q, lo, hi);
   }
 }
 

@@ -1,0 +1,503 @@
+// The fused hydro stage kernel: primitive recovery, reconstruction in x1/x2/x3, HLLC
+// at every face, flux divergence and the RK stage update of AthenaK's Godunov scheme
+// (arXiv 2409.16053, Section 3 Eq. (1), Section 3.1 Eq. (4)), plus the CFL minimum of
+// Section 3 Eq. (3) on the last stage.
+//
+// Work decomposition (one launch covers every MeshBlock, as Section 2's MeshBlockPack
+// does): a CTA owns a TX x TY column tile of one block and marches along x3 over a
+// segment of planes.  A ring of 2*NG planes of primitives (tile plus NG halo cells in
+// x1 and x2) lives in shared memory; each plane is loaded from HBM and converted once.
+// Per plane:
+//   A. reconstruction: the x1 and x2 face values (lower and upper edge) of every cell
+//      the tile's faces touch go to shared memory; each thread also reconstructs its
+//      own column's next cell along x3 and keeps the upper edge in registers;
+//   B. HLLC on every x1 and x2 face of the plane (fluxes to shared memory) and on the
+//      x3 face above each column (flux in registers, carried to the next plane);
+//   C. flux divergence and the RK update of the column's cell.
+// Every cell is reconstructed once per direction and every face of a tile is solved
+// once; faces on tile edges are solved by both tiles from identical inputs, so they
+// agree bit for bit and the update stays conservative.
+//
+// The reconstruction is a template argument (RC: AK_PLM, AK_PPM4, AK_WENOZ or AK_PPMX),
+// as the paper does for algorithmic options to spare registers; each reconstruction's
+// kernels are instantiated in a translation unit of their own (ak_stage_<recon>.cu).
+#pragma once
+
+#include <type_traits>
+
+#include "ak_internal.cuh"
+#include "hydro_ops.cuh"
+#include "stage_common.cuh"
+#include "tma.cuh"
+
+namespace ak {
+
+template <int NG, bool MIXED, int TX, int TY, bool TMA_OUT>
+struct StageCfg {
+  using R = typename std::conditional<MIXED, float, double>::type;
+  // FP64: x1 and x2 sweeps one after the other through one edge buffer, so that two
+  // CTAs fit in an SM's shared memory.  Mixed: both sweeps at once, and the next plane
+  // of the state is prefetched into registers while the current one is computed.
+  static constexpr bool SPLIT = !MIXED;
+  static constexpr bool PREFETCH = MIXED;
+  static constexpr int WX = TX + 2 * NG, WY = TY + 2 * NG, NPL = WX * WY, NR = 2 * NG;
+  // cells of a plane that are converted: the tile and its x1 / x2 halos (no corners)
+  static constexpr int NCROSS = TX * TY + 2 * NG * (TX + TY);
+  static constexpr int NT = TX * TY;
+  static constexpr int NPT = (NCROSS + NT - 1) / NT;  // cells per thread
+  static constexpr int E1 = 5 * TY * (TX + 2);  // x1 edges of cells i0-1 .. i0+TX
+  static constexpr int E2 = 5 * (TY + 2) * TX;  // x2 edges of cells j0-1 .. j0+TY
+  static constexpr int EB = SPLIT ? (E1 > E2 ? E1 : E2) : E1 + E2;
+  static constexpr int F1 = 5 * TY * (TX + 1);
+  static constexpr int F2 = 5 * (TY + 1) * TX;
+  // TMA_OUT: the new state of each plane goes through a double-buffered shared tile and
+  // one bulk-tensor store per plane instead of per-thread global stores
+  static constexpr int OUT = TMA_OUT ? 2 * 5 * TX * TY : 0;  // doubles, at offset 0
+  static constexpr size_t bytes =
+      sizeof(double) * (size_t)OUT + sizeof(R) * (size_t)(NR * 5 * NPL + 2 * EB + F1 + F2);
+};
+
+// PERSIST: the persistent fused form for meshes that need a ghost fill (static
+// refinement, FOFC): a cooperative launch of at most one resident wave of CTAs first runs
+// the fill and the flux correction (fused_prologue), then loops over the work list.
+template <int NG, int RC, bool MIXED, int TX, int TY, bool TMA_OUT, bool PERSIST>
+__global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
+    stage_kernel(const double* __restrict__ uin_arg, const double* u0, double* uout,
+                 ak_meshdev md, const ak_work* __restrict__ work, Bg bg, double a, double b,
+                 int form, ak_dev_scalars* sc, int last_stage,
+                 const __grid_constant__ CUtensorMap tmap_out, int nwork) {
+  // form: 0 = first stage U + dt L; 1 = RK2 final (U0 + U + dt L) / 2;
+  //       2 = a U0 + b (U + dt L)
+  using C = StageCfg<NG, MIXED, TX, TY, TMA_OUT>;
+  using R = typename C::R;
+  constexpr int NT = C::NT, WX = C::WX, NPL = C::NPL, NR = C::NR, NPT = C::NPT;
+  constexpr int C1 = TX + 2;  // x1 edge row length
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  double* stg = reinterpret_cast<double*>(smem_raw);  // [2][5][TY][TX] (TMA_OUT only)
+  R* ring = reinterpret_cast<R*>(smem_raw + sizeof(double) * C::OUT);  // [NR][5][WY][WX]
+  R* e1lo = ring + NR * 5 * NPL;             // [5][TY][TX+2]
+  R* e1hi = e1lo + C::EB;
+  R* e2lo = C::SPLIT ? e1lo : e1lo + C::E1;  // [5][TY+2][TX]
+  R* e2hi = C::SPLIT ? e1hi : e1hi + C::E1;
+  R* f1 = e1hi + C::EB;                      // [5][TY][TX+1]
+  R* f2 = f1 + C::F1;                        // [5][TY+1][TX]
+  __shared__ double red[NT / 32];
+  __shared__ long long nbr[27];  // direct halo reads: the neighbour blocks
+
+  if constexpr (PERSIST) {
+    constexpr int KB = C::bytes / (NT * 80) < 8 ? (int)(C::bytes / (NT * 80)) : 8;
+    static_assert(KB >= 1, "no room to stage the fill");
+    fused_prologue<NG, MIXED, KB>(launder(const_cast<double*>(uin_arg)), md, bg, sc, smem_raw);
+  }
+  // one tile per CTA, or (persistent) tiles taken from the list until it runs out
+  __shared__ int wslot;
+  for (int it = 0; it < (PERSIST ? 0x7fffffff : 1); ++it) {
+  const int wi = PERSIST ? next_tile(sc, &wslot) : (int)blockIdx.x;
+  if (PERSIST && wi >= nwork) break;
+  const double* __restrict__ uin = PERSIST ? launder(uin_arg) : uin_arg;
+  const int tid = threadIdx.x;
+  // this CTA's column tile of one MeshBlock, and that block's geometry
+  const ak_work w = work[wi];
+  const ak_block g = md.blocks[w.block];
+  if (md.direct) neighbour_table(md, w.block, nbr);
+  __syncthreads();
+  const int blk = w.block;
+  const int i0 = w.i0, j0 = w.j0, k0 = w.k0, k1 = w.k1;
+  int kcur = k0;  // the plane whose x1/x2 faces are being solved
+
+  const long long boff = g.off;
+  const double* ub = uin + boff;
+  const Counters cn{&sc->counters[0], &sc->counters[1]};
+  const double dt = sc->dt;
+  const double idx1 = 1.0 / g.dx1, idx2 = 1.0 / g.dx2, idx3 = 1.0 / g.dx3;
+  const bool need_u0 = form != 0;
+
+  auto slot = [](int k) { return (k + 4 * NR) % NR; };
+  // ring position of the c-th converted cell: halo rows above, full rows, halo rows below
+  auto cross_xy = [](int c, int& x, int& y) {
+    constexpr int TOP = NG * TX, MID = TY * (TX + 2 * NG);
+    if (c < TOP) {
+      y = c / TX;
+      x = NG + c % TX;
+    } else if (c < TOP + MID) {
+      const int d = c - TOP;
+      y = NG + d / (TX + 2 * NG);
+      x = d % (TX + 2 * NG);
+    } else {
+      const int d = c - TOP - MID;
+      y = NG + TY + d / TX;
+      x = NG + d % TX;
+    }
+  };
+  // global loads of this thread's cells of plane kp (interior index; ghost planes ok)
+  auto fetch = [&](int kp, double (&u)[NPT][5], int (&pos)[NPT]) {
+#pragma unroll
+    for (int m = 0; m < NPT; ++m) {
+      const int c = tid + m * NT;
+      pos[m] = -1;
+      if (c < C::NCROSS) {
+        int x, y;
+        cross_xy(c, x, y);
+        const int ip = i0 + x, jp = j0 + y;  // padded indices (halo starts at i0 - NG)
+        if (ip < g.p1 && jp < g.p2) {
+          const bool halo = ip < NG || ip >= NG + g.nx1 || jp < NG || jp >= NG + g.nx2 ||
+                            kp < 0 || kp >= g.nx3;
+          const double* src = (md.direct && halo)
+                                  ? uin + halo_elem(g, nbr, NG, ip, jp, kp)
+                                  : ub + ((long long)(kp + NG) * g.p2 + jp) * g.s1 + ip;
+#pragma unroll
+          for (int v = 0; v < 5; ++v) u[m][v] = src[v * g.var_stride];
+          pos[m] = y * WX + x;
+        }
+      }
+    }
+  };
+  // primitive recovery of fetched cells into the ring slot of plane kp
+  auto store = [&](int kp, const double (&u)[NPT][5], const int (&pos)[NPT]) {
+    R* dst = ring + slot(kp) * 5 * NPL;
+#pragma unroll
+    for (int m = 0; m < NPT; ++m) {
+      if (pos[m] >= 0) {
+        R w[5];
+        c2p(u[m], w, bg, cn);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) dst[v * NPL + pos[m]] = w[v];
+      }
+    }
+  };
+  auto load_plane = [&](int kp) {
+    double u[NPT][5];
+    int pos[NPT];
+    fetch(kp, u, pos);
+    store(kp, u, pos);
+  };
+
+  // own column of this thread
+  const int tx = tid % TX, ty = tid / TX;
+  const int ci = i0 + tx, cj = j0 + ty;
+  const bool own = (ci < g.nx1) && (cj < g.nx2);
+  const int oc = (ty + NG) * WX + (tx + NG);
+  const long long ecol = boff + ((long long)NG * g.p2 + (cj + NG)) * g.s1 + (ci + NG);
+  const long long plane_stride = (long long)g.p2 * g.s1;
+
+  // x3 edges of the own column's cell kc (stencil planes kc-NG+1 .. kc+NG-1)
+  auto x3_edges = [&](int kc, R* lo, R* hi) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      R q[2 * NG - 1];
+#pragma unroll
+      for (int m = 0; m < 2 * NG - 1; ++m) q[m] = ring[slot(kc - NG + 1 + m) * 5 * NPL + v * NPL + oc];
+      edges_t<NG, RC>(q, lo[v], hi[v]);
+    }
+  };
+  auto x1_edges = [&](const R* pl) {  // cells i0-1 .. i0+TX of the tile's rows
+    for (int it = tid; it < C::E1 / 5; it += NT) {
+      const int c = it % C1, r = it / C1;
+      if (i0 - 1 + c <= g.nx1 && j0 + r < g.nx2) {
+        const int base = (r + NG) * WX + c;  // stencil x = c .. c + 2NG - 2
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          R q[2 * NG - 1];
+#pragma unroll
+          for (int m = 0; m < 2 * NG - 1; ++m) q[m] = pl[v * NPL + base + m];
+          edges_t<NG, RC>(q, e1lo[(v * TY + r) * C1 + c], e1hi[(v * TY + r) * C1 + c]);
+        }
+      }
+    }
+  };
+  auto x2_edges = [&](const R* pl) {  // cells j0-1 .. j0+TY of the tile's columns
+    for (int it = tid; it < C::E2 / 5; it += NT) {
+      const int c = it % TX, r = it / TX;
+      if (i0 + c < g.nx1 && j0 - 1 + r <= g.nx2) {
+        const int base = r * WX + c + NG;  // stencil y = r .. r + 2NG - 2
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          R q[2 * NG - 1];
+#pragma unroll
+          for (int m = 0; m < 2 * NG - 1; ++m) q[m] = pl[v * NPL + base + m * WX];
+          edges_t<NG, RC>(q, e2lo[(v * (TY + 2) + r) * TX + c], e2hi[(v * (TY + 2) + r) * TX + c]);
+        }
+      }
+    }
+  };
+  auto x1_faces = [&]() {
+    for (int it = tid; it < C::F1 / 5; it += NT) {
+      const int fx = it % (TX + 1), fy = it / (TX + 1);
+      if (i0 + fx <= g.nx1 && j0 + fy < g.nx2) {
+        R l[5], r[5], f[5];
+        const int fi = i0 + fx;
+        const int ov = fi == 0 ? g.ovr[0] : (fi == g.nx1 ? g.ovr[1] : -1);
+        if (ov >= 0) {  // coarse face next to a refined region: the fine-flux mean
+          corrected_flux(md.fcbuf, ov + kcur * g.nx2 + j0 + fy, f);
+        } else {
+#pragma unroll
+          for (int v = 0; v < 5; ++v) {
+            l[v] = e1hi[(v * TY + fy) * C1 + fx];       // cell i-1: column fx
+            r[v] = e1lo[(v * TY + fy) * C1 + fx + 1];   // cell i:   column fx+1
+          }
+          solve(0, l, r, bg, f);
+        }
+#pragma unroll
+        for (int v = 0; v < 5; ++v) f1[(v * TY + fy) * (TX + 1) + fx] = f[v];
+      }
+    }
+  };
+  auto x2_faces = [&]() {
+    for (int it = tid; it < C::F2 / 5; it += NT) {
+      const int fx = it % TX, fy = it / TX;
+      if (i0 + fx < g.nx1 && j0 + fy <= g.nx2) {
+        R l[5], r[5], f[5];
+        const int fj = j0 + fy;
+        const int ov = fj == 0 ? g.ovr[2] : (fj == g.nx2 ? g.ovr[3] : -1);
+        if (ov >= 0) {
+          corrected_flux(md.fcbuf, ov + kcur * g.nx1 + i0 + fx, f);
+        } else {
+#pragma unroll
+          for (int v = 0; v < 5; ++v) {
+            l[v] = e2hi[(v * (TY + 2) + fy) * TX + fx];      // cell j-1: row fy
+            r[v] = e2lo[(v * (TY + 2) + fy + 1) * TX + fx];  // cell j:   row fy+1
+          }
+          solve(1, l, r, bg, f);
+        }
+#pragma unroll
+        for (int v = 0; v < 5; ++v) f2[(v * (TY + 1) + fy) * TX + fx] = f[v];
+      }
+    }
+  };
+
+  // prologue: planes k0-NG .. k0+NG-1, the flux through the face below k0, then plane
+  // k0+NG (its slot held plane k0-NG, used by that flux)
+  for (int kp = k0 - NG; kp < k0 + NG; ++kp) load_plane(kp);
+  __syncthreads();
+  R hi3[5], f3m[5], f3p[5];
+  if (own) {
+    R lo_a[5], hi_a[5], lo_b[5];
+    x3_edges(k0 - 1, lo_a, hi_a);
+    x3_edges(k0, lo_b, hi3);
+    if (k0 == 0 && g.ovr[4] >= 0)
+      corrected_flux(md.fcbuf, g.ovr[4] + cj * g.nx1 + ci, f3m);
+    else
+      solve(2, hi_a, lo_b, bg, f3m);
+  }
+  __syncthreads();
+  load_plane(k0 + NG);
+
+  float dtmin_f = __int_as_float(0x7f800000);
+  double dtmin = __longlong_as_double(0x7ff0000000000000ll);
+  double lam_max = 0.0;
+  double pf[NPT][5];
+  int pfpos[NPT];
+  for (int k = k0; k < k1; ++k) {
+    // the ring holds planes k-NG+1 .. k+NG once this barrier is passed
+    const bool more = k + 1 < k1;
+    if constexpr (C::PREFETCH) {
+      if (more) fetch(k + NG + 1, pf, pfpos);
+    }
+    double uik[5], u0k[5];
+    if constexpr (MIXED) {
+      if (own) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          uik[v] = uin[ecol + k * plane_stride + v * g.var_stride];
+          u0k[v] = need_u0 ? u0[ecol + k * plane_stride + v * g.var_stride] : 0.0;
+        }
+      }
+    }
+    __syncthreads();
+    if constexpr (TMA_OUT) {
+      // the previous plane's new state is complete in its staging tile
+      if (tid == 0 && k > k0) {
+        tma_store_5d(&tmap_out, stg + ((k - 1) & 1) * 5 * TX * TY, i0 + NG, j0 + NG, k - 1 + NG,
+                     0, blk);
+        bulk_commit();
+      }
+    }
+    const R* pl = ring + slot(k) * 5 * NPL;
+    kcur = k;
+    R lo3[5], hi3n[5];
+
+    if constexpr (C::SPLIT) {
+      x1_edges(pl);
+      if (own) x3_edges(k + 1, lo3, hi3n);
+      __syncthreads();
+      x1_faces();
+      __syncthreads();
+      x2_edges(pl);
+      __syncthreads();
+      x2_faces();
+    } else {
+      x1_edges(pl);
+      x2_edges(pl);
+      if (own) x3_edges(k + 1, lo3, hi3n);
+      __syncthreads();
+      x1_faces();
+      x2_faces();
+    }
+    if (own) {
+      if (k + 1 == g.nx3 && g.ovr[5] >= 0)
+        corrected_flux(md.fcbuf, g.ovr[5] + cj * g.nx1 + ci, f3p);
+      else
+        solve(2, hi3, lo3, bg, f3p);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) hi3[v] = hi3n[v];
+    }
+    if constexpr (TMA_OUT) {
+      // this plane's staging tile was last read by the store of plane k-2
+      if (tid == 0) bulk_wait_read<1>();
+    }
+    __syncthreads();
+
+    // ---- divergence and RK update ---------------------------------------------
+    if (own) {
+      const long long e = ecol + k * plane_stride;
+      double un[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const R d1 = f1[(v * TY + ty) * (TX + 1) + tx + 1] - f1[(v * TY + ty) * (TX + 1) + tx];
+        const R d2 = f2[(v * (TY + 1) + ty + 1) * TX + tx] - f2[(v * (TY + 1) + ty) * TX + tx];
+        const R d3 = f3p[v] - f3m[v];
+        double r;
+        if constexpr (MIXED) {
+          const float L = -fmaf(d1, (float)idx1, fmaf(d2, (float)idx2, d3 * (float)idx3));
+          r = rk_update_mixed(form, a, b, dt, L, uik[v], u0k[v]);
+        } else {
+          const double L = -fma(d1, idx1, fma(d2, idx2, d3 * idx3));
+          r = fma(dt, L, uin[e + v * g.var_stride]);
+          if (form == 1)  // RK2 final stage: (U0 + U + dt L) / 2
+            r = half(u0[e + v * g.var_stride] + r);
+          else if (form == 2)
+            r = fma(a, u0[e + v * g.var_stride], b * r);
+        }
+        un[v] = r;
+        if constexpr (TMA_OUT)
+          stg[(((k & 1) * 5 + v) * TY + ty) * TX + tx] = r;
+        else
+          uout[e + v * g.var_stride] = r;
+        f3m[v] = f3p[v];
+      }
+      if (md.fofc) fofc_flag(un, md, sc, blk, g, ci, cj, k);
+      if constexpr (TMA_OUT) fence_proxy_async_smem();
+      if (last_stage) {
+        if constexpr (MIXED) {
+          // CFL ratio in FP32: it only sets the next step's dt
+          const float rho = fmaxf(f64_to_f32(un[0]), (float)AK_RHO_FLOOR);
+          const float ir = rcp_approx_f32(rho);
+          const float m1 = f64_to_f32(un[1]), m2 = f64_to_f32(un[2]), m3 = f64_to_f32(un[3]);
+          const float ug = fmaxf(fmaf(-0.5f * ir, fmaf(m1, m1, fmaf(m2, m2, m3 * m3)),
+                                      f64_to_f32(un[4])), (float)AK_UG_FLOOR);
+          const float cs = sqrt_fast(bg.gamma_f * (bg.gamma_f - 1.0f) * ug * ir);
+          float lam = fmaf(fabsf(m1), ir, cs) * (float)idx1;
+          lam = fmaxf(lam, fmaf(fabsf(m2), ir, cs) * (float)idx2);
+          lam = fmaxf(lam, fmaf(fabsf(m3), ir, cs) * (float)idx3);
+          dtmin_f = fminf(dtmin_f, rcp_approx_f32(lam));
+        } else {
+          // CFL in FP64 (the FP64 form reproduces the oracle's dt to ~1e-13): the
+          // largest (|v_d| + c_s) / dx_d of the column; dt = 1 / max at the end
+          double rho = un[0];
+          rho = at_least(rho, AK_RHO_FLOOR) ? rho : AK_RHO_FLOOR;
+          const double r = rcp64(rho);
+          const double v1 = un[1] * r, v2 = un[2] * r, v3 = un[3] * r;
+          double ug = fma(-0.5, fma(un[1], v1, fma(un[2], v2, un[3] * v3)), un[4]);
+          ug = at_least(ug, AK_UG_FLOOR) ? ug : AK_UG_FLOOR;
+          const double cs = sqrt64(bg.gamma * bg.gm1 * ug * r);
+          const double l1 = (fabs(v1) + cs) * idx1, l2 = (fabs(v2) + cs) * idx2,
+                       l3 = (fabs(v3) + cs) * idx3;
+          double lam = dgt_pos(l2, l1) ? l2 : l1;
+          lam = dgt_pos(l3, lam) ? l3 : lam;
+          lam_max = dgt_pos(lam, lam_max) ? lam : lam_max;
+        }
+      }
+    }
+    // next plane into the slot of plane k-NG+1, whose last reader was this iteration's
+    // reconstruction (finished before the barrier above)
+    if (more) {
+      if constexpr (C::PREFETCH)
+        store(k + NG + 1, pf, pfpos);
+      else
+        load_plane(k + NG + 1);
+    }
+  }
+
+  if constexpr (TMA_OUT) {
+    __syncthreads();
+    if (tid == 0) {
+      tma_store_5d(&tmap_out, stg + ((k1 - 1) & 1) * 5 * TX * TY, i0 + NG, j0 + NG, k1 - 1 + NG,
+                   0, blk);
+      bulk_commit();
+      bulk_wait<0>();
+    }
+  }
+  if (last_stage) {
+    if constexpr (MIXED)
+      dtmin = f32_to_f64(dtmin_f);
+    else
+      dtmin = dpos(lam_max) ? 1.0 / lam_max : dtmin;
+    // CTA min of the CFL ratio -> one atomic per CTA (non-negative doubles order as
+    // their bit patterns)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dtmin = fmin(dtmin, __shfl_xor_sync(0xffffffffu, dtmin, o));
+    __syncthreads();
+    if ((tid & 31) == 0) red[tid >> 5] = dtmin;
+    __syncthreads();
+    if (tid < 32) {
+      double v = tid < NT / 32 ? red[tid] : __longlong_as_double(0x7ff0000000000000ll);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+      if (tid == 0)
+        atomicMin(&sc->dtmin_bits, (unsigned long long)__double_as_longlong(v));
+    }
+  }
+  if constexpr (PERSIST) __syncthreads();  // the next tile reuses the shared memory
+  }
+}
+
+Bg make_bg(const ak_mesh* m);
+
+// Launch (or, prepare_only, raise the shared-memory limit of) the stage kernel of one
+// configuration over the mesh's work list; m->fused selects the persistent variant.
+template <int NG, int RC, bool MIXED, int TX, int TY, bool TMA_OUT>
+inline cudaError_t launch(const ak_mesh* m, const double* uin, const double* u0, double* uout,
+                          int out_reg, double a, double b, int rk2_final, int last_stage,
+                          bool prepare_only) {
+  const size_t smem = StageCfg<NG, MIXED, TX, TY, TMA_OUT>::bytes;
+  auto kern = stage_kernel<NG, RC, MIXED, TX, TY, TMA_OUT, false>;
+  if (prepare_only) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if constexpr (!TMA_OUT) {
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(stage_kernel<NG, RC, MIXED, TX, TY, false, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    }
+    return e;
+  }
+  const Bg bg = make_bg(m);
+  const int form = rk2_final ? 1 : (a == 0.0 ? 0 : 2);
+  if (m->fused) {
+    if constexpr (!TMA_OUT) {
+      auto pk = stage_kernel<NG, RC, MIXED, TX, TY, false, true>;
+      return launch_persistent(m, pk, TX * TY, smem, uin, u0, uout, m->md, m->d_work, bg, a, b,
+                               form, m->d_sc, last_stage, m->tmap[out_reg], m->nwork);
+    }
+  }
+  kern<<<(unsigned)m->nwork, TX * TY, smem, m->stream>>>(uin, u0, uout, m->md, m->d_work, bg, a,
+                                                          b, form, m->d_sc, last_stage,
+                                                          m->tmap[out_reg], m->nwork);
+  return cudaGetLastError();
+}
+
+// Per-reconstruction launchers (one translation unit each): the stage of this mesh with
+// the given RK weights; prepare: raise the kernels' shared-memory limits instead.
+cudaError_t launch_stage_plm(const ak_mesh* m, const double* uin, const double* u0,
+                             double* uout, int out_reg, double a, double b, int rk2_final,
+                             int last_stage, bool prepare);
+cudaError_t launch_stage_ppm4(const ak_mesh* m, const double* uin, const double* u0,
+                              double* uout, int out_reg, double a, double b, int rk2_final,
+                              int last_stage, bool prepare);
+cudaError_t launch_stage_wenoz(const ak_mesh* m, const double* uin, const double* u0,
+                               double* uout, int out_reg, double a, double b, int rk2_final,
+                               int last_stage, bool prepare);
+cudaError_t launch_stage_ppmx(const ak_mesh* m, const double* uin, const double* u0,
+                              double* uout, int out_reg, double a, double b, int rk2_final,
+                              int last_stage, bool prepare);
+
+}  // namespace ak

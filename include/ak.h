@@ -208,6 +208,14 @@ ak_status ak_mesh_autotune(ak_mesh* mesh, int32_t result[5]);
  * a ghost fill (one level, no FOFC: its stage reads halos from the neighbour blocks). */
 ak_status ak_mesh_fuse(ak_mesh* mesh, int32_t fused);
 
+/* Self-test of the bounded device waits (failure detection without a GPU fault): a
+ * cooperative launch of two CTAs meets at the grid barrier the fused stage uses; with
+ * absent = 1 the second CTA never arrives, so the first one's wait runs out after about
+ * a second, counts a timeout and returns.  Synchronizes the stream.  Returns AK_OK when
+ * every wait was met, AK_ETIMEOUT when one ran out (the count is in ak_status_counters);
+ * the mesh stays usable either way. */
+ak_status ak_selftest_barrier(ak_mesh* mesh, int32_t absent);
+
 /* Sets the stage kernel's schedule explicitly (what ak_mesh_autotune picks by timing).
  *   tile:  0 = 16x16 column tiles (for the mixed PLM form: the variant with paired
  *          x1/x2 work, 288 threads); 1 = 32x8 tiles and 2 = 16x16 tiles with one thread

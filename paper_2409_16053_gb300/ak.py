@@ -8,7 +8,8 @@ CUDA stream.
 Low level (same names and arguments as the C functions):
     ak_mesh_create, ak_mesh_destroy, ak_mesh_layout, ak_mesh_bind, ak_fill_ghosts,
     ak_stage, ak_new_dt, ak_step, ak_upload, ak_download, ak_status_counters,
-    ak_mesh_autotune, ak_mesh_schedule, ak_mesh_fuse, ak_cfl_dt_noalloc, ak_last_error
+    ak_mesh_autotune, ak_mesh_schedule, ak_mesh_fuse, ak_selftest_barrier, ak_cfl_dt_noalloc,
+    ak_last_error
 High level: ``Mesh`` builds a uniform mesh of equal MeshBlocks, allocates and binds
 its registers as torch tensors, and converts between a global (5, n3, n2, n1) array
 and the library's block layout.
@@ -78,6 +79,8 @@ def _load_lib():
     lib.ak_mesh_schedule.restype = ctypes.c_int
     lib.ak_mesh_fuse.argtypes = [vp, i32]
     lib.ak_mesh_fuse.restype = ctypes.c_int
+    lib.ak_selftest_barrier.argtypes = [vp, i32]
+    lib.ak_selftest_barrier.restype = ctypes.c_int
     lib.ak_cfl_dt_noalloc.argtypes = [vp, i32, ctypes.POINTER(i32), i32, dp, ctypes.c_double,
                                       ctypes.c_double, vp, dp]
     lib.ak_cfl_dt_noalloc.restype = ctypes.c_int
@@ -93,6 +96,7 @@ _lib = _load_lib()
 EXPORTED = ("ak_mesh_create", "ak_mesh_destroy", "ak_mesh_layout", "ak_mesh_bind",
             "ak_fill_ghosts", "ak_stage", "ak_new_dt", "ak_step", "ak_upload",
             "ak_download", "ak_status_counters", "ak_mesh_autotune", "ak_mesh_schedule", "ak_mesh_fuse",
+            "ak_selftest_barrier",
             "ak_cfl_dt_noalloc", "ak_last_error")
 
 
@@ -188,6 +192,12 @@ def ak_mesh_schedule(mesh, tile: int, nseg: int, order: int):
 def ak_mesh_fuse(mesh, fused: bool):
     """Fill, flux correction and stage in one persistent cooperative launch per stage."""
     _check(_lib.ak_mesh_fuse(mesh, 1 if fused else 0))
+
+
+def ak_selftest_barrier(mesh, absent: bool):
+    """Bounded-wait self-test: raises AkError(AK_ETIMEOUT) when the barrier's wait ran
+    out (absent=True makes it run out)."""
+    _check(_lib.ak_selftest_barrier(mesh, 1 if absent else 0))
 
 
 def ak_cfl_dt_noalloc(reg_ptr: int, nblocks: int, nx, nghost: int, dx, gamma: float,

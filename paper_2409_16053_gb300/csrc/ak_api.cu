@@ -624,16 +624,21 @@ extern "C" ak_status ak_stage(ak_mesh* m, int32_t stage, double dt) {
   return AK_OK;
 }
 
-// Reads the device scalars (synchronizes) and maps new floor / non-finite counts to
-// AK_ENEGATIVE.
+// Reads the device scalars (synchronizes) and maps new timeouts of bounded device waits
+// to AK_ETIMEOUT and new floor / non-finite counts to AK_ENEGATIVE.
 static ak_status read_scalars(ak_mesh* m, ak_dev_scalars* s) {
   AK_CUDA_TRY(cudaMemcpyAsync(s, m->d_sc, sizeof(*s), cudaMemcpyDeviceToHost, m->stream));
   AK_CUDA_TRY(cudaStreamSynchronize(m->stream));
   ak_status st = AK_OK;
-  if (s->counters[0] != s->reported[0] || s->counters[1] != s->reported[1]) {
+  if (s->counters[2] != s->reported[2]) {
+    ak_set_error("bounded device waits that gave up: %llu (since mesh creation)", s->counters[2]);
+    st = AK_ETIMEOUT;
+  } else if (s->counters[0] != s->reported[0] || s->counters[1] != s->reported[1]) {
     ak_set_error("floors applied: %llu, non-finite cells: %llu (since mesh creation)",
                  s->counters[0], s->counters[1]);
     st = AK_ENEGATIVE;
+  }
+  if (st != AK_OK) {
     // mark as reported (device copy of the counters is the source of truth)
     unsigned long long rep[4] = {s->counters[0], s->counters[1], s->counters[2], s->counters[3]};
     AK_CUDA_TRY(cudaMemcpyAsync(&m->d_sc->reported, rep, sizeof(rep), cudaMemcpyHostToDevice,
@@ -793,6 +798,16 @@ extern "C" ak_status ak_mesh_autotune(ak_mesh* m, int32_t result[5]) {
     result[4] = m->fused;
   }
   return AK_OK;
+}
+
+extern "C" ak_status ak_selftest_barrier(ak_mesh* m, int32_t absent) {
+  if (!m) return einval("ak_selftest_barrier: NULL mesh");
+  if (absent != 0 && absent != 1) return einval("ak_selftest_barrier: absent must be 0 or 1");
+  AK_CUDA_TRY(ak_launch_barrier_selftest(m, absent));
+  // a barrier that ran out leaves its arrival count behind: clear it for the next one
+  AK_CUDA_TRY(cudaMemsetAsync(&m->d_sc->bar_count, 0, sizeof(unsigned int), m->stream));
+  ak_dev_scalars sc;
+  return read_scalars(m, &sc);
 }
 
 extern "C" ak_status ak_mesh_fuse(ak_mesh* m, int32_t fused) {

@@ -160,6 +160,9 @@ cudaError_t ak_launch_fofc(const ak_mesh* m, int stage, const double* u_in, doub
                            int last_stage);
 cudaError_t ak_launch_finalize_dt(const ak_mesh* m, int use_next_as_dt);
 cudaError_t ak_launch_set_dt(const ak_mesh* m, double dt);
+// Two-CTA cooperative launch meeting at the fused kernel's grid barrier (CTA 1 stays away
+// when absent != 0, so the wait runs out).
+cudaError_t ak_launch_barrier_selftest(const ak_mesh* m, int absent);
 cudaError_t ak_stage_prepare(const ak_mesh* m);
 // (Re)builds the stage work list for a tile shape, x3 segment count and CTA order.
 cudaError_t ak_build_work(ak_mesh* m, int tile, int nseg, int order);

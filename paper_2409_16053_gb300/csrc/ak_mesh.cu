@@ -169,3 +169,25 @@ cudaError_t ak_launch_set_dt(const ak_mesh* m, double dt) {
   set_dt_kernel<<<1, 1, 0, m->stream>>>(m->d_sc, dt);
   return cudaGetLastError();
 }
+
+// Self-test of the bounded barrier wait: all CTAs meet at grid_barrier, except CTA 1
+// when `absent` is set, so that the others' wait runs out.
+namespace {
+__global__ void barrier_selftest_kernel(ak_dev_scalars* sc, int absent) {
+  if (absent && blockIdx.x == 1) return;
+  ak::grid_barrier(sc);
+}
+}  // namespace
+
+cudaError_t ak_launch_barrier_selftest(const ak_mesh* m, int absent) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2);
+  cfg.blockDim = dim3(32);
+  cfg.stream = m->stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, barrier_selftest_kernel, m->d_sc, absent);
+}

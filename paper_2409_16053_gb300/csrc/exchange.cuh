@@ -149,8 +149,8 @@ __device__ __forceinline__ void xfer_prolong(double* reg, const ak_meshdev& md, 
 
 // Barrier of all CTAs of a cooperative launch (all of them are resident).  One thread per
 // CTA arrives on sc->bar_count; the last one resets it and advances sc->bar_gen, which
-// the others wait for.  The wait is bounded (about a second of clock): a CTA that gives
-// up counts a timeout (AK_ETIMEOUT on the host) and goes on.
+// the others wait for.  The wait is bounded (2e9 clocks, about a second at the maximum
+// SM clock): a CTA that gives up counts a timeout (AK_ETIMEOUT on the host) and goes on.
 __device__ __forceinline__ void grid_barrier(ak_dev_scalars* sc) {
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -165,7 +165,7 @@ __device__ __forceinline__ void grid_barrier(ak_dev_scalars* sc) {
     } else {
       const long long t0 = clock64();
       while (*gen == g0) {
-        if (clock64() - t0 > 4000000000ll) {  // ~2 s at the maximum SM clock
+        if (clock64() - t0 > 2000000000ll) {
           atomicAdd(&sc->counters[2], 1ull);
           break;
         }

@@ -218,6 +218,7 @@ def time_form(ak, torch, precision, U0, steps, warmup):
     total_ms = start.elapsed_time(end)
     st1 = [e[0].elapsed_time(e[1]) for e in evs]
     st2 = [e[2].elapsed_time(e[3]) for e in evs]
+    per_step = [e[0].elapsed_time(e[3]) for e in evs]  # stage 1 start to stage 2 end
     dt_next, status = ak.ak_new_dt(h, 0)
     counters = mesh.counters()
     direct = mesh.direct
@@ -225,7 +226,9 @@ def time_form(ak, torch, precision, U0, steps, warmup):
     del mesh
     torch.cuda.empty_cache()
     return {"total_ms": total_ms, "stage1_ms": statistics.mean(st1),
-            "stage2_ms": statistics.mean(st2), "dt_after": dt_next, "counters": counters,
+            "stage2_ms": statistics.mean(st2),
+            "step_ms": {"best": min(per_step), "median": statistics.median(per_step)},
+            "dt_after": dt_next, "counters": counters,
             "direct": direct,
             "schedule": {"tile": schedule[0], "x3_segments": schedule[1],
                          "order": schedule[2]}}
@@ -565,6 +568,7 @@ def main():
         },
         "stage_ms": {"fp64": [r64["stage1_ms"], r64["stage2_ms"]],
                      "mixed": [rmx["stage1_ms"], rmx["stage2_ms"]]},
+        "step_ms_best_median": {"fp64": r64["step_ms"], "mixed": rmx["step_ms"]},
         "counters": {"fp64": r64["counters"], "mixed": rmx["counters"]},
         "l1_error": l1,
         "smr": smr,

@@ -323,6 +323,21 @@ def cpu_baseline(sample_n=96, budget_s=12.0, steps_max=None):
                       f"recipe, FP64 oracle, OpenMP), {el:.1f} s"}
 
 
+def cpu_baseline_one_core(sample_n=48, budget_s=5.0):
+    """The same oracle sample on one host core (a child process with OMP_NUM_THREADS=1,
+    since the thread count is fixed when the oracle library loads)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench.cpu_baseline(sample_n=%d, budget_s=%r)))"
+            % (ROOT, sample_n, budget_s))
+    try:
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True,
+                           env=env, timeout=120)
+        return json.loads(r.stdout.strip().splitlines()[-1])
+    except Exception as e:  # reported, not fatal: the headline numbers do not depend on it
+        return {"unavailable": str(e)[:200]}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -580,6 +595,7 @@ def main():
     }
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
+        line["cpu_baseline"]["one_core"] = cpu_baseline_one_core()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -6,6 +6,7 @@ paper reports for PLM/PPM4 on linear waves (Section 3.1).  A plausible mistake i
 oracle (a dropped term, a wrong sign or index, a transposed operand) fails one of them.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -209,6 +210,19 @@ def test_exact_riemann_jump_conditions(wl, wr, g):
             cs = math.sqrt(g * ps / rs)
             assert math.isclose(u - sgn * 2 * c / (g - 1), us - sgn * 2 * cs / (g - 1),
                                 rel_tol=1e-12, abs_tol=1e-12)
+
+
+def test_exact_riemann_star_states_match_toro_table():
+    # golden fixture: Toro (2009) Chapter 4, the five test problems' star states
+    path = os.path.join(os.path.dirname(__file__), "golden", "toro_exact_star.txt")
+    rows = [list(map(float, ln.split())) for ln in open(path)
+            if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 5
+    for r in rows:
+        ps, us = oracle.exact_star(r[0:3], r[3:6], 1.4)
+        # printed to ~6 digits (test 5's inputs are themselves rounded): 2e-5 relative
+        assert abs(ps - r[6]) <= 2e-5 * r[6] + 1e-5, (r, ps)
+        assert abs(us - r[7]) <= 2e-5 * abs(r[7]) + 1e-5, (r, us)
 
 
 def test_exact_riemann_fan_is_self_similar_isentrope():

@@ -101,6 +101,8 @@ def _load():
             lib.orc_llf.argtypes = [_dp, _dp, ctypes.c_double, _dp]
             lib.orc_rhs.argtypes = [G, _dp, _dp]
             lib.orc_rhs.restype = ctypes.c_int64
+            lib.orc_rhs_flagged.argtypes = [G, _dp, _dp, ctypes.POINTER(ctypes.c_uint8)]
+            lib.orc_rhs_flagged.restype = ctypes.c_int64
             lib.orc_rk_step.argtypes = [G, _dp, ctypes.c_double, ctypes.c_int]
             lib.orc_rk_step.restype = ctypes.c_int64
             lib.orc_rk_step_fofc.argtypes = [G, _dp, ctypes.c_double, ctypes.c_int, _i64p]
@@ -243,6 +245,17 @@ def rhs(U, grid: Grid):
     nf = _load().orc_rhs(grid._c(), _ptr(U), _ptr(L))
     if nf < 0:
         raise MemoryError("oracle rhs allocation failed")
+    return L, int(nf)
+
+
+def rhs_flagged(U, grid: Grid, flag):
+    """L(U) with first-order LLF fluxes on the faces of the cells where flag (shape
+    (n3, n2, n1)) is nonzero: the FOFC right-hand side of one stage."""
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    f = np.ascontiguousarray(flag, dtype=np.uint8)
+    L = np.zeros_like(U)
+    nf = _load().orc_rhs_flagged(grid._c(), _ptr(U), _ptr(L),
+                                f.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
     return L, int(nf)
 
 

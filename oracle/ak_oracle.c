@@ -541,6 +541,13 @@ int64_t orc_rhs(const orc_grid* g, const double* U, double* L) {
   return rhs_impl(g, U, L, NULL);
 }
 
+/* L(U) with the first-order LLF flux on every face next to a flagged cell (flag: one
+ * byte per cell, x1 fastest). */
+int64_t orc_rhs_flagged(const orc_grid* g, const double* U, double* L,
+                        const unsigned char* flag) {
+  return rhs_impl(g, U, L, flag);
+}
+
 /* ---------------------------------------------------------------------------------
  * One SSP-RK step (Section 3, method of lines with SSP-RK; reading of the standard
  * coefficients).  Stage s: U <- a_s*U0 + b_s*(U + dt*L(U)).  Returns the number of

@@ -420,9 +420,11 @@ extern "C" ak_status ak_mesh_create(const ak_mesh_desc* d, void* cuda_stream, ak
     m->md.fofc = 1;
     dmalloc((void**)&m->d_fflag, (size_t)m->interior_cells);
     dmalloc((void**)&m->d_flist, sizeof(int4) * (size_t)m->md.fcap);
+    dmalloc((void**)&m->d_fu0, sizeof(double) * 5 * (size_t)m->md.fcap);
     if (e == cudaSuccess) e = cudaMemset(m->d_fflag, 0, (size_t)m->interior_cells);
     m->md.fflag = m->d_fflag;
     m->md.flist = m->d_flist;
+    m->md.fu0 = m->d_fu0;
   }
   if (e == cudaSuccess) e = ak_build_work(m, 0, seg, 0);
   if (e == cudaSuccess) e = ak_stage_prepare(m);
@@ -502,6 +504,7 @@ extern "C" void ak_mesh_destroy(ak_mesh* m) {
   cudaFree(m->d_xb);
   cudaFree(m->d_fflag);
   cudaFree(m->d_flist);
+  cudaFree(m->d_fu0);
   cudaFree(m->d_work);
   cudaFree(m->d_sc);
   cudaFree(m->d_staging);

@@ -89,6 +89,7 @@ struct ak_meshdev {
   const long long* cell_off;  // first interior cell of each block in the global count
   unsigned char* fflag; // FOFC: 1 for a flagged interior cell (global count), else 0
   int4* flist;          // FOFC: flagged cells (block, i, j, k) of the current stage
+  double* fu0;          // FOFC: U0 of each listed cell, [entry][5] (stages that use U0)
   int fcap;             // capacity of flist
   int fofc;             // FOFC on
   int direct;           // stage kernels read halo cells from the neighbour blocks (uniform
@@ -122,6 +123,7 @@ struct ak_mesh {
   long long* d_pad_off;         // padded-cell prefix sums per block (nblocks + 1)
   unsigned char* d_fflag;       // FOFC flags and list (see ak_meshdev)
   int4* d_flist;
+  double* d_fu0;
   ak_xfer* d_xa;                // exchange plan (see ak_xfer)
   ak_xfer* d_xb;
   ak_work* d_work;

@@ -340,7 +340,13 @@ __global__ void __launch_bounds__(MxCfg<NG, T>::NTH, 2)
           un[v] = r;
           uout[e + v * vst] = r;
         }
-        if (md.fofc) fofc_flag(un, md, sc, w.block, g, ci, cj, kc);
+        if (md.fofc) {
+          const int fi = fofc_flag(un, md, sc, w.block, g, ci, cj, kc);
+          if (fi >= 0 && form != 0) {
+#pragma unroll
+            for (int v = 0; v < 5; ++v) md.fu0[(long long)fi * 5 + v] = ucol[(5 + v) * NOWN + tid];
+          }
+        }
         if (last_stage) {
           // CFL ratio in FP32: it only sets the next step's dt
           const float rho = fmaxf(f64_to_f32(un[0]), (float)AK_RHO_FLOOR);

@@ -184,6 +184,33 @@ __device__ __forceinline__ void ppmx_edges(R q0, R q1, R q2, R q3, R q4, R& lo, 
   hi = ahi;
 }
 
+// WENO-Z value at the face between c and d of the cells a, b, c, d, e (c the cell), in
+// FP64 with IEEE division and the plain left-to-right order of the definition: the
+// candidates (2a - 7b + 11c)/6, (-b + 5c + 2d)/6, (2c + 5d - e)/6, the indicators
+// 13/12 (second difference)^2 + 1/4 (first difference)^2, tau5 = |beta_0 - beta_2| and
+// the weights d_k (1 + tau5 / (beta_k + eps)).  The FP64 form uses it for both faces
+// (the lower one on the mirrored stencil): in extreme flows, where a reconstructed
+// pressure sits at zero, the last bit of these weights decides which faces FOFC
+// corrects.  The FP32 form uses wenoz_edges below.
+__device__ __forceinline__ double wenoz_value_fp64(double a, double b, double c, double d,
+                                                   double e) {
+  const double p0 = (2.0 * a - 7.0 * b + 11.0 * c) / 6.0;
+  const double p1 = (-b + 5.0 * c + 2.0 * d) / 6.0;
+  const double p2 = (2.0 * c + 5.0 * d - e) / 6.0;
+  const double s0 = a - 2.0 * b + c, t0 = a - 4.0 * b + 3.0 * c;
+  const double s1 = b - 2.0 * c + d, t1 = b - d;
+  const double s2 = c - 2.0 * d + e, t2 = 3.0 * c - 4.0 * d + e;
+  const double b0 = 13.0 / 12.0 * s0 * s0 + 0.25 * t0 * t0;
+  const double b1 = 13.0 / 12.0 * s1 * s1 + 0.25 * t1 * t1;
+  const double b2 = 13.0 / 12.0 * s2 * s2 + 0.25 * t2 * t2;
+  const double tau = fabs(b0 - b2);
+  const double eps = 1e-40;
+  const double a0 = 0.1 * (1.0 + tau / (b0 + eps));
+  const double a1 = 0.6 * (1.0 + tau / (b1 + eps));
+  const double a2 = 0.3 * (1.0 + tau / (b2 + eps));
+  return (a0 * p0 + a1 * p1 + a2 * p2) / (a0 + a1 + a2);
+}
+
 // WENO-Z (Borges et al. 2008) values at both faces of the middle cell of q0..q4: the
 // three third-order candidates of Jiang & Shu (1996), their smoothness indicators
 // beta_k, tau5 = |beta_0 - beta_2| and weights alpha_k = d_k (1 + tau5 / (beta_k + eps))
@@ -227,10 +254,26 @@ __device__ __forceinline__ void wenoz_edges(R a, R b, R c, R d, R e, R& lo, R& h
   }
 }
 
+// A face state without a sound speed (rho p < 0 after reconstruction) has no physical
+// flux: with NANCHK the flux is NaN, as the IEEE square root makes it.  The integer-pipe
+// comparisons of the solvers would otherwise carry on with finite wave speeds; a NaN
+// flux instead leaves the cells next to the face not a number, which FOFC flags and
+// replaces by first-order fluxes.  Only reconstructions that can overshoot (WENO-Z,
+// PPMX) need it: PLM and PPM4 keep face values between the cells' values.
+__device__ __forceinline__ bool no_sound_speed(double cl, double cr) {
+  return ((unsigned)__double2hiint(cl) & 0x7ff00000u) == 0x7ff00000u ||
+         ((unsigned)__double2hiint(cr) & 0x7ff00000u) == 0x7ff00000u;
+}
+__device__ __forceinline__ void nan_flux(double* f) {
+#pragma unroll
+  for (int v = 0; v < 5; ++v) f[v] = __longlong_as_double(0x7ff8000000000000ll);
+}
+
 // ------------------------------------------------------------------------------
 // HLLC, FP64 form.  w = (rho, u_n, u_t1, u_t2, u_g); f = flux of
 // (rho, M_n, M_t1, M_t2, E).
 // ------------------------------------------------------------------------------
+template <bool NANCHK = false>
 __device__ __forceinline__ void hllc_fp64(const double* wl, const double* wr, const Bg& bg,
                                           double* f) {
   // Comparisons run on the integer pipe (dgt/dpos/dnonneg) and powers of two scale
@@ -240,10 +283,10 @@ __device__ __forceinline__ void hllc_fp64(const double* wl, const double* wr, co
   const double rl = wl[0], ul = wl[1], rr = wr[0], ur = wr[1];
   const double pl = gm1 * wl[4];
   const double pr = gm1 * wr[4];
-  // c = sqrt(gamma p / rho) = (gamma p) / sqrt(gamma p rho)
+  // c = sqrt(gamma p / rho) = |gamma p| / sqrt(gamma p rho)
   const double gpl = gamma * pl, gpr = gamma * pr;
-  const double cl = gpl * rsqrt64(gpl * rl);
-  const double cr = gpr * rsqrt64(gpr * rr);
+  const double cl = fabs(gpl) * rsqrt64(gpl * rl);
+  const double cr = fabs(gpr) * rsqrt64(gpr * rr);
 
   // pressure estimate of the linearised (PVRS) solver, then shock-aware speeds
   double ps = fma(-dscale_down((ur - ul) * (rl + rr), 3), cl + cr, dscale_down(pl + pr, 1));
@@ -252,6 +295,7 @@ __device__ __forceinline__ void hllc_fp64(const double* wl, const double* wr, co
   double ql = 1.0, qr = 1.0;
   if (dgt_pos(ps, pl)) ql = sqrt64(fma(kq * (ps - pl), rcp64(pl), 1.0));
   if (dgt_pos(ps, pr)) qr = sqrt64(fma(kq * (ps - pr), rcp64(pr), 1.0));
+  const bool bad = NANCHK && (no_sound_speed(cl, cr) || no_sound_speed(ql, qr));
   double sl = fma(-cl, ql, ul);
   double sr = fma(cr, qr, ur);
   const double dl = ur - cr, dr = ul + cl;
@@ -271,6 +315,7 @@ __device__ __forceinline__ void hllc_fp64(const double* wl, const double* wr, co
     f[2] = mu * wu[2];
     f[3] = mu * wu[3];
     f[4] = (eu + pu) * uu;
+    if (bad) nan_flux(f);
     return;
   }
   const double ml = rl * (sl - ul);  // mass flux through the left wave (frame of S_L)
@@ -296,19 +341,25 @@ __device__ __forceinline__ void hllc_fp64(const double* wl, const double* wr, co
   f[2] = mt * w[2];
   f[3] = mt * w[3];
   f[4] = fma(s, us4 - ek, (ek + pk) * uk);
+  if (bad) nan_flux(f);
 }
 
 // ------------------------------------------------------------------------------
 // LLF (Rusanov), FP64 form: F = (F_L + F_R)/2 - S+ (U_R - U_L)/2,
 // S+ = max(|u_L| + c_L, |u_R| + c_R).
 // ------------------------------------------------------------------------------
+template <bool NANCHK = false>
 __device__ __forceinline__ void llf_fp64(const double* wl, const double* wr, const Bg& bg,
                                          double* f) {
   const double gamma = bg.gamma, gm1 = bg.gm1;
   const double rl = wl[0], ul = wl[1], rr = wr[0], ur = wr[1];
   const double pl = gm1 * wl[4], pr = gm1 * wr[4];
   const double gpl = gamma * pl, gpr = gamma * pr;
-  const double cl = gpl * rsqrt64(gpl * rl), cr = gpr * rsqrt64(gpr * rr);
+  const double cl = fabs(gpl) * rsqrt64(gpl * rl), cr = fabs(gpr) * rsqrt64(gpr * rr);
+  if (NANCHK && no_sound_speed(cl, cr)) {
+    nan_flux(f);
+    return;
+  }
   const double al = fabs(ul) + cl, ar = fabs(ur) + cr;
   const double sm = -(dgt_pos(al, ar) ? al : ar);
   const double el = fma(dscale(rl, -1), fma(ul, ul, fma(wl[2], wl[2], wl[3] * wl[3])), wl[4]);
@@ -326,13 +377,18 @@ __device__ __forceinline__ void llf_fp64(const double* wl, const double* wr, con
 // b- = min(S_L, 0), b+ = max(S_R, 0), S_L = min(u_L - c_L, u~ - c~),
 // S_R = max(u_R + c_R, u~ + c~) from the Roe averages (weights sqrt(rho)).
 // ------------------------------------------------------------------------------
+template <bool NANCHK = false>
 __device__ __forceinline__ void hlle_fp64(const double* wl, const double* wr, const Bg& bg,
                                           double* f) {
   const double gamma = bg.gamma, gm1 = bg.gm1;
   const double rl = wl[0], ul = wl[1], rr = wr[0], ur = wr[1];
   const double pl = gm1 * wl[4], pr = gm1 * wr[4];
   const double gpl = gamma * pl, gpr = gamma * pr;
-  const double cl = gpl * rsqrt64(gpl * rl), cr = gpr * rsqrt64(gpr * rr);
+  const double cl = fabs(gpl) * rsqrt64(gpl * rl), cr = fabs(gpr) * rsqrt64(gpr * rr);
+  if (NANCHK && no_sound_speed(cl, cr)) {
+    nan_flux(f);
+    return;
+  }
   const double el = fma(dscale(rl, -1), fma(ul, ul, fma(wl[2], wl[2], wl[3] * wl[3])), wl[4]);
   const double er = fma(dscale(rr, -1), fma(ur, ur, fma(wr[2], wr[2], wr[3] * wr[3])), wr[4]);
   const double isl = rsqrt64(rl), isr = rsqrt64(rr);  // 1 / sqrt(rho)
@@ -439,8 +495,8 @@ __device__ __forceinline__ void hllc_mixed(const V* wl, const V* wr, const Bg& b
   const V hl = vfma(gg, pl, kel);                          // E + p
   const V hr = vfma(gg, pr, ker);
   const V gpl = vmul(g, pl), gpr = vmul(g, pr);
-  const V cl = vmul(gpl, vrsqrt(vmul(gpl, rl)));           // sqrt(gamma p / rho)
-  const V cr = vmul(gpr, vrsqrt(vmul(gpr, rr)));
+  const V cl = vmul(vabs(gpl), vrsqrt(vmul(gpl, rl)));           // sqrt(gamma p / rho)
+  const V cr = vmul(vabs(gpr), vrsqrt(vmul(gpr, rr)));
 
   // PVRS estimate as a deviation from p_b; p* = max(0, p_b + dps)
   V dps = vfma(vmul(vmul(vset<V>(-0.125f), vsub(ur, ul)), vadd(rl, rr)), vadd(cl, cr),
@@ -531,8 +587,8 @@ __device__ __forceinline__ void llf_mixed(const V* wl, const V* wr, const Bg& bg
   const V kel = vmul(vmul(half, rl), vfma(wl[1], wl[1], vfma(wl[2], wl[2], vmul(wl[3], wl[3]))));
   const V ker = vmul(vmul(half, rr), vfma(wr[1], wr[1], vfma(wr[2], wr[2], vmul(wr[3], wr[3]))));
   const V gpl = vmul(g, pl), gpr = vmul(g, pr);
-  const V cl = vmul(gpl, vrsqrt(vmul(gpl, rl)));
-  const V cr = vmul(gpr, vrsqrt(vmul(gpr, rr)));
+  const V cl = vmul(vabs(gpl), vrsqrt(vmul(gpl, rl)));
+  const V cr = vmul(vabs(gpr), vrsqrt(vmul(gpr, rr)));
   const V al = vadd(vabs(wl[1]), cl), ar = vadd(vabs(wr[1]), cr);
   const V sm = vneg(vsel(vgt(al, ar), al, ar));
   V fl[5], fr[5], d[5];
@@ -557,8 +613,8 @@ __device__ __forceinline__ void hlle_mixed(const V* wl, const V* wr, const Bg& b
   const V ker = vmul(vmul(half, rr), vfma(ur, ur, vfma(wr[2], wr[2], vmul(wr[3], wr[3]))));
   const V hl = vfma(gg, pl, kel), hr = vfma(gg, pr, ker);  // E + p
   const V gpl = vmul(g, pl), gpr = vmul(g, pr);
-  const V cl = vmul(gpl, vrsqrt(vmul(gpl, rl)));
-  const V cr = vmul(gpr, vrsqrt(vmul(gpr, rr)));
+  const V cl = vmul(vabs(gpl), vrsqrt(vmul(gpl, rl)));
+  const V cr = vmul(vabs(gpr), vrsqrt(vmul(gpr, rr)));
   const V isl = vrsqrt(rl), isr = vrsqrt(rr);              // 1 / sqrt(rho)
   const V iw = vrcp(vadd(vmul(rl, isl), vmul(rr, isr)));   // 1 / (sqrt(rho_L) + sqrt(rho_R))
   const V sl = vmul(rl, isl), sr = vmul(rr, isr);

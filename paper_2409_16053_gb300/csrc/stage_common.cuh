@@ -83,17 +83,54 @@ __device__ __forceinline__ void c2p(const double* u, float* w, const Bg& bg, Cou
   w[4] = dugf;
 }
 
-// The Riemann solver of the mesh (one choice per launch, a uniform branch)
+// FP64 primitive recovery with IEEE division in the plain order of Eq. (4), for the
+// reconstructions that can overshoot (WENO-Z, PPMX): there the sign of a reconstructed
+// face pressure near zero decides which faces FOFC corrects, so their primitives carry
+// the bits of the definition rather than those of the Newton reciprocal.
+__device__ __forceinline__ void c2p_exact(const double* u, double* w, const Bg&, Counters cn) {
+  double rho = u[0];
+  if (not_finite(rho) || not_finite(u[4])) count(cn.nonfinite);
+  if (!(rho >= AK_RHO_FLOOR)) {
+    rho = AK_RHO_FLOOR;
+    count(cn.floors);
+  }
+  w[1] = u[1] / rho;
+  w[2] = u[2] / rho;
+  w[3] = u[3] / rho;
+  double ug = u[4] - 0.5 * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) / rho;
+  if (!(ug >= AK_UG_FLOOR)) {
+    ug = AK_UG_FLOOR;
+    count(cn.floors);
+  }
+  w[0] = rho;
+  w[4] = ug;
+}
+// primitive recovery of the stage kernels: EXACT selects c2p_exact in the FP64 form
+template <bool EXACT>
+__device__ __forceinline__ void c2p_t(const double* u, double* w, const Bg& bg, Counters cn) {
+  if constexpr (EXACT)
+    c2p_exact(u, w, bg, cn);
+  else
+    c2p(u, w, bg, cn);
+}
+template <bool EXACT>
+__device__ __forceinline__ void c2p_t(const double* u, float* w, const Bg& bg, Counters cn) {
+  c2p(u, w, bg, cn);
+}
+
+// The Riemann solver of the mesh (one choice per launch, a uniform branch); NANCHK:
+// NaN flux for a face state without a sound speed (FP64 form)
+template <bool NANCHK = false>
 __device__ __forceinline__ void riemann(const double* wl, const double* wr, const Bg& bg,
                                         double* f) {
   if (bg.rsolver == AK_HLLE)
-    hlle_fp64(wl, wr, bg, f);
+    hlle_fp64<NANCHK>(wl, wr, bg, f);
   else if (bg.rsolver == AK_LLF)
-    llf_fp64(wl, wr, bg, f);
+    llf_fp64<NANCHK>(wl, wr, bg, f);
   else
-    hllc_fp64(wl, wr, bg, f);
+    hllc_fp64<NANCHK>(wl, wr, bg, f);
 }
-template <typename V>
+template <bool NANCHK = false, typename V>
 __device__ __forceinline__ void riemann(const V* wl, const V* wr, const Bg& bg, V* f) {
   if (bg.rsolver == AK_HLLE)
     hlle_mixed(wl, wr, bg, f);
@@ -108,7 +145,12 @@ __device__ __forceinline__ void riemann(const V* wl, const V* wr, const Bg& bg, 
 template <int NG, int RC, typename R>
 __device__ __forceinline__ void edges_t(const R* q, R& lo, R& hi) {
   if constexpr (NG == 3 && RC == AK_WENOZ) {
-    wenoz_edges(q[0], q[1], q[2], q[3], q[4], lo, hi);
+    if constexpr (std::is_same<R, double>::value) {
+      hi = wenoz_value_fp64(q[0], q[1], q[2], q[3], q[4]);
+      lo = wenoz_value_fp64(q[4], q[3], q[2], q[1], q[0]);
+    } else {
+      wenoz_edges(q[0], q[1], q[2], q[3], q[4], lo, hi);
+    }
   } else if constexpr (NG == 3 && RC == AK_PPMX) {
     ppmx_edges(q[0], q[1], q[2], q[3], q[4], lo, hi);
   } else if constexpr (std::is_same<R, float>::value) {
@@ -143,7 +185,7 @@ __device__ __forceinline__ void edges(const R* q, R& lo, R& hi, int recon) {
 
 // HLLC on one face of direction d from edge values in natural variable order; the
 // flux comes back in natural order (rho, M1, M2, M3, E).
-template <typename R>
+template <bool NANCHK = false, typename R>
 __device__ __forceinline__ void solve(int d, const R* l, const R* r, const Bg& bg, R* f) {
   const int perm[5] = {0, 1 + d, 1 + (d + 1) % 3, 1 + (d + 2) % 3, 4};
   R wl[5], wr[5], fn[5];
@@ -152,7 +194,10 @@ __device__ __forceinline__ void solve(int d, const R* l, const R* r, const Bg& b
     wl[n] = l[perm[n]];
     wr[n] = r[perm[n]];
   }
-  riemann(wl, wr, bg, fn);
+  if constexpr (std::is_same<R, double>::value)
+    riemann<NANCHK>(wl, wr, bg, fn);
+  else
+    riemann(wl, wr, bg, fn);
 #pragma unroll
   for (int n = 0; n < 5; ++n) f[perm[n]] = fn[n];
 }
@@ -235,7 +280,10 @@ __device__ __forceinline__ void flux_correction_cell(const double* reg, const ak
         double u[5];
 #pragma unroll
         for (int v = 0; v < 5; ++v) u[v] = __ldcg(reg + e + v * Fb.var_stride);
-        c2p(u, W[mm], bg, cn);
+        if (bg.recon == AK_WENOZ || bg.recon == AK_PPMX)
+          c2p_t<true>(u, W[mm], bg, cn);
+        else
+          c2p_t<false>(u, W[mm], bg, cn);
       }
       R lo_a[5], hi_a[5], lo_b[5], hi_b[5];
 #pragma unroll
@@ -250,7 +298,10 @@ __device__ __forceinline__ void flux_correction_cell(const double* reg, const ak
         edges<NG>(qb, lo_b[v], hi_b[v], bg.recon);
       }
       R f[5];
-      solve(d, hi_a, lo_b, bg, f);
+      if (bg.recon == AK_WENOZ || bg.recon == AK_PPMX)
+        solve<true>(d, hi_a, lo_b, bg, f);
+      else
+        solve<false>(d, hi_a, lo_b, bg, f);
 #pragma unroll
       for (int v = 0; v < 5; ++v) sum[v] += f[v];
     }
@@ -355,22 +406,31 @@ __device__ __forceinline__ double rk_update_mixed(int form, double a, double b, 
   return fma(b, fma(dt, Ld, u), a * u0);
 }
 
+// x > 0 and not NaN (as the comparison x > 0 is), on the integer pipe
+__device__ __forceinline__ bool dpos_num(double x) {
+  const long long b = __double_as_longlong(x);
+  return b > 0 && b <= 0x7ff0000000000000ll;
+}
+
 // FOFC flag of an updated cell (Section 3): density or internal energy not positive,
-// i.e. rho <= 0 or rho (2E) - |M|^2 <= 0.  Flagged cells go to the mesh's list and
-// flag array for the correction kernel (cells beyond the list's capacity are counted
-// and left to the floors).
-__device__ __forceinline__ void fofc_flag(const double* un, const ak_meshdev& md,
-                                          ak_dev_scalars* sc, int blk, const ak_block& g,
-                                          int i, int j, int k) {
+// i.e. not (rho > 0 and rho (2E) - |M|^2 > 0) -- a NaN state, which a high-order flux
+// through a face with negative reconstructed pressure leaves, is flagged as well.
+// Flagged cells go to the mesh's list and flag array for the correction kernel; the
+// list entry is returned (the caller saves the cell's U0 there), or -1 (not flagged, or
+// beyond the list's capacity: counted and left to the floors).
+__device__ __forceinline__ int fofc_flag(const double* un, const ak_meshdev& md,
+                                         ak_dev_scalars* sc, int blk, const ak_block& g,
+                                         int i, int j, int k) {
   const double m2 = fma(un[1], un[1], fma(un[2], un[2], un[3] * un[3]));
-  if (dpos(un[0]) && dpos(fma(un[0], un[4] + un[4], -m2))) return;
+  if (dpos_num(un[0]) && dpos_num(fma(un[0], un[4] + un[4], -m2))) return -1;
   const unsigned idx = atomicAdd(&sc->fofc_n, 1u);
   if (idx < (unsigned)md.fcap) {
     md.flist[idx] = make_int4(blk, i, j, k);
     md.fflag[md.cell_off[blk] + ((long long)k * g.nx2 + j) * g.nx1 + i] = 1;
-  } else {
-    atomicAdd(&sc->fofc_dropped, 1u);
+    return (int)idx;
   }
+  atomicAdd(&sc->fofc_dropped, 1u);
+  return -1;
 }
 
 // Direct halo reads (uniform meshes without FOFC): the element offsets of the first

@@ -70,6 +70,8 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
   //       2 = a U0 + b (U + dt L)
   using C = StageCfg<NG, MIXED, TX, TY, TMA_OUT>;
   using R = typename C::R;
+  // reconstructions that can overshoot: a face without a sound speed gives a NaN flux
+  constexpr bool NANCHK = RC == AK_WENOZ || RC == AK_PPMX;
   constexpr int NT = C::NT, WX = C::WX, NPL = C::NPL, NR = C::NR, NPT = C::NPT;
   constexpr int C1 = TX + 2;  // x1 edge row length
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -159,7 +161,7 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
     for (int m = 0; m < NPT; ++m) {
       if (pos[m] >= 0) {
         R w[5];
-        c2p(u[m], w, bg, cn);
+        c2p_t<NANCHK>(u[m], w, bg, cn);
 #pragma unroll
         for (int v = 0; v < 5; ++v) dst[v * NPL + pos[m]] = w[v];
       }
@@ -235,7 +237,7 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
             l[v] = e1hi[(v * TY + fy) * C1 + fx];       // cell i-1: column fx
             r[v] = e1lo[(v * TY + fy) * C1 + fx + 1];   // cell i:   column fx+1
           }
-          solve(0, l, r, bg, f);
+          solve<NANCHK>(0, l, r, bg, f);
         }
 #pragma unroll
         for (int v = 0; v < 5; ++v) f1[(v * TY + fy) * (TX + 1) + fx] = f[v];
@@ -257,7 +259,7 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
             l[v] = e2hi[(v * (TY + 2) + fy) * TX + fx];      // cell j-1: row fy
             r[v] = e2lo[(v * (TY + 2) + fy + 1) * TX + fx];  // cell j:   row fy+1
           }
-          solve(1, l, r, bg, f);
+          solve<NANCHK>(1, l, r, bg, f);
         }
 #pragma unroll
         for (int v = 0; v < 5; ++v) f2[(v * (TY + 1) + fy) * TX + fx] = f[v];
@@ -277,7 +279,7 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
     if (k0 == 0 && g.ovr[4] >= 0)
       corrected_flux(md.fcbuf, g.ovr[4] + cj * g.nx1 + ci, f3m);
     else
-      solve(2, hi_a, lo_b, bg, f3m);
+      solve<NANCHK>(2, hi_a, lo_b, bg, f3m);
   }
   __syncthreads();
   load_plane(k0 + NG);
@@ -337,7 +339,7 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
       if (k + 1 == g.nx3 && g.ovr[5] >= 0)
         corrected_flux(md.fcbuf, g.ovr[5] + cj * g.nx1 + ci, f3p);
       else
-        solve(2, hi3, lo3, bg, f3p);
+        solve<NANCHK>(2, hi3, lo3, bg, f3p);
 #pragma unroll
       for (int v = 0; v < 5; ++v) hi3[v] = hi3n[v];
     }
@@ -369,13 +371,28 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
             r = fma(a, u0[e + v * g.var_stride], b * r);
         }
         un[v] = r;
-        if constexpr (TMA_OUT)
-          stg[(((k & 1) * 5 + v) * TY + ty) * TX + tx] = r;
-        else
-          uout[e + v * g.var_stride] = r;
         f3m[v] = f3p[v];
       }
-      if (md.fofc) fofc_flag(un, md, sc, blk, g, ci, cj, k);
+      if (md.fofc) {
+        // a flagged cell's U0, saved before the output (which may overwrite U0) is stored
+        const int fi = fofc_flag(un, md, sc, blk, g, ci, cj, k);
+        if (fi >= 0 && form != 0) {
+#pragma unroll
+          for (int v = 0; v < 5; ++v) {
+            if constexpr (MIXED)
+              md.fu0[(long long)fi * 5 + v] = u0k[v];
+            else
+              md.fu0[(long long)fi * 5 + v] = u0[e + v * g.var_stride];
+          }
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        if constexpr (TMA_OUT)
+          stg[(((k & 1) * 5 + v) * TY + ty) * TX + tx] = un[v];
+        else
+          uout[e + v * g.var_stride] = un[v];
+      }
       if constexpr (TMA_OUT) fence_proxy_async_smem();
       if (last_stage) {
         if constexpr (MIXED) {

@@ -130,3 +130,22 @@ def test_refined_mesh_parity(ak):
     err = np.abs(m.download_packed() - ref).max() / np.abs(ref).max()
     assert err <= 1e-12, err
     m.close()
+
+
+def test_refined_mesh_mixed_close_to_oracle(ak):
+    t = pgen.nested_refinement_blocks(16, 4, 8, 1)
+    P = pgen.blocks_from_fine(t, pgen.turbulence((32, 32, 32), seed=59, kmin=1, kmax=6,
+                                                 mach=0.8))
+    om = oracle.SmrMesh(t, (16, 16, 16), recon=oracle.PPMX)
+    U = om.from_packed(P)
+    dt = om.new_dt(U, 0.3)
+    m = ak.Mesh((16,) * 3, table=t, recon=ak.AK_PPMX, rk=3, precision=1, ref_rho=1.0,
+                ref_p=1.0, xmin=(-0.5,) * 3, xmax=(0.5,) * 3)
+    m.upload_packed(P)
+    U = om.rk_step(U, dt, 3)
+    m.step(dt, want_dt_next=False)
+    ref = om.to_packed(U)
+    err = np.abs(m.download_packed() - ref).max() / np.abs(ref).max()
+    assert err <= 2e-6, err
+    assert m.counters()[:2] == [0, 0]
+    m.close()

@@ -254,20 +254,12 @@ __device__ __forceinline__ void wenoz_edges(R a, R b, R c, R d, R e, R& lo, R& h
   }
 }
 
-// A face state without a sound speed (rho p < 0 after reconstruction) has no physical
-// flux: with NANCHK the flux is NaN, as the IEEE square root makes it.  The integer-pipe
-// comparisons of the solvers would otherwise carry on with finite wave speeds; a NaN
-// flux instead leaves the cells next to the face not a number, which FOFC flags and
-// replaces by first-order fluxes.  Only reconstructions that can overshoot (WENO-Z,
-// PPMX) need it: PLM and PPM4 keep face values between the cells' values.
-__device__ __forceinline__ bool no_sound_speed(double cl, double cr) {
-  return ((unsigned)__double2hiint(cl) & 0x7ff00000u) == 0x7ff00000u ||
-         ((unsigned)__double2hiint(cr) & 0x7ff00000u) == 0x7ff00000u;
-}
-__device__ __forceinline__ void nan_flux(double* f) {
-#pragma unroll
-  for (int v = 0; v < 5; ++v) f[v] = __longlong_as_double(0x7ff8000000000000ll);
-}
+// NANCHK (the FP64 solvers of the reconstructions that can overshoot, WENO-Z and PPMX):
+// the wave-speed tests use IEEE comparisons written as in the definition (a test with a
+// NaN operand is false), instead of the integer-pipe ones, which order a NaN like a large
+// number.  A face state with rho p < 0 has a NaN sound speed; the IEEE tests then pick
+// the same branch -- an upwind flux, or a NaN flux that leaves the cells next to the
+// face not a number for FOFC to flag -- as the definition does.
 
 // ------------------------------------------------------------------------------
 // HLLC, FP64 form.  w = (rho, u_n, u_t1, u_t2, u_g); f = flux of
@@ -290,19 +282,32 @@ __device__ __forceinline__ void hllc_fp64(const double* wl, const double* wr, co
 
   // pressure estimate of the linearised (PVRS) solver, then shock-aware speeds
   double ps = fma(-dscale_down((ur - ul) * (rl + rr), 3), cl + cr, dscale_down(pl + pr, 1));
-  ps = dpos(ps) ? ps : 0.0;
   const double kq = bg.kq;
   double ql = 1.0, qr = 1.0;
-  if (dgt_pos(ps, pl)) ql = sqrt64(fma(kq * (ps - pl), rcp64(pl), 1.0));
-  if (dgt_pos(ps, pr)) qr = sqrt64(fma(kq * (ps - pr), rcp64(pr), 1.0));
-  const bool bad = NANCHK && (no_sound_speed(cl, cr) || no_sound_speed(ql, qr));
-  double sl = fma(-cl, ql, ul);
-  double sr = fma(cr, qr, ur);
-  const double dl = ur - cr, dr = ul + cl;
-  sl = dgt(sl, dl) ? dl : sl;
-  sr = dgt(dr, sr) ? dr : sr;
-
-  const bool sup_l = dnonneg(sl), sup_r = !dpos(sr);
+  double sl, sr;
+  bool sup_l, sup_r;
+  if constexpr (NANCHK) {
+    ps = ps > 0.0 ? ps : 0.0;
+    if (ps > pl) ql = sqrt64(fma(kq * (ps - pl), rcp64(pl), 1.0));
+    if (ps > pr) qr = sqrt64(fma(kq * (ps - pr), rcp64(pr), 1.0));
+    sl = fma(-cl, ql, ul);
+    sr = fma(cr, qr, ur);
+    if (ur - cr < sl) sl = ur - cr;
+    if (ul + cl > sr) sr = ul + cl;
+    sup_l = sl >= 0.0;
+    sup_r = !sup_l && sr <= 0.0;
+  } else {
+    ps = dpos(ps) ? ps : 0.0;
+    if (dgt_pos(ps, pl)) ql = sqrt64(fma(kq * (ps - pl), rcp64(pl), 1.0));
+    if (dgt_pos(ps, pr)) qr = sqrt64(fma(kq * (ps - pr), rcp64(pr), 1.0));
+    sl = fma(-cl, ql, ul);
+    sr = fma(cr, qr, ur);
+    const double dl = ur - cr, dr = ul + cl;
+    sl = dgt(sl, dl) ? dl : sl;
+    sr = dgt(dr, sr) ? dr : sr;
+    sup_l = dnonneg(sl);
+    sup_r = !dpos(sr);
+  }
   if (sup_l || sup_r) {
     // supersonic: the upwind physical flux (S_L >= 0 takes the left state)
     const double* wu = sup_l ? wl : wr;
@@ -315,14 +320,13 @@ __device__ __forceinline__ void hllc_fp64(const double* wl, const double* wr, co
     f[2] = mu * wu[2];
     f[3] = mu * wu[3];
     f[4] = (eu + pu) * uu;
-    if (bad) nan_flux(f);
     return;
   }
   const double ml = rl * (sl - ul);  // mass flux through the left wave (frame of S_L)
   const double mr = rr * (sr - ur);
   const double sstar = fma(ul, ml, fma(-ur, mr, pr - pl)) * rcp64(ml - mr);
 
-  const bool left = dnonneg(sstar);
+  const bool left = NANCHK ? sstar >= 0.0 : dnonneg(sstar);
   const double* w = left ? wl : wr;
   const double rk = w[0], uk = w[1];
   const double pk = left ? pl : pr;
@@ -341,7 +345,6 @@ __device__ __forceinline__ void hllc_fp64(const double* wl, const double* wr, co
   f[2] = mt * w[2];
   f[3] = mt * w[3];
   f[4] = fma(s, us4 - ek, (ek + pk) * uk);
-  if (bad) nan_flux(f);
 }
 
 // ------------------------------------------------------------------------------
@@ -356,12 +359,8 @@ __device__ __forceinline__ void llf_fp64(const double* wl, const double* wr, con
   const double pl = gm1 * wl[4], pr = gm1 * wr[4];
   const double gpl = gamma * pl, gpr = gamma * pr;
   const double cl = fabs(gpl) * rsqrt64(gpl * rl), cr = fabs(gpr) * rsqrt64(gpr * rr);
-  if (NANCHK && no_sound_speed(cl, cr)) {
-    nan_flux(f);
-    return;
-  }
   const double al = fabs(ul) + cl, ar = fabs(ur) + cr;
-  const double sm = -(dgt_pos(al, ar) ? al : ar);
+  const double sm = NANCHK ? -(al > ar ? al : ar) : -(dgt_pos(al, ar) ? al : ar);
   const double el = fma(dscale(rl, -1), fma(ul, ul, fma(wl[2], wl[2], wl[3] * wl[3])), wl[4]);
   const double er = fma(dscale(rr, -1), fma(ur, ur, fma(wr[2], wr[2], wr[3] * wr[3])), wr[4]);
   const double ml = rl * ul, mr = rr * ur;
@@ -385,10 +384,6 @@ __device__ __forceinline__ void hlle_fp64(const double* wl, const double* wr, co
   const double pl = gm1 * wl[4], pr = gm1 * wr[4];
   const double gpl = gamma * pl, gpr = gamma * pr;
   const double cl = fabs(gpl) * rsqrt64(gpl * rl), cr = fabs(gpr) * rsqrt64(gpr * rr);
-  if (NANCHK && no_sound_speed(cl, cr)) {
-    nan_flux(f);
-    return;
-  }
   const double el = fma(dscale(rl, -1), fma(ul, ul, fma(wl[2], wl[2], wl[3] * wl[3])), wl[4]);
   const double er = fma(dscale(rr, -1), fma(ur, ur, fma(wr[2], wr[2], wr[3] * wr[3])), wr[4]);
   const double isl = rsqrt64(rl), isr = rsqrt64(rr);  // 1 / sqrt(rho)
@@ -399,13 +394,21 @@ __device__ __forceinline__ void hlle_fp64(const double* wl, const double* wr, co
   const double wb = fma(sl, wl[3], sr * wr[3]) * iw;
   const double hb = fma(el + pl, isl, (er + pr) * isr) * iw;  // Roe-averaged (E + p)/rho
   const double cb2 = gm1 * fma(-0.5, fma(ub, ub, fma(vb, vb, wb * wb)), hb);
-  const double cb = dpos(cb2) ? sqrt64(cb2) : 0.0;
-  double sL = ul - cl, sR = ur + cr;
-  const double ea = ub - cb, eb = ub + cb;
-  sL = dgt(sL, ea) ? ea : sL;
-  sR = dgt(eb, sR) ? eb : sR;
-  const double bm = dnonneg(sL) ? 0.0 : sL;
-  const double bp = dpos(sR) ? sR : 0.0;
+  double sL = ul - cl, sR = ur + cr, bm, bp;
+  if constexpr (NANCHK) {
+    const double cb = cb2 > 0.0 ? sqrt64(cb2) : 0.0;
+    if (ub - cb < sL) sL = ub - cb;
+    if (ub + cb > sR) sR = ub + cb;
+    bm = sL < 0.0 ? sL : 0.0;
+    bp = sR > 0.0 ? sR : 0.0;
+  } else {
+    const double cb = dpos(cb2) ? sqrt64(cb2) : 0.0;
+    const double ea = ub - cb, eb = ub + cb;
+    sL = dgt(sL, ea) ? ea : sL;
+    sR = dgt(eb, sR) ? eb : sR;
+    bm = dnonneg(sL) ? 0.0 : sL;
+    bp = dpos(sR) ? sR : 0.0;
+  }
   const double ib = rcp64(bp - bm);
   const double bpm = bp * bm;
   const double ml = rl * ul, mr = rr * ur;

@@ -46,8 +46,8 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes per cell of the stage kernels (dram__bytes_read.sum + dram__bytes_write.sum
 # of one ncu capture, 192^3 in 64^3 blocks; the per-cell figure carries over to 256^3 in
 # the same blocks), valid for the kernel sources with this hash (else traffic = null)
-TRAFFIC_SRC_HASH = "221d74966e41126f685d573627029febe2afb69b"
-TRAFFIC_B_PER_CELL = {"fp64": (85.68, 128.72), "mixed": (83.87, 126.87)}
+TRAFFIC_SRC_HASH = "c81eb947d44a150875bbc05774e6c680b6a9fbe0"
+TRAFFIC_B_PER_CELL = {"fp64": (85.48, 128.70), "mixed": (83.83, 126.95)}
 
 
 def kernel_source_hash():

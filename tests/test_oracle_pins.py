@@ -642,3 +642,58 @@ def test_ppmx_rk3_sound_wave_fourth_order():
     x = errs[oracle.PPMX]
     assert x[0] / x[1] > 12 and x[1] / x[2] > 12, x
     assert all(a < 0.1 * b for a, b in zip(x, errs[oracle.PPM4])), errs
+
+
+def test_flagged_rhs_no_flags_and_all_flags():
+    # no flag: the plain right-hand side bit for bit; every cell flagged: the first-order
+    # LLF (Rusanov) scheme on the cells' own states, assembled here face by face
+    n = (6, 5, 4)
+    U = pgen.turbulence(n, seed=12, kmin=1, kmax=2, mach=1.2)
+    g = oracle.Grid(n, recon=oracle.PPMX)
+    L0, _ = oracle.rhs(U, g)
+    L1, _ = oracle.rhs_flagged(U, g, np.zeros((n[2], n[1], n[0]), np.uint8))
+    assert np.array_equal(L0, L1)
+    La, _ = oracle.rhs_flagged(U, g, np.ones((n[2], n[1], n[0]), np.uint8))
+    W = np.stack([oracle.cons_to_prim(U[:, k, j, i])[0]
+                  for k in range(n[2]) for j in range(n[1]) for i in range(n[0])])
+    W = W.reshape(n[2], n[1], n[0], 5)
+    ref = np.zeros_like(U)
+    for d in range(3):
+        perm = [0, 1 + d, 1 + (d + 1) % 3, 1 + (d + 2) % 3, 4]
+        ax = 2 - d
+        for k in range(n[2]):
+            for j in range(n[1]):
+                for i in range(n[0]):
+                    c = [k, j, i]
+                    m = list(c)
+                    m[ax] = (m[ax] - 1) % n[d]
+                    f = oracle.llf(W[tuple(m)][perm], W[tuple(c)][perm], 5.0 / 3.0)
+                    flux = np.empty(5)
+                    flux[perm] = f
+                    # the face below cell c: it adds to c and subtracts from cell m
+                    ref[:, k, j, i] += flux / g.dx[d]
+                    ref[:, m[0], m[1], m[2]] -= flux / g.dx[d]
+    assert np.allclose(La, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+
+
+def test_flagged_rhs_single_cell_is_local_and_conservative():
+    # one flagged cell changes L only in itself and its six face neighbours (every face
+    # of the flagged cell turns first order), and conserves the totals
+    n = (8, 7, 6)
+    U = pgen.turbulence(n, seed=13, kmin=1, kmax=3, mach=1.0)
+    g = oracle.Grid(n, recon=oracle.WENOZ)
+    flag = np.zeros((n[2], n[1], n[0]), np.uint8)
+    fk, fj, fi = 3, 2, 5
+    flag[fk, fj, fi] = 1
+    L0, _ = oracle.rhs(U, g)
+    L1, _ = oracle.rhs_flagged(U, g, flag)
+    changed = np.argwhere(np.abs(L1 - L0).max(axis=0) > 0)
+    expect = {(fk, fj, fi)}
+    for ax, size in ((0, n[2]), (1, n[1]), (2, n[0])):
+        for s in (-1, 1):
+            c = [fk, fj, fi]
+            c[ax] = (c[ax] + s) % size
+            expect.add(tuple(c))
+    assert {tuple(c) for c in changed.tolist()} == expect
+    vol = np.prod(g.dx)
+    assert np.all(np.abs((L1 - L0).reshape(5, -1).sum(axis=1)) * vol < 1e-12)

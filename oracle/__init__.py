@@ -124,6 +124,8 @@ def _load():
             lib.orc_smr_rk_step.argtypes = [S, _dp, ctypes.c_double, ctypes.c_int]
             lib.orc_smr_rk_step.restype = ctypes.c_int64
             lib.orc_smr_rk_step_fofc.argtypes = [S, _dp, ctypes.c_double, ctypes.c_int, _i64p]
+            lib.orc_smr_rhs_flagged.argtypes = [S, _dp, _dp, ctypes.POINTER(ctypes.c_uint8)]
+            lib.orc_smr_rhs_flagged.restype = ctypes.c_int64
             lib.orc_smr_rk_step_fofc.restype = ctypes.c_int64
             lib.orc_smr_new_dt.argtypes = [S, _dp, ctypes.c_double]
             lib.orc_smr_new_dt.restype = ctypes.c_double
@@ -418,6 +420,16 @@ class SmrMesh:
         if _load().orc_smr_rk_step(self._ref(), _ptr(Un), float(dt), int(rk)) != 0:
             raise ValueError("inconsistent SMR mesh")
         return Un
+
+    def rhs_flagged(self, U, flag_packed):
+        """L(U) (ghosts of U filled) with FOFC flags given per interior cell, packed block
+        after block as [block][k][j][i]."""
+        L = np.zeros_like(U)
+        f = np.ascontiguousarray(flag_packed, dtype=np.uint8)
+        if _load().orc_smr_rhs_flagged(self._ref(), _ptr(U), _ptr(L),
+                                       f.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))) != 0:
+            raise ValueError("inconsistent SMR mesh")
+        return L
 
     def rk_step_fofc(self, U, dt, rk=2):
         """One RK step with FOFC (the mesh must be built with fofc=True); returns the new

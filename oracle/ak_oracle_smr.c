@@ -487,6 +487,36 @@ int64_t orc_smr_rhs(const orc_smr* m, const double* U, double* L) {
   return smr_rhs_impl(m, U, L, NULL);
 }
 
+/* L(U) with FOFC flags (Section 3): flag holds one byte per interior cell, block after
+ * block as [block][k][j][i]; the ghost cells take the flags of fill_flag_ghosts, and every
+ * face next to a flagged cell takes the LLF flux of the two cells' own states.  U's ghost
+ * cells must be filled. */
+int64_t orc_smr_rhs_flagged(const orc_smr* m, const double* U, double* L,
+                            const unsigned char* flag_packed) {
+  smr_index x;
+  if (index_build(m, &x) != 0) {
+    index_free(&x);
+    return -1;
+  }
+  int64_t n = orc_smr_storage(m);
+  unsigned char* flag = (unsigned char*)calloc(n / NV, 1);
+  int g = m->ng;
+  int64_t o = 0;
+  for (int b = 0; b < m->nblocks; ++b) {
+    const int32_t* e = m->blocks + 7 * b;
+    int64_t p1 = e[4] + 2 * g, p2 = e[5] + 2 * g;
+    for (int k = 0; k < e[6]; ++k)
+      for (int j = 0; j < e[5]; ++j)
+        for (int i = 0; i < e[4]; ++i)
+          flag[x.off[b] / NV + ((int64_t)(k + g) * p2 + j + g) * p1 + i + g] = flag_packed[o++];
+  }
+  fill_flag_ghosts(&x, flag);
+  int64_t rc = smr_rhs_impl(m, U, L, flag);
+  free(flag);
+  index_free(&x);
+  return rc;
+}
+
 /* One SSP-RK step of every leaf with one dt: ghost fill, then U <- a U0 + b (U + dt L)
  * on interior cells, for each stage.  With m->fofc, each stage first makes the update
  * tentatively, flags the cells whose density or internal energy would not be positive,

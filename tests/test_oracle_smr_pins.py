@@ -243,3 +243,60 @@ def test_blocks_from_fine_keeps_totals():
     tot = m.totals(m.from_packed(pgen.blocks_from_fine(t, Uf)))
     ref = Uf.reshape(5, -1).sum(axis=1) / 32 ** 3
     assert np.allclose(tot, ref, rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("where", ["coarse", "fine"])
+def test_smr_flagged_cell_next_to_the_level_boundary_is_local(where):
+    # Section 3 (FOFC) on two levels.  A flagged coarse cell next to the refined region:
+    # its level-boundary face is the mean of four fine faces, and those turn first order
+    # too (the fine blocks see the flag in their ghost cells), so L changes in the cell,
+    # its five same-level neighbours and the four fine cells across that face.  A flagged
+    # fine cell on the level boundary: L changes in the cell, its five fine neighbours and,
+    # through the flux correction of the face it shares, the coarse cell across it.
+    # Nothing else changes in either case.
+    t = pgen.nested_refinement_blocks(16, 4, 8, 1)
+    P = _smooth_blocks(t, 16)
+    m = oracle.SmrMesh(t, (16, 16, 16))
+    U = m.from_packed(P)
+    m.fill_ghosts(U)
+    sizes = [int(r[4] * r[5] * r[6]) for r in t]
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+
+    def packed_index(level, q):
+        for b, r in enumerate(t):
+            lo = r[1:4]
+            if r[0] == level and all(lo[d] <= q[d] < lo[d] + r[4 + d] for d in range(3)):
+                i, j, k = (q[d] - lo[d] for d in range(3))
+                return int(offs[b] + (k * r[5] + j) * r[4] + i)
+        raise AssertionError(q)
+
+    def around(c):
+        return [c] + [tuple(c[e] + (s if e == d else 0) for e in range(3))
+                      for d in range(3) for s in (-1, 1)]
+
+    flag = np.zeros(offs[-1], np.uint8)
+    # the refined region covers [4, 12)^3 of level 0, [8, 24)^3 of level 1
+    if where == "coarse":
+        c = (3, 6, 6)
+        flag[packed_index(0, c)] = 1
+        expect = {packed_index(0, q) for q in around(c)
+                  if not all(4 <= q[d] < 12 for d in range(3))}
+        expect |= {packed_index(1, (8, 12 + dy, 12 + dz)) for dy in (0, 1) for dz in (0, 1)}
+    else:
+        c = (8, 12, 12)
+        flag[packed_index(1, c)] = 1
+        expect = {packed_index(1, q) for q in around(c) if q[0] >= 8}
+        expect.add(packed_index(0, (3, 6, 6)))
+    Lf = m.rhs_flagged(U, flag)
+    # the flux correction keeps the composite sum of L dV at zero with the flag too
+    scale = m.totals(np.abs(Lf)) + 1.0
+    assert np.all(np.abs(m.totals(Lf)) <= 1e-13 * scale), m.totals(Lf)
+    L0 = m.to_packed(m.rhs(U))
+    L1 = m.to_packed(Lf)
+    # the packed layout is [block][var][k][j][i]: reduce over the variables per block
+    d = np.abs(L1 - L0)
+    per_cell = np.concatenate([d[5 * offs[b]:5 * offs[b + 1]].reshape(5, -1).max(axis=0)
+                               for b in range(len(t))])
+    changed = {int(p) for p in np.nonzero(per_cell > 0)[0]}
+    assert len(expect) == (10 if where == "coarse" else 7)
+    assert changed == expect, (sorted(changed), sorted(expect))

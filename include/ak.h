@@ -28,8 +28,10 @@
  *     one register's interior size; ak_mesh_destroy frees them.
  *   - Argument errors are returned synchronously.  Device-side problems (density or
  *     internal energy below the floors, non-finite states) are counted in a device
- *     status word and reported by the next synchronizing call as AK_ENEGATIVE; the
- *     counters stay readable through ak_status_counters.
+ *     status word and reported by the next synchronizing call as AK_ENEGATIVE (a
+ *     bounded device wait that gave up as AK_ETIMEOUT, an overflowing FOFC list as
+ *     AK_EOVERFLOW, in that order of precedence); the counters stay readable through
+ *     ak_status_counters.
  *   - A mesh object is not thread safe; distinct meshes may be used from distinct
  *     host threads.
  *
@@ -62,7 +64,10 @@ typedef enum {
   AK_ECUDA = -3,      /* a CUDA runtime call failed (see ak_last_error) */
   AK_ENEGATIVE = -4,  /* rho or u_g fell below the floors (see ak_status_counters) */
   AK_ETIMEOUT = -5,   /* a bounded device wait gave up */
-  AK_ESTATE = -6      /* call out of order (e.g. a register not bound) */
+  AK_ESTATE = -6,     /* call out of order (e.g. a register not bound) */
+  AK_EOVERFLOW = -7   /* FOFC: a stage flagged more cells than its list holds
+                         (max(65536, interior cells / 64)); the cells beyond it kept
+                         their uncorrected state */
 } ak_status;
 
 enum { AK_PLM = 0, AK_PPM4 = 1, AK_WENOZ = 2, AK_PPMX = 3 };  /* reconstruction (Section 3) */
@@ -100,7 +105,11 @@ typedef struct {
                                fluxes on all its faces, before the level flux correction
                                on refined meshes (a fine face at a level boundary turns
                                first-order when the fine or the coarse cell is flagged;
-                               the coarse side takes the fine mean).  0: off. */
+                               the coarse side takes the fine mean).  The flagged
+                               cells of one stage go to a list of max(65536, interior
+                               cells / 64) entries; cells beyond it are not corrected
+                               and the next synchronizing call returns AK_EOVERFLOW.
+                               0: off. */
   double gamma;             /* gamma-law EOS, > 1 */
   double cfl;               /* Courant number of Eq. (3), in (0, 1] */
   double ref_rho, ref_p;    /* AK_MIXED only: background density and pressure that are

@@ -23,15 +23,15 @@ import numpy as np
 
 from . import build as _build
 
-AK_OK, AK_EINVAL, AK_ENOMEM, AK_ECUDA, AK_ENEGATIVE, AK_ETIMEOUT, AK_ESTATE = \
-    0, -1, -2, -3, -4, -5, -6
+AK_OK, AK_EINVAL, AK_ENOMEM, AK_ECUDA, AK_ENEGATIVE, AK_ETIMEOUT, AK_ESTATE, AK_EOVERFLOW = \
+    0, -1, -2, -3, -4, -5, -6, -7
 AK_PLM, AK_PPM4, AK_WENOZ, AK_PPMX = 0, 1, 2, 3
 AK_FP64, AK_MIXED = 0, 1
 AK_HLLC, AK_HLLE, AK_LLF = 0, 1, 2
 AK_BLOCK_INTS = 7
 
 _STATUS_NAMES = {0: "AK_OK", -1: "AK_EINVAL", -2: "AK_ENOMEM", -3: "AK_ECUDA",
-                 -4: "AK_ENEGATIVE", -5: "AK_ETIMEOUT", -6: "AK_ESTATE"}
+                 -4: "AK_ENEGATIVE", -5: "AK_ETIMEOUT", -6: "AK_ESTATE", -7: "AK_EOVERFLOW"}
 
 
 class AkError(RuntimeError):
@@ -152,7 +152,8 @@ def ak_new_dt(mesh, reg: int):
 
 
 def ak_step(mesh, dt: float, want_dt_next: bool = True):
-    """Returns (dt_next or None, status); AK_ENEGATIVE is returned, not raised."""
+    """Returns (dt_next or None, status); AK_ENEGATIVE is returned, not raised (any other
+    error, e.g. AK_ETIMEOUT or AK_EOVERFLOW, raises AkError)."""
     if want_dt_next:
         dn = ctypes.c_double()
         st = _check(_lib.ak_step(mesh, float(dt), ctypes.byref(dn)), allow=(AK_ENEGATIVE,))

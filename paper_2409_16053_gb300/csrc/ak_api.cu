@@ -628,7 +628,8 @@ extern "C" ak_status ak_stage(ak_mesh* m, int32_t stage, double dt) {
 }
 
 // Reads the device scalars (synchronizes) and maps new timeouts of bounded device waits
-// to AK_ETIMEOUT and new floor / non-finite counts to AK_ENEGATIVE.
+// to AK_ETIMEOUT, flagged cells beyond the FOFC list to AK_EOVERFLOW and new floor /
+// non-finite counts to AK_ENEGATIVE.
 static ak_status read_scalars(ak_mesh* m, ak_dev_scalars* s) {
   AK_CUDA_TRY(cudaMemcpyAsync(s, m->d_sc, sizeof(*s), cudaMemcpyDeviceToHost, m->stream));
   AK_CUDA_TRY(cudaStreamSynchronize(m->stream));
@@ -636,6 +637,10 @@ static ak_status read_scalars(ak_mesh* m, ak_dev_scalars* s) {
   if (s->counters[2] != s->reported[2]) {
     ak_set_error("bounded device waits that gave up: %llu (since mesh creation)", s->counters[2]);
     st = AK_ETIMEOUT;
+  } else if (s->fofc_dropped != 0) {
+    ak_set_error("FOFC: %u flagged cells beyond the list's %d entries were not corrected",
+                 s->fofc_dropped, m->md.fcap);
+    st = AK_EOVERFLOW;
   } else if (s->counters[0] != s->reported[0] || s->counters[1] != s->reported[1]) {
     ak_set_error("floors applied: %llu, non-finite cells: %llu (since mesh creation)",
                  s->counters[0], s->counters[1]);
@@ -646,6 +651,11 @@ static ak_status read_scalars(ak_mesh* m, ak_dev_scalars* s) {
     unsigned long long rep[4] = {s->counters[0], s->counters[1], s->counters[2], s->counters[3]};
     AK_CUDA_TRY(cudaMemcpyAsync(&m->d_sc->reported, rep, sizeof(rep), cudaMemcpyHostToDevice,
                                 m->stream));
+    // an overflow is reported once: the drop count starts again from zero
+    const unsigned int zero = 0;
+    if (st == AK_EOVERFLOW)
+      AK_CUDA_TRY(cudaMemcpyAsync(&m->d_sc->fofc_dropped, &zero, sizeof(zero),
+                                  cudaMemcpyHostToDevice, m->stream));
     AK_CUDA_TRY(cudaStreamSynchronize(m->stream));
   }
   return st;

@@ -135,3 +135,21 @@ def test_refined_mesh_validation(ak):
     d = _desc_table(ak, bad, 32)
     assert ak._lib.ak_mesh_create(ctypes.byref(d), None, ctypes.byref(out)) == ak.AK_EINVAL
     assert len(lv1) == 56
+
+
+def test_binding_constants_match_the_header(ak):
+    # every enum value and integer #define of include/ak.h that the binding names has the
+    # header's value, and every status code of the header has a name in the binding
+    src = open(os.path.join(ROOT, "include", "ak.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    consts = {n: int(v) for n, v in re.findall(r"\b(AK_[A-Z0-9_]+)\s*=\s*(-?\d+)", src)}
+    consts.update({n: int(v) for n, v in re.findall(r"#define\s+(AK_[A-Z0-9_]+)\s+(-?\d+)\s*$",
+                                                    src, re.M)})
+    assert {"AK_OK", "AK_EOVERFLOW", "AK_PPMX", "AK_LLF", "AK_MIXED"} <= set(consts)
+    named = [n for n in consts if hasattr(ak, n)]
+    assert len(named) >= 16, named
+    for n in named:
+        assert getattr(ak, n) == consts[n], n
+    status = re.search(r"typedef enum \{(.*?)\} ak_status;", src, re.S).group(1)
+    for n in re.findall(r"\b(AK_[A-Z0-9_]+)\s*=", status):
+        assert ak._STATUS_NAMES[consts[n]] == n

@@ -145,3 +145,27 @@ def test_fused_launch_bitwise_with_fofc(ak):
         m.close()
     assert np.array_equal(outs[0][0], outs[1][0])
     assert outs[0][1] == outs[1][1] and outs[0][1][3] > 0
+
+
+def test_list_overflow_is_reported(ak):
+    # A uniform state with negative internal energy flags every cell of a 64^3 mesh, four
+    # times the list's 65536 entries (max(65536, cells / 64)).  The listed cells are
+    # corrected, the others keep their stage output; with uniform fluxes both leave the
+    # state as it was.  Each step reports AK_EOVERFLOW (the drop count starts again after
+    # a report), and every stage counts a full list of corrected cells.
+    n = (64, 64, 64)
+    U = np.zeros((5,) + n)
+    U[0] = 1.0
+    U[4] = -0.1
+    m = ak.Mesh(n, (32, 32, 32), fofc=True)
+    m.upload(U)
+    for s in (1, 2):
+        with pytest.raises(ak.AkError) as e:
+            m.step(1e-4)
+        assert e.value.status == ak.AK_EOVERFLOW, str(e.value)
+        assert "not corrected" in str(e.value)
+        c = m.counters()
+        assert c[3] == 2 * s * 65536 and c[0] > 0 and c[1] == 0 and c[2] == 0, c
+    out = m.download()
+    m.close()
+    assert np.allclose(out, U, rtol=0.0, atol=1e-12)

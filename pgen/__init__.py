@@ -235,12 +235,14 @@ def nested_refinement_blocks(root_nx=128, root_block=32, fine_block=16, levels=2
 
 
 def block_cell_centres(table, root_nx, lo=-0.5, length=1.0):
-    """Per leaf block, the cell-centre coordinates (x1, x2, x3) as 1-D arrays."""
+    """Per leaf block, the cell-centre coordinates (x1, x2, x3) as 1-D arrays.  root_nx:
+    root cells per direction, one int (a cube) or three."""
+    rn = (int(root_nx),) * 3 if np.isscalar(root_nx) else tuple(int(n) for n in root_nx)
     out = []
     for r in np.asarray(table):
         lev = int(r[0])
-        dx = length / (root_nx << lev)
-        out.append(tuple(lo + (r[1 + d] + np.arange(r[4 + d]) + 0.5) * dx for d in range(3)))
+        out.append(tuple(lo + (r[1 + d] + np.arange(r[4 + d]) + 0.5) * (length / (rn[d] << lev))
+                         for d in range(3)))
     return out
 
 
@@ -270,7 +272,8 @@ def sedov_blocks(table, root_nx, e_blast=1.0, r0=0.02, rho=1.0, p_amb=1.0e-5,
 
 def field_blocks(table, root_nx, fn, gamma=5.0 / 3.0, lo=-0.5, length=1.0):
     """Conserved variables from a primitive-state function fn(x, y, z) -> (rho, v1, v2,
-    v3, p) evaluated at the cell centres of every leaf; packed block after block."""
+    v3, p) evaluated at the cell centres of every leaf; packed block after block.
+    root_nx: root cells per direction, one int (a cube) or three."""
     parts = []
     for r, (x, y, z) in zip(np.asarray(table), block_cell_centres(table, root_nx, lo, length)):
         shape = (len(z), len(y), len(x))

@@ -1,7 +1,9 @@
 """Pins of the static-refinement (SMR) oracle: prolongation and restriction against their
 definitions, a uniform state across levels, composite conservation with flux correction
 (and its failure without, as a negative control), equality with the uniform-grid oracle
-when every block is on one level, and the Sedov-Taylor blast radius across levels."""
+when every block is on one level, the Sedov-Taylor blast radius across levels, second-
+order convergence of a sound wave through two level boundaries, and the locality of FOFC
+on two levels."""
 import math
 
 import numpy as np
@@ -300,3 +302,57 @@ def test_smr_flagged_cell_next_to_the_level_boundary_is_local(where):
     changed = {int(p) for p in np.nonzero(per_cell > 0)[0]}
     assert len(expect) == (10 if where == "coarse" else 7)
     assert changed == expect, (sorted(changed), sorted(expect))
+
+
+def _slab_table(n1, n23=8, b=4):
+    # root (n1, n23, n23) in b^3 blocks; level 1 (2b)^3 blocks over the slab of root
+    # cells n1/4 <= x1 < 3 n1/4, across the whole x2-x3 extent: the level boundaries are
+    # two x1 faces
+    rows = [(0, i, j, k, b, b, b) for k in range(0, n23, b) for j in range(0, n23, b)
+            for i in range(0, n1, b) if not n1 // 4 <= i < 3 * n1 // 4]
+    rows += [(1, i, j, k, 2 * b, 2 * b, 2 * b) for k in range(0, 2 * n23, 2 * b)
+             for j in range(0, 2 * n23, 2 * b) for i in range(n1 // 2, 3 * n1 // 2, 2 * b)]
+    return np.array(rows, dtype=np.int32)
+
+
+def _sound_wave_l1(n1, refined):
+    # sound eigenmode along x1 (rho = 1, p = 1/gamma, c_s = 1, amplitude 1e-6), one
+    # period, PLM + HLLC + RK2, CFL 0.3; L1 error (volume weighted) against the start
+    n23 = 8
+    if refined:
+        t = _slab_table(n1, n23)
+    else:
+        t = np.array([(0, i, j, k, 4, 4, 4) for k in range(0, n23, 4)
+                      for j in range(0, n23, 4) for i in range(0, n1, 4)], dtype=np.int32)
+    root = (n1, n23, n23)
+
+    def fn(x, y, z):
+        s = 1e-6 * np.sin(2 * np.pi * (x + 0.5))
+        return 1.0 + s, s, 0.0 * x, 0.0 * x, 1.0 / G53 + s
+    P = pgen.field_blocks(t, root, fn)
+    m = oracle.SmrMesh(t, root)
+    U, time = m.from_packed(P), 0.0
+    while time < 1.0:
+        dt = min(m.new_dt(U, 0.3), 1.0 - time)
+        U = m.rk_step(U, dt, 2)
+        time += dt
+    Q = m.to_packed(U)
+    err, off = np.zeros(5), 0
+    for r in t:
+        n = int(r[4] * r[5] * r[6])
+        dv = 1.0 / ((n1 << int(r[0])) * (n23 << int(r[0])) ** 2)
+        err += np.abs(Q[5 * off:5 * (off + n)] - P[5 * off:5 * (off + n)]).reshape(5, -1).sum(axis=1) * dv
+        off += n
+    return math.sqrt(float((err ** 2).sum()))
+
+
+def test_sound_wave_through_two_level_boundaries_converges():
+    # Section 3.1 (PLM is second order) with the refinement of Section 2: the wave
+    # crosses both level boundaries each period.  The two-level error converges like the
+    # uniform one, and lies between the uniform errors at the root and at the fine
+    # resolution (the slab holds half the box).
+    e = {(n, r): _sound_wave_l1(n, r) for n in (16, 32) for r in (True, False)}
+    e[(64, False)] = _sound_wave_l1(64, False)
+    assert e[(16, True)] / e[(32, True)] > 2.5, e
+    for n in (16, 32):
+        assert e[(2 * n, False)] < e[(n, True)] < e[(n, False)], (n, e)

@@ -153,3 +153,84 @@ def test_binding_constants_match_the_header(ak):
     status = re.search(r"typedef enum \{(.*?)\} ak_status;", src, re.S).group(1)
     for n in re.findall(r"\b(AK_[A-Z0-9_]+)\s*=", status):
         assert ak._STATUS_NAMES[consts[n]] == n
+
+
+def _uniform_rows(n, b, level=0, skip=()):
+    return [(level, i, j, k, b, b, b) for k in range(0, n, b) for j in range(0, n, b)
+            for i in range(0, n, b) if (i, j, k) not in skip]
+
+
+def _invalid_table(case):
+    """(table, root, recon, message fragment) of a mesh that breaks one rule."""
+    import pgen
+    base = pgen.nested_refinement_blocks(16, 4, 8, 1)
+    if case == "level":
+        t = base.copy()
+        t[0, 0] = 16
+        return t, 16, 0, "level out of range"
+    if case == "small_block":
+        return np.array(_uniform_rows(4, 1), np.int32), 4, 0, "block sizes must be >= nghost"
+    if case == "mixed_sizes":
+        t = base.copy()
+        t[0, 4] = 2
+        return t, 16, 0, "same size"
+    if case == "off_lattice":
+        t = base.copy()
+        t[1, 1] += 1
+        return t, 16, 0, "block lattice"
+    if case == "not_tiling_level":
+        # 16^3 in 4^3 blocks on a root of 18: the blocks do not divide the level
+        return np.array(_uniform_rows(16, 4), np.int32), 18, 0, "tile each level"
+    if case == "single_block_refined":
+        t = np.array([(0, 0, 0, 0, 8, 8, 8), (1, 0, 0, 0, 4, 4, 4)], np.int32)
+        return t, 8, 0, "more than one block per level"
+    if case == "odd_refined":
+        t = np.array(_uniform_rows(20, 5) + [(1, 0, 0, 0, 10, 10, 10)], np.int32)
+        return t, 20, 0, "even block sizes"
+    if case == "over_coarser":
+        # a level-0 block put back where level 1 already covers the box
+        t = np.concatenate([base, np.array([(0, 4, 4, 4, 4, 4, 4)], np.int32)])
+        return t, 16, 0, "overlaps a coarser block"
+    if case == "gap":
+        return base[1:].copy(), 16, 0, "do not tile the domain"
+    if case == "level_jump":
+        # root 16 in 4^3 blocks; the corner block refined to level 1, and that block's
+        # own corner block refined to level 2, which then touches level 0 (periodic)
+        rows = _uniform_rows(16, 4, 0, skip={(0, 0, 0)})
+        rows += _uniform_rows(8, 4, 1, skip={(0, 0, 0)})
+        rows += _uniform_rows(8, 4, 2)
+        return np.array(rows, np.int32), 16, 0, "more than one level"
+    raise KeyError(case)
+
+
+@pytest.mark.parametrize("case", [
+    "level", "small_block", "mixed_sizes", "off_lattice", "not_tiling_level",
+    "single_block_refined", "odd_refined", "over_coarser", "gap", "level_jump"])
+def test_each_mesh_rule_is_enforced(ak, case):
+    # every refusal of ak_mesh_create's mesh validation, one broken rule at a time; the
+    # checks run on the host before any device call
+    t, root, recon, msg = _invalid_table(case)
+    d = _desc_table(ak, t, root, recon)
+    out = ctypes.c_void_p()
+    st = ak._lib.ak_mesh_create(ctypes.byref(d), None, ctypes.byref(out))
+    assert st == ak.AK_EINVAL, (case, st, ak.ak_last_error())
+    assert msg in ak.ak_last_error(), (case, ak.ak_last_error())
+    assert out.value is None
+
+
+def test_valid_tables_pass_the_host_checks(ak):
+    # the refined tables of the tests and the bench pass validation (a machine without a
+    # GPU then stops at the first device call, with AK_ECUDA)
+    import pgen
+    tables = [(pgen.nested_refinement_blocks(16, 4, 8, 1), 16),
+              (pgen.nested_refinement_blocks(32, 8, 8, 2), 32),
+              (pgen.nested_refinement_blocks(), 128)]
+    rows = _uniform_rows(16, 4, 0, skip={(0, 0, 0)}) + _uniform_rows(8, 4, 1)
+    tables.append((np.array(rows, np.int32), 16))
+    for t, root in tables:
+        d = _desc_table(ak, t, root)
+        out = ctypes.c_void_p()
+        st = ak._lib.ak_mesh_create(ctypes.byref(d), None, ctypes.byref(out))
+        assert st in (ak.AK_OK, ak.AK_ECUDA, ak.AK_ENOMEM), (st, ak.ak_last_error())
+        if st == ak.AK_OK:
+            ak.ak_mesh_destroy(out)

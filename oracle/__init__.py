@@ -14,14 +14,30 @@ Parity status of each function (what pins it, see tests/test_oracle_*.py):
   ppm4_edges                    parabola reproduction, monotonicity
   ppmx_edges                    cubic / smooth-extremum reproduction, spike and step
                                 cases by hand, mirror symmetry, 1D wave convergence
+  wenoz_edges                   exact for quadratic cell averages, 5th order on
+                                smooth data, mirror symmetry, step; RK3 wave rate
   hllc                          supersonic upwinding, stationary contact, symmetry,
                                 consistency, entropy-wave/sound-wave convergence
+  hlle / llf                    consistency, reflection symmetry, upwinding, LLF's
+                                closed form on a contact, Sod errors ordered
+                                HLLC < HLLE < LLF
   rhs / rk_step                 2nd-order sound and entropy wave convergence,
                                 uniform state bitwise, periodic conservation,
                                 x1/x2/x3 bitwise permutation, Sod vs exact solver
+  rhs_flagged / rk_step_fofc    identity without flags, Rusanov scheme with every
+                                cell flagged, one flagged cell local and
+                                conservative, Mach-5 turbulence kept positive
   new_dt                        closed form on uniform states
   exact_star / exact_sample     Rankine-Hugoniot and isentrope/Riemann-invariant
-                                relations across each wave
+                                relations across each wave; Toro's star states
+  prolong / restrict            linear data exact, restriction of prolongation is
+                                the identity, limited at extrema
+  SmrMesh (ak_oracle_smr.c)     uniform state bitwise across levels, composite
+                                conservation (and its failure without the flux
+                                correction), single-level equality with rk_step /
+                                rk_step_fofc, Sedov-Taylor radius, 2nd-order sound
+                                wave through two level boundaries, FOFC locality
+                                across a level boundary
 """
 from __future__ import annotations
 

@@ -17,10 +17,19 @@ Parity status of each function (what pins it, see tests/test_oracle_*.py):
   wenoz_edges                   exact for quadratic cell averages, 5th order on
                                 smooth data, mirror symmetry, step; RK3 wave rate
   hllc                          supersonic upwinding, stationary contact, symmetry,
-                                consistency, entropy-wave/sound-wave convergence
+                                consistency, entropy-wave/sound-wave convergence;
+                                no mass or energy flux through symmetric colliding
+                                streams up to Mach 50 (the Davis bound)
+  pvrs_pressure / shock_factor  p_pv within O(eps^2) of the exact star pressure for
+  / hllc_speeds                 jumps of size eps; u_K -+ c_K q_K(p*) equals the
+                                Rankine-Hugoniot shock speed for the exact p*; the
+                                speeds bracket the exact fan of weak shocks
+  roe_average / hlle_speeds     u~ -+ c~ equals the shock speed across any single
+                                shock (Roe's property)
   hlle / llf                    consistency, reflection symmetry, upwinding, LLF's
                                 closed form on a contact, Sod errors ordered
-                                HLLC < HLLE < LLF
+                                HLLC < HLLE < LLF; HLLE gives the exact Godunov
+                                flux of an isolated shock in any frame
   rhs / rk_step                 2nd-order sound and entropy wave convergence,
                                 uniform state bitwise, periodic conservation,
                                 x1/x2/x3 bitwise permutation, Sod vs exact solver
@@ -115,6 +124,14 @@ def _load():
             lib.orc_hllc.argtypes = [_dp, _dp, ctypes.c_double, _dp]
             lib.orc_hlle.argtypes = [_dp, _dp, ctypes.c_double, _dp]
             lib.orc_llf.argtypes = [_dp, _dp, ctypes.c_double, _dp]
+            lib.orc_pvrs_pressure.argtypes = [_dp, _dp, ctypes.c_double]
+            lib.orc_pvrs_pressure.restype = ctypes.c_double
+            lib.orc_shock_factor.argtypes = [ctypes.c_double] * 3
+            lib.orc_shock_factor.restype = ctypes.c_double
+            _d = ctypes.POINTER(ctypes.c_double)
+            lib.orc_hllc_speeds.argtypes = [_dp, _dp, ctypes.c_double, _d, _d]
+            lib.orc_hlle_speeds.argtypes = [_dp, _dp, ctypes.c_double, _d, _d]
+            lib.orc_roe_average.argtypes = [_dp, _dp, ctypes.c_double, _d, _d]
             lib.orc_rhs.argtypes = [G, _dp, _dp]
             lib.orc_rhs.restype = ctypes.c_int64
             lib.orc_rhs_flagged.argtypes = [G, _dp, _dp, ctypes.POINTER(ctypes.c_uint8)]
@@ -254,6 +271,41 @@ def hlle(wl, wr, gamma):
 def llf(wl, wr, gamma):
     """LLF (Rusanov) flux."""
     return _flux("orc_llf", wl, wr, gamma)
+
+
+def pvrs_pressure(wl, wr, gamma) -> float:
+    """PVRS star-pressure estimate p_pv of the HLLC wave speeds; w as for hllc()."""
+    wl = np.ascontiguousarray(wl, dtype=np.float64)
+    wr = np.ascontiguousarray(wr, dtype=np.float64)
+    return float(_load().orc_pvrs_pressure(_ptr(wl), _ptr(wr), float(gamma)))
+
+
+def shock_factor(pstar, pk, gamma) -> float:
+    """Shock factor q_K of the HLLC wave speeds for star pressure pstar over p_K."""
+    return float(_load().orc_shock_factor(float(pstar), float(pk), float(gamma)))
+
+
+def _pair(name, wl, wr, gamma):
+    wl = np.ascontiguousarray(wl, dtype=np.float64)
+    wr = np.ascontiguousarray(wr, dtype=np.float64)
+    a, b = ctypes.c_double(), ctypes.c_double()
+    getattr(_load(), name)(_ptr(wl), _ptr(wr), float(gamma), ctypes.byref(a), ctypes.byref(b))
+    return a.value, b.value
+
+
+def hllc_speeds(wl, wr, gamma):
+    """(S_L, S_R) of the HLLC solver: PVRS speeds bounded outward by the Davis speeds."""
+    return _pair("orc_hllc_speeds", wl, wr, gamma)
+
+
+def hlle_speeds(wl, wr, gamma):
+    """(S_L, S_R) of the HLLE solver: Einfeldt's speeds from the Roe averages."""
+    return _pair("orc_hlle_speeds", wl, wr, gamma)
+
+
+def roe_average(wl, wr, gamma):
+    """(u~, c~): Roe-averaged normal velocity and sound speed of two states."""
+    return _pair("orc_roe_average", wl, wr, gamma)
 
 
 def rhs(U, grid: Grid):

@@ -297,22 +297,40 @@ static void phys_flux(const double w[5], double p, double e, double f[5]) {
   f[4] = (e + p) * w[1];
 }
 
-void orc_hllc(const double wl[5], const double wr[5], double gamma, double f[5]) {
+/* PVRS pressure estimate p_pv (Toro Sec. 9.3 and Sec. 10.5.2): the star pressure of
+ * the Riemann problem linearised about the mean state, with sound speeds
+ * c_K = sqrt(gamma p_K / rho_K). */
+double orc_pvrs_pressure(const double wl[5], const double wr[5], double gamma) {
   double rl = wl[0], ul = wl[1];
   double rr = wr[0], ur = wr[1];
   double pl = (gamma - 1.0) * wl[4];
   double pr = (gamma - 1.0) * wr[4];
-  double el = wl[4] + 0.5 * rl * (wl[1] * wl[1] + wl[2] * wl[2] + wl[3] * wl[3]);
-  double er = wr[4] + 0.5 * rr * (wr[1] * wr[1] + wr[2] * wr[2] + wr[3] * wr[3]);
   double cl = sqrt(gamma * pl / rl);
   double cr = sqrt(gamma * pr / rr);
+  return 0.5 * (pl + pr) - 0.125 * (ur - ul) * (rl + rr) * (cl + cr);
+}
 
-  /* Toro Sec. 10.5.2: pressure-based wave-speed estimate from the PVRS solver. */
-  double ppv = 0.5 * (pl + pr) - 0.125 * (ur - ul) * (rl + rr) * (cl + cr);
+/* Shock factor q_K (Toro Sec. 10.5.2): a wave of side K with star pressure p* above p_K
+ * is a shock, with speed S_L = u_L - c_L q_L (left) or S_R = u_R + c_R q_R (right) and
+ * q_K = sqrt(1 + (gamma + 1) / (2 gamma) (p* / p_K - 1)); otherwise q_K = 1. */
+double orc_shock_factor(double pstar, double pk, double gamma) {
+  if (pstar > pk) return sqrt(1.0 + (gamma + 1.0) / (2.0 * gamma) * (pstar / pk - 1.0));
+  return 1.0;
+}
+
+/* HLLC wave-speed estimates S_L, S_R: the pressure-based speeds of Toro Sec. 10.5.2
+ * with p* = max(0, p_pv), bounded outward by the Davis speeds. */
+void orc_hllc_speeds(const double wl[5], const double wr[5], double gamma, double* sl_out,
+                     double* sr_out) {
+  double ul = wl[1], ur = wr[1];
+  double pl = (gamma - 1.0) * wl[4];
+  double pr = (gamma - 1.0) * wr[4];
+  double cl = sqrt(gamma * pl / wl[0]);
+  double cr = sqrt(gamma * pr / wr[0]);
+  double ppv = orc_pvrs_pressure(wl, wr, gamma);
   double pstar = ppv > 0.0 ? ppv : 0.0;
-  double ql = 1.0, qr = 1.0;
-  if (pstar > pl) ql = sqrt(1.0 + (gamma + 1.0) / (2.0 * gamma) * (pstar / pl - 1.0));
-  if (pstar > pr) qr = sqrt(1.0 + (gamma + 1.0) / (2.0 * gamma) * (pstar / pr - 1.0));
+  double ql = orc_shock_factor(pstar, pl, gamma);
+  double qr = orc_shock_factor(pstar, pr, gamma);
   double sl = ul - cl * ql;
   double sr = ur + cr * qr;
   /* Reading: in strongly colliding supersonic flow the PVRS estimates can cross
@@ -320,6 +338,19 @@ void orc_hllc(const double wl[5], const double wr[5], double gamma, double f[5])
    * keeps S_L < S_R, and changes nothing where the PVRS speeds already bracket them. */
   if (ur - cr < sl) sl = ur - cr;
   if (ul + cl > sr) sr = ul + cl;
+  *sl_out = sl;
+  *sr_out = sr;
+}
+
+void orc_hllc(const double wl[5], const double wr[5], double gamma, double f[5]) {
+  double rl = wl[0], ul = wl[1];
+  double rr = wr[0], ur = wr[1];
+  double pl = (gamma - 1.0) * wl[4];
+  double pr = (gamma - 1.0) * wr[4];
+  double el = wl[4] + 0.5 * rl * (wl[1] * wl[1] + wl[2] * wl[2] + wl[3] * wl[3]);
+  double er = wr[4] + 0.5 * rr * (wr[1] * wr[1] + wr[2] * wr[2] + wr[3] * wr[3]);
+  double sl, sr;
+  orc_hllc_speeds(wl, wr, gamma, &sl, &sr);
 
   /* Toro Eq. (10.37): contact speed. */
   double sstar = (pr - pl + rl * ul * (sl - ul) - rr * ur * (sr - ur)) /
@@ -386,16 +417,17 @@ void orc_llf(const double wl[5], const double wr[5], double gamma, double f[5]) 
   for (int n = 0; n < NVAR; ++n) f[n] = 0.5 * (fl[n] + fr[n]) - 0.5 * smax * (ur[n] - ul[n]);
 }
 
-/* HLLE: HLL flux with Einfeldt's wave speeds from the Roe averages. */
-void orc_hlle(const double wl[5], const double wr[5], double gamma, double f[5]) {
+/* Roe averages of two primitive states (Toro Sec. 10.5.1, Eqs. 10.49-10.53): weights
+ * sqrt(rho), total enthalpy H = (E + p) / rho; returns the averaged normal velocity u~
+ * and sound speed c~ = sqrt((gamma - 1) (H~ - |v~|^2 / 2)), taken as 0 where the
+ * square is not positive. */
+void orc_roe_average(const double wl[5], const double wr[5], double gamma, double* un,
+                     double* cb_out) {
   double rl = wl[0], rr = wr[0];
   double pl = (gamma - 1.0) * wl[4];
   double pr = (gamma - 1.0) * wr[4];
   double el = wl[4] + 0.5 * rl * (wl[1] * wl[1] + wl[2] * wl[2] + wl[3] * wl[3]);
   double er = wr[4] + 0.5 * rr * (wr[1] * wr[1] + wr[2] * wr[2] + wr[3] * wr[3]);
-  double cl = sqrt(gamma * pl / rl);
-  double cr = sqrt(gamma * pr / rr);
-  /* Roe averages (Toro Eq. 10.50): weights sqrt(rho), enthalpy H = (E + p) / rho */
   double sl = sqrt(rl), sr = sqrt(rr);
   double ub[3], hb, q2 = 0.0;
   for (int a = 0; a < 3; ++a) {
@@ -404,10 +436,35 @@ void orc_hlle(const double wl[5], const double wr[5], double gamma, double f[5])
   }
   hb = (sl * (el + pl) / rl + sr * (er + pr) / rr) / (sl + sr);
   double cb2 = (gamma - 1.0) * (hb - 0.5 * q2);
-  double cb = cb2 > 0.0 ? sqrt(cb2) : 0.0;
+  *un = ub[0];
+  *cb_out = cb2 > 0.0 ? sqrt(cb2) : 0.0;
+}
+
+/* Einfeldt's HLLE speeds S_L = min(u_L - c_L, u~ - c~), S_R = max(u_R + c_R, u~ + c~). */
+void orc_hlle_speeds(const double wl[5], const double wr[5], double gamma, double* sl_out,
+                     double* sr_out) {
+  double pl = (gamma - 1.0) * wl[4];
+  double pr = (gamma - 1.0) * wr[4];
+  double cl = sqrt(gamma * pl / wl[0]);
+  double cr = sqrt(gamma * pr / wr[0]);
+  double ub, cb;
+  orc_roe_average(wl, wr, gamma, &ub, &cb);
   double sL = wl[1] - cl, sR = wr[1] + cr;
-  if (ub[0] - cb < sL) sL = ub[0] - cb;
-  if (ub[0] + cb > sR) sR = ub[0] + cb;
+  if (ub - cb < sL) sL = ub - cb;
+  if (ub + cb > sR) sR = ub + cb;
+  *sl_out = sL;
+  *sr_out = sR;
+}
+
+/* HLLE: HLL flux with Einfeldt's wave speeds from the Roe averages. */
+void orc_hlle(const double wl[5], const double wr[5], double gamma, double f[5]) {
+  double rl = wl[0], rr = wr[0];
+  double pl = (gamma - 1.0) * wl[4];
+  double pr = (gamma - 1.0) * wr[4];
+  double el = wl[4] + 0.5 * rl * (wl[1] * wl[1] + wl[2] * wl[2] + wl[3] * wl[3]);
+  double er = wr[4] + 0.5 * rr * (wr[1] * wr[1] + wr[2] * wr[2] + wr[3] * wr[3]);
+  double sL, sR;
+  orc_hlle_speeds(wl, wr, gamma, &sL, &sR);
   double bm = sL < 0.0 ? sL : 0.0;
   double bp = sR > 0.0 ? sR : 0.0;
   double fl[5], fr[5], ul[5], ur[5];

@@ -172,6 +172,155 @@ def test_hllc_resolves_isolated_moving_contact():
 
 
 # ----------------------------------------------------------------------------------
+# Wave-speed estimates of HLLC and HLLE, pinned by the shock relations.
+# ----------------------------------------------------------------------------------
+def _cons(w, g):
+    r, u, v, ww, ug = w
+    return np.array([r, r * u, r * v, r * ww, ug + 0.5 * r * (u * u + v * v + ww * ww)])
+
+
+def _normal_shock(g, pre, mach, family, vt=(0.0, 0.0)):
+    """Face states (w_L, w_R) across one shock of relative Mach number `mach` > 1 moving
+    into the gas `pre` = (rho, u, p), from the normal-shock relations (pressure and
+    density ratios as functions of the Mach number, then the mass flux through the
+    shock).  family 3: the shock runs toward +x, pre-shock gas on the right; family 1:
+    toward -x, pre-shock gas on the left.  Returns (w_L, w_R, S)."""
+    r1, u1, p1 = pre
+    c1 = math.sqrt(g * p1 / r1)
+    m2 = mach * mach
+    s = u1 + mach * c1 if family == 3 else u1 - mach * c1
+    p2 = p1 * (2 * g * m2 - (g - 1)) / (g + 1)
+    r2 = r1 * (g + 1) * m2 / ((g - 1) * m2 + 2)
+    u2 = s + r1 * (u1 - s) / r2
+    w1 = np.array([r1, u1, vt[0], vt[1], p1 / (g - 1)])
+    w2 = np.array([r2, u2, vt[0], vt[1], p2 / (g - 1)])
+    return (w2, w1, s) if family == 3 else (w1, w2, s)
+
+
+def _shock_cases():
+    for g in (1.4, G53):
+        for pre in ((1.0, 0.0, 1.0), (0.3, 0.7, 0.05), (2.0, -1.5, 3.0)):
+            for mach in (1.02, 1.3, 2.0, 4.0, 12.0):
+                for family in (1, 3):
+                    yield g, pre, mach, family
+
+
+def test_normal_shock_states_satisfy_rankine_hugoniot():
+    # the construction used below: F(W_R) - F(W_L) = S (U_R - U_L) in all five rows
+    for g, pre, mach, family in _shock_cases():
+        wl, wr, s = _normal_shock(g, pre, mach, family, vt=(0.3, -0.4))
+        jf = _phys_flux(wr, g) - _phys_flux(wl, g)
+        ju = s * (_cons(wr, g) - _cons(wl, g))
+        assert np.allclose(jf, ju, rtol=0, atol=1e-12 * (np.abs(jf).max() + 1))
+
+
+def test_hllc_shock_factor_gives_the_rankine_hugoniot_shock_speed():
+    # With the exact post-shock pressure as p*, u_R + c_R q_R (right-moving shock) and
+    # u_L - c_L q_L (left-moving shock) are the shock speed the jump conditions give.
+    for g, pre, mach, family in _shock_cases():
+        wl, wr, s = _normal_shock(g, pre, mach, family)
+        pre_w, post_w = (wr, wl) if family == 3 else (wl, wr)
+        pk = (g - 1) * pre_w[4]
+        ck = math.sqrt(g * pk / pre_w[0])
+        q = oracle.shock_factor((g - 1) * post_w[4], pk, g)
+        est = pre_w[1] + ck * q if family == 3 else pre_w[1] - ck * q
+        assert math.isclose(est, s, rel_tol=0, abs_tol=2e-14 * (abs(s) + ck)), (g, mach, family)
+    # no shock (p* <= p_K): the acoustic speed, q_K = 1
+    assert oracle.shock_factor(0.5, 0.7, 1.4) == 1.0
+    assert oracle.shock_factor(0.7, 0.7, 1.4) == 1.0
+
+
+def test_pvrs_pressure_is_second_order_in_the_jump():
+    # p_pv is the star pressure of the linearised Riemann problem, so for data with
+    # jumps of size eps it misses the exact star pressure by O(eps^2): the error falls
+    # 100x when eps falls 10x, whatever the direction of the jump.
+    rng = np.random.default_rng(8)
+    for g in (1.4, G53):
+        for _ in range(20):
+            base = np.array([rng.uniform(0.5, 2.0), rng.normal(0, 0.5), rng.uniform(0.5, 2.0)])
+            d = rng.normal(0, 1, 3)
+            errs = []
+            for eps in (1e-2, 1e-3):
+                a, b = base * (1 - 0.5 * eps * d * [1, 0, 1]), base * (1 + 0.5 * eps * d * [1, 0, 1])
+                a[1], b[1] = base[1] - 0.5 * eps * d[1], base[1] + 0.5 * eps * d[1]
+                ps, _ = oracle.exact_star(a, b, g)
+                wl = np.array([a[0], a[1], 0.0, 0.0, a[2] / (g - 1)])
+                wr = np.array([b[0], b[1], 0.0, 0.0, b[2] / (g - 1)])
+                errs.append(abs(oracle.pvrs_pressure(wl, wr, g) - ps))
+            assert errs[1] < 2e-6 * base[2], errs
+            if errs[1] > 1e-13:
+                assert 40 < errs[0] / errs[1] < 250, errs
+
+
+def test_hllc_speeds_bracket_the_exact_waves_of_weak_shocks():
+    # For a weak isolated shock the PVRS speed matches the shock speed to O(eps^2), and
+    # the Davis bound on the other side of the fan (u_L + c_L behind a right-moving
+    # shock) lies beyond it: S_R = max(PVRS speed, u_L + c_L), the exact fan inside.
+    for g, pre, mach, family in _shock_cases():
+        if mach > 1.05:
+            continue
+        wl, wr, s = _normal_shock(g, pre, mach, family)
+        sl, sr = oracle.hllc_speeds(wl, wr, g)
+        ps, us = oracle.exact_star(wl[[0, 1, 4]] * [1, 1, g - 1], wr[[0, 1, 4]] * [1, 1, g - 1], g)
+        assert sl < us < sr
+        assert (sr >= s) if family == 3 else (sl <= s)
+
+
+def test_hllc_symmetric_collision_has_no_mass_or_energy_flux():
+    # Two equal streams colliding at the face: by mirror symmetry no mass, transverse
+    # momentum or energy crosses it, at any Mach number.  Beyond Mach ~3 the plain PVRS
+    # speeds both lie on one side of the face; bounding them by the Davis speeds
+    # u_R - c_R and u_L + c_L keeps the fan around it.
+    g = G53
+    for mach in (0.5, 2.0, 4.0, 10.0, 50.0):
+        r, p = 1.3, 0.8
+        c = math.sqrt(g * p / r)
+        u = mach * c
+        wl = np.array([r, u, 0.0, 0.0, p / (g - 1)])
+        wr = np.array([r, -u, 0.0, 0.0, p / (g - 1)])
+        f = oracle.hllc(wl, wr, g)
+        sc = r * u * (u + c) + p
+        assert abs(f[0]) <= 1e-14 * sc and abs(f[4]) <= 1e-13 * sc * (u + c), (mach, f)
+        assert f[1] > p
+
+
+def test_roe_average_has_the_shock_speed_as_eigenvalue():
+    # Roe's linearisation satisfies F_R - F_L = A~ (U_R - U_L), so across a single shock
+    # its eigenvalue of that family is the shock speed: u~ + c~ for a right-moving
+    # shock, u~ - c~ for a left-moving one (Toro Sec. 11.2).
+    for g, pre, mach, family in _shock_cases():
+        wl, wr, s = _normal_shock(g, pre, mach, family, vt=(0.2, 0.5))
+        ub, cb = oracle.roe_average(wl, wr, g)
+        est = ub + cb if family == 3 else ub - cb
+        c1 = math.sqrt(g * pre[2] / pre[0])
+        assert math.isclose(est, s, rel_tol=0, abs_tol=1e-13 * (abs(s) + c1)), (g, mach, family)
+
+
+def test_hlle_resolves_isolated_shocks_exactly():
+    # With the Roe speed equal to the shock speed, Einfeldt's S_R (right-moving shock)
+    # or S_L (left-moving) is the shock speed itself, and the HLL flux is the exact
+    # Godunov flux: F(W_L) when the shock has passed the face (S > 0 for a right-moving
+    # one), F(W_R) otherwise; mirror for left-moving shocks.  Frames put the shock at
+    # several speeds around the face.
+    for g, pre, mach, family in _shock_cases():
+        wl0, wr0, s0 = _normal_shock(g, pre, mach, family, vt=(0.1, -0.3))
+        c1 = math.sqrt(g * pre[2] / pre[0])
+        for frac in (-0.8, -0.3, 0.0, 0.4, 0.9):
+            shift = s0 - frac * c1          # frame in which the shock moves at frac * c1
+            wl, wr = wl0.copy(), wr0.copy()
+            wl[1] -= shift
+            wr[1] -= shift
+            s = s0 - shift
+            f = oracle.hlle(wl, wr, g)
+            want = _phys_flux(wl if s > 0 else wr, g)
+            if s == 0:
+                assert np.allclose(_phys_flux(wl, g), _phys_flux(wr, g), rtol=0,
+                                   atol=1e-12 * (np.abs(want).max() + 1))
+            assert np.allclose(f, want, rtol=0, atol=5e-13 * (np.abs(want).max() + 1)), \
+                (g, pre, mach, family, frac)
+
+
+# ----------------------------------------------------------------------------------
 # Exact Riemann solver: pinned by the jump conditions, not by itself.
 # ----------------------------------------------------------------------------------
 def _energy(r, u, p, g):

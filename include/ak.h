@@ -118,8 +118,11 @@ typedef struct {
                                typical state give the smallest rounding error. */
 } ak_mesh_desc;
 
-/* Validates `desc`, copies the block table to the device and allocates the device
- * scalars.  `cuda_stream` is a cudaStream_t (NULL = legacy default stream).
+/* A mesh of MeshBlocks aggregated on one device (Section 2, "MeshBlockPacks": all
+ * MeshBlocks on a device form one structure, so one launch covers them all; static
+ * refinement follows Section 2's block-based design with uniform time steps across
+ * levels).  Validates `desc`, copies the block table to the device and allocates the
+ * device scalars.  `cuda_stream` is a cudaStream_t (NULL = legacy default stream).
  * A valid mesh: blocks of one level share one size; origins lie on the level's block
  * lattice; the leaves tile the periodic box exactly (no overlap within or across
  * levels); and, with several levels, sizes and origins are even, ghost zones see at
@@ -130,19 +133,24 @@ typedef struct {
  * mesh (free with ak_mesh_destroy). */
 ak_status ak_mesh_create(const ak_mesh_desc* desc, void* cuda_stream, ak_mesh** out);
 
-/* Frees what the library allocated; bound registers are not touched.  NULL is a no-op. */
+/* Frees what ak_mesh_create allocated (Section 2's MeshBlockPack goes away with it);
+ * bound registers are not touched.  NULL is a no-op. */
 void ak_mesh_destroy(ak_mesh* mesh);
 
-/* Number of registers the configured integrator needs (2 for RK2, 3 for RK3), bytes of
- * one register, (if block_offset != NULL) the element offset of every block's first
+/* Layout of the dependent variables (Section 2, "Data locality": one device array per
+ * variable set, with the MeshBlock index as an extra dimension, kept on the device).
+ * Reports the number of registers the configured integrator needs (2 for RK2, 3 for
+ * RK3), bytes of one register, (if block_offset != NULL) the element offset of every block's first
  * ghost cell (nblocks entries), and (if strides != NULL) the element strides of
  * (var, k, j, i) inside block 0 (blocks of other sizes follow the same rule).  Any output pointer may be NULL.  Register 0 holds
  * U^n before ak_step and U^{n+1} after it. */
 ak_status ak_mesh_layout(const ak_mesh* mesh, int32_t* nregisters, size_t* register_bytes,
                          int64_t* block_offset, int64_t strides[4]);
 
-/* Borrows `dev_ptr` (device memory of register_bytes bytes, 256-byte aligned) as
- * register `reg` in [0, nregisters).  AK_EINVAL for a bad index, NULL or misaligned
+/* Binds device memory as one register (Section 2, "Data locality": the state lives in
+ * device memory and is never moved to the host by a step).  Borrows `dev_ptr` (device
+ * memory of register_bytes bytes, 256-byte aligned) as register `reg` in
+ * [0, nregisters); the caller keeps ownership.  AK_EINVAL for a bad index, NULL or misaligned
  * pointer. */
 ak_status ak_mesh_bind(ak_mesh* mesh, int32_t reg, double* dev_ptr);
 
@@ -236,16 +244,19 @@ ak_status ak_selftest_barrier(ak_mesh* mesh, int32_t absent);
  * synchronous (rebuilds a small device table), not during a stream capture. */
 ak_status ak_mesh_schedule(ak_mesh* mesh, int32_t tile, int32_t nseg, int32_t order);
 
-/* Host <-> device state transfer through a library staging buffer.  The host array is
+/* Host <-> device state transfer (Section 2, "Data locality": data reaches the host
+ * only for outputs) through a library staging buffer.  The host array is
  * the interior only, packed block after block: [block][var][k][j][i], i fastest
  * (nblocks * 5 * nx1*nx2*nx3 doubles for equal blocks).  Pinned host memory gives
  * asynchronous copies; ak_download synchronizes the stream. */
 ak_status ak_upload(ak_mesh* mesh, int32_t reg, const double* host_interior);
 ak_status ak_download(ak_mesh* mesh, int32_t reg, double* host_interior);
 
-/* Device counters (synchronizes): out[0] floors applied, out[1] non-finite cells seen,
- * out[2] bounded waits that timed out, out[3] cells corrected by FOFC (summed over
- * stages). */
+/* Positivity and failure counters (Section 3: density and internal energy must stay
+ * positive; cells that would not are corrected by FOFC, else floored).  Synchronizes the
+ * stream.  out[0] floors applied, out[1] non-finite cells seen, out[2] bounded waits
+ * that timed out, out[3] cells corrected by FOFC (summed over stages).  The counters
+ * accumulate over the mesh's lifetime. */
 ak_status ak_status_counters(ak_mesh* mesh, int64_t out[4]);
 
 /* Largest number of MeshBlocks ak_cfl_dt_noalloc accepts: the size of its static

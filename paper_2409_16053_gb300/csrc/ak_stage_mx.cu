@@ -12,8 +12,9 @@
 // Per plane k, between two barriers:
 //   P1  x1/x2 edges of plane k (paired); the column's x3 edge of cell k, the x3 face below
 //       it, and the divergence, RK update and CFL of cell k-1 (whose x1/x2 fluxes the
-//       previous P2 left in shared memory); primitive recovery of plane k+NG.  The FP64
-//       work of the update and the recovery overlaps the FP32 reconstruction;
+//       previous P2 left in shared memory); primitive recovery of plane k+NG (first, so
+//       that its dependent FP64 operations overlap the FP32 reconstruction; every column
+//       thread converts its own cell, the first ones also a halo cell);
 //   P2  x1/x2 faces of plane k (paired).
 // The conserved state of plane k+NG+1 and the columns' U_in / U0 of plane k arrive in
 // shared memory by cp.async issued at the start of P2, so no register holds data in
@@ -47,26 +48,34 @@ struct MxCfg {
   static constexpr int WX = TX + 2 * NG, WY = TY + 2 * NG, NPL = WX * WY, NR = 2 * NG;
   static constexpr int NCROSS = TX * TY + 2 * NG * (TX + TY);  // converted cells per plane
   static constexpr int NSPARE = NTH - NOWN;         // threads without a column
-  static constexpr int XPT = (NCROSS - NOWN + NSPARE - 1) / NSPARE;  // their cells
   static_assert(NE == (TY + 2) * TX && NF == (TY + 1) * TX, "square tiles");
-  static_assert(NSPARE > 0, "threads without a column take the extra cells");
+  static_assert(NSPARE > 0, "more edge items than columns");
   static constexpr size_t bytes = sizeof(double) * (5 * NCROSS + 2 * 5 * NOWN) +
                                   sizeof(float) * (NR * 5 * NPL + 4 * 5 * NE + 2 * 5 * NF);
 };
 
 // PERSIST: the persistent fused form (see stage_kernel): ghost fill and flux correction
 // in a cooperative prologue, then a loop over the work list.
-template <int NG, int T, bool PERSIST = false>
+// FORM >= 0, LAST >= 0: the RK form and the last-stage flag fixed at compile time (else
+// the run-time arguments).  FAST: a uniform mesh read through direct halo reads, HLLC,
+// no FOFC and no corrected faces -- the tests of those options compile away, which
+// shortens the plane loop and keeps its code in the instruction cache.
+template <int NG, int T, bool PERSIST = false, int FORM = -1, int LAST = -1, bool FAST = false>
 __global__ void __launch_bounds__(MxCfg<NG, T>::NTH, 2)
     stage_mx_kernel(const double* __restrict__ uin_arg, const double* u0, double* uout,
                     ak_meshdev md, const ak_work* __restrict__ work, Bg bg, double a, double b,
                     int form, ak_dev_scalars* sc, int last_stage, int nwork) {
   // form: 0 = first stage U + dt L; 1 = RK2 final (U0 + U + dt L) / 2;
   //       2 = a U0 + b (U + dt L)
+  static_assert(!(FAST && PERSIST), "the persistent form serves meshes with a ghost fill");
+  if constexpr (FORM >= 0) form = FORM;
+  if constexpr (LAST >= 0) last_stage = LAST;
+  const bool direct = FAST || md.direct;
+  const bool fofc = !FAST && md.fofc;
+  const bool hllc = FAST || bg.rsolver == AK_HLLC;
   using C = MxCfg<NG, T>;
   constexpr int TX = C::TX, WX = C::WX, NPL = C::NPL, NR = C::NR, NE = C::NE, NF = C::NF;
-  constexpr int C1 = C::C1, NOWN = C::NOWN, NCROSS = C::NCROSS, NSPARE = C::NSPARE;
-  constexpr int XPT = C::XPT;
+  constexpr int C1 = C::C1, NOWN = C::NOWN, NCROSS = C::NCROSS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* stg = reinterpret_cast<double*>(smem_raw);          // [5][NCROSS] next plane
   double* ucol = stg + 5 * NCROSS;                              // [2][5][NOWN] U_in, U0
@@ -94,7 +103,7 @@ __global__ void __launch_bounds__(MxCfg<NG, T>::NTH, 2)
   const int tid = threadIdx.x;
   const ak_work w = work[wi];
   const ak_block g = md.blocks[w.block];
-  if (md.direct) neighbour_table(md, w.block, nbr);
+  if (direct) neighbour_table(md, w.block, nbr);
   const int i0 = w.i0, j0 = w.j0, k0 = w.k0, k1 = w.k1;
   const double* ub = uin + g.off;
   const Counters cn{&sc->counters[0], &sc->counters[1]};
@@ -124,10 +133,16 @@ __global__ void __launch_bounds__(MxCfg<NG, T>::NTH, 2)
       x = NG + d % TX;
     }
   };
-  constexpr int NMY = 1 + XPT;  // slot 0: the column threads' cell; slots 1..: spare threads'
-  // cross cell of slot m of this thread (or >= NCROSS: none)
+  // Halo cells of the cross (NCROSS - NOWN) go one each to the first column threads,
+  // whole warps of them: a warp that converted several cells in a row would sit on the
+  // dependent FP64 operations of each and hold the plane's barrier; spread over the
+  // column warps, that latency overlaps their FP32 work.  The spare threads convert none.
+  constexpr int NLOW = NCROSS - NOWN;
+  static_assert(NLOW % 32 == 0 && NLOW <= NOWN, "whole warps of halo cells");
+  constexpr int NMY = 2;  // slot 0: the column's cell; slot 1: a halo cell
   auto cell_of = [&](int m) {
-    return tid < NOWN ? (m == 0 ? tid : NCROSS) : (m == 0 ? NCROSS : tid + NSPARE * (m - 1));
+    if (tid >= NOWN) return NCROSS;
+    return m == 0 ? tid : (tid < NLOW ? NOWN + tid : NCROSS);
   };
   int mypos[NMY];  // ring position of the slot's cell, or -1 (none, or outside the block)
 #pragma unroll
@@ -175,7 +190,7 @@ __global__ void __launch_bounds__(MxCfg<NG, T>::NTH, 2)
       int ip = i0 + x, jp = j0 + y;
       if (ip < g.p1 && jp < g.p2) {
         int code = 4;
-        if (md.direct) {  // a halo chunk comes from the x/y neighbour block
+        if (direct) {  // a halo chunk comes from the x/y neighbour block
           const int dx = ip < NG ? -1 : (ip >= NG + g.nx1 ? 1 : 0);
           const int dy = jp < NG ? -1 : (jp >= NG + g.nx2 ? 1 : 0);
           ip -= dx * g.nx1;
@@ -189,12 +204,12 @@ __global__ void __launch_bounds__(MxCfg<NG, T>::NTH, 2)
   }
   auto stage_plane = [&](int kp) {
     // direct halo reads: ghost planes come from the x3 neighbour blocks
-    const int dz = md.direct ? (kp < 0 ? -1 : (kp >= g.nx3 ? 1 : 0)) : 0;
+    const int dz = direct ? (kp < 0 ? -1 : (kp >= g.nx3 ? 1 : 0)) : 0;
     const long long po = (long long)(kp - dz * g.nx3) * pst;
 #pragma unroll
     for (int m = 0; m < NSC; ++m) {
       if (sc_s[m] >= 0) {
-        const long long base = md.direct ? nbr[(sc_s[m] >> 16) + 9 * (dz + 1)] : g.off;
+        const long long base = direct ? nbr[(sc_s[m] >> 16) + 9 * (dz + 1)] : g.off;
         cp_async16(&stg[sc_s[m] & 0xffff], uin + base + sc_g[m] + po);
       }
     }
@@ -231,7 +246,7 @@ __global__ void __launch_bounds__(MxCfg<NG, T>::NTH, 2)
         const int ip = i0 + x, jp = j0 + y;
         const bool halo = ip < NG || ip >= NG + g.nx1 || jp < NG || jp >= NG + g.nx2 || kp < 0 ||
                           kp >= g.nx3;
-        const double* src = (md.direct && halo)
+        const double* src = (direct && halo)
                                 ? uin + halo_elem(g, nbr, NG, ip, jp, kp)
                                 : ub + ((long long)(kp + NG) * g.p2 + jp) * g.s1 + ip;
         double u[5];
@@ -254,8 +269,10 @@ __global__ void __launch_bounds__(MxCfg<NG, T>::NTH, 2)
   const int fx2 = tid % TX, fy2 = tid / TX;              // x2 face: i0 + fx2, j = j0 + fy2
   const bool face1 = tid < NF && i0 + fx1 <= g.nx1 && j0 + fy1 < g.nx2;
   const bool face2 = tid < NF && i0 + fx2 < g.nx1 && j0 + fy2 <= g.nx2;
-  const int ov1 = !face1 ? -1 : (i0 + fx1 == 0 ? g.ovr[0] : (i0 + fx1 == g.nx1 ? g.ovr[1] : -1));
-  const int ov2 = !face2 ? -1 : (j0 + fy2 == 0 ? g.ovr[2] : (j0 + fy2 == g.nx2 ? g.ovr[3] : -1));
+  const int ov1 = (FAST || !face1) ? -1
+                                   : (i0 + fx1 == 0 ? g.ovr[0] : (i0 + fx1 == g.nx1 ? g.ovr[1] : -1));
+  const int ov2 = (FAST || !face2) ? -1
+                                   : (j0 + fy2 == 0 ? g.ovr[2] : (j0 + fy2 == g.nx2 ? g.ovr[3] : -1));
 
   const int tx = tid % TX, ty = tid / TX;
   const int ci = i0 + tx, cj = j0 + ty;
@@ -292,6 +309,7 @@ __global__ void __launch_bounds__(MxCfg<NG, T>::NTH, 2)
   float dtmin_f = __int_as_float(0x7f800000);
   for (int k = k0;; ++k) {
     const bool plane = k < k1;  // plane k is in this CTA's segment
+    if (plane) convert_staged(k + NG, 0, NMY);  // staged during the previous P2 (or the prologue)
     // ---- P1: x1/x2 edges of plane k (paired); x3 edge of cell k and the face below it;
     //      update of plane k-1; primitive recovery of plane k+NG --------------------------
     if (plane && tid < NE) {
@@ -316,11 +334,22 @@ __global__ void __launch_bounds__(MxCfg<NG, T>::NTH, 2)
     if (column) {
       float lo3[5], hi3k[5], f3hi[5];  // f3hi: the face between cells k-1 and k
       x3_edges(k, lo3, hi3k);
-      if (k == 0 && g.ovr[4] >= 0)
+      if (!FAST && k == 0 && g.ovr[4] >= 0)
         corrected_flux(md.fcbuf, g.ovr[4] + cj * g.nx1 + ci, f3hi);
-      else if (k == g.nx3 && g.ovr[5] >= 0)
+      else if (!FAST && k == g.nx3 && g.ovr[5] >= 0)
         corrected_flux(md.fcbuf, g.ovr[5] + cj * g.nx1 + ci, f3hi);
-      else
+      else if (FAST) {
+        // x3 face: (rho, v3; v1, v2, u_g)
+        const float wl3[5] = {hi3[0], hi3[3], hi3[1], hi3[2], hi3[4]};
+        const float wr3[5] = {lo3[0], lo3[3], lo3[1], lo3[2], lo3[4]};
+        float fn3[5];
+        hllc_mixed(wl3, wr3, bg, fn3);
+        f3hi[0] = fn3[0];
+        f3hi[3] = fn3[1];
+        f3hi[1] = fn3[2];
+        f3hi[2] = fn3[3];
+        f3hi[4] = fn3[4];
+      } else
         solve(2, hi3, lo3, bg, f3hi);
 #pragma unroll
       for (int v = 0; v < 5; ++v) hi3[v] = hi3k[v];
@@ -340,7 +369,7 @@ __global__ void __launch_bounds__(MxCfg<NG, T>::NTH, 2)
           un[v] = r;
           uout[e + v * vst] = r;
         }
-        if (md.fofc) {
+        if (fofc) {
           const int fi = fofc_flag(un, md, sc, w.block, g, ci, cj, kc);
           if (fi >= 0 && form != 0) {
 #pragma unroll
@@ -365,7 +394,6 @@ __global__ void __launch_bounds__(MxCfg<NG, T>::NTH, 2)
       for (int v = 0; v < 5; ++v) f3lo[v] = f3hi[v];
     }
     if (!plane) break;
-    convert_staged(k + NG, 0, NMY);  // staged during the previous P2 (or the prologue)
     __syncthreads();  // Y: edges, plane k+NG; the update's reads of fluxes and U_in / U0
 
     if (k + 1 < k1) stage_plane(k + NG + 1);
@@ -396,7 +424,7 @@ __global__ void __launch_bounds__(MxCfg<NG, T>::NTH, 2)
         wl[n] = make_float2(e1hi[n * NE + l1], e2hi[P2[n] * NE + l2]);
         wr[n] = make_float2(e1lo[n * NE + l1 + 1], e2lo[P2[n] * NE + l2 + TX]);
       }
-      if (bg.rsolver == AK_HLLC) {
+      if (hllc) {
         hllc_mixed(wl, wr, bg, fn);  // both faces in the two lanes
       } else {
         // HLLE / LLF: one face at a time (their packed form did not reproduce the
@@ -452,6 +480,15 @@ __global__ void __launch_bounds__(MxCfg<NG, T>::NTH, 2)
 
 }  // namespace
 
+template <int FORM, int LAST>
+static void launch_fast(const ak_mesh* m, size_t smem, const double* uin, const double* u0,
+                        double* uout, const Bg& bg, double a, double b, int form,
+                        int last_stage) {
+  stage_mx_kernel<2, 16, false, FORM, LAST, true>
+      <<<(unsigned)m->nwork, MxCfg<2, 16>::NTH, smem, m->stream>>>(
+          uin, u0, uout, m->md, m->d_work, bg, a, b, form, m->d_sc, last_stage, m->nwork);
+}
+
 cudaError_t launch_stage_mx(const ak_mesh* m, const double* uin, const double* u0, double* uout,
                             const Bg& bg, double a, double b, int form, int last_stage,
                             bool prepare_only) {
@@ -459,14 +496,34 @@ cudaError_t launch_stage_mx(const ak_mesh* m, const double* uin, const double* u
   auto kern = stage_mx_kernel<2, 16>;
   auto pk = stage_mx_kernel<2, 16, true>;
   if (prepare_only) {
+    void (*fast[6])(const double*, const double*, double*, ak_meshdev, const ak_work*, Bg,
+                    double, double, int, ak_dev_scalars*, int, int) = {
+        stage_mx_kernel<2, 16, false, 0, 0, true>, stage_mx_kernel<2, 16, false, 1, 0, true>,
+        stage_mx_kernel<2, 16, false, 2, 0, true>, stage_mx_kernel<2, 16, false, 0, 1, true>,
+        stage_mx_kernel<2, 16, false, 1, 1, true>, stage_mx_kernel<2, 16, false, 2, 1, true>};
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::bytes);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(pk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::bytes);
+    for (int i = 0; i < 6 && e == cudaSuccess; ++i)
+      e = cudaFuncSetAttribute(fast[i], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::bytes);
     return e;
   }
   if (m->fused)
     return launch_persistent(m, pk, C::NTH, C::bytes, uin, u0, uout, m->md, m->d_work, bg, a, b,
                              form, m->d_sc, last_stage, m->nwork);
+  // the common case: one level read through direct halo reads, HLLC, no FOFC
+  if (m->md.direct && !m->md.fofc && bg.rsolver == AK_HLLC && m->nfc == 0) {
+    const int key = form + 3 * (last_stage ? 1 : 0);
+    switch (key) {
+      case 0: launch_fast<0, 0>(m, C::bytes, uin, u0, uout, bg, a, b, form, last_stage); break;
+      case 1: launch_fast<1, 0>(m, C::bytes, uin, u0, uout, bg, a, b, form, last_stage); break;
+      case 2: launch_fast<2, 0>(m, C::bytes, uin, u0, uout, bg, a, b, form, last_stage); break;
+      case 3: launch_fast<0, 1>(m, C::bytes, uin, u0, uout, bg, a, b, form, last_stage); break;
+      case 4: launch_fast<1, 1>(m, C::bytes, uin, u0, uout, bg, a, b, form, last_stage); break;
+      default: launch_fast<2, 1>(m, C::bytes, uin, u0, uout, bg, a, b, form, last_stage); break;
+    }
+    return cudaGetLastError();
+  }
   kern<<<(unsigned)m->nwork, C::NTH, C::bytes, m->stream>>>(uin, u0, uout, m->md, m->d_work, bg,
                                                             a, b, form, m->d_sc, last_stage,
                                                             m->nwork);

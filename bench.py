@@ -6,7 +6,10 @@ random-phase Gaussian velocity field with shell spectrum E(k) ~ k^-2 on 2 <= |k|
 rms Mach 0.5.  A step is one full RK2 step: ghost fill, stage 1, ghost fill, stage 2
 with the CFL reduction, dt finalisation -- all in libak's CUDA kernels, dt device
 resident (no host round trip inside the timed region).  `value` is the FP64 form; the
-`mixed` object is the same workload in the mixed FP32/FP64 form.
+`mixed` object is the same workload in the mixed FP32/FP64 form.  The line also carries
+the other configurations, each with its own roofline: `smr` (the static-refinement batch,
+1016 leaves), and `large` -- 512^3 in 128^3 blocks with PPM4 + RK3 (FP64 and mixed) and
+768^3 in 96^3 blocks at Mach 2 (mixed, 50 steps).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 N > 1 (under torchrun) runs independent replicas, one per GPU (weak scaling, no data
@@ -295,7 +298,15 @@ def time_smr(ak, torch, precision, steps, warmup):
     c = m.counters()
     m.close()
     torch.cuda.empty_cache()
-    return {"value": cells * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
+    value = cells * steps / (ms * 1e-3)
+    peaks, peak_kind = load_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    gbs = value * 200.0 / 1e9
+    return {"value": value, "unit": UNIT, "ms_per_step": ms / steps,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                         "frac": gbs / hbm, "bytes_per_cell_update": 200.0,
+                         "cells": "leaf cells", "traffic": None,
+                         "peak_source": f"{peak_kind} hbm_gbs"},
             "counters": c, "schedule": {"tile": schedule[0], "x3_segments": schedule[1],
                                         "order": schedule[2], "fused": schedule[4]}}
 
@@ -405,64 +416,65 @@ def run_profile_case(args):
     return 0 if c[:2] == [0, 0] else 1
 
 
-def run_large_case(args):
-    """The large configurations, timed like the main line (device-resident dt,
-    graph-replayed ak_step, CUDA events on the mesh's stream):
+def time_large(ak, torch, case, steps, warmup):
+    """The large configurations, timed like the main line (graph-replayed ak_step with the
+    device-resident dt, CUDA events on the mesh's stream, clocks sampled meanwhile):
       c3: 512^3 in 64 MeshBlocks of 128^3, PPM4 + HLLC + RK3, k^-2 turbulence Mach 0.5,
           FP64 and mixed;
       c5: 768^3 in 512 MeshBlocks of 96^3, PLM + HLLC + RK2, mixed, solenoidal k^-2
-          (2 <= |k| <= 16) turbulence, rms Mach 2, 50 steps.
-    Inputs come from the torch form of the turbulence recipe, generated on the GPU.  Each
-    form also reports the L1 difference from the FP64 oracle after one step on a 64^3
-    sub-box replay (the interior beyond the step's stencil reach), sqrt(sum_k L1_k^2)
-    with L1_k the mean |U_k(GPU) - U_k(oracle)|."""
-    import torch
-    import oracle
+          (2 <= |k| <= 16) turbulence, rms Mach 2, at least 50 steps.
+    Inputs come from the torch form of the turbulence recipe, generated on the GPU.  For
+    c3 the first step of both forms starts from the same state, and the line reports the
+    L1 difference of the mixed state from the FP64 one after it, sqrt(sum_k L1_k^2) with
+    L1_k the mean |U_k(mixed) - U_k(FP64)| over all cells (the FP64 GPU path itself
+    matches the FP64 oracle to 1e-12 on sub-box replays, tests/test_gpu_large.py)."""
     import pgen
-    from paper_2409_16053_gb300 import ak
-    oracle.build()
-    c3 = args.case == "c3"
+    c3 = case == "c3"
     root = 512 if c3 else 768
     nblk = 128 if c3 else 96
     rk = 3 if c3 else 2
     recon = ak.AK_PPM4 if c3 else ak.AK_PLM
-    reach = 9 if c3 else 4
-    steps = args.steps if c3 else max(args.steps, 50)
+    steps = steps if c3 else max(steps, 50)
     forms = [("fp64", ak.AK_FP64), ("mixed", ak.AK_MIXED)] if c3 else [("mixed", ak.AK_MIXED)]
     gen = dict(seed=3, kmin=2, kmax=8, mach=0.5) if c3 else \
         dict(seed=5, kmin=2, kmax=16, mach=2.0, solenoidal=True)
-    lo = (100, 100, 100) if c3 else (90, 300, 700)
     cells = root ** 3
     peaks, peak_kind = load_peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     bytes_cu = 320.0 if rk == 3 else 200.0
-    out = {"case": args.case, "workload": (
+    out = {"workload": (
         f"{root}^3 periodic in {(root // nblk) ** 3} MeshBlocks of {nblk}^3, "
         + ("PPM4+HLLC+RK3, k^-2 turbulence Mach 0.5" if c3 else
            "PLM+HLLC+RK2, solenoidal k^-2 turbulence (2<=|k|<=16) Mach 2")),
-        "metric": "cell-updates/s", "steps": steps, "warmup": args.warmup, "forms": {}}
-    clocks = ClockSampler(0)
+        "cells": cells, "steps": steps, "warmup": warmup,
+        "l2": "inputs larger than L2"}
+    ref = None
     for name, prec in forms:
         U0 = pgen.turbulence_device((root,) * 3, **gen)
-        sub = U0[:, lo[2]:lo[2] + 64, lo[1]:lo[1] + 64, lo[0]:lo[0] + 64].cpu().numpy()
         m = ak.Mesh((root,) * 3, (nblk,) * 3, recon=recon, rk=rk, precision=prec,
                     ref_rho=1.0, ref_p=1.0)
         m.upload_device(U0)
         del U0
         torch.cuda.empty_cache()
-        dt = m.new_dt()
-        m.step(dt, want_dt_next=False)  # one step from the initial state: the replay
-        got = m.download_box(lo, (64,) * 3)
-        grid = oracle.Grid((64,) * 3, length=(64 / root,) * 3,
-                           recon=oracle.PPM4 if c3 else oracle.PLM)
-        ref, _ = oracle.rk_step(sub, grid, dt, rk)
-        c = slice(reach, 64 - reach)
-        l1 = float(np.sqrt(sum(np.mean(np.abs(got[k, c, c, c] - ref[k, c, c, c])) ** 2
-                               for k in range(5))))
-        for _ in range(args.warmup):
+        dt0 = m.new_dt()
+        m.step(dt0, want_dt_next=False)
+        m.stream.synchronize()  # the state is read on another stream below
+        g = m.ng
+        inner = m.register_view(0)[:, :, g:-g, g:-g, g:-g]
+        l1 = None
+        if c3 and name == "fp64":
+            ref = inner.clone()
+        elif c3 and ref is not None:
+            l1 = float(torch.sqrt(sum(((inner[:, v] - ref[:, v]).abs().mean()) ** 2
+                                      for v in range(5))))
+            ref = None
+            torch.cuda.empty_cache()
+        del inner
+        for _ in range(warmup):
             m.step(0.0, want_dt_next=False)
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        clocks = ClockSampler(torch.cuda.current_device())
         clocks.start()
         a.record(m.stream)
         for _ in range(steps):
@@ -473,18 +485,31 @@ def run_large_case(args):
         ms = a.elapsed_time(b)
         value = cells * steps / (ms * 1e-3)
         gbs = value * bytes_cu / 1e9
-        out["forms"][name] = {
-            "value": value, "ms_per_step": ms / steps,
-            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
-                         "frac": gbs / hbm, "bytes_per_cell_update": bytes_cu,
-                         "peak_source": f"{peak_kind} hbm_gbs"},
-            "l1_vs_oracle_subbox": l1, "dt0": dt, "dt_after": m.new_dt(),
-            "counters": m.counters(), "clocks": clk}
+        f = {"value": value, "unit": UNIT, "ms_per_step": ms / steps,
+             "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                          "frac": gbs / hbm, "bytes_per_cell_update": bytes_cu,
+                          "traffic": None, "peak_source": f"{peak_kind} hbm_gbs"},
+             "dt0": dt0, "counters": m.counters(), "clocks": clk}
+        if name == "fp64":
+            f["roofline"]["note"] = "FP64 form: bound by the FP64 unit, not by HBM"
+        if l1 is not None:
+            f["l1_vs_fp64_after_one_step"] = l1
+        out[name] = f
         m.close()
         del m
         torch.cuda.empty_cache()
+    return out
+
+
+def run_large_case(args):
+    """--case c3 / c5: one large configuration on its own, printed as one JSON line."""
+    import torch
+    from paper_2409_16053_gb300 import ak
+    out = time_large(ak, torch, args.case, args.steps, args.warmup)
+    out["case"] = args.case
     print(json.dumps(out), flush=True)
-    return 0 if all(f["counters"][:2] == [0, 0] for f in out["forms"].values()) else 1
+    forms = [v for k, v in out.items() if k in ("fp64", "mixed")]
+    return 0 if all(f["counters"][:2] == [0, 0] for f in forms) else 1
 
 
 def main():
@@ -494,6 +519,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the 512^3 PPM4+RK3 and 768^3 Mach-2 legs")
     ap.add_argument("--case", default="bench",
                     choices=["bench", "profile", "profile-smr", "c3", "c5"])
     ap.add_argument("--form", default="fp64", choices=["fp64", "mixed"])
@@ -542,6 +569,10 @@ def main():
     value64 = job_rate(ws, cells, args.steps, t64)
     valuemx = job_rate(ws, cells, args.steps, tmx)
 
+    large = None
+    if rank == 0 and not args.no_large:
+        large = {"c3": time_large(ak, torch, "c3", min(args.steps, 3), max(args.warmup, 3)),
+                 "c5": time_large(ak, torch, "c5", 50, max(args.warmup, 3))}
     e2e = e2e_form(ak, torch, ak.AK_FP64, U0, max(2, args.steps // 2)) if rank == 0 else None
     e2e_mx = e2e_form(ak, torch, ak.AK_MIXED, U0, max(2, args.steps // 2)) if rank == 0 else None
 
@@ -587,6 +618,7 @@ def main():
         "counters": {"fp64": r64["counters"], "mixed": rmx["counters"]},
         "l1_error": l1,
         "smr": smr,
+        "large": large,
         "e2e": e2e,
         # per form and step: 2 stage launches, the dt finalisation, and a ghost fill
         # before each stage unless the stage kernels read halos directly

@@ -8,7 +8,6 @@
 #include <unordered_map>
 #include <vector>
 
-#include <cudaTypedefs.h>
 
 #include "ak_internal.cuh"
 
@@ -542,43 +541,8 @@ extern "C" ak_status ak_mesh_bind(ak_mesh* m, int32_t reg, double* p) {
   if (reg < 0 || reg >= m->nreg) return einval("ak_mesh_bind: register index out of range");
   if (!p || ((uintptr_t)p & 255u)) return einval("ak_mesh_bind: pointer NULL or not 256-byte aligned");
   m->reg[reg] = p;
-  m->tmap_ok[reg] = ak_encode_register_tmap(m, reg) == 0;
   invalidate_graph(m);
   return AK_OK;
-}
-
-// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link).
-int ak_encode_register_tmap(ak_mesh* m, int reg) {
-  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-  if (!encode) {
-    void* fn = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
-                                         &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess || !fn)
-      return 1;
-    encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
-  }
-  if (m->multilevel) return 4;  // the bulk-tensor view needs blocks of one size
-  const ak_block& g = m->h_blk[0];
-  for (int b = 1; b < m->nblocks; ++b)
-    if (m->h_blk[b].nx1 != g.nx1 || m->h_blk[b].nx2 != g.nx2 || m->h_blk[b].nx3 != g.nx3) return 4;
-  const long long front = g.off;
-  const long long block_stride = m->nblocks > 1 ? m->h_blk[1].off - m->h_blk[0].off : 0;
-  char* base = (char*)m->reg[reg] + sizeof(double) * front;
-  if (((uintptr_t)base & 15u) != 0) return 2;
-  cuuint64_t dims[5] = {(cuuint64_t)g.p1, (cuuint64_t)g.p2, (cuuint64_t)g.p3, 5,
-                        (cuuint64_t)m->nblocks};
-  cuuint64_t strides[4] = {sizeof(double) * (cuuint64_t)g.s1,
-                           sizeof(double) * (cuuint64_t)g.s1 * g.p2,
-                           sizeof(double) * (cuuint64_t)g.var_stride,
-                           sizeof(double) * (cuuint64_t)(block_stride ? block_stride : 32)};
-  cuuint32_t box[5] = {16, 16, 1, 5, 1};
-  cuuint32_t estr[5] = {1, 1, 1, 1, 1};
-  CUresult r = encode(&m->tmap[reg], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 5, base, dims, strides, box,
-                      estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                      CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS ? 0 : 3;
 }
 
 static ak_status need_reg(const ak_mesh* m, int reg, const char* who) {
@@ -604,7 +568,7 @@ extern "C" ak_status ak_fill_ghosts(ak_mesh* m, int32_t reg) {
 static ak_status enqueue_stage(ak_mesh* m, int stage) {
   const int rk = m->desc.rk;
   const int in = stage_in_reg(rk, stage), outr = stage_out_reg(rk, stage);
-  AK_CUDA_TRY(ak_launch_stage(m, stage, m->reg[in], m->reg[0], m->reg[outr], outr, stage == rk));
+  AK_CUDA_TRY(ak_launch_stage(m, stage, m->reg[in], m->reg[0], m->reg[outr], stage == rk));
   if (m->md.fofc)
     AK_CUDA_TRY(ak_launch_fofc(m, stage, m->reg[in], m->reg[outr], stage == rk));
   return AK_OK;
@@ -757,7 +721,7 @@ extern "C" ak_status ak_mesh_autotune(ak_mesh* m, int32_t result[5]) {
         float t = 1e30f;
         for (int rep = 0; rep < 5 && e == cudaSuccess; ++rep) {
           e = cudaEventRecord(ev[0], m->stream);
-          if (e == cudaSuccess) e = ak_launch_stage(m, 1, m->reg[0], m->reg[0], m->reg[1], 1, 0);
+          if (e == cudaSuccess) e = ak_launch_stage(m, 1, m->reg[0], m->reg[0], m->reg[1], 0);
           if (e == cudaSuccess) e = cudaEventRecord(ev[1], m->stream);
           if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
           float ms = 0.f;
@@ -783,7 +747,7 @@ extern "C" ak_status ak_mesh_autotune(ak_mesh* m, int32_t result[5]) {
         e = cudaEventRecord(ev[0], m->stream);
         if (e == cudaSuccess && !fu) e = ak_launch_fill_ghosts(m, m->reg[0]);
         if (e == cudaSuccess && !fu && m->nfc) e = ak_launch_flux_correction(m, m->reg[0]);
-        if (e == cudaSuccess) e = ak_launch_stage(m, 1, m->reg[0], m->reg[0], m->reg[1], 1, 0);
+        if (e == cudaSuccess) e = ak_launch_stage(m, 1, m->reg[0], m->reg[0], m->reg[1], 0);
         if (e == cudaSuccess) e = cudaEventRecord(ev[1], m->stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
         float ms = 0.f;

@@ -2,7 +2,6 @@
 // scalars and the kernel launchers shared by the translation units of the library.
 #pragma once
 
-#include <cuda.h>  // CUtensorMap (tensor maps are encoded through the runtime's entry point)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -100,8 +99,6 @@ struct ak_meshdev {
 };
 
 struct ak_mesh {
-  CUtensorMap tmap[AK_MAX_REG];  // bulk-tensor (TMA) view of each bound register
-  int tmap_ok[AK_MAX_REG];
   ak_mesh_desc desc;
   cudaStream_t stream;
   int nreg;
@@ -154,7 +151,7 @@ cudaError_t ak_launch_flux_correction(const ak_mesh* m, const double* reg);
 cudaError_t ak_launch_pack(const ak_mesh* m, const double* reg, double* packed);
 cudaError_t ak_launch_unpack(const ak_mesh* m, const double* packed, double* reg);
 cudaError_t ak_launch_stage(const ak_mesh* m, int stage, const double* u_in, const double* u0,
-                            double* u_out, int out_reg, int last_stage);
+                            double* u_out, int last_stage);
 cudaError_t ak_launch_cfl(const ak_mesh* m, const double* reg);
 // First-order flux correction after a stage launch (FOFC meshes): corrects the stage's
 // output for the cells it flagged and their neighbours, then clears the flags.
@@ -168,5 +165,4 @@ cudaError_t ak_launch_barrier_selftest(const ak_mesh* m, int absent);
 cudaError_t ak_stage_prepare(const ak_mesh* m);
 // (Re)builds the stage work list for a tile shape, x3 segment count and CTA order.
 cudaError_t ak_build_work(ak_mesh* m, int tile, int nseg, int order);
-// Encodes m->tmap[reg] for register `reg` (uniform meshes); returns 0 on success.
-int ak_encode_register_tmap(ak_mesh* m, int reg);
+

@@ -44,34 +44,34 @@ Bg make_bg(const ak_mesh* m) {
 }
 
 static cudaError_t dispatch(const ak_mesh* m, const double* uin, const double* u0, double* uout,
-                            int out_reg, double a, double b, int rk2_final, int last_stage,
+                            double a, double b, int rk2_final, int last_stage,
                             bool prepare) {
   if (m->desc.recon == AK_PLM)
-    return launch_stage_plm(m, uin, u0, uout, out_reg, a, b, rk2_final, last_stage, prepare);
+    return launch_stage_plm(m, uin, u0, uout, a, b, rk2_final, last_stage, prepare);
   if (m->desc.recon == AK_WENOZ)
-    return launch_stage_wenoz(m, uin, u0, uout, out_reg, a, b, rk2_final, last_stage, prepare);
+    return launch_stage_wenoz(m, uin, u0, uout, a, b, rk2_final, last_stage, prepare);
   if (m->desc.recon == AK_PPMX)
-    return launch_stage_ppmx(m, uin, u0, uout, out_reg, a, b, rk2_final, last_stage, prepare);
-  return launch_stage_ppm4(m, uin, u0, uout, out_reg, a, b, rk2_final, last_stage, prepare);
+    return launch_stage_ppmx(m, uin, u0, uout, a, b, rk2_final, last_stage, prepare);
+  return launch_stage_ppm4(m, uin, u0, uout, a, b, rk2_final, last_stage, prepare);
 }
 
 }  // namespace ak
 
 cudaError_t ak_launch_stage(const ak_mesh* m, int stage, const double* u_in, const double* u0,
-                            double* u_out, int out_reg, int last_stage) {
+                            double* u_out, int last_stage) {
   static const double a2[2] = {0.0, 0.5}, b2[2] = {1.0, 0.5};
   static const double a3[3] = {0.0, 0.75, 1.0 / 3.0}, b3[3] = {1.0, 0.25, 2.0 / 3.0};
   const bool rk3 = m->desc.rk == 3;
   const double a = rk3 ? a3[stage - 1] : a2[stage - 1];
   const double b = rk3 ? b3[stage - 1] : b2[stage - 1];
   const int rk2_final = (!rk3 && stage == 2) ? 1 : 0;
-  return ak::dispatch(m, u_in, u0, u_out, out_reg, a, b, rk2_final, last_stage, false);
+  return ak::dispatch(m, u_in, u0, u_out, a, b, rk2_final, last_stage, false);
 }
 
 // Raises the dynamic shared-memory limit of the stage kernels this mesh uses (called
 // once at mesh creation, outside any stream capture).
 cudaError_t ak_stage_prepare(const ak_mesh* m) {
-  return ak::dispatch(m, nullptr, nullptr, nullptr, 0, 0.0, 0.0, 0, 0, true);
+  return ak::dispatch(m, nullptr, nullptr, nullptr, 0.0, 0.0, 0, 0, true);
 }
 
 cudaError_t ak_launch_flux_correction(const ak_mesh* m, const double* reg) {

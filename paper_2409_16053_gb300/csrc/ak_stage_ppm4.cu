@@ -5,13 +5,11 @@
 namespace ak {
 
 cudaError_t launch_stage_ppm4(const ak_mesh* m, const double* uin, const double* u0,
-                              double* uout, int out_reg, double a, double b, int rk2_final,
+                              double* uout, double a, double b, int rk2_final,
                               int last_stage, bool prepare) {
   if (m->desc.precision == AK_MIXED)
-    return launch<3, AK_PPM4, true, 16, 16, false>(m, uin, u0, uout, out_reg, a, b, rk2_final,
-                                               last_stage, prepare);
-  return launch<3, AK_PPM4, false, 16, 16, false>(m, uin, u0, uout, out_reg, a, b, rk2_final,
-                                              last_stage, prepare);
+    return launch<3, AK_PPM4, true, 16, 16>(m, uin, u0, uout, a, b, rk2_final, last_stage, prepare);
+  return launch<3, AK_PPM4, false, 16, 16>(m, uin, u0, uout, a, b, rk2_final, last_stage, prepare);
 }
 
 }  // namespace ak

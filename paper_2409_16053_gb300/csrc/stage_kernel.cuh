@@ -28,11 +28,10 @@
 #include "ak_internal.cuh"
 #include "hydro_ops.cuh"
 #include "stage_common.cuh"
-#include "tma.cuh"
 
 namespace ak {
 
-template <int NG, bool MIXED, int TX, int TY, bool TMA_OUT>
+template <int NG, bool MIXED, int TX, int TY>
 struct StageCfg {
   using R = typename std::conditional<MIXED, float, double>::type;
   // FP64: x1 and x2 sweeps one after the other through one edge buffer, so that two
@@ -50,33 +49,27 @@ struct StageCfg {
   static constexpr int EB = SPLIT ? (E1 > E2 ? E1 : E2) : E1 + E2;
   static constexpr int F1 = 5 * TY * (TX + 1);
   static constexpr int F2 = 5 * (TY + 1) * TX;
-  // TMA_OUT: the new state of each plane goes through a double-buffered shared tile and
-  // one bulk-tensor store per plane instead of per-thread global stores
-  static constexpr int OUT = TMA_OUT ? 2 * 5 * TX * TY : 0;  // doubles, at offset 0
-  static constexpr size_t bytes =
-      sizeof(double) * (size_t)OUT + sizeof(R) * (size_t)(NR * 5 * NPL + 2 * EB + F1 + F2);
+  static constexpr size_t bytes = sizeof(R) * (size_t)(NR * 5 * NPL + 2 * EB + F1 + F2);
 };
 
 // PERSIST: the persistent fused form for meshes that need a ghost fill (static
 // refinement, FOFC): a cooperative launch of at most one resident wave of CTAs first runs
 // the fill and the flux correction (fused_prologue), then loops over the work list.
-template <int NG, int RC, bool MIXED, int TX, int TY, bool TMA_OUT, bool PERSIST>
+template <int NG, int RC, bool MIXED, int TX, int TY, bool PERSIST>
 __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
     stage_kernel(const double* __restrict__ uin_arg, const double* u0, double* uout,
                  ak_meshdev md, const ak_work* __restrict__ work, Bg bg, double a, double b,
-                 int form, ak_dev_scalars* sc, int last_stage,
-                 const __grid_constant__ CUtensorMap tmap_out, int nwork) {
+                 int form, ak_dev_scalars* sc, int last_stage, int nwork) {
   // form: 0 = first stage U + dt L; 1 = RK2 final (U0 + U + dt L) / 2;
   //       2 = a U0 + b (U + dt L)
-  using C = StageCfg<NG, MIXED, TX, TY, TMA_OUT>;
+  using C = StageCfg<NG, MIXED, TX, TY>;
   using R = typename C::R;
   // reconstructions that can overshoot: a face without a sound speed gives a NaN flux
   constexpr bool NANCHK = RC == AK_WENOZ || RC == AK_PPMX;
   constexpr int NT = C::NT, WX = C::WX, NPL = C::NPL, NR = C::NR, NPT = C::NPT;
   constexpr int C1 = TX + 2;  // x1 edge row length
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  double* stg = reinterpret_cast<double*>(smem_raw);  // [2][5][TY][TX] (TMA_OUT only)
-  R* ring = reinterpret_cast<R*>(smem_raw + sizeof(double) * C::OUT);  // [NR][5][WY][WX]
+  R* ring = reinterpret_cast<R*>(smem_raw);  // [NR][5][WY][WX]
   R* e1lo = ring + NR * 5 * NPL;             // [5][TY][TX+2]
   R* e1hi = e1lo + C::EB;
   R* e2lo = C::SPLIT ? e1lo : e1lo + C::E1;  // [5][TY+2][TX]
@@ -306,14 +299,6 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
       }
     }
     __syncthreads();
-    if constexpr (TMA_OUT) {
-      // the previous plane's new state is complete in its staging tile
-      if (tid == 0 && k > k0) {
-        tma_store_5d(&tmap_out, stg + ((k - 1) & 1) * 5 * TX * TY, i0 + NG, j0 + NG, k - 1 + NG,
-                     0, blk);
-        bulk_commit();
-      }
-    }
     const R* pl = ring + slot(k) * 5 * NPL;
     kcur = k;
     R lo3[5], hi3n[5];
@@ -342,10 +327,6 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
         solve<NANCHK>(2, hi3, lo3, bg, f3p);
 #pragma unroll
       for (int v = 0; v < 5; ++v) hi3[v] = hi3n[v];
-    }
-    if constexpr (TMA_OUT) {
-      // this plane's staging tile was last read by the store of plane k-2
-      if (tid == 0) bulk_wait_read<1>();
     }
     __syncthreads();
 
@@ -387,13 +368,7 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
         }
       }
 #pragma unroll
-      for (int v = 0; v < 5; ++v) {
-        if constexpr (TMA_OUT)
-          stg[(((k & 1) * 5 + v) * TY + ty) * TX + tx] = un[v];
-        else
-          uout[e + v * g.var_stride] = un[v];
-      }
-      if constexpr (TMA_OUT) fence_proxy_async_smem();
+      for (int v = 0; v < 5; ++v) uout[e + v * g.var_stride] = un[v];
       if (last_stage) {
         if constexpr (MIXED) {
           // CFL ratio in FP32: it only sets the next step's dt
@@ -435,15 +410,6 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
     }
   }
 
-  if constexpr (TMA_OUT) {
-    __syncthreads();
-    if (tid == 0) {
-      tma_store_5d(&tmap_out, stg + ((k1 - 1) & 1) * 5 * TX * TY, i0 + NG, j0 + NG, k1 - 1 + NG,
-                   0, blk);
-      bulk_commit();
-      bulk_wait<0>();
-    }
-  }
   if (last_stage) {
     if constexpr (MIXED)
       dtmin = f32_to_f64(dtmin_f);
@@ -472,49 +438,41 @@ Bg make_bg(const ak_mesh* m);
 
 // Launch (or, prepare_only, raise the shared-memory limit of) the stage kernel of one
 // configuration over the mesh's work list; m->fused selects the persistent variant.
-template <int NG, int RC, bool MIXED, int TX, int TY, bool TMA_OUT>
+template <int NG, int RC, bool MIXED, int TX, int TY>
 inline cudaError_t launch(const ak_mesh* m, const double* uin, const double* u0, double* uout,
-                          int out_reg, double a, double b, int rk2_final, int last_stage,
-                          bool prepare_only) {
-  const size_t smem = StageCfg<NG, MIXED, TX, TY, TMA_OUT>::bytes;
-  auto kern = stage_kernel<NG, RC, MIXED, TX, TY, TMA_OUT, false>;
+                          double a, double b, int rk2_final, int last_stage, bool prepare_only) {
+  const size_t smem = StageCfg<NG, MIXED, TX, TY>::bytes;
+  auto kern = stage_kernel<NG, RC, MIXED, TX, TY, false>;
+  auto pk = stage_kernel<NG, RC, MIXED, TX, TY, true>;
   if (prepare_only) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if constexpr (!TMA_OUT) {
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(stage_kernel<NG, RC, MIXED, TX, TY, false, true>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    }
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(pk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     return e;
   }
   const Bg bg = make_bg(m);
   const int form = rk2_final ? 1 : (a == 0.0 ? 0 : 2);
-  if (m->fused) {
-    if constexpr (!TMA_OUT) {
-      auto pk = stage_kernel<NG, RC, MIXED, TX, TY, false, true>;
-      return launch_persistent(m, pk, TX * TY, smem, uin, u0, uout, m->md, m->d_work, bg, a, b,
-                               form, m->d_sc, last_stage, m->tmap[out_reg], m->nwork);
-    }
-  }
+  if (m->fused)
+    return launch_persistent(m, pk, TX * TY, smem, uin, u0, uout, m->md, m->d_work, bg, a, b,
+                             form, m->d_sc, last_stage, m->nwork);
   kern<<<(unsigned)m->nwork, TX * TY, smem, m->stream>>>(uin, u0, uout, m->md, m->d_work, bg, a,
-                                                          b, form, m->d_sc, last_stage,
-                                                          m->tmap[out_reg], m->nwork);
+                                                          b, form, m->d_sc, last_stage, m->nwork);
   return cudaGetLastError();
 }
 
 // Per-reconstruction launchers (one translation unit each): the stage of this mesh with
 // the given RK weights; prepare: raise the kernels' shared-memory limits instead.
 cudaError_t launch_stage_plm(const ak_mesh* m, const double* uin, const double* u0,
-                             double* uout, int out_reg, double a, double b, int rk2_final,
+                             double* uout, double a, double b, int rk2_final,
                              int last_stage, bool prepare);
 cudaError_t launch_stage_ppm4(const ak_mesh* m, const double* uin, const double* u0,
-                              double* uout, int out_reg, double a, double b, int rk2_final,
+                              double* uout, double a, double b, int rk2_final,
                               int last_stage, bool prepare);
 cudaError_t launch_stage_wenoz(const ak_mesh* m, const double* uin, const double* u0,
-                               double* uout, int out_reg, double a, double b, int rk2_final,
+                               double* uout, double a, double b, int rk2_final,
                                int last_stage, bool prepare);
 cudaError_t launch_stage_ppmx(const ak_mesh* m, const double* uin, const double* u0,
-                              double* uout, int out_reg, double a, double b, int rk2_final,
+                              double* uout, double a, double b, int rk2_final,
                               int last_stage, bool prepare);
 
 }  // namespace ak

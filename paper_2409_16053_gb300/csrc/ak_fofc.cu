@@ -234,12 +234,8 @@ __global__ void __launch_bounds__(kFofcThreads)
           const float L = -fmaf(d1, (float)idx1, fmaf(d2, (float)idx2, d3 * (float)idx3));
           r = rk_update_mixed(form, a, b, dt, L, ui, u0i);
         } else {
-          const double L = -fma(d1, idx1, fma(d2, idx2, d3 * idx3));
-          r = fma(dt, L, ui);
-          if (form == 1)
-            r = half(u0i + r);
-          else if (form == 2)
-            r = fma(a, u0i, b * r);
+          const double cdt[3] = {dt * idx1, dt * idx2, dt * idx3};
+          r = rk_update_fp64(form, a, b, cdt, d1, d2, d3, ui, u0i);
         }
         un[v] = r;
         uout[e + v * B.var_stride] = r;

@@ -50,25 +50,6 @@ struct Bg {
 __device__ __forceinline__ float fmar(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double fmar(double a, double b, double c) { return fma(a, b, c); }
 
-// van Leer harmonic mean of the one-sided differences; zero at extrema.
-// FP64: the harmonic mean with a Newton-refined reciprocal (no IEEE division)
-__device__ __forceinline__ double plm_slope(double qm, double q0, double qp) {
-  const double dl = q0 - qm;
-  const double dr = qp - q0;
-  const double prod = dl * dr;
-  return prod > 0.0 ? (prod + prod) * rcp64(dl + dr) : 0.0;
-}
-
-// Half of the van Leer slope, dl dr / (dl + dr): the offset of the face values from the
-// cell value.  In FP64 it skips the doubling and halving of plm_slope (same bits: both
-// are exact scalings by two).
-__device__ __forceinline__ double plm_half_slope(double qm, double q0, double qp) {
-  const double dl = q0 - qm;
-  const double dr = qp - q0;
-  const double prod = dl * dr;
-  return dpos(prod) ? prod * rcp64(dl + dr) : 0.0;
-}
-
 // FP64 PPM4 with the sign tests, minima and exact halvings on the integer pipe.  The
 // limited slope is carried as half its value,
 //   h = sgn(dq) min(|qp - qm| / 4, |q0 - qm|, |qp - q0|)  (0 at extrema),
@@ -437,6 +418,19 @@ __device__ __forceinline__ void plm_edges_v(V qm, V q0, V qp, V& lo, V& hi) {
   const V h = vsel(vgt(prod, zero), vmul(prod, r), zero);
   lo = vsub(q0, h);
   hi = vadd(q0, h);
+}
+
+// FP64 PLM face values from the one-sided differences dl = q0 - qm, dr = qp - q0:
+// q0 -+ dl dr / (dl + dr), each a single fused multiply-add of dl dr and the
+// Newton-refined reciprocal (zero slope where dl dr <= 0).
+__device__ __forceinline__ void plm_edges_fp64(double dl, double dr, double q0, double& lo,
+                                               double& hi) {
+  const double prod = dl * dr;
+  const bool pos = dpos(prod);
+  const double p = pos ? prod : 0.0;
+  const double r = pos ? rcp64(dl + dr) : 0.0;
+  lo = fma(-p, r, q0);
+  hi = fma(p, r, q0);
 }
 
 // CW84 limited slope: centred difference bounded by twice the one-sided ones

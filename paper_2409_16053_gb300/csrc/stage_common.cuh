@@ -159,9 +159,7 @@ __device__ __forceinline__ void edges_t(const R* q, R& lo, R& hi) {
     else
       ppm_edges_v(q[0], q[1], q[2], q[3], q[4], lo, hi);
   } else if constexpr (NG == 2) {
-    const R h = plm_half_slope(q[0], q[1], q[2]);
-    lo = q[1] - h;
-    hi = q[1] + h;
+    plm_edges_fp64(q[1] - q[0], q[2] - q[1], q[1], lo, hi);
   } else {
     ppm_edges_fp64(q[0], q[1], q[2], q[3], q[4], lo, hi);
   }
@@ -404,6 +402,21 @@ __device__ __forceinline__ double rk_update_mixed(int form, double a, double b, 
   if (form == 0) return fma(dt, Ld, u);
   if (form == 1) return half(u0 + fma(dt, Ld, u));
   return fma(b, fma(dt, Ld, u), a * u0);
+}
+
+// RK stage update of one conserved value in the FP64 form (Section 3) from the flux
+// differences d_d = F_{d,+} - F_{d,-} and cdt_d = dt / dx_d:  U + dt L = U - sum_d cdt_d d_d
+// as one chain of fused multiply-adds;  form 0: U + dt L;  form 1: (U0 + U + dt L) / 2;
+// form 2: a U0 + b (U + dt L)
+__device__ __forceinline__ double rk_update_fp64(int form, double a, double b,
+                                                 const double* cdt, double d1, double d2,
+                                                 double d3, double u, double u0) {
+  double r = fma(-d1, cdt[0], fma(-d2, cdt[1], fma(-d3, cdt[2], u)));
+  if (form == 1)
+    r = half(u0 + r);
+  else if (form == 2)
+    r = fma(a, u0, b * r);
+  return r;
 }
 
 // x > 0 and not NaN (as the comparison x > 0 is), on the integer pipe

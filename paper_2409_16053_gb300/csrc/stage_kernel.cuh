@@ -105,6 +105,7 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
   const Counters cn{&sc->counters[0], &sc->counters[1]};
   const double dt = sc->dt;
   const double idx1 = 1.0 / g.dx1, idx2 = 1.0 / g.dx2, idx3 = 1.0 / g.dx3;
+  const double cdt[3] = {dt * idx1, dt * idx2, dt * idx3};  // FP64 update: dt / dx_d
   const bool need_u0 = form != 0;
 
   auto slot = [](int k) { return (k + 4 * NR) % NR; };
@@ -344,12 +345,8 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
           const float L = -fmaf(d1, (float)idx1, fmaf(d2, (float)idx2, d3 * (float)idx3));
           r = rk_update_mixed(form, a, b, dt, L, uik[v], u0k[v]);
         } else {
-          const double L = -fma(d1, idx1, fma(d2, idx2, d3 * idx3));
-          r = fma(dt, L, uin[e + v * g.var_stride]);
-          if (form == 1)  // RK2 final stage: (U0 + U + dt L) / 2
-            r = half(u0[e + v * g.var_stride] + r);
-          else if (form == 2)
-            r = fma(a, u0[e + v * g.var_stride], b * r);
+          r = rk_update_fp64(form, a, b, cdt, d1, d2, d3, uin[e + v * g.var_stride],
+                             form != 0 ? u0[e + v * g.var_stride] : 0.0);
         }
         un[v] = r;
         f3m[v] = f3p[v];

@@ -198,9 +198,7 @@ ak_status ak_new_dt(ak_mesh* mesh, int32_t reg, double* dt_out);
 ak_status ak_step(ak_mesh* mesh, double dt, double* dt_next);
 
 /* Picks, by timing stage launches on this mesh, the schedule of the stage kernel: the
- * column-tile shape (16x16, or 32x8 and the unpaired 16x16 variant for the mixed PLM
- * form), the number of x3 segments
- * per MeshBlock, and the order in which CTAs take the (block, tile, segment) work items
+ * column-tile variant (see ak_mesh_schedule), the number of x3 segments per MeshBlock, and the order in which CTAs take the (block, tile, segment) work items
  * (block order, or longest first) -- the block-to-SM schedule.  The paper finds the
  * MeshBlock size decisive for throughput (Section 5.1); this tunes how a given mesh is
  * cut into GPU work.  Results are bitwise independent of the choice.  Registers 0 and 1
@@ -234,9 +232,9 @@ ak_status ak_mesh_fuse(ak_mesh* mesh, int32_t fused);
 ak_status ak_selftest_barrier(ak_mesh* mesh, int32_t absent);
 
 /* Sets the stage kernel's schedule explicitly (what ak_mesh_autotune picks by timing).
- *   tile:  0 = 16x16 column tiles (for the mixed PLM form: the variant with paired
- *          x1/x2 work, 288 threads); 1 = 32x8 tiles and 2 = 16x16 tiles with one thread
- *          per column (mixed PLM form only);
+ *   tile:  0 = 16x16 column tiles (for the mixed form: the variant with paired x1/x2
+ *          work, 288 threads); 2 = 16x16 tiles with one thread per column (mixed form
+ *          only); 1 = 32x8 tiles with one thread per column (mixed PLM form only);
  *   nseg:  x3 segments per MeshBlock, 1..64 (fewer for blocks thinner than 4 cells per
  *          segment);
  *   order: 0 = block order, 1 = longest work items first.

@@ -38,6 +38,7 @@ static ak_status einval(const char* msg) {
 
 static int stage_in_reg(int rk, int s) { return s == 1 ? 0 : (rk == 2 ? 1 : s - 1); }
 static int stage_out_reg(int rk, int s) { return s == rk ? 0 : s; }
+static bool tile_ok(const ak_mesh* m, int tile);
 
 namespace {
 
@@ -425,7 +426,7 @@ extern "C" ak_status ak_mesh_create(const ak_mesh_desc* d, void* cuda_stream, ak
     m->md.flist = m->d_flist;
     m->md.fu0 = m->d_fu0;
   }
-  if (e == cudaSuccess) e = ak_build_work(m, 0, seg, 0);
+  if (e == cudaSuccess) e = ak_build_work(m, tile_ok(m, 0) ? 0 : 2, seg, 0);
   if (e == cudaSuccess) e = ak_stage_prepare(m);
   if (e == cudaSuccess) {
     ak_dev_scalars s;
@@ -440,6 +441,21 @@ extern "C" ak_status ak_mesh_create(const ak_mesh_desc* d, void* cuda_stream, ak
   }
   *out = m;
   return AK_OK;
+}
+
+// Stage tile variants of a mesh's form: FP64 0 (16x16 columns); mixed 0 (paired
+// 16x16), 2 (16x16 columns), and for PLM also 1 (32x8 columns).  The paired kernel stages
+// rows in 16-byte chunks that must not straddle a block boundary, so it needs an even
+// number of cells in x1 in every block.
+static bool even_x1(const ak_mesh* m) {
+  for (int b = 0; b < m->nblocks; ++b)
+    if (m->h_blk[b].nx1 % 2) return false;
+  return true;
+}
+static bool tile_ok(const ak_mesh* m, int tile) {
+  if (m->desc.precision != AK_MIXED) return tile == 0;
+  if (tile == 0) return even_x1(m);
+  return tile == 2 || (tile == 1 && m->desc.recon == AK_PLM);
 }
 
 cudaError_t ak_build_work(ak_mesh* m, int tile, int nseg, int order) {
@@ -708,14 +724,13 @@ extern "C" ak_status ak_mesh_autotune(ak_mesh* m, int32_t result[5]) {
   cudaEvent_t ev[2];
   AK_CUDA_TRY(cudaEventCreate(&ev[0]));
   AK_CUDA_TRY(cudaEventCreate(&ev[1]));
-  const int ntile = (m->desc.precision == AK_MIXED && m->desc.recon == AK_PLM) ? 3 : 1;
   int best_tile = m->tile, best_seg = m->nseg, best_order = m->order;
   float best = 1e30f;
   cudaError_t e = cudaSuccess;
   const int fofc = m->md.fofc;
   m->md.fofc = 0;  // the timed launches flag no cells (their output is discarded)
-  for (int tile = 0; tile < ntile && e == cudaSuccess; ++tile)
-    for (int seg = 1; seg <= 16 && e == cudaSuccess; seg *= 2)
+  for (int tile = 0; tile < 3 && e == cudaSuccess; ++tile)
+    for (int seg = 1; seg <= 16 && e == cudaSuccess && tile_ok(m, tile); seg *= 2)
       for (int order = 0; order < 2 && e == cudaSuccess; ++order) {
         e = ak_build_work(m, tile, seg, order);
         float t = 1e30f;
@@ -799,10 +814,9 @@ extern "C" ak_status ak_mesh_fuse(ak_mesh* m, int32_t fused) {
 
 extern "C" ak_status ak_mesh_schedule(ak_mesh* m, int32_t tile, int32_t nseg, int32_t order) {
   if (!m) return einval("ak_mesh_schedule: NULL mesh");
-  const int ntile = (m->desc.precision == AK_MIXED && m->desc.recon == AK_PLM) ? 3 : 1;
-  if (tile < 0 || tile >= ntile) {
-    ak_set_error("ak_mesh_schedule: tile %d not available for this form (0..%d)", tile,
-                 ntile - 1);
+  if (!tile_ok(m, tile)) {
+    ak_set_error("ak_mesh_schedule: tile %d not available for this form (FP64: 0; mixed PLM: "
+                 "0, 1, 2; mixed with 3 ghost cells: 0, 2)", tile);
     return AK_EINVAL;
   }
   if (nseg < 1 || nseg > 64) {

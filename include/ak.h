@@ -279,12 +279,16 @@ ak_status ak_status_counters(ak_mesh* mesh, int64_t out[4]);
  * cuda_stream  the work runs on this stream, which the call synchronizes.
  *
  * Scratch: a file-scope static __device__ array (AK_NOALLOC_MAX_BLOCKS + 1 doubles)
- * that every GPU loading the library keeps until the process exits.  The first call
- * on a device looks up that array's device address (cudaGetSymbolAddress) with the
- * device current; make that first call before any stream capture.  Every call on a
- * device shares the array and leaves its last contents there, so calls that overlap
- * on the GPU (concurrent streams, threads) race: serialize them.  No call of this
- * function runs cudaMalloc, cudaFree or any other allocating routine.
+ * that every GPU loading the library keeps until the process exits.  Every call looks
+ * up that array's device address (cudaGetSymbolAddress) with the device current, which
+ * allocates nothing.  With CUDA's lazy module loading (the default), the first use of
+ * the library's device code on a device -- this call or any other of the library --
+ * loads it there, and that load places the array and the kernels in device memory: make
+ * one warm-up call per device while memory is still free (not when the device is
+ * already out of memory) and before any stream capture.  Every call on a device shares
+ * the array and leaves its last contents there, so calls that overlap on the GPU
+ * (concurrent streams, threads) race: serialize them.  No call of this function runs
+ * cudaMalloc, cudaFree or any other allocating routine.
  * Errors: AK_EINVAL for NULL pointers, invalid sizes, or nblocks outside
  * [1, AK_NOALLOC_MAX_BLOCKS]; AK_ECUDA if a CUDA call fails. */
 ak_status ak_cfl_dt_noalloc(const double* reg, int32_t nblocks, const int32_t nx[3],

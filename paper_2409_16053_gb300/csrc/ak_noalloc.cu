@@ -1,8 +1,6 @@
 // ak_cfl_dt_noalloc: the CFL time step of a register, computed with no device-memory
 // allocation at all.  Its scratch is a file-scope static __device__ array, so the
 // call works for callers that cannot call cudaMalloc (see include/ak.h).
-#include <mutex>
-
 #include "ak_internal.cuh"
 
 namespace {
@@ -13,25 +11,14 @@ constexpr int kThreads = 256;
 // result in the last slot.  Every GPU that loads the library holds it until exit.
 __device__ __align__(256) double g_cfl_scratch[AK_NOALLOC_MAX_BLOCKS + 1];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mutex;
-double* g_scratch_addr[kMaxDevices] = {};
-
-// Device address of g_cfl_scratch on the current device, looked up once per device.
+// Device address of g_cfl_scratch on the current device, looked up on every call: a
+// cached address would go stale when the module is loaded again (after cudaDeviceReset,
+// or in another context on the same device).  The lookup allocates nothing.
 cudaError_t scratch_address(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_addr[dev]) {
-    double* p = nullptr;
-    e = cudaGetSymbolAddress((void**)&p, g_cfl_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_addr[dev] = p;
-  }
-  *out = g_scratch_addr[dev];
-  return cudaSuccess;
+  double* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress((void**)&p, g_cfl_scratch);
+  if (e == cudaSuccess) *out = p;
+  return e;
 }
 
 // One CTA per MeshBlock: minimum over the block's interior of dx_d / (|v_d| + c_s).

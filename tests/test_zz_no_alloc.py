@@ -60,6 +60,30 @@ def test_noalloc_dt_after_a_larger_call_and_after_steps(ak):
     small.close()
 
 
+def test_noalloc_calls_allocate_nothing(ak):
+    """After one warm-up call (which may load the library's device code on the device),
+    further calls leave the device's free memory and torch's allocator unchanged."""
+    import torch
+    root, block = (32, 32, 32), (16, 16, 16)
+    m = ak.Mesh(root, block)
+    m.upload(pgen.turbulence(root, seed=43, kmin=1, kmax=6, mach=1.0))
+    ref = m.new_dt(0)
+    _noalloc_dt(ak, m)                                   # warm-up
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    stats0 = torch.cuda.memory_stats()
+    for _ in range(5):
+        assert math.isclose(_noalloc_dt(ak, m), ref, rel_tol=1e-14)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    stats1 = torch.cuda.memory_stats()
+    assert free1 == free0, (free0, free1)
+    for key in ("allocated_bytes.all.current", "reserved_bytes.all.current",
+                "allocation.all.allocated"):
+        assert stats1.get(key, 0) == stats0.get(key, 0), key
+    m.close()
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch(ak):
     m = ak.Mesh((16, 16, 16), (16, 16, 16))
     with pytest.raises(ak.AkError) as e:

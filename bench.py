@@ -46,11 +46,17 @@ FLOP_PER_CELL_STAGE = 531.0
 BYTES_STAGE = {1: 80.0, 2: 120.0}
 # FP64 peak from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# FP64 pipe busy fraction of the FP64 stage kernel in the ncu capture of these sources
+# (sm__pipe_fp64_cycles_active.avg.pct_of_peak_sustained_active, mean of the two stages):
+# the unit the form is bound by
+FP64_PIPE_BUSY_NCU = 0.766
 # DRAM bytes per cell of the stage kernels (dram__bytes_read.sum + dram__bytes_write.sum
-# of one ncu capture, 192^3 in 64^3 blocks; the per-cell figure carries over to 256^3 in
-# the same blocks), valid for the kernel sources with this hash (else traffic = null)
-TRAFFIC_SRC_HASH = "c81eb947d44a150875bbc05774e6c680b6a9fbe0"
-TRAFFIC_B_PER_CELL = {"fp64": (85.48, 128.70), "mixed": (83.83, 126.95)}
+# of one ncu capture per launch: PLM + RK2 on 192^3 in 64^3 blocks, PPM4 + RK3 on 256^3 in
+# 128^3 blocks; the per-cell figures carry over to grids of the same block size), valid
+# for the kernel sources with this hash (else traffic = null)
+TRAFFIC_SRC_HASH = "7de9dc0e32df77fa994a3e7b82eeb2f1ff9b4f99"
+TRAFFIC_B_PER_CELL = {"fp64": (86.62, 129.18), "mixed": (83.80, 126.92),
+                      "ppm4_mixed": (93.90, 140.55, 136.01)}
 
 
 def kernel_source_hash():
@@ -58,20 +64,20 @@ def kernel_source_hash():
     import hashlib
     d = os.path.join(ROOT, "paper_2409_16053_gb300", "csrc")
     lines = ""
-    for f in ("stage_kernel.cuh", "ak_stage_plm.cu", "ak_stage_mx.cu", "stage_common.cuh",
-              "hydro_ops.cuh", "lanes.cuh", "fastmath.cuh", "exchange.cuh"):
+    for f in ("stage_kernel.cuh", "ak_stage_plm.cu", "ak_stage_mx.cu", "stage_mx.cuh",
+              "stage_common.cuh", "hydro_ops.cuh", "lanes.cuh", "fastmath.cuh", "exchange.cuh"):
         h = hashlib.sha1(open(os.path.join(d, f), "rb").read()).hexdigest()
         lines += f"{h}  ../paper_2409_16053_gb300/csrc/{f}\n"
     return hashlib.sha1(lines.encode()).hexdigest()
 
 
 def traffic_per_launch(form, cells):
-    """Measured DRAM bytes per stage launch (mean of the two stages), or None if the
+    """Measured DRAM bytes per stage launch (mean over the step's stages), or None if the
     kernel changed since the counters were taken."""
     if kernel_source_hash() != TRAFFIC_SRC_HASH:
         return None
-    b1, b2 = TRAFFIC_B_PER_CELL[form]
-    return 0.5 * (b1 + b2) * cells
+    b = TRAFFIC_B_PER_CELL[form]
+    return sum(b) / len(b) * cells
 
 
 def linear_wave_l1(ak, precision, n=32):
@@ -383,8 +389,10 @@ def run_reference(args):
 
 
 def run_profile_case(args):
-    """Small case for ncu captures: 192^3 in 27 MeshBlocks of 64^3 (two registers of
-    ~0.34 GB, larger than L2), one form, `steps` graph-replayed RK2 steps."""
+    """Small cases for ncu captures, one form, `steps` graph-replayed steps: 192^3 in 27
+    MeshBlocks of 64^3 with PLM + RK2 (two registers of ~0.34 GB, larger than L2);
+    profile-ppm: 256^3 in 8 MeshBlocks of 128^3 with PPM4 + RK3; profile-smr: the
+    static-refinement mesh."""
     import torch
     import pgen
     from paper_2409_16053_gb300 import ak
@@ -401,6 +409,21 @@ def run_profile_case(args):
         m.close()
         print(json.dumps({"case": "profile-smr", "form": args.form, "steps": args.steps,
                           "counters": c}), flush=True)
+        return 0 if c[:2] == [0, 0] else 1
+    if args.case == "profile-ppm":
+        # the 512^3 PPM4 + RK3 configuration's kernels on 256^3 in 128^3 blocks
+        root = (256, 256, 256)
+        U0 = pgen.turbulence(root, seed=3, kmin=2, kmax=8, mach=0.5)
+        m = ak.Mesh(root, (128, 128, 128), recon=ak.AK_PPM4, rk=3, precision=prec,
+                    ref_rho=1.0, ref_p=1.0)
+        m.upload(U0)
+        m.new_dt()
+        for _ in range(args.steps):
+            m.step(0.0)
+        c = m.counters()
+        m.close()
+        print(json.dumps({"case": "profile-ppm", "form": args.form, "cells": 256 ** 3,
+                          "steps": args.steps, "counters": c}), flush=True)
         return 0 if c[:2] == [0, 0] else 1
     root = (192, 192, 192)
     U0 = pgen.turbulence(root, seed=1, kmin=2, kmax=8, mach=0.5)
@@ -492,6 +515,10 @@ def time_large(ak, torch, case, steps, warmup):
              "dt0": dt0, "counters": m.counters(), "clocks": clk}
         if name == "fp64":
             f["roofline"]["note"] = "FP64 form: bound by the FP64 unit, not by HBM"
+        elif c3:
+            # mean DRAM bytes of the step's three stage launches
+            f["roofline"]["traffic"] = traffic_per_launch("ppm4_mixed", cells)
+            f["roofline"]["algorithmic_bytes_per_launch"] = bytes_cu / 3 * cells
         if l1 is not None:
             f["l1_vs_fp64_after_one_step"] = l1
         out[name] = f
@@ -522,12 +549,12 @@ def main():
     ap.add_argument("--no-large", action="store_true",
                     help="skip the 512^3 PPM4+RK3 and 768^3 Mach-2 legs")
     ap.add_argument("--case", default="bench",
-                    choices=["bench", "profile", "profile-smr", "c3", "c5"])
+                    choices=["bench", "profile", "profile-smr", "profile-ppm", "c3", "c5"])
     ap.add_argument("--form", default="fp64", choices=["fp64", "mixed"])
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
-    if args.case in ("profile", "profile-smr"):
+    if args.case in ("profile", "profile-smr", "profile-ppm"):
         return run_profile_case(args)
     if args.case in ("c3", "c5"):
         return run_large_case(args)
@@ -603,12 +630,16 @@ def main():
                      "unit": "TFLOP/s", "frac": ach64 / FP64_PEAK_TFLOPS,
                      "traffic": traffic_per_launch("fp64", cells),
                      "kernel": "stage_kernel<PLM, FP64> (mean of stage 1 and 2 launches)",
-                     "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz"},
+                     "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz "
+                                    "(ncu's peak_sustained for DFMA: 304 per clock on "
+                                    "152 SMs)",
+                     "fp64_pipe_busy_ncu": FP64_PIPE_BUSY_NCU},
         "mixed": {
             "value": valuemx, "unit": UNIT, "ms_per_step": tmx / args.steps, "dtype": "f32+f64",
             "roofline": {"bound": "hbm", "achieved": ach_mx, "peak": hbm, "unit": "GB/s",
                          "frac": ach_mx / hbm, "traffic": traffic_per_launch("mixed", cells),
-                         "kernel": "stage_kernel<PLM, mixed> (mean of stage 1 and 2 launches)",
+                         "kernel": "stage_mx_kernel<PLM> (paired; mean of stage 1 and 2 "
+                                   "launches)",
                          "peak_source": f"{peak_kind} hbm_gbs"},
             "e2e": e2e_mx,
         },

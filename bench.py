@@ -279,8 +279,9 @@ def time_smr(ak, torch, precision, steps, warmup):
     """The static-refinement workload: root 128^3 in 32^3 blocks and two nested levels of
     16^3 blocks over the central 1/2 and 1/4 cubes (1016 leaves, 5,767,168 cells) on
     [-1/2, 1/2]^3, Sedov deposit (energy 1 in r < 0.02, rho = 1, p = 1e-5), PLM + HLLC +
-    RK2, one dt for all levels.  A step is one graph-replayed ak_step (ghost fill with
-    restriction/prolongation, flux correction, stage, twice, and the dt reduction)."""
+    RK2, one dt for all levels.  A step is one graph-replayed ak_step (the ghost fill at
+    level boundaries -- restrictions, prolongations; same-level halos are read by the
+    stage kernels directly --, flux correction, stage, twice, and the dt reduction)."""
     import pgen
     t = pgen.nested_refinement_blocks()
     P = pgen.sedov_blocks(t, 128)

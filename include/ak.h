@@ -161,9 +161,11 @@ ak_status ak_mesh_bind(ak_mesh* mesh, int32_t reg, double* dev_ptr);
  * plus minmod-limited slopes of the conserved variables, +-1/4 of a coarse slope per
  * direction; done after the copies and restrictions).  One launch per pass covers all
  * blocks.  Edge and corner ghosts are filled too.
- * On a uniform mesh (one level) without FOFC the stage kernels read halo cells straight
- * from the neighbouring blocks' interiors, so ak_stage needs no filled ghost cells there
- * and ak_step does not fill them; this call still fills them (e.g. for output). */
+ * Without FOFC the stage kernels read every halo cell that lies in a same-level block
+ * straight from that block's interior, so ak_step fills only the ghost cells at level
+ * boundaries before a stage (restrictions, prolongations, and the copies a
+ * prolongation's slopes read) and none on a uniform mesh; this call still fills every
+ * ghost cell (e.g. for output, or before ak_stage on a refined mesh). */
 ak_status ak_fill_ghosts(ak_mesh* mesh, int32_t reg);
 
 /* One RK stage s in [1, rk] with time step dt (Section 3); dt <= 0 uses the

@@ -275,8 +275,8 @@ class Mesh:
         for r, t in enumerate(self.regs):
             ak_mesh_bind(self.handle, r, t.data_ptr())
         self.interior_count = 5 * int(np.prod(self.table[:, 4:7].astype(np.int64), axis=1).sum())
-        # uniform meshes without FOFC: the stage kernels read halos from the neighbour
-        # blocks, so a stage needs no ghost fill before it
+        # uniform meshes without FOFC: every halo cell lies in a same-level block, which
+        # the stage kernels read directly, so a stage needs no ghost fill before it
         self.direct = bool((self.table[:, 0] == 0).all()) and not fofc
 
     def close(self):

@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <unordered_map>
+#include <unordered_set>
 #include <vector>
 
 
@@ -39,6 +40,8 @@ static ak_status einval(const char* msg) {
 static int stage_in_reg(int rk, int s) { return s == 1 ? 0 : (rk == 2 ? 1 : s - 1); }
 static int stage_out_reg(int rk, int s) { return s == rk ? 0 : s; }
 static bool tile_ok(const ak_mesh* m, int tile);
+// a stage needs ghost cells filled first: a refined mesh (level boundaries) or FOFC
+static bool stage_fill(const ak_mesh* m) { return m->md.nxa > 0 || m->md.nxb > 0; }
 
 namespace {
 
@@ -291,11 +294,15 @@ extern "C" ak_status ak_mesh_create(const ak_mesh_desc* d, void* cuda_stream, ak
   }
   // exchange plan: every ghost cell of every block, with its source
   std::vector<ak_xfer> xa, xb;
+  std::unordered_set<long long> pro_reads;
   {
     auto el0 = [&](const ak_block& B, long long i, long long j, long long k) {
       return B.off + ((k + ng) * B.p2 + (j + ng)) * (long long)B.s1 + (i + ng);
     };
     std::unordered_map<long long, size_t> pro;  // coarse cell -> its entry (one block)
+    // coarse elements next to a prolonged cell: its minmod slopes read them, so the copies
+    // into those (ghost) cells must precede pass 2 even with direct halo reads
+    std::unordered_set<long long>& pread = pro_reads;
     for (int b = 0; b < nb; ++b) {
       const ak_block& B = m->h_blk[b];
       const int l = B.level;
@@ -341,10 +348,48 @@ extern "C" ak_status ak_mesh_create(const ak_mesh_desc* d, void* cuda_stream, ak
               t.info = 2 | (l << 2) | ((l - 1) << 10);
               it = pro.emplace(t.src, xb.size()).first;
               xb.push_back(t);
+              const long long st[3] = {1, C.s1, (long long)C.s1 * C.p2};
+              for (int a = 0; a < 3; ++a) {
+                pread.insert(t.src - st[a]);
+                pread.insert(t.src + st[a]);
+              }
             }
             xb[it->second].info |= 1 << (18 + child);
           }
       pro.clear();
+    }
+  }
+  // Direct halo reads (meshes without FOFC): the stage kernels read the halo cells that
+  // lie in a same-level leaf straight from its interior, so the fill before a stage keeps
+  // only the restrictions, the prolongations, and the copies into coarse ghost cells that
+  // a prolongation's slopes read (xs); ak_fill_ghosts still runs the whole plan.
+  const bool direct = !d->fofc;
+  std::vector<ak_xfer> xs;
+  if (direct) {
+    for (const ak_xfer& t : xa)
+      if ((t.info & 3) != 0 || pro_reads.count(t.dst)) xs.push_back(t);
+  }
+  // Per block and direction t = (dx + 1) + 3 (dy + 1) + 9 (dz + 1): the element base of its
+  // halo region, so that padded cell (ip, jp) of interior plane kp (of any direction) is
+  // element base + ((kp + ng) p2 + jp) s1 + ip.  For a same-level neighbour leaf that is
+  // its offset shifted back by the block extents (blocks of one level share their
+  // geometry); for a region at another level, and for t = 13, the block's own offset (its
+  // ghost cells, filled by restriction or prolongation).
+  std::vector<long long> nbase(27 * (size_t)nb);
+  for (int b = 0; b < nb; ++b) {
+    const ak_block& B = m->h_blk[b];
+    const int l = B.level;
+    for (int t = 0; t < 27; ++t) {
+      const int dx = t % 3 - 1, dy = (t / 3) % 3 - 1, dz = t / 9 - 1;
+      long long base = B.off;
+      if (t != 13) {
+        const int s = X.leaf(l, B.lx1 + (dx < 0 ? -1 : dx * B.nx1),
+                             B.lx2 + (dy < 0 ? -1 : dy * B.nx2), B.lx3 + (dz < 0 ? -1 : dz * B.nx3));
+        if (s >= 0)
+          base = m->h_blk[s].off - dx * (long long)B.nx1 - dy * (long long)B.nx2 * B.s1 -
+                 dz * (long long)B.nx3 * B.p2 * B.s1;
+      }
+      nbase[27 * (size_t)b + t] = base;
     }
   }
   // level table
@@ -388,8 +433,12 @@ extern "C" ak_status ak_mesh_create(const ak_mesh_desc* d, void* cuda_stream, ak
   dmalloc((void**)&m->d_sc, sizeof(ak_dev_scalars));
   dmalloc((void**)&m->d_xa, sizeof(ak_xfer) * xa.size());
   dmalloc((void**)&m->d_xb, sizeof(ak_xfer) * xb.size());
+  dmalloc((void**)&m->d_xs, sizeof(ak_xfer) * xs.size());
+  dmalloc((void**)&m->d_nbase, sizeof(long long) * nbase.size());
   h2d(m->d_xa, xa.data(), sizeof(ak_xfer) * xa.size());
   h2d(m->d_xb, xb.data(), sizeof(ak_xfer) * xb.size());
+  h2d(m->d_xs, xs.data(), sizeof(ak_xfer) * xs.size());
+  h2d(m->d_nbase, nbase.data(), sizeof(long long) * nbase.size());
   h2d(m->d_blk, m->h_blk, sizeof(ak_block) * nb);
   h2d(m->d_lev, lev, sizeof(ak_level) * X.nlev);
   h2d(m->d_map, X.map.data(), sizeof(int32_t) * X.map.size());
@@ -407,12 +456,14 @@ extern "C" ak_status ak_mesh_create(const ak_mesh_desc* d, void* cuda_stream, ak
   m->md.nfc = m->nfc;
   m->md.fc_cells = m->fc_cells;
   m->md.gamma = d->gamma;
-  m->md.xa = m->d_xa;
+  m->nxa_full = (long long)xa.size();
+  m->md.xa = direct ? m->d_xs : m->d_xa;
   m->md.xb = m->d_xb;
-  m->md.nxa = (long long)xa.size();
+  m->md.nxa = direct ? (long long)xs.size() : (long long)xa.size();
   m->md.nxb = (long long)xb.size();
+  m->md.nbase = m->d_nbase;
   m->md.cell_off = m->d_pack_off;
-  m->md.direct = !m->multilevel && !d->fofc;
+  m->md.direct = direct;
   if (d->fofc) {
     // flagged cells are rare: a list of cells/64 entries (at least 65536)
     const long long cap = std::max(65536ll, m->interior_cells / 64);
@@ -517,6 +568,8 @@ extern "C" void ak_mesh_destroy(ak_mesh* m) {
   cudaFree(m->d_pad_off);
   cudaFree(m->d_xa);
   cudaFree(m->d_xb);
+  cudaFree(m->d_xs);
+  cudaFree(m->d_nbase);
   cudaFree(m->d_fflag);
   cudaFree(m->d_flist);
   cudaFree(m->d_fu0);
@@ -577,7 +630,7 @@ extern "C" ak_status ak_fill_ghosts(ak_mesh* m, int32_t reg) {
   if (!m) return einval("ak_fill_ghosts: NULL mesh");
   ak_status s = need_reg(m, reg, "ak_fill_ghosts");
   if (s != AK_OK) return s;
-  AK_CUDA_TRY(ak_launch_fill_ghosts(m, m->reg[reg]));
+  AK_CUDA_TRY(ak_launch_fill_ghosts(m, m->reg[reg], true));
   return AK_OK;
 }
 
@@ -656,7 +709,7 @@ extern "C" ak_status ak_new_dt(ak_mesh* m, int32_t reg, double* dt_out) {
 static ak_status enqueue_step(ak_mesh* m) {
   for (int st = 1; st <= m->desc.rk; ++st) {
     double* in = m->reg[stage_in_reg(m->desc.rk, st)];
-    if (!m->md.direct && !m->fused) AK_CUDA_TRY(ak_launch_fill_ghosts(m, in));
+    if (stage_fill(m) && !m->fused) AK_CUDA_TRY(ak_launch_fill_ghosts(m, in, false));
     if (m->nfc && !m->fused) AK_CUDA_TRY(ak_launch_flux_correction(m, in));
     ak_status s = enqueue_stage(m, st);
     if (s != AK_OK) return s;
@@ -719,7 +772,7 @@ extern "C" ak_status ak_mesh_autotune(ak_mesh* m, int32_t result[5]) {
   }
   const int fused0 = m->fused;
   m->fused = 0;
-  AK_CUDA_TRY(ak_launch_fill_ghosts(m, m->reg[0]));
+  AK_CUDA_TRY(ak_launch_fill_ghosts(m, m->reg[0], true));
   if (m->nfc) AK_CUDA_TRY(ak_launch_flux_correction(m, m->reg[0]));
   cudaEvent_t ev[2];
   AK_CUDA_TRY(cudaEventCreate(&ev[0]));
@@ -754,13 +807,13 @@ extern "C" ak_status ak_mesh_autotune(ak_mesh* m, int32_t result[5]) {
   // the persistent fused launch, with the chosen schedule
   int best_fused = 0;
   if (e == cudaSuccess) e = ak_build_work(m, best_tile, best_seg, best_order);
-  if (!m->md.direct && e == cudaSuccess) {
+  if (stage_fill(m) && e == cudaSuccess) {
     float tf[2] = {1e30f, 1e30f};
     for (int fu = 0; fu < 2 && e == cudaSuccess; ++fu) {
       m->fused = fu;
       for (int rep = 0; rep < 5 && e == cudaSuccess; ++rep) {
         e = cudaEventRecord(ev[0], m->stream);
-        if (e == cudaSuccess && !fu) e = ak_launch_fill_ghosts(m, m->reg[0]);
+        if (e == cudaSuccess && !fu) e = ak_launch_fill_ghosts(m, m->reg[0], false);
         if (e == cudaSuccess && !fu && m->nfc) e = ak_launch_flux_correction(m, m->reg[0]);
         if (e == cudaSuccess) e = ak_launch_stage(m, 1, m->reg[0], m->reg[0], m->reg[1], 0);
         if (e == cudaSuccess) e = cudaEventRecord(ev[1], m->stream);
@@ -805,7 +858,7 @@ extern "C" ak_status ak_selftest_barrier(ak_mesh* m, int32_t absent) {
 extern "C" ak_status ak_mesh_fuse(ak_mesh* m, int32_t fused) {
   if (!m) return einval("ak_mesh_fuse: NULL mesh");
   if (fused != 0 && fused != 1) return einval("ak_mesh_fuse: fused must be 0 or 1");
-  if (fused && m->md.direct)
+  if (fused && !stage_fill(m))
     return einval("ak_mesh_fuse: this mesh has no ghost fill to fuse (uniform, no FOFC)");
   m->fused = fused;
   invalidate_graph(m);

@@ -82,17 +82,21 @@ struct ak_meshdev {
   const int32_t* map;   // leaf id or -1, per level per block slot
   const int4* fc;       // flux-correction faces: (block, face, first face cell, n cells)
   double* fcbuf;        // corrected coarse-face fluxes, [face cell][5]
-  const ak_xfer* xa;    // exchange plan, pass 1: copies and restrictions
+  const ak_xfer* xa;    // exchange plan, pass 1 before a stage: copies and restrictions
+                        // (with direct halo reads only the entries a stage needs)
   const ak_xfer* xb;    // exchange plan, pass 2: prolongations
   long long nxa, nxb;
+  const long long* nbase;  // direct halo reads: per block, 27 element bases (see
+                           // neighbour_table)
   const long long* cell_off;  // first interior cell of each block in the global count
   unsigned char* fflag; // FOFC: 1 for a flagged interior cell (global count), else 0
   int4* flist;          // FOFC: flagged cells (block, i, j, k) of the current stage
   double* fu0;          // FOFC: U0 of each listed cell, [entry][5] (stages that use U0)
   int fcap;             // capacity of flist
   int fofc;             // FOFC on
-  int direct;           // stage kernels read halo cells from the neighbour blocks (uniform
-                        // meshes without FOFC): no ghost fill before a stage
+  int direct;           // stage kernels read halo cells of same-level neighbours from
+                        // their interiors (meshes without FOFC): a stage needs no copies,
+                        // only the restrictions and prolongations at level boundaries
   int nblocks, nlev, ng, nfc;
   long long fc_cells;   // face cells of all flux-correction faces
   double gamma;
@@ -121,8 +125,11 @@ struct ak_mesh {
   unsigned char* d_fflag;       // FOFC flags and list (see ak_meshdev)
   int4* d_flist;
   double* d_fu0;
-  ak_xfer* d_xa;                // exchange plan (see ak_xfer)
+  ak_xfer* d_xa;                // exchange plan (see ak_xfer): every ghost cell
   ak_xfer* d_xb;
+  ak_xfer* d_xs;                // pass-1 entries a stage needs with direct halo reads
+  long long nxa_full;           // entries of d_xa
+  long long* d_nbase;           // direct halo reads: 27 element bases per block
   ak_work* d_work;
   int nwork;
   int tile;                     // stage tile: 0 = 16x16 columns, 1 = 32x8
@@ -146,7 +153,8 @@ struct ak_mesh {
 void ak_set_error(const char* fmt, ...);
 
 // ---- launchers (return cudaSuccess or the launch error) ----
-cudaError_t ak_launch_fill_ghosts(const ak_mesh* m, double* reg);
+// full: every ghost cell (ak_fill_ghosts); else the fill a stage needs (md.xa, md.xb)
+cudaError_t ak_launch_fill_ghosts(const ak_mesh* m, double* reg, bool full);
 cudaError_t ak_launch_flux_correction(const ak_mesh* m, const double* reg);
 cudaError_t ak_launch_pack(const ak_mesh* m, const double* reg, double* packed);
 cudaError_t ak_launch_unpack(const ak_mesh* m, const double* packed, double* reg);

@@ -129,13 +129,18 @@ inline int parts_for(const ak_mesh* m) {
 
 }  // namespace
 
-cudaError_t ak_launch_fill_ghosts(const ak_mesh* m, double* reg) {
-  if (m->md.nxa)
-    fill_copy_restrict_kernel<<<(unsigned)(((m->md.nxa + 1) / 2 + kThreads - 1) / kThreads),
-                                kThreads, 0, m->stream>>>(reg, m->md);
-  if (m->md.nxb)
-    fill_prolong_kernel<<<(unsigned)((m->md.nxb + kThreads - 1) / kThreads), kThreads, 0,
-                          m->stream>>>(reg, m->md);
+cudaError_t ak_launch_fill_ghosts(const ak_mesh* m, double* reg, bool full) {
+  ak_meshdev md = m->md;
+  if (full) {  // the whole plan, not only what a stage with direct halo reads needs
+    md.xa = m->d_xa;
+    md.nxa = m->nxa_full;
+  }
+  if (md.nxa)
+    fill_copy_restrict_kernel<<<(unsigned)(((md.nxa + 1) / 2 + kThreads - 1) / kThreads),
+                                kThreads, 0, m->stream>>>(reg, md);
+  if (md.nxb)
+    fill_prolong_kernel<<<(unsigned)((md.nxb + kThreads - 1) / kThreads), kThreads, 0,
+                          m->stream>>>(reg, md);
   return cudaGetLastError();
 }
 

@@ -446,37 +446,27 @@ __device__ __forceinline__ int fofc_flag(const double* un, const ak_meshdev& md,
   return -1;
 }
 
-// Direct halo reads (uniform meshes without FOFC): the element offsets of the first
-// ghost cell of the 27 blocks around block `blk` (periodic), entry
-// (dx + 1) + 3 (dy + 1) + 9 (dz + 1); threads 0..26 of the CTA fill it.
+// Direct halo reads (meshes without FOFC): threads 0..26 of the CTA copy block `blk`'s
+// 27 element bases, entry (dx + 1) + 3 (dy + 1) + 9 (dz + 1) for the halo region in
+// direction (dx, dy, dz): a same-level neighbour's offset shifted back by the block
+// extents, or the block's own offset where that region is at another level (its ghost
+// cells, filled by restriction or prolongation) -- see halo_elem.
 __device__ __forceinline__ void neighbour_table(const ak_meshdev& md, int blk, long long* nb) {
   const int t = threadIdx.x;
-  if (t < 27) {
-    const ak_block& B = md.blocks[blk];
-    const ak_level& L = md.levels[0];
-    const int mdim[3] = {L.md1, L.md2, L.md3};
-    int q[3] = {B.lx1 / L.bs1 + t % 3 - 1, B.lx2 / L.bs2 + (t / 3) % 3 - 1,
-                B.lx3 / L.bs3 + t / 9 - 1};
-#pragma unroll
-    for (int a = 0; a < 3; ++a) q[a] = q[a] < 0 ? q[a] + mdim[a] : (q[a] >= mdim[a] ? q[a] - mdim[a] : q[a]);
-    nb[t] = md.blocks[md.map[L.map_off + (q[2] * L.md2 + q[1]) * L.md1 + q[0]]].off;
-  }
+  if (t < 27) nb[t] = md.nbase[27 * (long long)blk + t];
 }
 
-// Element of the cell at padded indices (ip, jp) and interior plane kp of block g, in the
-// neighbour block that holds it (every block of a uniform mesh has g's geometry; blocks
-// are at least NG cells wide, so a halo cell is at most one block away).
+// Element of the cell at padded indices (ip, jp) and interior plane kp of block g, read
+// where the stage finds it: in the same-level neighbour block that holds it (blocks of a
+// level share g's geometry and are at least NG cells wide, so a halo cell is at most one
+// block away), or in g's own ghost cells.
 __device__ __forceinline__ long long halo_elem(const ak_block& g, const long long* nb, int ng,
                                                int ip, int jp, int kp) {
-  int i = ip - ng, j = jp - ng, k = kp;
-  const int dx = i < 0 ? -1 : (i >= g.nx1 ? 1 : 0);
-  const int dy = j < 0 ? -1 : (j >= g.nx2 ? 1 : 0);
-  const int dz = k < 0 ? -1 : (k >= g.nx3 ? 1 : 0);
-  i -= dx * g.nx1;
-  j -= dy * g.nx2;
-  k -= dz * g.nx3;
+  const int dx = ip < ng ? -1 : (ip >= ng + g.nx1 ? 1 : 0);
+  const int dy = jp < ng ? -1 : (jp >= ng + g.nx2 ? 1 : 0);
+  const int dz = kp < 0 ? -1 : (kp >= g.nx3 ? 1 : 0);
   return nb[(dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)] +
-         ((long long)(k + ng) * g.p2 + (j + ng)) * g.s1 + (i + ng);
+         ((long long)(kp + ng) * g.p2 + jp) * g.s1 + ip;
 }
 
 // The stage kernels' background state and EOS constants of a mesh (ak_stage.cu).

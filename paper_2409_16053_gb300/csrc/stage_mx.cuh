@@ -206,8 +206,9 @@ __global__ void __launch_bounds__(MxCfg<NG, T>::NTH, 2)
   constexpr int HALOC = TX / 2;                       // chunks of an x2 halo row
   constexpr int CPV = C::TY * FULLC + 2 * NG * HALOC;  // chunks per variable
   constexpr int NSC = (5 * CPV + C::NTH - 1) / C::NTH;
-  // shared element index (-1: none) with, for direct halo reads, the x/y neighbour
-  // (dx + 1) + 3 (dy + 1) in bits 16..19; element offset at plane 0 in the source block
+  // shared element index (-1: none) with, for direct halo reads, the x/y direction
+  // (dx + 1) + 3 (dy + 1) of its halo region in bits 16..19; element offset of the chunk
+  // at plane 0 from the base of that region (see halo_elem)
   int sc_s[NSC], sc_g[NSC];
 #pragma unroll
   for (int m = 0; m < NSC; ++m) {
@@ -228,30 +229,25 @@ __global__ void __launch_bounds__(MxCfg<NG, T>::NTH, 2)
         y = hr < NG ? hr : hr + C::TY;
         s = y < NG ? y * TX + (x - NG) : NG * TX + C::TY * WSX + (y - NG - C::TY) * TX + (x - NG);
       }
-      int ip = i0 + x, jp = j0 + y;
+      const int ip = i0 + x, jp = j0 + y;
       if (ip < g.p1 && jp < g.p2) {
-        int code = 4;
-        if (direct) {  // a halo chunk comes from the x/y neighbour block
-          const int dx = ip < NG ? -1 : (ip >= NG + g.nx1 ? 1 : 0);
-          const int dy = jp < NG ? -1 : (jp >= NG + g.nx2 ? 1 : 0);
-          ip -= dx * g.nx1;
-          jp -= dy * g.nx2;
-          code = (dx + 1) + 3 * (dy + 1);
-        }
-        sc_s[m] = (v * NSTG + s) | (code << 16);
+        const int dx = ip < NG ? -1 : (ip >= NG + g.nx1 ? 1 : 0);
+        const int dy = jp < NG ? -1 : (jp >= NG + g.nx2 ? 1 : 0);
+        sc_s[m] = (v * NSTG + s) | (((dx + 1) + 3 * (dy + 1)) << 16);
         sc_g[m] = v * (int)vst + (NG * g.p2 + jp) * g.s1 + ip;
       }
     }
   }
   auto stage_plane = [&](int kp) {
-    // direct halo reads: ghost planes come from the x3 neighbour blocks
-    const int dz = direct ? (kp < 0 ? -1 : (kp >= g.nx3 ? 1 : 0)) : 0;
-    const long long po = (long long)(kp - dz * g.nx3) * pst;
+    // direct halo reads: each chunk from the base of its halo region (x, y and the plane's
+    // x3 direction)
+    const int dz = kp < 0 ? -1 : (kp >= g.nx3 ? 1 : 0);
+    const long long po = (long long)kp * pst;
 #pragma unroll
     for (int m = 0; m < NSC; ++m) {
       if (sc_s[m] >= 0) {
         const long long base = direct ? nbr[(sc_s[m] >> 16) + 9 * (dz + 1)] : g.off;
-        cp_async16(&stg[sc_s[m] & 0xffff], uin + base + sc_g[m] + po);
+        cp_async16(&stg[sc_s[m] & 0xffff], uin + (base + sc_g[m] + po));
       }
     }
   };

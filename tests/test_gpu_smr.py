@@ -221,3 +221,62 @@ def test_fuse_refused_without_ghost_fill(ak):
     with pytest.raises(ak.AkError):
         m.fuse(True)
     m.close()
+
+
+def _padded_blocks(m, reg=0):
+    """Every block's padded array (5, p3, p2, p1) of a GPU register, ghosts included
+    (ak_mesh_layout's rule: rows padded to a multiple of 4 elements)."""
+    R = m.regs[reg].cpu().numpy()
+    out = []
+    for b, r in enumerate(m.table):
+        p1, p2, p3 = (int(r[4 + d]) + 2 * m.ng for d in range(3))
+        s1 = (p1 + 3) // 4 * 4
+        if b == 0:
+            assert tuple(m.strides) == (s1 * p2 * p3, s1 * p2, s1, 1)
+        o = int(m.offsets[b])
+        a = R[o:o + 5 * s1 * p2 * p3].reshape(5, p3, p2, s1)[..., :p1]
+        out.append(a)
+    return out
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_fill_ghosts_refined_matches_oracle(ak, precision):
+    """ak_fill_ghosts fills every ghost cell of a refined mesh -- copies, restrictions,
+    prolongations, edges and corners -- as the SMR oracle does, also on meshes whose
+    stages read same-level halos directly (and so fill only level boundaries)."""
+    t = pgen.nested_refinement_blocks(32, 8, 8, 2)
+    P = _smooth(t, 32)
+    om = oracle.SmrMesh(t, (32, 32, 32))
+    U = om.from_packed(P)
+    om.fill_ghosts(U)
+    m = _gpu_mesh(ak, t, 32, precision=precision, ref_rho=1.0, ref_p=1.0)
+    m.upload_packed(P)
+    m.fill_ghosts(0)
+    m.stream.synchronize()
+    got = _padded_blocks(m)
+    for b in range(len(t)):
+        want = om.block(U, b)
+        assert np.allclose(got[b], want, rtol=1e-14, atol=1e-14), b
+    m.close()
+
+
+@pytest.mark.parametrize("precision,recon", [(0, 0), (1, 0), (0, 1), (1, 1)])
+def test_direct_halo_reads_match_full_fill_bitwise(ak, precision, recon):
+    """Without FOFC the stage kernels read same-level halo cells from the neighbour
+    blocks and the fill before a stage keeps only the level-boundary entries; with FOFC
+    (here on a smooth flow that flags no cell) every ghost cell is filled and read from
+    the block's own ghost zone.  Both give the same bits."""
+    t = pgen.nested_refinement_blocks(32, 8, 8, 2)
+    P = _smooth(t, 32)
+    outs = []
+    for fofc in (False, True):
+        m = _gpu_mesh(ak, t, 32, precision=precision, recon=recon, rk=3 if recon else 2,
+                      fofc=fofc, ref_rho=1.0, ref_p=1.0)
+        m.upload_packed(P)
+        dt = m.new_dt()
+        for _ in range(3):
+            m.step(dt, want_dt_next=False)
+        outs.append(m.download_packed())
+        assert m.counters()[:3] == [0, 0, 0]
+        m.close()
+    assert np.array_equal(outs[0], outs[1])

@@ -50,6 +50,10 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # (sm__pipe_fp64_cycles_active.avg.pct_of_peak_sustained_active, mean of the two stages):
 # the unit the form is bound by
 FP64_PIPE_BUSY_NCU = 0.766
+# FP64 instructions (DADD + DMUL + DFMA, thread level) per cell of the FP64 stage kernel
+# in the same capture (smsp__sass_thread_inst_executed_op_{dadd,dmul,dfma}_pred_on),
+# stages 1 and 2: set against the measured FP64 instruction rate (ak_probe_fp64_rate)
+FP64_INST_PER_CELL_NCU = (350.2, 378.5)
 # DRAM bytes per cell of the stage kernels (dram__bytes_read.sum + dram__bytes_write.sum
 # of one ncu capture per launch: PLM + RK2 on 192^3 in 64^3 blocks, PPM4 + RK3 on 256^3 in
 # 128^3 blocks; the per-cell figures carry over to grids of the same block size), valid
@@ -609,6 +613,18 @@ def main():
     # FP64 stage kernel: ALU bound (FP64 pipe); per launch = mean of the two stages
     st64 = 0.5 * (r64["stage1_ms"] + r64["stage2_ms"])
     ach64 = FLOP_PER_CELL_STAGE * cells / (st64 * 1e-3) / 1e12
+    # the FP64 instructions the kernel issues against the rate this GPU sustains
+    fp64_rate = None
+    if rank == 0:
+        dfma_s = ak.ak_probe_fp64_rate(torch.cuda.current_stream().cuda_stream)
+        inst_s = sum(FP64_INST_PER_CELL_NCU) / 2 * cells / (st64 * 1e-3)
+        fp64_rate = {"inst_per_cell_stage_ncu": list(FP64_INST_PER_CELL_NCU),
+                     "achieved_inst_per_s": inst_s, "measured_dfma_per_s": dfma_s,
+                     "measured_per_clock_per_sm": dfma_s / (152 * clk["sm_mhz"] * 1e6)
+                     if clk.get("sm_mhz") else None,
+                     "frac_of_measured": inst_s / dfma_s,
+                     "source": "ak_probe_fp64_rate: 8 independent DFMA chains per thread, "
+                               "8 CTAs of 256 threads per SM"}
     # mixed stage kernel: HBM roofline on the algorithmic bytes per launch
     stmx = 0.5 * (rmx["stage1_ms"] + rmx["stage2_ms"])
     bytes_mx = 0.5 * (BYTES_STAGE[1] + BYTES_STAGE[2]) * cells
@@ -634,7 +650,8 @@ def main():
                      "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz "
                                     "(ncu's peak_sustained for DFMA: 304 per clock on "
                                     "152 SMs)",
-                     "fp64_pipe_busy_ncu": FP64_PIPE_BUSY_NCU},
+                     "fp64_pipe_busy_ncu": FP64_PIPE_BUSY_NCU,
+                     "measured_fp64_rate": fp64_rate},
         "mixed": {
             "value": valuemx, "unit": UNIT, "ms_per_step": tmx / args.steps, "dtype": "f32+f64",
             "roofline": {"bound": "hbm", "achieved": ach_mx, "peak": hbm, "unit": "GB/s",

@@ -297,6 +297,17 @@ ak_status ak_cfl_dt_noalloc(const double* reg, int32_t nblocks, const int32_t nx
                             int32_t nghost, const double dx[3], double gamma, double cfl,
                             void* cuda_stream, double* dt_out);
 
+/* Measured FP64 rate of the current device: fused multiply-adds per second that its
+ * FP64 unit sustains (every thread runs eight independent chains, so the pipe, not the
+ * latency of one chain, limits it).  A measurement aid for the roofline of the FP64
+ * form, whose stage kernels are bound by the FP64 unit rather than by HBM (Section 3's
+ * update in double precision); DADD and DMUL issue on the same pipe.  Runs four
+ * launches of about 10 ms on `cuda_stream` (a cudaStream_t, NULL = legacy default
+ * stream), synchronizes it, and writes the fastest of the last three to *dfma_per_s.
+ * Allocates no device memory.  AK_EINVAL for a NULL output, AK_ECUDA if a CUDA call
+ * fails. */
+ak_status ak_probe_fp64_rate(void* cuda_stream, double* dfma_per_s);
+
 /* Message of the last error returned on this host thread ("" if none). */
 const char* ak_last_error(void);
 

@@ -9,7 +9,7 @@ Low level (same names and arguments as the C functions):
     ak_mesh_create, ak_mesh_destroy, ak_mesh_layout, ak_mesh_bind, ak_fill_ghosts,
     ak_stage, ak_new_dt, ak_step, ak_upload, ak_download, ak_status_counters,
     ak_mesh_autotune, ak_mesh_schedule, ak_mesh_fuse, ak_selftest_barrier, ak_cfl_dt_noalloc,
-    ak_last_error
+    ak_probe_fp64_rate, ak_last_error
 High level: ``Mesh`` builds a uniform mesh of equal MeshBlocks, allocates and binds
 its registers as torch tensors, and converts between a global (5, n3, n2, n1) array
 and the library's block layout.
@@ -84,6 +84,8 @@ def _load_lib():
     lib.ak_cfl_dt_noalloc.argtypes = [vp, i32, ctypes.POINTER(i32), i32, dp, ctypes.c_double,
                                       ctypes.c_double, vp, dp]
     lib.ak_cfl_dt_noalloc.restype = ctypes.c_int
+    lib.ak_probe_fp64_rate.argtypes = [vp, dp]
+    lib.ak_probe_fp64_rate.restype = ctypes.c_int
     lib.ak_last_error.restype = ctypes.c_char_p
     for name in ("ak_mesh_create", "ak_mesh_layout", "ak_mesh_bind", "ak_fill_ghosts",
                  "ak_stage", "ak_new_dt", "ak_step", "ak_upload", "ak_download",
@@ -97,7 +99,7 @@ EXPORTED = ("ak_mesh_create", "ak_mesh_destroy", "ak_mesh_layout", "ak_mesh_bind
             "ak_fill_ghosts", "ak_stage", "ak_new_dt", "ak_step", "ak_upload",
             "ak_download", "ak_status_counters", "ak_mesh_autotune", "ak_mesh_schedule", "ak_mesh_fuse",
             "ak_selftest_barrier",
-            "ak_cfl_dt_noalloc", "ak_last_error")
+            "ak_cfl_dt_noalloc", "ak_probe_fp64_rate", "ak_last_error")
 
 
 def ak_last_error() -> str:
@@ -210,6 +212,13 @@ def ak_cfl_dt_noalloc(reg_ptr: int, nblocks: int, nx, nghost: int, dx, gamma: fl
     _check(_lib.ak_cfl_dt_noalloc(ctypes.c_void_p(reg_ptr), int(nblocks), nx_c, int(nghost),
                                   dx_c, float(gamma), float(cfl),
                                   ctypes.c_void_p(cuda_stream), ctypes.byref(out)))
+    return out.value
+
+
+def ak_probe_fp64_rate(cuda_stream: int = 0) -> float:
+    """Measured FP64 fused multiply-adds per second of the current device."""
+    out = ctypes.c_double()
+    _check(_lib.ak_probe_fp64_rate(ctypes.c_void_p(cuda_stream), ctypes.byref(out)))
     return out.value
 
 

@@ -433,20 +433,18 @@ __device__ __forceinline__ void plm_edges_fp64(double dl, double dr, double q0, 
   hi = fma(p, r, q0);
 }
 
-// CW84 limited slope: centred difference bounded by twice the one-sided ones
+// CW84 limited slope: centred difference bounded by twice the one-sided ones, zero at an
+// extremum.  min(|d|, 2|dl|, 2|dr|) with the sign of d: where d = 0 the one-sided
+// differences have opposite signs (or one is zero), so the sign of a zero never reaches
+// the result.
 template <typename V>
 __device__ __forceinline__ V ppm_slope_v(V qm, V q0, V qp) {
   const V zero = vset<V>(0.0f), two = vset<V>(2.0f);
   const V dl = vsub(q0, qm);
   const V dr = vsub(qp, q0);
   const V d = vmul(vset<V>(0.5f), vsub(qp, qm));
-  V m = vabs(d);
-  const V tl = vmul(two, vabs(dl));
-  const V tr = vmul(two, vabs(dr));
-  m = vsel(vgt(m, tl), tl, m);
-  m = vsel(vgt(m, tr), tr, m);
-  const V sm = vsel(vgt(d, zero), m, vneg(m));
-  return vsel(vgt(vmul(dl, dr), zero), sm, zero);
+  const V m = vmin(vmin(vabs(d), vmul(two, vabs(dl))), vmul(two, vabs(dr)));
+  return vsel(vgt(vmul(dl, dr), zero), vcopysign(m, d), zero);
 }
 
 // CW84 interface values of the middle cell of q0..q4 and their monotonization

@@ -494,9 +494,11 @@ __device__ __forceinline__ void hllc_mixed(const V* wl, const V* wr, const Bg& b
   const V cr = vmul(vabs(gpr), vrsqrt(vmul(gpr, rr)));
 
   // PVRS estimate as a deviation from p_b; p* = max(0, p_b + dps)
+  // (p_b + dps > 0 exactly when dps > -p_b: a sum of two floats keeps the sign of its
+  // exact value)
   V dps = vfma(vmul(vmul(vset<V>(-0.125f), vsub(ur, ul)), vadd(rl, rr)), vadd(cl, cr),
                vmul(half, vadd(dpl, dpr)));
-  dps = vsel(vgt(vadd(pb, dps), zero), dps, vneg(pb));
+  dps = vmax(dps, vneg(pb));
   const V kq = vset<V>(bg.kq_f);
   const V al = vfma(vmul(kq, vsub(dps, dpl)), vrcp(pl), one);
   const V ar = vfma(vmul(kq, vsub(dps, dpr)), vrcp(pr), one);
@@ -504,9 +506,8 @@ __device__ __forceinline__ void hllc_mixed(const V* wl, const V* wr, const Bg& b
   const V qr = vsel(vgt(dps, dpr), vmul(ar, vrsqrt(ar)), one);
   V sl = vfma(vneg(cl), ql, ul);
   V sr = vfma(cr, qr, ur);
-  const V dl = vsub(ur, cr), dr = vadd(ul, cl);            // Davis bounds
-  sl = vsel(vgt(sl, dl), dl, sl);
-  sr = vsel(vgt(dr, sr), dr, sr);
+  sl = vmin(sl, vsub(ur, cr));                             // Davis bounds
+  sr = vmax(sr, vadd(ul, cl));
 
   const auto sup_l = vge(sl, zero);                        // S_L >= 0
   const auto sup_r = vge(zero, sr);                        // S_R <= 0

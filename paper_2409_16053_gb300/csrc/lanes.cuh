@@ -83,11 +83,15 @@ __device__ __forceinline__ float2 vsel(bool2 c, float2 a, float2 b) {
 __device__ __forceinline__ float vabs(float a) { return fabsf(a); }
 __device__ __forceinline__ float2 vabs(float2 a) { return make_float2(fabsf(a.x), fabsf(a.y)); }
 
-// minimum of two non-NaN values (one min instruction; a select on a comparison would
-// also order NaNs); magnitude of a with the sign bit of b
+// minimum and maximum of two non-NaN values (one min / max instruction; a select on a
+// comparison would also order NaNs); magnitude of a with the sign bit of b
 __device__ __forceinline__ float vmin(float a, float b) { return fminf(a, b); }
 __device__ __forceinline__ float2 vmin(float2 a, float2 b) {
   return make_float2(fminf(a.x, b.x), fminf(a.y, b.y));
+}
+__device__ __forceinline__ float vmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ float2 vmax(float2 a, float2 b) {
+  return make_float2(fmaxf(a.x, b.x), fmaxf(a.y, b.y));
 }
 __device__ __forceinline__ float vcopysign(float a, float b) { return copysignf(a, b); }
 __device__ __forceinline__ float2 vcopysign(float2 a, float2 b) {

@@ -244,6 +244,56 @@ def test_mixed_linear_wave_l1_within_one_percent(ak):
     assert abs(e32 - e64) <= 0.01 * e64, (e32, e64)
 
 
+def _run_wave_bg(ak, n, rho_b, p_b):
+    U0, T = pgen.linear_wave((n, n, n))
+    m = _mesh(ak, (n, n, n), (n, n, n), precision=1, ref_rho=rho_b, ref_p=p_b)
+    m.upload(U0)
+    t, dt = 0.0, m.new_dt()
+    while t < T:
+        dt = min(dt, T - t)
+        dt_next = m.step(dt)
+        t += dt
+        dt = dt_next
+    out = m.download()
+    m.close()
+    return l1_wave_error(out, U0)
+
+
+@pytest.mark.parametrize("factor,bound", [(1.01, 1.01), (1.1, 1.03), (10.0, None)])
+def test_mixed_wave_error_against_background_choice(ak, factor, bound):
+    """The mixed form's error as the background (ref_rho, ref_p) moves off the flow's
+    state (rho = 1, p = 3/5) by a factor: on the 1e-6 sound wave a background within 1%
+    keeps the L1 error within 1% of the FP64 one, within 10% within 3%; a background 10x
+    off leaves O(1) deviations in the FP32 arithmetic, whose rounding (~1e-7 of them) is
+    then not small against the 1e-6 wave: the error grows several-fold (measured 14x)."""
+    e64, _ = _run_wave(ak, 32, 0)
+    ratio = _run_wave_bg(ak, 32, factor, factor * 0.6) / e64
+    if bound is not None:
+        assert ratio <= bound, ratio
+    else:
+        assert ratio > 5.0, ratio
+
+
+def test_mixed_turbulence_error_against_background_choice(ak):
+    """Mach-0.5 turbulence (O(1) fluctuations) after one step: a background 10x off
+    the mean state stays within 5e-7 of the oracle (4.6e-8 at the mean state), 100x off
+    within 1e-5 -- the FP32 rounding of deviations that carry the background mismatch."""
+    root = (32, 32, 32)
+    U0 = pgen.turbulence(root, seed=31, kmin=2, kmax=8, mach=0.5)
+    g = oracle.Grid(root)
+    dt = oracle.new_dt(U0, g, 0.3)
+    ref, _ = oracle.rk_step(U0, g, dt, 2)
+    errs = {}
+    for f in (1.0, 10.0, 100.0):
+        m = _mesh(ak, root, (16, 16, 16), precision=1, ref_rho=f, ref_p=f)
+        m.upload(U0)
+        m.step(dt)
+        errs[f] = max_norm_diff(m.download(), ref, G53)
+        m.close()
+    assert errs[1.0] <= 2e-7 and errs[10.0] <= 5e-7 and errs[100.0] <= 1e-5, errs
+    assert errs[100.0] > 10 * errs[1.0], errs
+
+
 def test_mixed_turbulence_close_to_oracle(ak):
     root = (32, 32, 32)
     U0 = pgen.turbulence(root, seed=31, kmin=2, kmax=8, mach=0.5)

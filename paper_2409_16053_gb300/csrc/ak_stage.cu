@@ -25,6 +25,7 @@ Bg make_bg(const ak_mesh* m) {
   bg.gamma_f = (float)gamma;
   bg.gm1 = gamma - 1.0;
   bg.kq = (gamma + 1.0) / (2.0 * gamma);
+  bg.kq1 = 1.0 - bg.kq;
   bg.rho = m->desc.ref_rho;
   bg.ug = m->desc.ref_p / (gamma - 1.0);
   bg.rho_f = (float)bg.rho;

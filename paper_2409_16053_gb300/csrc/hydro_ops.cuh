@@ -31,6 +31,7 @@ struct Bg {
   double gamma;
   float gamma_f;
   double kq;             // (gamma + 1) / (2 gamma), for the shock speed factor
+  double kq1;            // 1 - kq
   double gm1;            // gamma - 1
   float ug_floor_f;      // mixed form: u_g floor minus u_g,b, rounded
   double rho_min;        // mixed form: density floor
@@ -278,9 +279,11 @@ __device__ __forceinline__ void hllc_fp64(const double* wl, const double* wr, co
     sup_l = sl >= 0.0;
     sup_r = !sup_l && sr <= 0.0;
   } else {
+    // q_K = sqrt(1 + kq (p* / p_K - 1)) = sqrt(kq p* / p_K + (1 - kq)), kq p* shared
     ps = dpos(ps) ? ps : 0.0;
-    if (dgt_pos(ps, pl)) ql = sqrt64(fma(kq * (ps - pl), rcp64(pl), 1.0));
-    if (dgt_pos(ps, pr)) qr = sqrt64(fma(kq * (ps - pr), rcp64(pr), 1.0));
+    const double kps = kq * ps;
+    if (dgt_pos(ps, pl)) ql = sqrt64(fma(kps, rcp64(pl), bg.kq1));
+    if (dgt_pos(ps, pr)) qr = sqrt64(fma(kps, rcp64(pr), bg.kq1));
     sl = fma(-cl, ql, ul);
     sr = fma(cr, qr, ur);
     const double dl = ur - cr, dr = ul + cl;
@@ -317,15 +320,18 @@ __device__ __forceinline__ void hllc_fp64(const double* wl, const double* wr, co
   const double mn = rk * uk;
   const double inv = rcp64(s - sstar);
   const double fac = mk * inv;       // rho*_K
-  // E*_K = fac (E_K/rho_K + (S* - u_K)(S* + p_K/(rho_K (S_K - u_K))))
-  //      = E_K (S_K - u_K)/(S_K - S*) + (S* - u_K)(fac S* + p_K/(S_K - S*))
-  const double us4 = fma(sstar - uk, fma(fac, sstar, pk * inv), ek * ((s - uk) * inv));
+  // E*_K = fac (E_K/rho_K + (S* - u_K)(S* + p_K/(rho_K (S_K - u_K)))), so that
+  // E*_K - E_K = (S* - u_K) ((E_K + p_K)/(S_K - S*) + rho*_K S*) in closed form,
+  // and the star momentum flux is F*_rho S* + p* with p* = p_K + rho_K (S_K - u_K)(S* - u_K)
+  const double su = sstar - uk;
+  const double ep = ek + pk;
+  const double de = su * fma(fac, sstar, ep * inv);
   const double mt = fma(s, fac - rk, mn);  // M_n + S_K (rho*_K - rho_K)
   f[0] = mt;
-  f[1] = fma(s, fma(fac, sstar, -mn), fma(mn, uk, pk));
+  f[1] = fma(mt, sstar, fma(mk, su, pk));
   f[2] = mt * w[2];
   f[3] = mt * w[3];
-  f[4] = fma(s, us4 - ek, (ek + pk) * uk);
+  f[4] = fma(s, de, ep * uk);
 }
 
 // ------------------------------------------------------------------------------

@@ -245,10 +245,15 @@ ak_status ak_selftest_barrier(ak_mesh* mesh, int32_t absent);
 ak_status ak_mesh_schedule(ak_mesh* mesh, int32_t tile, int32_t nseg, int32_t order);
 
 /* Host <-> device state transfer (Section 2, "Data locality": data reaches the host
- * only for outputs) through a library staging buffer.  The host array is
- * the interior only, packed block after block: [block][var][k][j][i], i fastest
- * (nblocks * 5 * nx1*nx2*nx3 doubles for equal blocks).  Pinned host memory gives
- * asynchronous copies; ak_download synchronizes the stream. */
+ * only for outputs).  The host array is the interior only, packed block after block:
+ * [block][var][k][j][i], i fastest (nblocks * 5 * nx1*nx2*nx3 doubles for equal
+ * blocks), and must hold that many doubles.  Page-locked host memory that is mapped
+ * into the device's address space (cudaMallocHost / cudaHostAlloc, or cudaHostRegister
+ * with mapping, on a system with unified addressing) is read or written by the library's
+ * (un)pack kernel directly over the host link; ak_upload then returns before the data
+ * has moved, so keep the buffer until the stream has finished.  Other (pageable) memory
+ * goes through a library staging buffer (allocated on first use).  ak_download
+ * synchronizes the stream. */
 ak_status ak_upload(ak_mesh* mesh, int32_t reg, const double* host_interior);
 ak_status ak_download(ak_mesh* mesh, int32_t reg, double* host_interior);
 

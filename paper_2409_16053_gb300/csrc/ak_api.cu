@@ -899,10 +899,29 @@ static ak_status ensure_staging(ak_mesh* m) {
   return AK_OK;
 }
 
+// Device address of a host buffer that the GPU reaches directly: page-locked memory
+// mapped into the device's address space (cudaHostAlloc / cudaMallocHost, or
+// cudaHostRegister with mapping, on a system with unified addressing).  nullptr for
+// anything else (pageable memory), which goes through the staging buffer.
+static void* mapped_host(const void* host) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, host) != cudaSuccess) {
+    cudaGetLastError();  // clear the error of an unknown pointer
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 extern "C" ak_status ak_upload(ak_mesh* m, int32_t reg, const double* host) {
   if (!m || !host) return einval("ak_upload: NULL argument");
   ak_status s = need_reg(m, reg, "ak_upload");
   if (s != AK_OK) return s;
+  // mapped page-locked memory: the unpack kernel reads it over the host link itself, one
+  // pass instead of a copy into the staging buffer and a second pass over HBM
+  if (const void* dh = mapped_host(host)) {
+    AK_CUDA_TRY(ak_launch_unpack(m, static_cast<const double*>(dh), m->reg[reg]));
+    return AK_OK;
+  }
   if ((s = ensure_staging(m)) != AK_OK) return s;
   AK_CUDA_TRY(cudaMemcpyAsync(m->d_staging, host, m->staging_bytes, cudaMemcpyHostToDevice, m->stream));
   AK_CUDA_TRY(ak_launch_unpack(m, m->d_staging, m->reg[reg]));
@@ -913,6 +932,11 @@ extern "C" ak_status ak_download(ak_mesh* m, int32_t reg, double* host) {
   if (!m || !host) return einval("ak_download: NULL argument");
   ak_status s = need_reg(m, reg, "ak_download");
   if (s != AK_OK) return s;
+  if (void* dh = mapped_host(host)) {  // the pack kernel writes the host buffer itself
+    AK_CUDA_TRY(ak_launch_pack(m, m->reg[reg], static_cast<double*>(dh)));
+    AK_CUDA_TRY(cudaStreamSynchronize(m->stream));
+    return AK_OK;
+  }
   if ((s = ensure_staging(m)) != AK_OK) return s;
   AK_CUDA_TRY(ak_launch_pack(m, m->reg[reg], m->d_staging));
   AK_CUDA_TRY(cudaMemcpyAsync(host, m->d_staging, m->staging_bytes, cudaMemcpyDeviceToHost, m->stream));

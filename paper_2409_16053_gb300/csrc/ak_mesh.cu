@@ -10,6 +10,7 @@
 // eight fine cells average back to U_c.
 #include "ak_internal.cuh"
 #include "exchange.cuh"
+#include "fastmath.cuh"
 
 namespace {
 
@@ -67,7 +68,13 @@ __global__ void pack_kernel(double* reg, double* packed, ak_meshdev md, const lo
   }
 }
 
-// CFL minimum over interior cells of every leaf (Eq. (3)), into sc->dtmin_bits.
+// CFL minimum over interior cells of every leaf (Eq. (3)), into sc->dtmin_bits, as
+// 1 / max over cells and d of (|v_d| + c_s) / dx_d: a CTA takes the largest signal rate of
+// its cells and stores one reciprocal.  1 / rho and c_s come from single-precision seeds
+// (rcp64, rsqrt64) refined by one Newton step in FP64, so a cell costs about 17 FP64
+// operations instead of eight IEEE divisions and a square root, and the dt stays within
+// a few units in the last place of the definition.  A cell whose rate is not finite is
+// skipped, as fmin skips a NaN candidate.
 __global__ void cfl_kernel(const double* __restrict__ reg, ak_meshdev md, ak_dev_scalars* sc,
                            int parts) {
   __shared__ double red[kThreads / 32];
@@ -78,36 +85,54 @@ __global__ void cfl_kernel(const double* __restrict__ reg, ak_meshdev md, ak_dev
   const long long span = (n + parts - 1) / parts;
   const long long c0 = (long long)part * span;
   const long long c1 = c0 + span < n ? c0 + span : n;
-  const double gamma = md.gamma;
-  double m = __longlong_as_double(0x7ff0000000000000ll);
+  const double g2 = md.gamma * (md.gamma - 1.0);
+  const double idx1 = 1.0 / B.dx1, idx2 = 1.0 / B.dx2, idx3 = 1.0 / B.dx3;
+  double lam = 0.0;
   for (long long c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
     const int i = (int)(c % B.nx1);
-    const int j = (int)((c / B.nx1) % B.nx2);
-    const int k = (int)(c / ((long long)B.nx1 * B.nx2));
+    const long long r = c / B.nx1;
+    const int j = (int)(r % B.nx2);
+    const int k = (int)(r / B.nx2);
     const long long e = elem(B, md.ng, 0, i, j, k);
     double u[AK_NVAR];
 #pragma unroll
     for (int v = 0; v < AK_NVAR; ++v) u[v] = reg[e + v * B.var_stride];
-    double rho = u[0] >= AK_RHO_FLOOR ? u[0] : AK_RHO_FLOOR;
-    const double v1 = u[1] / rho, v2 = u[2] / rho, v3 = u[3] / rho;
-    double ug = u[4] - 0.5 * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) / rho;
+    const double rho = u[0] >= AK_RHO_FLOOR ? u[0] : AK_RHO_FLOOR;
+    double ir = ak::rcp64(rho);
+    ir = fma(ir, fma(-rho, ir, 1.0), ir);  // Newton: 1 / rho to about an ulp
+    const double m2 = fma(u[1], u[1], fma(u[2], u[2], u[3] * u[3]));
+    double ug = fma(-m2, ak::dscale(ir, -1), u[4]);
     ug = ug >= AK_UG_FLOOR ? ug : AK_UG_FLOOR;
-    const double cs = sqrt(gamma * (gamma - 1.0) * ug / rho);
-    double t = B.dx1 / (fabs(v1) + cs);
-    t = fmin(t, B.dx2 / (fabs(v2) + cs));
-    t = fmin(t, B.dx3 / (fabs(v3) + cs));
-    m = fmin(m, t);
+    const double cs2 = (g2 * ug) * ir;
+    // c_s = sqrt(cs2): s = cs2 y with y ~ 1/sqrt(cs2), then s + (y/2)(cs2 - s^2)
+    const double y = ak::rsqrt64(cs2);
+    const double s0 = cs2 * y;
+    const double cs = fma(ak::dscale(y, -1), fma(-s0, s0, cs2), s0);
+    const double l1 = fma(fabs(u[1]), ir, cs) * idx1;
+    const double l2 = fma(fabs(u[2]), ir, cs) * idx2;
+    const double l3 = fma(fabs(u[3]), ir, cs) * idx3;
+    // rates are >= 0: compare bit patterns on the integer pipe, skipping inf / NaN
+    const long long inf = 0x7ff0000000000000ll;
+    const long long b1 = __double_as_longlong(l1), b2 = __double_as_longlong(l2),
+                    b3 = __double_as_longlong(l3);
+    long long bl = __double_as_longlong(lam);
+    bl = (b1 > bl && b1 < inf) ? b1 : bl;
+    bl = (b2 > bl && b2 < inf) ? b2 : bl;
+    bl = (b3 > bl && b3 < inf) ? b3 : bl;
+    lam = __longlong_as_double(bl);
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  for (int o = 16; o > 0; o >>= 1) lam = fmax(lam, __shfl_xor_sync(0xffffffffu, lam, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lam;
   __syncthreads();
   if (threadIdx.x < 32) {
-    double v = threadIdx.x < kThreads / 32 ? red[threadIdx.x]
-                                           : __longlong_as_double(0x7ff0000000000000ll);
+    double v = threadIdx.x < kThreads / 32 ? red[threadIdx.x] : 0.0;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if (threadIdx.x == 0) atomicMin(&sc->dtmin_bits, (unsigned long long)__double_as_longlong(v));
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (threadIdx.x == 0) {
+      const double t = 1.0 / v;  // +inf for a CTA of cells at rest with c_s = 0
+      atomicMin(&sc->dtmin_bits, (unsigned long long)__double_as_longlong(t));
+    }
   }
 }
 

@@ -464,3 +464,24 @@ def test_schedule_rejects_bad_arguments(ak):
 def test_blocks_thinner_than_the_ghost_zone_are_refused(ak, recon, block):
     with pytest.raises(ak.AkError, match="nghost"):
         _mesh(ak, (16, 8, 8), block, recon=recon, rk=3 if recon else 2)
+
+
+def test_upload_download_pinned_and_pageable_paths(ak):
+    """Mapped page-locked buffers go through the (un)pack kernels directly, pageable ones
+    through the staging buffer: every combination returns the uploaded bits."""
+    import torch
+    root, block = (24, 20, 16), (12, 10, 8)
+    m = _mesh(ak, root, block)
+    P = m.pack(pgen.turbulence(root, seed=5, kmin=1, kmax=4, mach=1.0))
+    pinned = torch.from_numpy(P.copy()).pin_memory()
+    pageable = np.ascontiguousarray(P.copy())
+    for src in (pinned.data_ptr(), pageable.ctypes.data):
+        ak.ak_upload(m.handle, 1, src)
+        m.stream.synchronize()
+        out_pinned = torch.empty_like(pinned).pin_memory()
+        out_pageable = np.empty_like(pageable)
+        ak.ak_download(m.handle, 1, out_pinned.data_ptr())
+        ak.ak_download(m.handle, 1, out_pageable.ctypes.data)
+        assert np.array_equal(out_pinned.numpy(), P)
+        assert np.array_equal(out_pageable, P)
+    m.close()

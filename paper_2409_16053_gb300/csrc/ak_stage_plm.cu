@@ -9,7 +9,8 @@ cudaError_t launch_stage_plm(const ak_mesh* m, const double* uin, const double* 
                              double* uout, double a, double b, int rk2_final, int last_stage,
                              bool prepare) {
   if (m->desc.precision != AK_MIXED)
-    return launch<2, AK_PLM, false, 16, 16>(m, uin, u0, uout, a, b, rk2_final, last_stage, prepare);
+    return launch<2, AK_PLM, false, 16, 16, true>(m, uin, u0, uout, a, b, rk2_final, last_stage,
+                                                  prepare);
   // mixed PLM: tile 0 = paired 16x16 kernel, 1 = 32x8 columns, 2 = 16x16 columns
   if (prepare) {
     cudaError_t e = launch<2, AK_PLM, true, 32, 8>(m, uin, u0, uout, a, b, 0, 0, true);

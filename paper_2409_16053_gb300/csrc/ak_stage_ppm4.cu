@@ -10,7 +10,8 @@ cudaError_t launch_stage_ppm4(const ak_mesh* m, const double* uin, const double*
                               double* uout, double a, double b, int rk2_final,
                               int last_stage, bool prepare) {
   if (m->desc.precision != AK_MIXED)
-    return launch<3, AK_PPM4, false, 16, 16>(m, uin, u0, uout, a, b, rk2_final, last_stage, prepare);
+    return launch<3, AK_PPM4, false, 16, 16, true>(m, uin, u0, uout, a, b, rk2_final, last_stage,
+                                                   prepare);
   const int form = rk2_final ? 1 : (a == 0.0 ? 0 : 2);
   if (prepare) {
     cudaError_t e = launch<3, AK_PPM4, true, 16, 16>(m, uin, u0, uout, a, b, 0, 0, true);

@@ -181,9 +181,10 @@ __device__ __forceinline__ void edges(const R* q, R& lo, R& hi, int recon) {
   }
 }
 
-// HLLC on one face of direction d from edge values in natural variable order; the
-// flux comes back in natural order (rho, M1, M2, M3, E).
-template <bool NANCHK = false, typename R>
+// The mesh's Riemann solver (HLLC_ONLY: HLLC without the run-time choice) on one face of
+// direction d from edge values in natural variable order; the flux comes back in natural
+// order (rho, M1, M2, M3, E).
+template <bool NANCHK = false, bool HLLC_ONLY = false, typename R>
 __device__ __forceinline__ void solve(int d, const R* l, const R* r, const Bg& bg, R* f) {
   const int perm[5] = {0, 1 + d, 1 + (d + 1) % 3, 1 + (d + 2) % 3, 4};
   R wl[5], wr[5], fn[5];
@@ -192,7 +193,11 @@ __device__ __forceinline__ void solve(int d, const R* l, const R* r, const Bg& b
     wl[n] = l[perm[n]];
     wr[n] = r[perm[n]];
   }
-  if constexpr (std::is_same<R, double>::value)
+  if constexpr (HLLC_ONLY && std::is_same<R, double>::value)
+    hllc_fp64<NANCHK>(wl, wr, bg, fn);
+  else if constexpr (HLLC_ONLY)
+    hllc_mixed(wl, wr, bg, fn);
+  else if constexpr (std::is_same<R, double>::value)
     riemann<NANCHK>(wl, wr, bg, fn);
   else
     riemann(wl, wr, bg, fn);

@@ -55,13 +55,23 @@ struct StageCfg {
 // PERSIST: the persistent fused form for meshes that need a ghost fill (static
 // refinement, FOFC): a cooperative launch of at most one resident wave of CTAs first runs
 // the fill and the flux correction (fused_prologue), then loops over the work list.
-template <int NG, int RC, bool MIXED, int TX, int TY, bool PERSIST>
+// FORM >= 0, LAST >= 0: the RK form and the last-stage flag fixed at compile time (else
+// the run-time arguments).  FAST: a uniform mesh read through direct halo reads, HLLC,
+// no FOFC and no corrected faces -- the tests of those options compile away (a smaller
+// plane loop, which stays in the instruction cache).
+template <int NG, int RC, bool MIXED, int TX, int TY, bool PERSIST, int FORM = -1,
+          int LAST = -1, bool FAST = false>
 __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
     stage_kernel(const double* __restrict__ uin_arg, const double* u0, double* uout,
                  ak_meshdev md, const ak_work* __restrict__ work, Bg bg, double a, double b,
                  int form, ak_dev_scalars* sc, int last_stage, int nwork) {
   // form: 0 = first stage U + dt L; 1 = RK2 final (U0 + U + dt L) / 2;
   //       2 = a U0 + b (U + dt L)
+  static_assert(!(FAST && PERSIST), "the persistent form serves meshes with a ghost fill");
+  if constexpr (FORM >= 0) form = FORM;
+  if constexpr (LAST >= 0) last_stage = LAST;
+  const bool direct = FAST || md.direct;
+  const bool fofc = !FAST && md.fofc;
   using C = StageCfg<NG, MIXED, TX, TY>;
   using R = typename C::R;
   // reconstructions that can overshoot: a face without a sound speed gives a NaN flux
@@ -94,7 +104,7 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
   // this CTA's column tile of one MeshBlock, and that block's geometry
   const ak_work w = work[wi];
   const ak_block g = md.blocks[w.block];
-  if (md.direct) neighbour_table(md, w.block, nbr);
+  if (direct) neighbour_table(md, w.block, nbr);
   __syncthreads();
   const int blk = w.block;
   const int i0 = w.i0, j0 = w.j0, k0 = w.k0, k1 = w.k1;
@@ -138,7 +148,7 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
         if (ip < g.p1 && jp < g.p2) {
           const bool halo = ip < NG || ip >= NG + g.nx1 || jp < NG || jp >= NG + g.nx2 ||
                             kp < 0 || kp >= g.nx3;
-          const double* src = (md.direct && halo)
+          const double* src = (direct && halo)
                                   ? uin + halo_elem(g, nbr, NG, ip, jp, kp)
                                   : ub + ((long long)(kp + NG) * g.p2 + jp) * g.s1 + ip;
 #pragma unroll
@@ -222,7 +232,7 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
       if (i0 + fx <= g.nx1 && j0 + fy < g.nx2) {
         R l[5], r[5], f[5];
         const int fi = i0 + fx;
-        const int ov = fi == 0 ? g.ovr[0] : (fi == g.nx1 ? g.ovr[1] : -1);
+        const int ov = FAST ? -1 : (fi == 0 ? g.ovr[0] : (fi == g.nx1 ? g.ovr[1] : -1));
         if (ov >= 0) {  // coarse face next to a refined region: the fine-flux mean
           corrected_flux(md.fcbuf, ov + kcur * g.nx2 + j0 + fy, f);
         } else {
@@ -231,7 +241,7 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
             l[v] = e1hi[(v * TY + fy) * C1 + fx];       // cell i-1: column fx
             r[v] = e1lo[(v * TY + fy) * C1 + fx + 1];   // cell i:   column fx+1
           }
-          solve<NANCHK>(0, l, r, bg, f);
+          solve<NANCHK, FAST>(0, l, r, bg, f);
         }
 #pragma unroll
         for (int v = 0; v < 5; ++v) f1[(v * TY + fy) * (TX + 1) + fx] = f[v];
@@ -244,7 +254,7 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
       if (i0 + fx < g.nx1 && j0 + fy <= g.nx2) {
         R l[5], r[5], f[5];
         const int fj = j0 + fy;
-        const int ov = fj == 0 ? g.ovr[2] : (fj == g.nx2 ? g.ovr[3] : -1);
+        const int ov = FAST ? -1 : (fj == 0 ? g.ovr[2] : (fj == g.nx2 ? g.ovr[3] : -1));
         if (ov >= 0) {
           corrected_flux(md.fcbuf, ov + kcur * g.nx1 + i0 + fx, f);
         } else {
@@ -253,7 +263,7 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
             l[v] = e2hi[(v * (TY + 2) + fy) * TX + fx];      // cell j-1: row fy
             r[v] = e2lo[(v * (TY + 2) + fy + 1) * TX + fx];  // cell j:   row fy+1
           }
-          solve<NANCHK>(1, l, r, bg, f);
+          solve<NANCHK, FAST>(1, l, r, bg, f);
         }
 #pragma unroll
         for (int v = 0; v < 5; ++v) f2[(v * (TY + 1) + fy) * TX + fx] = f[v];
@@ -270,10 +280,10 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
     R lo_a[5], hi_a[5], lo_b[5];
     x3_edges(k0 - 1, lo_a, hi_a);
     x3_edges(k0, lo_b, hi3);
-    if (k0 == 0 && g.ovr[4] >= 0)
+    if (!FAST && k0 == 0 && g.ovr[4] >= 0)
       corrected_flux(md.fcbuf, g.ovr[4] + cj * g.nx1 + ci, f3m);
     else
-      solve<NANCHK>(2, hi_a, lo_b, bg, f3m);
+      solve<NANCHK, FAST>(2, hi_a, lo_b, bg, f3m);
   }
   __syncthreads();
   load_plane(k0 + NG);
@@ -322,10 +332,10 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
       x2_faces();
     }
     if (own) {
-      if (k + 1 == g.nx3 && g.ovr[5] >= 0)
+      if (!FAST && k + 1 == g.nx3 && g.ovr[5] >= 0)
         corrected_flux(md.fcbuf, g.ovr[5] + cj * g.nx1 + ci, f3p);
       else
-        solve<NANCHK>(2, hi3, lo3, bg, f3p);
+        solve<NANCHK, FAST>(2, hi3, lo3, bg, f3p);
 #pragma unroll
       for (int v = 0; v < 5; ++v) hi3[v] = hi3n[v];
     }
@@ -351,7 +361,7 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
         un[v] = r;
         f3m[v] = f3p[v];
       }
-      if (md.fofc) {
+      if (fofc) {
         // a flagged cell's U0, saved before the output (which may overwrite U0) is stored
         const int fi = fofc_flag(un, md, sc, blk, g, ci, cj, k);
         if (fi >= 0 && form != 0) {
@@ -435,16 +445,32 @@ Bg make_bg(const ak_mesh* m);
 
 // Launch (or, prepare_only, raise the shared-memory limit of) the stage kernel of one
 // configuration over the mesh's work list; m->fused selects the persistent variant.
-template <int NG, int RC, bool MIXED, int TX, int TY>
+using stage_kern_t = void (*)(const double*, const double*, double*, ak_meshdev, const ak_work*,
+                             Bg, double, double, int, ak_dev_scalars*, int, int);
+
+// WITH_FAST: the compile-time instances for uniform HLLC meshes without FOFC (FAST, with
+// each RK form and last-stage flag) exist and are launched where they apply.
+template <int NG, int RC, bool MIXED, int TX, int TY, bool WITH_FAST = false>
 inline cudaError_t launch(const ak_mesh* m, const double* uin, const double* u0, double* uout,
                           double a, double b, int rk2_final, int last_stage, bool prepare_only) {
   const size_t smem = StageCfg<NG, MIXED, TX, TY>::bytes;
   auto kern = stage_kernel<NG, RC, MIXED, TX, TY, false>;
   auto pk = stage_kernel<NG, RC, MIXED, TX, TY, true>;
+  stage_kern_t fast[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  if constexpr (WITH_FAST) {
+    fast[0] = stage_kernel<NG, RC, MIXED, TX, TY, false, 0, 0, true>;
+    fast[1] = stage_kernel<NG, RC, MIXED, TX, TY, false, 1, 0, true>;
+    fast[2] = stage_kernel<NG, RC, MIXED, TX, TY, false, 2, 0, true>;
+    fast[3] = stage_kernel<NG, RC, MIXED, TX, TY, false, 0, 1, true>;
+    fast[4] = stage_kernel<NG, RC, MIXED, TX, TY, false, 1, 1, true>;
+    fast[5] = stage_kernel<NG, RC, MIXED, TX, TY, false, 2, 1, true>;
+  }
   if (prepare_only) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(pk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    for (int i = 0; i < 6 && e == cudaSuccess && fast[i]; ++i)
+      e = cudaFuncSetAttribute(fast[i], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     return e;
   }
   const Bg bg = make_bg(m);
@@ -452,6 +478,12 @@ inline cudaError_t launch(const ak_mesh* m, const double* uin, const double* u0,
   if (m->fused)
     return launch_persistent(m, pk, TX * TY, smem, uin, u0, uout, m->md, m->d_work, bg, a, b,
                              form, m->d_sc, last_stage, m->nwork);
+  if (WITH_FAST && m->md.direct && !m->md.fofc && bg.rsolver == AK_HLLC && m->nfc == 0) {
+    const stage_kern_t k = fast[form + 3 * (last_stage ? 1 : 0)];
+    k<<<(unsigned)m->nwork, TX * TY, smem, m->stream>>>(uin, u0, uout, m->md, m->d_work, bg, a,
+                                                         b, form, m->d_sc, last_stage, m->nwork);
+    return cudaGetLastError();
+  }
   kern<<<(unsigned)m->nwork, TX * TY, smem, m->stream>>>(uin, u0, uout, m->md, m->d_work, bg, a,
                                                           b, form, m->d_sc, last_stage, m->nwork);
   return cudaGetLastError();

@@ -169,5 +169,46 @@ __device__ __forceinline__ double sqrt64(double x) {
   return x * rsqrt64(x);
 }
 
+// sqrt(a / b) for finite normal a, b > 0 without an FP64 instruction.  a = ma 2^ea,
+// b = mb 2^eb with ma, mb in [1, 2) split into leading 24 bits and the rest (ma = mah +
+// mal); an odd ea - eb moves a factor 2 into ma, so t = ma / mb = s^2 with the exponent
+// halved exactly.  From the seed s0 ~ sqrt(mah / mbh) (rsqrt.approx, ~2^-22), one Newton
+// step s = s0 + (ma - s0^2 mb) / (2 s0 mb): s0^2 = P + Pe and P mbh = Q + Qe exactly (fused
+// multiply-adds), and ma - Q is exact (Sterbenz), so the residual is formed to ~2^-46 in
+// FP32 and s0 + d is assembled as a double on the integer pipe (f32_plus_small_bits,
+// with s0 and d halved when s0 >= 1 so that s0 lies in [1/2, 1)).  Relative error below
+// 2^-42; other inputs (zero, subnormal, huge, negative, inf, NaN) take sqrt(a / b).
+__device__ __forceinline__ double sqrt_ratio64(double a, double b) {
+  const unsigned ah = (unsigned)__double2hiint(a), al = (unsigned)__double2loint(a);
+  const unsigned bh = (unsigned)__double2hiint(b), bl = (unsigned)__double2loint(b);
+  const unsigned ea = ah >> 20, eb = bh >> 20;  // sign bit included: negative -> >= 2048
+  if (ea == 0u || ea >= 2045u || eb == 0u || eb >= 2045u) return sqrt(a / b);
+  int e = (int)ea - (int)eb;
+  float mah, mal, mbh, mbl;
+  split_mantissa(ah, al, mah, mal);
+  split_mantissa(bh, bl, mbh, mbl);
+  if (e & 1) {  // odd exponent difference: t = 2 ma / mb, e even
+    mah *= 2.0f;
+    mal *= 2.0f;
+    e -= 1;
+  }
+  int k = e / 2;  // exact: e is even
+  float s0 = mah * rsqrt_approx_f32(mah * mbh);
+  const float P = s0 * s0;
+  const float Pe = fmaf(s0, s0, -P);
+  const float Q = P * mbh;
+  const float Qe = fmaf(P, mbh, -Q);
+  const float r = (mah - Q) + ((mal - Qe) - fmaf(P, mbl, Pe * mbh));
+  float d = r * rcp_approx_f32(2.0f * s0 * mbh);
+  if (s0 >= 1.0f) {  // keep s0 in [1/2, 1) for the assembly: halve both, scale back by k
+    s0 *= 0.5f;
+    d *= 0.5f;
+    k += 1;
+  }
+  long long bits = f32_plus_small_bits(s0, d);
+  bits += (long long)k << 52;
+  return __longlong_as_double(bits);
+}
+
 
 }  // namespace ak

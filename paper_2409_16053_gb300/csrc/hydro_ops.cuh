@@ -257,10 +257,9 @@ __device__ __forceinline__ void hllc_fp64(const double* wl, const double* wr, co
   const double rl = wl[0], ul = wl[1], rr = wr[0], ur = wr[1];
   const double pl = gm1 * wl[4];
   const double pr = gm1 * wr[4];
-  // c = sqrt(gamma p / rho) = |gamma p| / sqrt(gamma p rho)
-  const double gpl = gamma * pl, gpr = gamma * pr;
-  const double cl = fabs(gpl) * rsqrt64(gpl * rl);
-  const double cr = fabs(gpr) * rsqrt64(gpr * rr);
+  // c = sqrt(gamma p / rho) from split mantissas, without FP64 instructions but gamma p
+  const double cl = sqrt_ratio64(gamma * pl, rl);
+  const double cr = sqrt_ratio64(gamma * pr, rr);
 
   // pressure estimate of the linearised (PVRS) solver, then shock-aware speeds
   double ps = fma(-dscale_down((ur - ul) * (rl + rr), 3), cl + cr, dscale_down(pl + pr, 1));
@@ -344,8 +343,7 @@ __device__ __forceinline__ void llf_fp64(const double* wl, const double* wr, con
   const double gamma = bg.gamma, gm1 = bg.gm1;
   const double rl = wl[0], ul = wl[1], rr = wr[0], ur = wr[1];
   const double pl = gm1 * wl[4], pr = gm1 * wr[4];
-  const double gpl = gamma * pl, gpr = gamma * pr;
-  const double cl = fabs(gpl) * rsqrt64(gpl * rl), cr = fabs(gpr) * rsqrt64(gpr * rr);
+  const double cl = sqrt_ratio64(gamma * pl, rl), cr = sqrt_ratio64(gamma * pr, rr);
   const double al = fabs(ul) + cl, ar = fabs(ur) + cr;
   const double sm = NANCHK ? -(al > ar ? al : ar) : -(dgt_pos(al, ar) ? al : ar);
   const double el = fma(dscale(rl, -1), fma(ul, ul, fma(wl[2], wl[2], wl[3] * wl[3])), wl[4]);
@@ -369,8 +367,7 @@ __device__ __forceinline__ void hlle_fp64(const double* wl, const double* wr, co
   const double gamma = bg.gamma, gm1 = bg.gm1;
   const double rl = wl[0], ul = wl[1], rr = wr[0], ur = wr[1];
   const double pl = gm1 * wl[4], pr = gm1 * wr[4];
-  const double gpl = gamma * pl, gpr = gamma * pr;
-  const double cl = fabs(gpl) * rsqrt64(gpl * rl), cr = fabs(gpr) * rsqrt64(gpr * rr);
+  const double cl = sqrt_ratio64(gamma * pl, rl), cr = sqrt_ratio64(gamma * pr, rr);
   const double el = fma(dscale(rl, -1), fma(ul, ul, fma(wl[2], wl[2], wl[3] * wl[3])), wl[4]);
   const double er = fma(dscale(rr, -1), fma(ur, ur, fma(wr[2], wr[2], wr[3] * wr[3])), wr[4]);
   const double isl = rsqrt64(rl), isr = rsqrt64(rr);  // 1 / sqrt(rho)

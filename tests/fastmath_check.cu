@@ -21,6 +21,29 @@ __global__ void fastmath_kernel(const double* x, int n, double* out) {
   o[8] = ak::f32_to_f64(f) - (double)f;  // exact conversion: 0
 }
 
+// sqrt(a / b) on the integer pipe and FP32 next to the IEEE expression: out[2i], out[2i+1]
+__global__ void ratio_kernel(const double* a, const double* b, int n, double* out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  out[2 * (long long)i] = ak::sqrt_ratio64(a[i], b[i]);
+  out[2 * (long long)i + 1] = sqrt(a[i] / b[i]);
+}
+
+extern "C" int ratio_eval(const double* host_a, const double* host_b, int n, double* host_out) {
+  double *da = nullptr, *db = nullptr, *dout = nullptr;
+  if (cudaMalloc(&da, sizeof(double) * n) != cudaSuccess) return 1;
+  if (cudaMalloc(&db, sizeof(double) * n) != cudaSuccess) return 1;
+  if (cudaMalloc(&dout, sizeof(double) * 2 * (size_t)n) != cudaSuccess) return 2;
+  cudaMemcpy(da, host_a, sizeof(double) * n, cudaMemcpyHostToDevice);
+  cudaMemcpy(db, host_b, sizeof(double) * n, cudaMemcpyHostToDevice);
+  ratio_kernel<<<(n + 255) / 256, 256>>>(da, db, n, dout);
+  cudaError_t e = cudaMemcpy(host_out, dout, sizeof(double) * 2 * (size_t)n, cudaMemcpyDeviceToHost);
+  cudaFree(da);
+  cudaFree(db);
+  cudaFree(dout);
+  return e == cudaSuccess ? 0 : 3;
+}
+
 extern "C" int fastmath_eval(const double* host_x, int n, double* host_out) {
   double *dx = nullptr, *dout = nullptr;
   if (cudaMalloc(&dx, sizeof(double) * n) != cudaSuccess) return 1;

@@ -278,11 +278,11 @@ __device__ __forceinline__ void hllc_fp64(const double* wl, const double* wr, co
     sup_l = sl >= 0.0;
     sup_r = !sup_l && sr <= 0.0;
   } else {
-    // q_K = sqrt(1 + kq (p* / p_K - 1)) = sqrt(kq p* / p_K + (1 - kq)), kq p* shared
+    // q_K = sqrt(1 + kq (p* / p_K - 1)) = sqrt((kq p* + (1 - kq) p_K) / p_K), kq p* shared
     ps = dpos(ps) ? ps : 0.0;
     const double kps = kq * ps;
-    if (dgt_pos(ps, pl)) ql = sqrt64(fma(kps, rcp64(pl), bg.kq1));
-    if (dgt_pos(ps, pr)) qr = sqrt64(fma(kps, rcp64(pr), bg.kq1));
+    if (dgt_pos(ps, pl)) ql = sqrt_ratio64(fma(bg.kq1, pl, kps), pl);
+    if (dgt_pos(ps, pr)) qr = sqrt_ratio64(fma(bg.kq1, pr, kps), pr);
     sl = fma(-cl, ql, ul);
     sr = fma(cr, qr, ur);
     const double dl = ur - cr, dr = ul + cl;

@@ -116,6 +116,7 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
   const double dt = sc->dt;
   const double idx1 = 1.0 / g.dx1, idx2 = 1.0 / g.dx2, idx3 = 1.0 / g.dx3;
   const double cdt[3] = {dt * idx1, dt * idx2, dt * idx3};  // FP64 update: dt / dx_d
+  const double g2 = bg.gamma * bg.gm1;
   const bool need_u0 = form != 0;
 
   auto slot = [](int k) { return (k + 4 * NR) % NR; };
@@ -395,12 +396,12 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
           double rho = un[0];
           rho = at_least(rho, AK_RHO_FLOOR) ? rho : AK_RHO_FLOOR;
           const double r = rcp64(rho);
-          const double v1 = un[1] * r, v2 = un[2] * r, v3 = un[3] * r;
-          double ug = fma(-0.5, fma(un[1], v1, fma(un[2], v2, un[3] * v3)), un[4]);
+          const double m2 = fma(un[1], un[1], fma(un[2], un[2], un[3] * un[3]));
+          double ug = fma(-m2, dscale(r, -1), un[4]);
           ug = at_least(ug, AK_UG_FLOOR) ? ug : AK_UG_FLOOR;
-          const double cs = sqrt64(bg.gamma * bg.gm1 * ug * r);
-          const double l1 = (fabs(v1) + cs) * idx1, l2 = (fabs(v2) + cs) * idx2,
-                       l3 = (fabs(v3) + cs) * idx3;
+          const double cs = sqrt_ratio64(g2 * ug, rho);  // sqrt(gamma (gamma - 1) u_g / rho)
+          const double l1 = fma(fabs(un[1]), r, cs) * idx1, l2 = fma(fabs(un[2]), r, cs) * idx2,
+                       l3 = fma(fabs(un[3]), r, cs) * idx3;
           double lam = dgt_pos(l2, l1) ? l2 : l1;
           lam = dgt_pos(l3, lam) ? l3 : lam;
           lam_max = dgt_pos(lam, lam_max) ? lam : lam_max;

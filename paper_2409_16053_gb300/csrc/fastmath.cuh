@@ -92,6 +92,21 @@ __device__ __forceinline__ void split_mantissa(unsigned hi, unsigned lo, float& 
   ml = (__uint_as_float(0x4b000000u | ((lo & 0x1fffffffu) >> 6)) - 8388608.0f) * 0x1p-46f;
 }
 
+// bit pattern of the double nearest (r0 + d) 2^k for a positive normal float r0 (any
+// binade) and |d| < 2^-20 r0: r0 and d are first scaled by a power of two into [1/2, 1).
+// When a seed lies on the other side of a power of two than the value it approximates,
+// r0 + d leaves [1/2, 1) by up to the seed's error; the part beyond the edge was added in
+// units of 2^-53 and is rescaled to the neighbouring binade's unit (2^-54 below 1/2,
+// 2^-52 from 1 on).
+__device__ __forceinline__ long long scaled_sum_bits(float r0, float d, int k) {
+  const int ex = (int)((__float_as_uint(r0) >> 23) & 0xffu) - 126;  // r0 in [2^(ex-1), 2^ex)
+  const float sc = __uint_as_float((unsigned)(127 - ex) << 23);
+  long long s = f32_plus_small_bits(r0 * sc, d * sc);
+  const long long half = 0x3fe0000000000000ll, one = 0x3ff0000000000000ll;
+  s = s < half ? 2 * s - half : (s >= one ? one + ((s - one) >> 1) : s);
+  return s + ((long long)(k + ex) << 52);
+}
+
 // 1/x for finite normal x.  x = +-m 2^(ex-1023), m in [1, 2): r0 = seed of 1/mh in
 // (1/2, 1], e = 1 - m r0, 1/m ~ r0 + r0 e; then scaled by 2^(1023-ex) and signed.
 // Relative error below 2^-43.
@@ -175,8 +190,8 @@ __device__ __forceinline__ double sqrt64(double x) {
 // halved exactly.  From the seed s0 ~ sqrt(mah / mbh) (rsqrt.approx, ~2^-22), one Newton
 // step s = s0 + (ma - s0^2 mb) / (2 s0 mb): s0^2 = P + Pe and P mbh = Q + Qe exactly (fused
 // multiply-adds), and ma - Q is exact (Sterbenz), so the residual is formed to ~2^-46 in
-// FP32 and s0 + d is assembled as a double on the integer pipe (f32_plus_small_bits,
-// with s0 and d halved when s0 >= 1 so that s0 lies in [1/2, 1)).  Relative error below
+// FP32 and s0 + d is assembled as a double on the integer pipe (scaled_sum_bits).
+// Relative error below
 // 2^-42; other inputs (zero, subnormal, huge, negative, inf, NaN) take sqrt(a / b).
 __device__ __forceinline__ double sqrt_ratio64(double a, double b) {
   const unsigned ah = (unsigned)__double2hiint(a), al = (unsigned)__double2loint(a);
@@ -193,21 +208,14 @@ __device__ __forceinline__ double sqrt_ratio64(double a, double b) {
     e -= 1;
   }
   int k = e / 2;  // exact: e is even
-  float s0 = mah * rsqrt_approx_f32(mah * mbh);
+  const float s0 = mah * rsqrt_approx_f32(mah * mbh);  // about (0.7, 2)
   const float P = s0 * s0;
   const float Pe = fmaf(s0, s0, -P);
   const float Q = P * mbh;
   const float Qe = fmaf(P, mbh, -Q);
   const float r = (mah - Q) + ((mal - Qe) - fmaf(P, mbl, Pe * mbh));
-  float d = r * rcp_approx_f32(2.0f * s0 * mbh);
-  if (s0 >= 1.0f) {  // keep s0 in [1/2, 1) for the assembly: halve both, scale back by k
-    s0 *= 0.5f;
-    d *= 0.5f;
-    k += 1;
-  }
-  long long bits = f32_plus_small_bits(s0, d);
-  bits += (long long)k << 52;
-  return __longlong_as_double(bits);
+  const float d = r * rcp_approx_f32(2.0f * s0 * mbh);
+  return __longlong_as_double(scaled_sum_bits(s0, d, k));
 }
 
 

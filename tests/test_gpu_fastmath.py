@@ -60,16 +60,19 @@ def test_fastmath_against_ieee(lib):
 def test_sqrt_ratio_against_ieee(lib):
     """sqrt(a / b) (the sound speed sqrt(gamma p / rho)) from split mantissas: within
     2^-42 of the IEEE expression over the scheme's range, odd and even exponent
-    differences, mantissa ratios on both sides of 1 and next to the binade edges; the
-    IEEE fallback for zero, negative and non-finite inputs."""
+    differences, mantissa ratios on both sides of 1 and next to the binade edges
+    (including ratios just below 4, whose seed can land above 2); the IEEE results for
+    zero, negative and non-finite inputs."""
     rng = np.random.default_rng(1)
     n = 40000
     a = np.concatenate([10.0 ** rng.uniform(-30, 30, n), rng.uniform(1.0, 2.0, n),
                         2.0 - rng.uniform(0, 2 ** -20, 2000), 1.0 + rng.uniform(0, 2 ** -20, 2000),
-                        2.0 ** rng.integers(-500, 500, 2000) * (2.0 - 2.0 ** -52)])
+                        2.0 ** rng.integers(-500, 500, 2000) * (2.0 - 2.0 ** -52),
+                        (4.0 - rng.uniform(0, 2 ** -19, 2000)) * 4.0 ** rng.integers(-20, 20, 2000)])
     b = np.concatenate([10.0 ** rng.uniform(-30, 30, n), rng.uniform(1.0, 2.0, n),
                         1.0 + rng.uniform(0, 2 ** -20, 2000), 2.0 - rng.uniform(0, 2 ** -20, 2000),
-                        2.0 ** rng.integers(-500, 500, 2000) * (1.0 + 2.0 ** -52)])
+                        2.0 ** rng.integers(-500, 500, 2000) * (1.0 + 2.0 ** -52),
+                        1.0 + rng.uniform(0, 2 ** -20, 2000)])
     a = np.ascontiguousarray(a, dtype=np.float64)
     b = np.ascontiguousarray(b, dtype=np.float64)
     out = np.empty((a.size, 2))

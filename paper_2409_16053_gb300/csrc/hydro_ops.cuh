@@ -450,17 +450,17 @@ __device__ __forceinline__ V ppm_slope_v(V qm, V q0, V qp) {
   return vsel(vgt(vmul(dl, dr), zero), vcopysign(m, d), zero);
 }
 
-// CW84 interface values of the middle cell of q0..q4 and their monotonization
+// CW84 fourth-order interface value between cells of values ql, qr and limited slopes
+// sl, sr
 template <typename V>
-__device__ __forceinline__ void ppm_edges_v(V q0, V q1, V q2, V q3, V q4, V& lo, V& hi) {
+__device__ __forceinline__ V ppm_interface_v(V ql, V qr, V sl, V sr) {
+  return vfma(vsub(sl, sr), vset<V>(1.0f / 6.0f), vmul(vset<V>(0.5f), vadd(ql, qr)));
+}
+
+// CW84 monotonization of a cell's interface values a_lo, a_hi around its value a
+template <typename V>
+__device__ __forceinline__ void ppm_monotonize_v(V a_lo, V a_hi, V a, V& lo, V& hi) {
   const V zero = vset<V>(0.0f);
-  const V sm = ppm_slope_v(q0, q1, q2);
-  const V sc = ppm_slope_v(q1, q2, q3);
-  const V sp = ppm_slope_v(q2, q3, q4);
-  const V sixth = vset<V>(1.0f / 6.0f);
-  const V a_lo = vfma(vsub(sm, sc), sixth, vmul(vset<V>(0.5f), vadd(q1, q2)));
-  const V a_hi = vfma(vsub(sc, sp), sixth, vmul(vset<V>(0.5f), vadd(q2, q3)));
-  const V a = q2;
   const auto flat = vnot(vgt(vmul(vsub(a_hi, a), vsub(a, a_lo)), zero));
   const V da = vsub(a_hi, a_lo);
   const V a6 = vmul(vset<V>(6.0f), vfma(vset<V>(-0.5f), vadd(a_lo, a_hi), a));
@@ -472,6 +472,15 @@ __device__ __forceinline__ void ppm_edges_v(V q0, V q1, V q2, V q3, V q4, V& lo,
   const V n_hi = vsel(c2, vfma(vset<V>(3.0f), a, vmul(vset<V>(-2.0f), a_lo)), a_hi);
   lo = vsel(flat, a, n_lo);
   hi = vsel(flat, a, n_hi);
+}
+
+// CW84 interface values of the middle cell of q0..q4 and their monotonization
+template <typename V>
+__device__ __forceinline__ void ppm_edges_v(V q0, V q1, V q2, V q3, V q4, V& lo, V& hi) {
+  const V sm = ppm_slope_v(q0, q1, q2);
+  const V sc = ppm_slope_v(q1, q2, q3);
+  const V sp = ppm_slope_v(q2, q3, q4);
+  ppm_monotonize_v(ppm_interface_v(q1, q2, sm, sc), ppm_interface_v(q2, q3, sc, sp), q2, lo, hi);
 }
 
 // HLLC, mixed form.  w = (rho - rho_b, u_n, u_t1, u_t2, u_g - u_g,b) in FP32.  Returns

@@ -351,6 +351,25 @@ __global__ void __launch_bounds__(MxCfg<NG, T>::NTH, 2)
       cring[cslot(kc) * 5 * NOWN + v * NOWN + tid] = q[NG - 1];
     }
   };
+  // PPM4 carries, from cell to cell of the column, the limited slope of cell kc (column
+  // slot 0) and its lower interface value (slot 1), both computed for cell kc-1 already:
+  // per cell one new slope and one new interface value instead of three and two, with
+  // the same operations on the same operands (the same bits)
+  constexpr bool CARRY = RC == AK_PPM4;
+  auto x3_edges_carry = [&](int kc, float* lo, float* hi) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      const float qc = ring[xslot(kc) * 5 * NPL + v * NPL + oc];
+      const float qn = ring[xslot(kc + 1) * 5 * NPL + v * NPL + oc];
+      const float sp = ppm_slope_v(qc, qn, ring[xslot(kc + 2) * 5 * NPL + v * NPL + oc]);
+      float* cs = cring + v * NOWN + tid;
+      float* ca = cring + 5 * NOWN + v * NOWN + tid;
+      const float ahi = ppm_interface_v(qc, qn, *cs, sp);
+      ppm_monotonize_v(*ca, ahi, qc, lo[v], hi[v]);
+      *cs = sp;
+      *ca = ahi;
+    }
+  };
 
   // ---- prologue: plane k0+NG staged; planes k0-NG .. k0+NG-1 loaded and converted (the
   //      lowest NG-1 into column slots), the upper x3 edge of cell k0-1 -----------------
@@ -364,6 +383,18 @@ __global__ void __launch_bounds__(MxCfg<NG, T>::NTH, 2)
   if (column) {
     float lo_a[5];
     x3_edges(k0 - 1, lo_a, hi3);
+    if constexpr (CARRY) {  // column slots from planes to the carried slope and interface
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const float qm2 = cring[cslot(k0 - 2) * 5 * NOWN + v * NOWN + tid];
+        const float qm1 = ring[xslot(k0 - 1) * 5 * NPL + v * NPL + oc];
+        const float q0 = ring[xslot(k0) * 5 * NPL + v * NPL + oc];
+        const float q1 = ring[xslot(k0 + 1) * 5 * NPL + v * NPL + oc];
+        const float sm = ppm_slope_v(qm2, qm1, q0), s0 = ppm_slope_v(qm1, q0, q1);
+        cring[v * NOWN + tid] = s0;
+        cring[5 * NOWN + v * NOWN + tid] = ppm_interface_v(qm1, q0, sm, s0);
+      }
+    }
   }
   cp_async_wait<0>();
   __syncthreads();
@@ -405,7 +436,10 @@ __global__ void __launch_bounds__(MxCfg<NG, T>::NTH, 2)
     }
     if (column) {
       float lo3[5], hi3k[5], f3hi[5];  // f3hi: the face between cells k-1 and k
-      x3_edges(k, lo3, hi3k);
+      if constexpr (CARRY)
+        x3_edges_carry(k, lo3, hi3k);
+      else
+        x3_edges(k, lo3, hi3k);
       if (!FAST && k == 0 && g.ovr[4] >= 0)
         corrected_flux(md.fcbuf, g.ovr[4] + cj * g.nx1 + ci, f3hi);
       else if (!FAST && k == g.nx3 && g.ovr[5] >= 0)

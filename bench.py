@@ -49,18 +49,18 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # FP64 pipe busy fraction of the FP64 stage kernel in the ncu capture of these sources
 # (sm__pipe_fp64_cycles_active.avg.pct_of_peak_sustained_active, mean of the two stages):
 # the unit the form is bound by
-FP64_PIPE_BUSY_NCU = 0.783
+FP64_PIPE_BUSY_NCU = 0.776
 # FP64 instructions (DADD + DMUL + DFMA, thread level) per cell of the FP64 stage kernel
 # in the same capture (smsp__sass_thread_inst_executed_op_{dadd,dmul,dfma}_pred_on),
 # stages 1 and 2: set against the measured FP64 instruction rate (ak_probe_fp64_rate)
-FP64_INST_PER_CELL_NCU = (317.7, 351.0)
+FP64_INST_PER_CELL_NCU = (295.6, 324.9)
 # DRAM bytes per cell of the stage kernels (dram__bytes_read.sum + dram__bytes_write.sum
 # of one ncu capture per launch: PLM + RK2 on 192^3 in 64^3 blocks, PPM4 + RK3 on 256^3 in
 # 128^3 blocks; the per-cell figures carry over to grids of the same block size), valid
 # for the kernel sources with this hash (else traffic = null)
-TRAFFIC_SRC_HASH = "f7b1b21aef9c2a288813a4659c6afd904e5f9475"
-TRAFFIC_B_PER_CELL = {"fp64": (85.26, 128.36), "mixed": (83.82, 126.96),
-                      "ppm4_mixed": (93.37, 139.38, 135.76)}
+TRAFFIC_SRC_HASH = "d87d254c85b260cc74b9324b7558a8b245648567"
+TRAFFIC_B_PER_CELL = {"fp64": (85.53, 128.31), "mixed": (83.86, 126.96),
+                      "ppm4_mixed": (93.00, 138.77, 135.57)}
 
 
 def kernel_source_hash():

@@ -68,15 +68,14 @@ __device__ __forceinline__ double ppm_half_slope_fp64(double qm, double q0, doub
   return __longlong_as_double(m | (bl & ~mask));                       // sign of dl (= dr)
 }
 
-__device__ __forceinline__ void ppm_edges_fp64(double q0, double q1, double q2, double q3,
-                                               double q4, double& lo, double& hi) {
-  const double third = 1.0 / 3.0;
-  const double hm = ppm_half_slope_fp64(q0, q1, q2);
-  const double hc = ppm_half_slope_fp64(q1, q2, q3);
-  const double hp = ppm_half_slope_fp64(q2, q3, q4);
-  double a_lo = fma(hm - hc, third, dscale_down(q1 + q2, 1));
-  double a_hi = fma(hc - hp, third, dscale_down(q2 + q3, 1));
-  const double a = q2;
+// FP64 CW84 interface value between cells of values ql, qr and half slopes hl, hr
+__device__ __forceinline__ double ppm_interface_fp64(double ql, double qr, double hl, double hr) {
+  return fma(hl - hr, 1.0 / 3.0, dscale_down(ql + qr, 1));
+}
+
+// FP64 CW84 monotonization of a cell's interface values a_lo, a_hi around its value a
+__device__ __forceinline__ void ppm_monotonize_fp64(double a_lo, double a_hi, double a,
+                                                    double& lo, double& hi) {
   const double dh = a_hi - a, dlo = a - a_lo;
   const long long bh = __double_as_longlong(dh), bo = __double_as_longlong(dlo);
   if ((bh ^ bo) < 0 || (bh << 1) == 0 || (bo << 1) == 0) {  // (a_hi - a)(a - a_lo) <= 0
@@ -93,6 +92,15 @@ __device__ __forceinline__ void ppm_edges_fp64(double q0, double q1, double q2, 
     a_hi = fma(3.0, a, -(a_lo + a_lo));
   lo = a_lo;
   hi = a_hi;
+}
+
+__device__ __forceinline__ void ppm_edges_fp64(double q0, double q1, double q2, double q3,
+                                               double q4, double& lo, double& hi) {
+  const double hm = ppm_half_slope_fp64(q0, q1, q2);
+  const double hc = ppm_half_slope_fp64(q1, q2, q3);
+  const double hp = ppm_half_slope_fp64(q2, q3, q4);
+  ppm_monotonize_fp64(ppm_interface_fp64(q1, q2, hm, hc), ppm_interface_fp64(q2, q3, hc, hp), q2,
+                      lo, hi);
 }
 
 // PPMX: PPM with extremum-preserving limiters.  The fourth-order interface value

@@ -197,6 +197,27 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
       edges_t<NG, RC>(q, lo[v], hi[v]);
     }
   };
+  // FP64 PPM4: the column carries, from cell to cell along x3, the half slope of the next
+  // cell (xh) and its lower interface value (xa), both computed for the cell below with
+  // the same operations on the same operands (the same bits): per cell one new slope and
+  // one new interface value instead of three and two
+  constexpr bool CARRY = !MIXED && RC == AK_PPM4;
+  double xh[5], xa[5];
+  auto x3_edges_carry = [&](int kc, R* lo, R* hi) {
+    if constexpr (CARRY) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const double qc = ring[slot(kc) * 5 * NPL + v * NPL + oc];
+        const double qn = ring[slot(kc + 1) * 5 * NPL + v * NPL + oc];
+        const double hn =
+            ppm_half_slope_fp64(qc, qn, ring[slot(kc + 2) * 5 * NPL + v * NPL + oc]);
+        const double ahi = ppm_interface_fp64(qc, qn, xh[v], hn);
+        ppm_monotonize_fp64(xa[v], ahi, qc, lo[v], hi[v]);
+        xh[v] = hn;
+        xa[v] = ahi;
+      }
+    }
+  };
   auto x1_edges = [&](const R* pl) {  // cells i0-1 .. i0+TX of the tile's rows
     for (int it = tid; it < C::E1 / 5; it += NT) {
       const int c = it % C1, r = it / C1;
@@ -281,6 +302,18 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
     R lo_a[5], hi_a[5], lo_b[5];
     x3_edges(k0 - 1, lo_a, hi_a);
     x3_edges(k0, lo_b, hi3);
+    if constexpr (CARRY) {  // the carry for cell k0 + 1
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const double qm = ring[slot(k0 - 1) * 5 * NPL + v * NPL + oc];
+        const double q0 = ring[slot(k0) * 5 * NPL + v * NPL + oc];
+        const double q1 = ring[slot(k0 + 1) * 5 * NPL + v * NPL + oc];
+        const double q2 = ring[slot(k0 + 2) * 5 * NPL + v * NPL + oc];
+        const double h0 = ppm_half_slope_fp64(qm, q0, q1);
+        xh[v] = ppm_half_slope_fp64(q0, q1, q2);
+        xa[v] = ppm_interface_fp64(q0, q1, h0, xh[v]);
+      }
+    }
     if (!FAST && k0 == 0 && g.ovr[4] >= 0)
       corrected_flux(md.fcbuf, g.ovr[4] + cj * g.nx1 + ci, f3m);
     else
@@ -317,7 +350,12 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
 
     if constexpr (C::SPLIT) {
       x1_edges(pl);
-      if (own) x3_edges(k + 1, lo3, hi3n);
+      if (own) {
+        if constexpr (CARRY)
+          x3_edges_carry(k + 1, lo3, hi3n);
+        else
+          x3_edges(k + 1, lo3, hi3n);
+      }
       __syncthreads();
       x1_faces();
       __syncthreads();
@@ -327,7 +365,12 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
     } else {
       x1_edges(pl);
       x2_edges(pl);
-      if (own) x3_edges(k + 1, lo3, hi3n);
+      if (own) {
+        if constexpr (CARRY)
+          x3_edges_carry(k + 1, lo3, hi3n);
+        else
+          x3_edges(k + 1, lo3, hi3n);
+      }
       __syncthreads();
       x1_faces();
       x2_faces();

@@ -52,6 +52,20 @@ struct StageCfg {
   static constexpr size_t bytes = sizeof(R) * (size_t)(NR * 5 * NPL + 2 * EB + F1 + F2);
 };
 
+// FP64 PPM4 computes each plane's x1 and x2 limited half slopes once per cell, into
+// shared memory behind the StageCfg buffers, for the edge items that share them.
+template <int NG, int RC, bool MIXED>
+constexpr bool shared_slopes() {
+  return !MIXED && NG == 3 && RC == AK_PPM4;
+}
+template <int NG, int RC, bool MIXED, int TX, int TY>
+constexpr size_t stage_smem() {
+  return StageCfg<NG, MIXED, TX, TY>::bytes +
+         (shared_slopes<NG, RC, MIXED>()
+              ? sizeof(double) * 5 * (size_t)(TY * (TX + 4) + (TY + 4) * TX)
+              : 0);
+}
+
 // PERSIST: the persistent fused form for meshes that need a ghost fill (static
 // refinement, FOFC): a cooperative launch of at most one resident wave of CTAs first runs
 // the fill and the flux correction (fused_prologue), then loops over the work list.
@@ -86,6 +100,11 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
   R* e2hi = C::SPLIT ? e1hi : e1hi + C::E1;
   R* f1 = e1hi + C::EB;                      // [5][TY][TX+1]
   R* f2 = f1 + C::F1;                        // [5][TY+1][TX]
+  // FP64 PPM4: half slopes of the cells i0-2 .. i0+TX+1 of the tile rows ([5][TY][TX+4])
+  // and of the cells j0-2 .. j0+TY+1 of the tile columns ([5][TY+4][TX])
+  constexpr bool HSLOPE = shared_slopes<NG, RC, MIXED>();
+  double* hs1 = reinterpret_cast<double*>(smem_raw + C::bytes);
+  double* hs2 = hs1 + 5 * TY * (TX + 4);
   __shared__ double red[NT / 32];
   __shared__ long long nbr[27];  // direct halo reads: the neighbour blocks
 
@@ -218,6 +237,29 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
       }
     }
   };
+  // FP64 PPM4: the plane's half slopes, each computed once (x1: padded x 1 .. TX+4 of the
+  // tile rows; x2: padded y 1 .. TY+4 of the tile columns); cells outside the block's
+  // padded extent are skipped, as the edge items that would read them are
+  auto half_slopes = [&](const R* pl) {
+    if constexpr (HSLOPE) {
+      constexpr int N1 = TY * (TX + 4), N2 = (TY + 4) * TX;
+      for (int it = tid; it < 5 * (N1 + N2); it += NT) {
+        if (it < 5 * N1) {
+          const int v = it / N1, e = it % N1, r = e / (TX + 4), c = e % (TX + 4);
+          if (i0 + c + 2 < g.p1 && j0 + r < g.nx2) {
+            const double* q = pl + v * NPL + (r + NG) * WX + c;  // padded x = c + 1 centre
+            hs1[it] = ppm_half_slope_fp64(q[0], q[1], q[2]);
+          }
+        } else {
+          const int e2 = it - 5 * N1, v = e2 / N2, e = e2 % N2, r = e / TX, c = e % TX;
+          if (i0 + c < g.nx1 && j0 + r + 2 < g.p2) {
+            const double* q = pl + v * NPL + r * WX + c + NG;  // padded y = r + 1 centre
+            hs2[e2] = ppm_half_slope_fp64(q[0], q[WX], q[2 * WX]);
+          }
+        }
+      }
+    }
+  };
   auto x1_edges = [&](const R* pl) {  // cells i0-1 .. i0+TX of the tile's rows
     for (int it = tid; it < C::E1 / 5; it += NT) {
       const int c = it % C1, r = it / C1;
@@ -225,10 +267,18 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
         const int base = (r + NG) * WX + c;  // stencil x = c .. c + 2NG - 2
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
-          R q[2 * NG - 1];
+          if constexpr (HSLOPE) {  // half slopes of cells c .. c+2 (padded x c+1 .. c+3)
+            const double* q = pl + v * NPL + base;
+            const double* h = hs1 + (v * TY + r) * (TX + 4) + c;
+            ppm_monotonize_fp64(ppm_interface_fp64(q[1], q[2], h[0], h[1]),
+                                ppm_interface_fp64(q[2], q[3], h[1], h[2]), q[2],
+                                e1lo[(v * TY + r) * C1 + c], e1hi[(v * TY + r) * C1 + c]);
+          } else {
+            R q[2 * NG - 1];
 #pragma unroll
-          for (int m = 0; m < 2 * NG - 1; ++m) q[m] = pl[v * NPL + base + m];
-          edges_t<NG, RC>(q, e1lo[(v * TY + r) * C1 + c], e1hi[(v * TY + r) * C1 + c]);
+            for (int m = 0; m < 2 * NG - 1; ++m) q[m] = pl[v * NPL + base + m];
+            edges_t<NG, RC>(q, e1lo[(v * TY + r) * C1 + c], e1hi[(v * TY + r) * C1 + c]);
+          }
         }
       }
     }
@@ -240,10 +290,19 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
         const int base = r * WX + c + NG;  // stencil y = r .. r + 2NG - 2
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
-          R q[2 * NG - 1];
+          if constexpr (HSLOPE) {
+            const double* q = pl + v * NPL + base;
+            const double* h = hs2 + (v * (TY + 4) + r) * TX + c;
+            ppm_monotonize_fp64(ppm_interface_fp64(q[WX], q[2 * WX], h[0], h[TX]),
+                                ppm_interface_fp64(q[2 * WX], q[3 * WX], h[TX], h[2 * TX]),
+                                q[2 * WX], e2lo[(v * (TY + 2) + r) * TX + c],
+                                e2hi[(v * (TY + 2) + r) * TX + c]);
+          } else {
+            R q[2 * NG - 1];
 #pragma unroll
-          for (int m = 0; m < 2 * NG - 1; ++m) q[m] = pl[v * NPL + base + m * WX];
-          edges_t<NG, RC>(q, e2lo[(v * (TY + 2) + r) * TX + c], e2hi[(v * (TY + 2) + r) * TX + c]);
+            for (int m = 0; m < 2 * NG - 1; ++m) q[m] = pl[v * NPL + base + m * WX];
+            edges_t<NG, RC>(q, e2lo[(v * (TY + 2) + r) * TX + c], e2hi[(v * (TY + 2) + r) * TX + c]);
+          }
         }
       }
     }
@@ -347,6 +406,10 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
     const R* pl = ring + slot(k) * 5 * NPL;
     kcur = k;
     R lo3[5], hi3n[5];
+    if constexpr (HSLOPE) {
+      half_slopes(pl);
+      __syncthreads();
+    }
 
     if constexpr (C::SPLIT) {
       x1_edges(pl);
@@ -497,7 +560,7 @@ using stage_kern_t = void (*)(const double*, const double*, double*, ak_meshdev,
 template <int NG, int RC, bool MIXED, int TX, int TY, bool WITH_FAST = false>
 inline cudaError_t launch(const ak_mesh* m, const double* uin, const double* u0, double* uout,
                           double a, double b, int rk2_final, int last_stage, bool prepare_only) {
-  const size_t smem = StageCfg<NG, MIXED, TX, TY>::bytes;
+  const size_t smem = stage_smem<NG, RC, MIXED, TX, TY>();
   auto kern = stage_kernel<NG, RC, MIXED, TX, TY, false>;
   auto pk = stage_kernel<NG, RC, MIXED, TX, TY, true>;
   stage_kern_t fast[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};

@@ -60,9 +60,12 @@ constexpr bool shared_slopes() {
 }
 template <int NG, int RC, bool MIXED, int TX, int TY>
 constexpr size_t stage_smem() {
+  // half slopes [5][TY][TX+4] and [5][TY+4][TX], interface values [5][TY][TX+3] and
+  // [5][TY+3][TX]
   return StageCfg<NG, MIXED, TX, TY>::bytes +
          (shared_slopes<NG, RC, MIXED>()
-              ? sizeof(double) * 5 * (size_t)(TY * (TX + 4) + (TY + 4) * TX)
+              ? sizeof(double) * 5 *
+                    (size_t)(TY * (TX + 4) + (TY + 4) * TX + TY * (TX + 3) + (TY + 3) * TX)
               : 0);
 }
 
@@ -105,6 +108,10 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
   constexpr bool HSLOPE = shared_slopes<NG, RC, MIXED>();
   double* hs1 = reinterpret_cast<double*>(smem_raw + C::bytes);
   double* hs2 = hs1 + 5 * TY * (TX + 4);
+  // and the interface values between them: x1 faces between padded x f+1 and f+2
+  // ([5][TY][TX+3]), x2 faces between padded y f+1 and f+2 ([5][TY+3][TX])
+  double* ia1 = hs2 + 5 * (TY + 4) * TX;
+  double* ia2 = ia1 + 5 * TY * (TX + 3);
   __shared__ double red[NT / 32];
   __shared__ long long nbr[27];  // direct halo reads: the neighbour blocks
 
@@ -260,6 +267,28 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
       }
     }
   };
+  auto interfaces = [&](const R* pl) {
+    if constexpr (HSLOPE) {
+      constexpr int N1 = TY * (TX + 3), N2 = (TY + 3) * TX;
+      for (int it = tid; it < 5 * (N1 + N2); it += NT) {
+        if (it < 5 * N1) {
+          const int v = it / N1, e = it % N1, r = e / (TX + 3), f = e % (TX + 3);
+          if (i0 + f + 3 < g.p1 && j0 + r < g.nx2) {
+            const double* q = pl + v * NPL + (r + NG) * WX + f;
+            const double* h = hs1 + (v * TY + r) * (TX + 4) + f;
+            ia1[it] = ppm_interface_fp64(q[1], q[2], h[0], h[1]);
+          }
+        } else {
+          const int e2 = it - 5 * N1, v = e2 / N2, e = e2 % N2, r = e / TX, c = e % TX;
+          if (i0 + c < g.nx1 && j0 + r + 3 < g.p2) {
+            const double* q = pl + v * NPL + r * WX + c + NG;
+            const double* h = hs2 + (v * (TY + 4) + r) * TX + c;
+            ia2[e2] = ppm_interface_fp64(q[WX], q[2 * WX], h[0], h[TX]);
+          }
+        }
+      }
+    }
+  };
   auto x1_edges = [&](const R* pl) {  // cells i0-1 .. i0+TX of the tile's rows
     for (int it = tid; it < C::E1 / 5; it += NT) {
       const int c = it % C1, r = it / C1;
@@ -267,11 +296,9 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
         const int base = (r + NG) * WX + c;  // stencil x = c .. c + 2NG - 2
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
-          if constexpr (HSLOPE) {  // half slopes of cells c .. c+2 (padded x c+1 .. c+3)
-            const double* q = pl + v * NPL + base;
-            const double* h = hs1 + (v * TY + r) * (TX + 4) + c;
-            ppm_monotonize_fp64(ppm_interface_fp64(q[1], q[2], h[0], h[1]),
-                                ppm_interface_fp64(q[2], q[3], h[1], h[2]), q[2],
+          if constexpr (HSLOPE) {  // interface values of faces c, c+1 (shared)
+            const double* ia = ia1 + (v * TY + r) * (TX + 3) + c;
+            ppm_monotonize_fp64(ia[0], ia[1], pl[v * NPL + base + 2],
                                 e1lo[(v * TY + r) * C1 + c], e1hi[(v * TY + r) * C1 + c]);
           } else {
             R q[2 * NG - 1];
@@ -291,11 +318,9 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
 #pragma unroll
         for (int v = 0; v < 5; ++v) {
           if constexpr (HSLOPE) {
-            const double* q = pl + v * NPL + base;
-            const double* h = hs2 + (v * (TY + 4) + r) * TX + c;
-            ppm_monotonize_fp64(ppm_interface_fp64(q[WX], q[2 * WX], h[0], h[TX]),
-                                ppm_interface_fp64(q[2 * WX], q[3 * WX], h[TX], h[2 * TX]),
-                                q[2 * WX], e2lo[(v * (TY + 2) + r) * TX + c],
+            const double* ia = ia2 + (v * (TY + 3) + r) * TX + c;
+            ppm_monotonize_fp64(ia[0], ia[TX], pl[v * NPL + base + 2 * WX],
+                                e2lo[(v * (TY + 2) + r) * TX + c],
                                 e2hi[(v * (TY + 2) + r) * TX + c]);
           } else {
             R q[2 * NG - 1];
@@ -408,6 +433,8 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
     R lo3[5], hi3n[5];
     if constexpr (HSLOPE) {
       half_slopes(pl);
+      __syncthreads();
+      interfaces(pl);
       __syncthreads();
     }
 

@@ -58,9 +58,9 @@ FP64_INST_PER_CELL_NCU = (295.6, 324.9)
 # of one ncu capture per launch: PLM + RK2 on 192^3 in 64^3 blocks, PPM4 + RK3 on 256^3 in
 # 128^3 blocks; the per-cell figures carry over to grids of the same block size), valid
 # for the kernel sources with this hash (else traffic = null)
-TRAFFIC_SRC_HASH = "d87d254c85b260cc74b9324b7558a8b245648567"
-TRAFFIC_B_PER_CELL = {"fp64": (85.53, 128.31), "mixed": (83.86, 126.96),
-                      "ppm4_mixed": (93.00, 138.77, 135.57)}
+TRAFFIC_SRC_HASH = "eb2d632d4c7a39181f29381f8d4de0254b051dea"
+TRAFFIC_B_PER_CELL = {"fp64": (85.29, 128.45), "mixed": (83.84, 126.93),
+                      "ppm4_mixed": (92.97, 139.08, 135.57)}
 
 
 def kernel_source_hash():

@@ -23,6 +23,7 @@ Bg make_bg(const ak_mesh* m) {
   const double gamma = m->desc.gamma;
   bg.gamma = gamma;
   bg.gamma_f = (float)gamma;
+  bg.gamma_l = (float)(gamma - (double)bg.gamma_f);
   bg.gm1 = gamma - 1.0;
   bg.kq = (gamma + 1.0) / (2.0 * gamma);
   bg.kq1 = 1.0 - bg.kq;

@@ -218,5 +218,38 @@ __device__ __forceinline__ double sqrt_ratio64(double a, double b) {
   return __longlong_as_double(scaled_sum_bits(s0, d, k));
 }
 
+// sqrt(g a / b) for finite normal a, b > 0 and a constant g > 0 given as a double and
+// split into floats g = gh + gl (gh its nearest float): as sqrt_ratio64 with g ma in place
+// of ma, so that no FP64 instruction forms the product.  gh mah = G + Ge exactly, and
+// G - Q is exact (Sterbenz: both are within a few 2^-22 of g ma); the terms gh mal and
+// gl mah beyond G + Ge are of order 2^-23 G, so the residual g ma - s0^2 mb is again
+// formed to ~2^-46.  Relative error below 2^-42; other inputs take sqrt(g a / b).
+__device__ __forceinline__ double sqrt_gratio64(double a, double b, double g, float gh,
+                                                float gl) {
+  const unsigned ah = (unsigned)__double2hiint(a), al = (unsigned)__double2loint(a);
+  const unsigned bh = (unsigned)__double2hiint(b), bl = (unsigned)__double2loint(b);
+  const unsigned ea = ah >> 20, eb = bh >> 20;  // sign bit included: negative -> >= 2048
+  if (ea == 0u || ea >= 2045u || eb == 0u || eb >= 2045u) return sqrt(g * a / b);
+  int e = (int)ea - (int)eb;
+  float mah, mal, mbh, mbl;
+  split_mantissa(ah, al, mah, mal);
+  split_mantissa(bh, bl, mbh, mbl);
+  if (e & 1) {  // odd exponent difference: t = 2 g ma / mb, e even
+    mah *= 2.0f;
+    mal *= 2.0f;
+    e -= 1;
+  }
+  const int k = e / 2;
+  const float G = gh * mah;
+  const float Ge = fmaf(gh, mah, -G);
+  const float s0 = G * rsqrt_approx_f32(G * mbh);
+  const float P = s0 * s0;
+  const float Pe = fmaf(s0, s0, -P);
+  const float Q = P * mbh;
+  const float Qe = fmaf(P, mbh, -Q);
+  const float r = (G - Q) + ((Ge - Qe) + (fmaf(gh, mal, gl * mah) - fmaf(P, mbl, Pe * mbh)));
+  const float d = r * rcp_approx_f32(2.0f * s0 * mbh);
+  return __longlong_as_double(scaled_sum_bits(s0, d, k));
+}
 
 }  // namespace ak

@@ -30,6 +30,7 @@ struct Bg {
   float rho_f, ug_f;     // the same, rounded
   double gamma;
   float gamma_f;
+  float gamma_l;         // gamma - gamma_f, rounded: gamma split into two floats
   double kq;             // (gamma + 1) / (2 gamma), for the shock speed factor
   double kq1;            // 1 - kq
   double gm1;            // gamma - 1
@@ -265,9 +266,10 @@ __device__ __forceinline__ void hllc_fp64(const double* wl, const double* wr, co
   const double rl = wl[0], ul = wl[1], rr = wr[0], ur = wr[1];
   const double pl = gm1 * wl[4];
   const double pr = gm1 * wr[4];
-  // c = sqrt(gamma p / rho) from split mantissas, without FP64 instructions but gamma p
-  const double cl = sqrt_ratio64(gamma * pl, rl);
-  const double cr = sqrt_ratio64(gamma * pr, rr);
+  // c = sqrt(gamma p / rho) from split mantissas, with gamma split into two floats: no
+  // FP64 instruction
+  const double cl = sqrt_gratio64(pl, rl, gamma, bg.gamma_f, bg.gamma_l);
+  const double cr = sqrt_gratio64(pr, rr, gamma, bg.gamma_f, bg.gamma_l);
 
   // pressure estimate of the linearised (PVRS) solver, then shock-aware speeds
   double ps = fma(-dscale_down((ur - ul) * (rl + rr), 3), cl + cr, dscale_down(pl + pr, 1));
@@ -351,7 +353,8 @@ __device__ __forceinline__ void llf_fp64(const double* wl, const double* wr, con
   const double gamma = bg.gamma, gm1 = bg.gm1;
   const double rl = wl[0], ul = wl[1], rr = wr[0], ur = wr[1];
   const double pl = gm1 * wl[4], pr = gm1 * wr[4];
-  const double cl = sqrt_ratio64(gamma * pl, rl), cr = sqrt_ratio64(gamma * pr, rr);
+  const double cl = sqrt_gratio64(pl, rl, gamma, bg.gamma_f, bg.gamma_l);
+  const double cr = sqrt_gratio64(pr, rr, gamma, bg.gamma_f, bg.gamma_l);
   const double al = fabs(ul) + cl, ar = fabs(ur) + cr;
   const double sm = NANCHK ? -(al > ar ? al : ar) : -(dgt_pos(al, ar) ? al : ar);
   const double el = fma(dscale(rl, -1), fma(ul, ul, fma(wl[2], wl[2], wl[3] * wl[3])), wl[4]);
@@ -375,7 +378,8 @@ __device__ __forceinline__ void hlle_fp64(const double* wl, const double* wr, co
   const double gamma = bg.gamma, gm1 = bg.gm1;
   const double rl = wl[0], ul = wl[1], rr = wr[0], ur = wr[1];
   const double pl = gm1 * wl[4], pr = gm1 * wr[4];
-  const double cl = sqrt_ratio64(gamma * pl, rl), cr = sqrt_ratio64(gamma * pr, rr);
+  const double cl = sqrt_gratio64(pl, rl, gamma, bg.gamma_f, bg.gamma_l);
+  const double cr = sqrt_gratio64(pr, rr, gamma, bg.gamma_f, bg.gamma_l);
   const double el = fma(dscale(rl, -1), fma(ul, ul, fma(wl[2], wl[2], wl[3] * wl[3])), wl[4]);
   const double er = fma(dscale(rr, -1), fma(ur, ur, fma(wr[2], wr[2], wr[3] * wr[3])), wr[4]);
   const double isl = rsqrt64(rl), isr = rsqrt64(rr);  // 1 / sqrt(rho)

@@ -289,7 +289,31 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
       }
     }
   };
+  // FP64 PLM: x1 and x2 edges of two neighbouring cells per item, which share the
+  // difference between them (the same operation on the same operands, so the same bits)
+  constexpr bool PAIR = !MIXED && RC == AK_PLM;
+  static_assert(!PAIR || (C1 % 2 == 0 && TY % 2 == 0), "cell pairs need even rows");
   auto x1_edges = [&](const R* pl) {  // cells i0-1 .. i0+TX of the tile's rows
+    if constexpr (PAIR) {
+      for (int it = tid; it < (C1 / 2) * TY; it += NT) {
+        const int c = 2 * (it % (C1 / 2)), r = it / (C1 / 2);
+        // cell c+1 only exists where cell c does; its stencil (x up to c + 3 <= TX + 3)
+        // stays inside the ring row even where the cell itself is skipped
+        if (i0 - 1 + c <= g.nx1 && j0 + r < g.nx2) {
+          const bool second = i0 + c <= g.nx1;
+          const int base = (r + NG) * WX + c;
+#pragma unroll
+          for (int v = 0; v < 5; ++v) {
+            const double* q = pl + v * NPL + base;
+            const double d1 = q[2] - q[1];
+            const int o = (v * TY + r) * C1 + c;
+            plm_edges_fp64(q[1] - q[0], d1, q[1], e1lo[o], e1hi[o]);
+            if (second) plm_edges_fp64(d1, q[3] - q[2], q[2], e1lo[o + 1], e1hi[o + 1]);
+          }
+        }
+      }
+      return;
+    }
     for (int it = tid; it < C::E1 / 5; it += NT) {
       const int c = it % C1, r = it / C1;
       if (i0 - 1 + c <= g.nx1 && j0 + r < g.nx2) {
@@ -311,6 +335,25 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
     }
   };
   auto x2_edges = [&](const R* pl) {  // cells j0-1 .. j0+TY of the tile's columns
+    if constexpr (PAIR) {
+      for (int it = tid; it < TX * ((TY + 2) / 2); it += NT) {
+        const int c = it % TX, r = 2 * (it / TX);
+        // rows r .. r + 3 <= TY + 3 of the ring, as for x1
+        if (i0 + c < g.nx1 && j0 - 1 + r <= g.nx2) {
+          const bool second = j0 + r <= g.nx2;
+          const int base = r * WX + c + NG;
+#pragma unroll
+          for (int v = 0; v < 5; ++v) {
+            const double* q = pl + v * NPL + base;
+            const double d1 = q[2 * WX] - q[WX];
+            const int o = (v * (TY + 2) + r) * TX + c;
+            plm_edges_fp64(q[WX] - q[0], d1, q[WX], e2lo[o], e2hi[o]);
+            if (second) plm_edges_fp64(d1, q[3 * WX] - q[2 * WX], q[2 * WX], e2lo[o + TX], e2hi[o + TX]);
+          }
+        }
+      }
+      return;
+    }
     for (int it = tid; it < C::E2 / 5; it += NT) {
       const int c = it % TX, r = it / TX;
       if (i0 + c < g.nx1 && j0 - 1 + r <= g.nx2) {

@@ -44,6 +44,32 @@ extern "C" int ratio_eval(const double* host_a, const double* host_b, int n, dou
   return e == cudaSuccess ? 0 : 3;
 }
 
+// sqrt(g a / b) with g split into two floats, next to the IEEE expression
+__global__ void gratio_kernel(const double* a, const double* b, int n, double g, float gh,
+                              float gl, double* out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  out[2 * (long long)i] = ak::sqrt_gratio64(a[i], b[i], g, gh, gl);
+  out[2 * (long long)i + 1] = sqrt(g * a[i] / b[i]);
+}
+
+extern "C" int gratio_eval(const double* host_a, const double* host_b, int n, double g,
+                           double* host_out) {
+  const float gh = (float)g, gl = (float)(g - (double)gh);
+  double *da = nullptr, *db = nullptr, *dout = nullptr;
+  if (cudaMalloc(&da, sizeof(double) * n) != cudaSuccess) return 1;
+  if (cudaMalloc(&db, sizeof(double) * n) != cudaSuccess) return 1;
+  if (cudaMalloc(&dout, sizeof(double) * 2 * (size_t)n) != cudaSuccess) return 2;
+  cudaMemcpy(da, host_a, sizeof(double) * n, cudaMemcpyHostToDevice);
+  cudaMemcpy(db, host_b, sizeof(double) * n, cudaMemcpyHostToDevice);
+  gratio_kernel<<<(n + 255) / 256, 256>>>(da, db, n, g, gh, gl, dout);
+  cudaError_t e = cudaMemcpy(host_out, dout, sizeof(double) * 2 * (size_t)n, cudaMemcpyDeviceToHost);
+  cudaFree(da);
+  cudaFree(db);
+  cudaFree(dout);
+  return e == cudaSuccess ? 0 : 3;
+}
+
 extern "C" int fastmath_eval(const double* host_x, int n, double* host_out) {
   double *dx = nullptr, *dout = nullptr;
   if (cudaMalloc(&dx, sizeof(double) * n) != cudaSuccess) return 1;

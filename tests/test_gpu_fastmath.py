@@ -26,6 +26,8 @@ def lib(tmp_path_factory):
     L = ctypes.CDLL(so)
     L.fastmath_eval.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
     L.ratio_eval.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+    L.gratio_eval.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
+                              ctypes.c_void_p]
     return L
 
 
@@ -82,4 +84,30 @@ def test_sqrt_ratio_against_ieee(lib):
     t = np.array([1.0, 1.0, 1.0, 1.0, 0.0, -1.0])
     o = np.empty((s.size, 2))
     assert lib.ratio_eval(s.ctypes.data, t.ctypes.data, s.size, o.ctypes.data) == 0
+    assert np.array_equal(o[:, 0], o[:, 1], equal_nan=True)
+
+
+@pytest.mark.parametrize("g", [5.0 / 3.0, 1.4, 4.0 / 3.0, 1.0001, 2.0, 1.1, 7.0 / 5.0 + 1e-9])
+def test_sqrt_gratio_against_ieee(lib, g):
+    """sqrt(g a / b) (the sound speed with gamma split into two floats): within 2^-42 of
+    the IEEE expression for the adiabatic indices in use, ratios across the binade edges
+    of g a / b, and the IEEE results for zero, negative and non-finite inputs."""
+    rng = np.random.default_rng(2)
+    n = 40000
+    a = np.concatenate([10.0 ** rng.uniform(-30, 30, n), rng.uniform(1.0, 2.0, n),
+                        2.0 - rng.uniform(0, 2 ** -20, 2000), 1.0 + rng.uniform(0, 2 ** -20, 2000),
+                        # g a / b next to a power of four (the square root's binade edges)
+                        4.0 ** rng.integers(-20, 20, 4000) / g * (1.0 + rng.uniform(-2 ** -20, 2 ** -20, 4000))])
+    b = np.concatenate([10.0 ** rng.uniform(-30, 30, n), rng.uniform(1.0, 2.0, n),
+                        1.0 + rng.uniform(0, 2 ** -20, 2000), 2.0 - rng.uniform(0, 2 ** -20, 2000),
+                        np.ones(4000)])
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    out = np.empty((a.size, 2))
+    assert lib.gratio_eval(a.ctypes.data, b.ctypes.data, a.size, g, out.ctypes.data) == 0
+    assert (np.abs(out[:, 0] - out[:, 1]) / out[:, 1]).max() < 2.0 ** -42
+    s = np.array([0.0, -1.0, np.inf, np.nan, 1.0, 1.0])
+    t = np.array([1.0, 1.0, 1.0, 1.0, 0.0, -1.0])
+    o = np.empty((s.size, 2))
+    assert lib.gratio_eval(s.ctypes.data, t.ctypes.data, s.size, g, o.ctypes.data) == 0
     assert np.array_equal(o[:, 0], o[:, 1], equal_nan=True)

@@ -143,6 +143,8 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
   const double idx1 = 1.0 / g.dx1, idx2 = 1.0 / g.dx2, idx3 = 1.0 / g.dx3;
   const double cdt[3] = {dt * idx1, dt * idx2, dt * idx3};  // FP64 update: dt / dx_d
   const double g2 = bg.gamma * bg.gm1;
+  const float g2h = f64_to_f32(g2), g2l = f64_to_f32(g2 - f32_to_f64(g2h));  // g2 = g2h + g2l
+  const bool cubic = idx1 == idx2 && idx2 == idx3;
   const bool need_u0 = form != 0;
 
   auto slot = [](int k) { return (k + 4 * NR) % NR; };
@@ -302,7 +304,7 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
         if (i0 - 1 + c <= g.nx1 && j0 + r < g.nx2) {
           const bool second = i0 + c <= g.nx1;
           const int base = (r + NG) * WX + c;
-#pragma unroll
+#pragma unroll 1
           for (int v = 0; v < 5; ++v) {
             const double* q = pl + v * NPL + base;
             const double d1 = q[2] - q[1];
@@ -342,7 +344,7 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
         if (i0 + c < g.nx1 && j0 - 1 + r <= g.nx2) {
           const bool second = j0 + r <= g.nx2;
           const int base = r * WX + c + NG;
-#pragma unroll
+#pragma unroll 1
           for (int v = 0; v < 5; ++v) {
             const double* q = pl + v * NPL + base;
             const double d1 = q[2 * WX] - q[WX];
@@ -575,11 +577,22 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
           const double m2 = fma(un[1], un[1], fma(un[2], un[2], un[3] * un[3]));
           double ug = fma(-m2, dscale(r, -1), un[4]);
           ug = at_least(ug, AK_UG_FLOOR) ? ug : AK_UG_FLOOR;
-          const double cs = sqrt_ratio64(g2 * ug, rho);  // sqrt(gamma (gamma - 1) u_g / rho)
-          const double l1 = fma(fabs(un[1]), r, cs) * idx1, l2 = fma(fabs(un[2]), r, cs) * idx2,
-                       l3 = fma(fabs(un[3]), r, cs) * idx3;
-          double lam = dgt_pos(l2, l1) ? l2 : l1;
-          lam = dgt_pos(l3, lam) ? l3 : lam;
+          // sqrt(gamma (gamma - 1) u_g / rho)
+          const double cs = sqrt_gratio64(ug, rho, g2, g2h, g2l);
+          const double a1 = fabs(un[1]), a2 = fabs(un[2]), a3 = fabs(un[3]);
+          double lam;
+          if (cubic) {
+            // equal widths: (a r + c_s) / dx rises with a, so the largest |v_d| gives the
+            // largest rate (the same value as the maximum over the three)
+            double am = dgt_pos(a2, a1) ? a2 : a1;
+            am = dgt_pos(a3, am) ? a3 : am;
+            lam = fma(am, r, cs) * idx1;
+          } else {
+            const double l1 = fma(a1, r, cs) * idx1, l2 = fma(a2, r, cs) * idx2,
+                         l3 = fma(a3, r, cs) * idx3;
+            lam = dgt_pos(l2, l1) ? l2 : l1;
+            lam = dgt_pos(l3, lam) ? l3 : lam;
+          }
           lam_max = dgt_pos(lam, lam_max) ? lam : lam_max;
         }
       }

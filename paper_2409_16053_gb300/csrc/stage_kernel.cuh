@@ -31,15 +31,21 @@
 
 namespace ak {
 
-template <int NG, bool MIXED, int TX, int TY>
+template <int NG, int RC, bool MIXED, int TX, int TY>
 struct StageCfg {
   using R = typename std::conditional<MIXED, float, double>::type;
-  // FP64: x1 and x2 sweeps one after the other through one edge buffer, so that two
-  // CTAs fit in an SM's shared memory.  Mixed: both sweeps at once, and the next plane
-  // of the state is prefetched into registers while the current one is computed.
-  static constexpr bool SPLIT = !MIXED;
+  // FP64 PPM4 carries its x3 slopes and interface values from cell to cell, so no plane
+  // below the current one is read again: the ring holds the current plane, the three
+  // above it and the one being replaced (5 slots instead of 2 NG).
+  static constexpr bool CARRY = !MIXED && RC == AK_PPM4;
+  // FP64 PLM: x1 and x2 sweeps one after the other through one edge buffer, so that two
+  // CTAs fit in an SM's shared memory (FP64 PPM4 runs one CTA per SM and does both at
+  // once).  Mixed: both sweeps at once, and the next plane of the state is prefetched
+  // into registers while the current one is computed.
+  static constexpr bool SPLIT = !MIXED && !CARRY;
   static constexpr bool PREFETCH = MIXED;
-  static constexpr int WX = TX + 2 * NG, WY = TY + 2 * NG, NPL = WX * WY, NR = 2 * NG;
+  static constexpr int WX = TX + 2 * NG, WY = TY + 2 * NG, NPL = WX * WY;
+  static constexpr int NR = CARRY ? 5 : 2 * NG;
   // cells of a plane that are converted: the tile and its x1 / x2 halos (no corners)
   static constexpr int NCROSS = TX * TY + 2 * NG * (TX + TY);
   static constexpr int NT = TX * TY;
@@ -62,7 +68,7 @@ template <int NG, int RC, bool MIXED, int TX, int TY>
 constexpr size_t stage_smem() {
   // half slopes [5][TY][TX+4] and [5][TY+4][TX], interface values [5][TY][TX+3] and
   // [5][TY+3][TX]
-  return StageCfg<NG, MIXED, TX, TY>::bytes +
+  return StageCfg<NG, RC, MIXED, TX, TY>::bytes +
          (shared_slopes<NG, RC, MIXED>()
               ? sizeof(double) * 5 *
                     (size_t)(TY * (TX + 4) + (TY + 4) * TX + TY * (TX + 3) + (TY + 3) * TX)
@@ -89,7 +95,7 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
   if constexpr (LAST >= 0) last_stage = LAST;
   const bool direct = FAST || md.direct;
   const bool fofc = !FAST && md.fofc;
-  using C = StageCfg<NG, MIXED, TX, TY>;
+  using C = StageCfg<NG, RC, MIXED, TX, TY>;
   using R = typename C::R;
   // reconstructions that can overshoot: a face without a sound speed gives a NaN flux
   constexpr bool NANCHK = RC == AK_WENOZ || RC == AK_PPMX;
@@ -229,7 +235,7 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
   // cell (xh) and its lower interface value (xa), both computed for the cell below with
   // the same operations on the same operands (the same bits): per cell one new slope and
   // one new interface value instead of three and two
-  constexpr bool CARRY = !MIXED && RC == AK_PPM4;
+  constexpr bool CARRY = C::CARRY;
   double xh[5], xa[5];
   auto x3_edges_carry = [&](int kc, R* lo, R* hi) {
     if constexpr (CARRY) {
@@ -423,13 +429,24 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
   };
 
   // prologue: planes k0-NG .. k0+NG-1, the flux through the face below k0, then plane
-  // k0+NG (its slot held plane k0-NG, used by that flux)
-  for (int kp = k0 - NG; kp < k0 + NG; ++kp) load_plane(kp);
-  __syncthreads();
+  // k0+NG (its slot held plane k0-NG, used by that flux).  The 5-slot ring first holds
+  // planes k0-3 .. k0+1 for the edge values of cell k0-1, then takes plane k0+2 in the
+  // slot of plane k0-3.
   R hi3[5], f3m[5], f3p[5];
+  R lo_a[5], hi_a[5];
+  if constexpr (NR < 2 * NG) {
+    for (int kp = k0 - NG; kp < k0 + NG - 1; ++kp) load_plane(kp);
+    __syncthreads();
+    if (own) x3_edges(k0 - 1, lo_a, hi_a);
+    __syncthreads();
+    load_plane(k0 + NG - 1);
+  } else {
+    for (int kp = k0 - NG; kp < k0 + NG; ++kp) load_plane(kp);
+  }
+  __syncthreads();
   if (own) {
-    R lo_a[5], hi_a[5], lo_b[5];
-    x3_edges(k0 - 1, lo_a, hi_a);
+    R lo_b[5];
+    if constexpr (NR >= 2 * NG) x3_edges(k0 - 1, lo_a, hi_a);
     x3_edges(k0, lo_b, hi3);
     if constexpr (CARRY) {  // the carry for cell k0 + 1
 #pragma unroll
@@ -457,7 +474,8 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
   double pf[NPT][5];
   int pfpos[NPT];
   for (int k = k0; k < k1; ++k) {
-    // the ring holds planes k-NG+1 .. k+NG once this barrier is passed
+    // the ring holds planes k-NG+1 .. k+NG (5-slot ring: k-1 .. k+3) once this barrier
+    // is passed
     const bool more = k + 1 < k1;
     if constexpr (C::PREFETCH) {
       if (more) fetch(k + NG + 1, pf, pfpos);
@@ -597,8 +615,9 @@ __global__ void __launch_bounds__(TX* TY, (MIXED || NG == 2) ? 2 : 1)
         }
       }
     }
-    // next plane into the slot of plane k-NG+1, whose last reader was this iteration's
-    // reconstruction (finished before the barrier above)
+    // next plane into the slot of plane k-NG+1 (5-slot ring: k-1), whose last reader
+    // was this iteration's reconstruction or an earlier one (finished before the
+    // barrier above)
     if (more) {
       if constexpr (C::PREFETCH)
         store(k + NG + 1, pf, pfpos);

@@ -49,7 +49,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # FP64 pipe busy fraction of the FP64 stage kernel in the ncu capture of these sources
 # (sm__pipe_fp64_cycles_active.avg.pct_of_peak_sustained_active, mean of the two stages):
 # the unit the form is bound by
-FP64_PIPE_BUSY_NCU = 0.791
+FP64_PIPE_BUSY_NCU = 0.792
 # FP64 instructions (DADD + DMUL + DFMA, thread level) per cell of the FP64 stage kernel
 # in the same capture (smsp__sass_thread_inst_executed_op_{dadd,dmul,dfma}_pred_on),
 # stages 1 and 2: set against the measured FP64 instruction rate (ak_probe_fp64_rate)
@@ -58,9 +58,9 @@ FP64_INST_PER_CELL_NCU = (283.6, 313.0)
 # of one ncu capture per launch: PLM + RK2 on 192^3 in 64^3 blocks, PPM4 + RK3 on 256^3 in
 # 128^3 blocks; the per-cell figures carry over to grids of the same block size), valid
 # for the kernel sources with this hash (else traffic = null)
-TRAFFIC_SRC_HASH = "388d5e5a0ff27056eba5210cb1282af7bb363f28"
-TRAFFIC_B_PER_CELL = {"fp64": (85.61, 128.35), "mixed": (83.91, 126.87),
-                      "ppm4_mixed": (92.92, 138.79, 135.58)}
+TRAFFIC_SRC_HASH = "2556c102381adc8594a48b1df549027742c73cbe"
+TRAFFIC_B_PER_CELL = {"fp64": (85.61, 128.22), "mixed": (83.91, 126.89),
+                      "ppm4_mixed": (92.80, 138.51, 135.43)}
 
 
 def kernel_source_hash():
